@@ -1,0 +1,460 @@
+#!/usr/bin/env python3
+"""Throughput of the non-separable lifting 2-D DWT (CDF 9/7) on GB300.
+
+One step is one forward pyramid (5 levels, CDF 9/7, FP32, the non-separable
+scheme with reduced operations) over one synthetic 16384 x 16384 FP32 image
+already resident in HBM.  The JSON line reports whole-job Gpixel/s (input
+pixels per second), the roofline of the level-1 kernel (algorithmic bytes over
+its CUDA-event time, against the measured HBM copy bandwidth), the oracle timed
+on the host cores, an end-to-end figure through the public API with host
+buffers, SM clocks sampled during the run, and a comparison of schemes and
+coefficient precisions on the same image.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank transforms its own image (replicas, weak scaling); the
+time is the maximum over ranks.  --impl reference times the CPU oracle.
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "2-D CDF 9/7 DWT Gpixel/s + % HBM peak: non-sep vs separable, FP32 vs FP16"
+UNIT = "Gpixel/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--size", type=int, default=16384)
+    ap.add_argument("--levels", type=int, default=5)
+    ap.add_argument("--scheme", default="reduced", choices=["nonsep", "reduced", "sep"])
+    ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--profile", action="store_true",
+                    help="warm-up and K steps only (for ncu captures); prints a minimal line")
+    return ap.parse_args()
+
+
+def workload_name(a) -> str:
+    return f"CDF 9/7 forward, {a.levels} levels, {a.size}x{a.size} FP32 image, scheme {a.scheme}"
+
+
+def config_of(a, world):
+    return {"workload": workload_name(a), "h": a.size, "w": a.size, "levels": a.levels, "wavelet": "cdf97",
+            "scheme": a.scheme, "coef_dtype": "f32", "input": "gradient (0.5*U[0,255] + ramp), seed 2",
+            "l2": "inputs larger than L2: 1 GiB read + 1 GiB written per step, no flush",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
+
+
+# ------------------------------------------------------------------ helpers
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    files = sorted(glob.glob(os.path.join(ROOT, "paper_1704_08657_gb300", "csrc", "*")))
+    for f in files:
+        with open(f, "rb") as fh:
+            h.update(os.path.basename(f).encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(h, w):
+    """Per-launch DRAM bytes of the level-1 kernel from the committed ncu
+    summary, when it was taken on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "forward_level1_traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    if d.get("kernel_hash") != kernel_hash():
+        return None
+    per_px = d.get("dram_bytes_per_pixel")
+    return None if per_px is None else float(per_px) * h * w
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 100 ms) of SM clock and throttle reasons."""
+
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: str):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", str(self.index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 10:
+                self.rows.append((time.time(), parts))
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=2)
+
+    def summary(self, t0, t1):
+        rows = [p for (t, p) in self.rows if t0 - 0.15 <= t <= t1 + 0.15]
+        if not rows:
+            rows = [p for (_, p) in self.rows]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        loaded = [r for r in rows if (num(r[5]) or 0) >= 50] or rows
+        sm = [num(r[2]) for r in loaded if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in loaded for i in range(4) if r[6 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": num(loaded[0][3]), "reasons": reasons, "samples": len(loaded),
+                "power_w_max": max((num(r[4]) or 0) for r in loaded)}
+
+
+def gpu_selector(dev, local: int) -> str:
+    """nvidia-smi -i argument for the torch device (its UUID when known)."""
+    try:
+        import torch
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        if u:
+            return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        pass
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    return vis.split(",")[local] if vis else str(local)
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ------------------------------------------------------------ CPU oracle
+
+def time_oracle(size: int, levels: int, budget_s: float, min_runs: int = 1):
+    """Oracle forward pyramid on a size x size gradient image; returns
+    (pixels per second, runs, seconds, threads)."""
+    import numpy as np
+
+    import oracle
+    from paper_1704_08657_gb300 import synth
+    oracle.build()
+    x = synth.gradient(size, size, seed=2).astype(np.float64)
+    runs, t = 0, 0.0
+    while runs < min_runs or t < budget_s:
+        t0 = time.perf_counter()
+        oracle.forward97(x, levels)
+        t += time.perf_counter() - t0
+        runs += 1
+        if runs >= 50:
+            break
+    return size * size * runs / t, runs, t, oracle.threads()
+
+
+def oracle_sample_side(levels: int, per_step_s: float) -> int:
+    """Side of the square sample the oracle transforms in about per_step_s."""
+    import numpy as np
+
+    import oracle
+    from paper_1704_08657_gb300 import synth
+    oracle.build()
+    x = synth.gradient(1024, 1024, seed=2).astype(np.float64)
+    oracle.forward97(x, levels)
+    t0 = time.perf_counter()
+    oracle.forward97(x, levels)
+    dt = max(time.perf_counter() - t0, 1e-4)
+    side = int((per_step_s / dt) ** 0.5 * 1024)
+    return max(256, min(16384, side // 64 * 64))
+
+
+def run_reference(a):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return  # only rank 0 runs the CPU oracle
+    per_step = min(3.0, max(0.05, 150.0 / max(1, a.steps + a.warmup)))
+    side = oracle_sample_side(a.levels, per_step)
+    import numpy as np
+
+    import oracle
+    from paper_1704_08657_gb300 import synth
+    x = synth.gradient(side, side, seed=2).astype(np.float64)
+    for _ in range(a.warmup):
+        oracle.forward97(x, a.levels)
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        oracle.forward97(x, a.levels)
+    dt = time.perf_counter() - t0
+    value = side * side * a.steps / dt / 1e9
+    sample = f"oracle (C, FP64 separable lifting) on a {side}x{side} crop-size image of the same recipe, per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": dt / a.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(a, 1),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# -------------------------------------------------------------- GPU arm
+
+def run_ours(a):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1704_08657_gb300 import abi, synth
+    from paper_1704_08657_gb300.dwt import Plan
+
+    n = a.size
+    x_host = synth.gradient(n, n, seed=2 + rank)
+    x = torch.from_numpy(x_host).to(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def make(scheme, coef_dtype=torch.float32, levels=a.levels, wavelet="cdf97"):
+        return Plan.single(n, n, levels, scheme=scheme, coef_dtype=coef_dtype, wavelet=wavelet, device=dev)
+
+    plan = make(a.scheme)
+    coef = torch.empty_like(x)
+    ws = plan.workspace
+
+    def step():
+        abi.dwt2_forward(plan.handle, x.data_ptr(), coef.data_ptr(), ws.data_ptr(), stream.cuda_stream)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if pg is not None:
+            pg.barrier()
+
+    # warm-up and clock soak (untimed)
+    for _ in range(max(3, a.warmup)):
+        step()
+    if a.profile:
+        torch.cuda.synchronize(dev)
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        for _ in range(a.steps):
+            step()
+        p1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = p0.elapsed_time(p1) / a.steps
+        print(json.dumps({"mode": "profile", "workload": workload_name(a), "ms_per_step": ms,
+                          "gpx_s": n * n / (ms * 1e-3) / 1e9, "status": plan.status()}), flush=True)
+        return
+    sampler = ClockSampler(gpu_selector(dev, local))
+    sampler.start()
+    t_soak = time.time()
+    barrier()
+    while time.time() - t_soak < 1.0:
+        for _ in range(50):
+            step()
+        torch.cuda.synchronize(dev)
+
+    # timed region: exactly K steps; the level-1 kernel timed by the plan's events
+    abi.dwt2_profile(plan.handle, True)
+    barrier()
+    t_wall0 = time.time()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        step()
+    e1.record(stream)
+    barrier()
+    t_wall1 = time.time()
+    ms_total = e0.elapsed_time(e1)
+    l1 = abi.dwt2_profile_read(plan.handle, 1)[0]  # mean over the last (up to 256) steps
+    abi.dwt2_profile(plan.handle, False)
+    sampler.stop()
+    clocks = sampler.summary(t_soak, t_wall1)
+    assert plan.status() == 0, "device status word set during the bench"
+
+    if pg is not None:
+        t = torch.tensor([ms_total], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / a.steps
+    px = n * n * world
+    value = px / (ms_step * 1e-3) / 1e9
+
+    # roofline of the level-1 kernel: 4 B read + 4 B written per pixel
+    peak, peak_kind = measured_peaks()
+    achieved = 8.0 * n * n / (l1 * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": f"fwd_tma_kernel<Fwd97<{a.scheme}>, float> (level 1)",
+            "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "peak_source": f"{peak_kind} HBM copy bandwidth", "level1_ms": l1,
+            "traffic": profiled_traffic(n, n), "algorithmic_bytes": 8 * n * n}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_of(a, world),
+            "roofline": roof, "gpu_launches": a.steps * a.levels, "clocks": clocks}
+
+    # end to end through the public API with host buffers
+    if rank == 0 or True:
+        hin = torch.from_numpy(x_host).pin_memory()
+        hout = torch.empty_like(hin).pin_memory()
+        xd = torch.empty_like(x)
+        cd = torch.empty_like(x)
+        for _ in range(2):
+            xd.copy_(hin, non_blocking=True)
+            plan.forward(xd, cd, stream)
+            hout.copy_(cd, non_blocking=True)
+        barrier()
+        ee0 = torch.cuda.Event(enable_timing=True)
+        ee1 = torch.cuda.Event(enable_timing=True)
+        ee0.record(stream)
+        for _ in range(a.e2e_steps):
+            xd.copy_(hin, non_blocking=True)
+            plan.forward(xd, cd, stream)
+            hout.copy_(cd, non_blocking=True)
+        ee1.record(stream)
+        barrier()
+        e2e_ms = ee0.elapsed_time(ee1) / a.e2e_steps
+        if pg is not None:
+            t = torch.tensor([e2e_ms], device=dev)
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        line["e2e"] = {"value": px / (e2e_ms * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": 4 * n * n,
+                       "d2h_bytes_per_step": 4 * n * n, "steps": a.e2e_steps,
+                       "path": "pinned host -> dwt2_forward -> pinned host"}
+        del hin, hout, xd, cd
+
+    # schemes and precisions on the same image (level-1 kernel and whole pyramid)
+    if not a.no_compare:
+        comp = {}
+        ksteps = max(3, min(a.steps, 100))
+        variants = [("nonsep", torch.float32), ("reduced", torch.float32), ("sep", torch.float32),
+                    ("reduced", torch.float16), ("reduced", torch.bfloat16), ("nonsep", torch.float16),
+                    ("sep", torch.float16)]
+        names = {torch.float32: "f32", torch.float16: "f16", torch.bfloat16: "bf16"}
+        for scheme, cdt in variants:
+            for levels in (1, a.levels):
+                p = make(scheme, cdt, levels)
+                out = torch.empty_like(x, dtype=cdt)
+                for _ in range(3):
+                    p.forward(x, out, stream)
+                abi.dwt2_profile(p.handle, True)
+                barrier()
+                c0 = torch.cuda.Event(enable_timing=True)
+                c1 = torch.cuda.Event(enable_timing=True)
+                c0.record(stream)
+                for _ in range(ksteps):
+                    p.forward(x, out, stream)
+                c1.record(stream)
+                barrier()
+                ms = c0.elapsed_time(c1) / ksteps
+                bpp = 4 + (4 if cdt == torch.float32 else 2)
+                l1m = abi.dwt2_profile_read(p.handle, 1)[0]
+                comp[f"{scheme}/{names[cdt]}/L{levels}"] = {
+                    "gpx_s": n * n / (ms * 1e-3) / 1e9, "ms": ms,
+                    "level1_gbs": bpp * n * n / (l1m * 1e-3) / 1e9,
+                    "level1_frac": bpp * n * n / (l1m * 1e-3) / 1e9 / peak}
+                p.close()
+                del out
+        for scheme in ("nonsep", "sep"):
+            xi = torch.from_numpy(synth.to_int(x_host)).to(dev)
+            p = make(scheme, torch.int32, a.levels, "cdf53")
+            out = torch.empty_like(xi)
+            for _ in range(3):
+                p.forward(xi, out, stream)
+            barrier()
+            c0 = torch.cuda.Event(enable_timing=True)
+            c1 = torch.cuda.Event(enable_timing=True)
+            c0.record(stream)
+            for _ in range(ksteps):
+                p.forward(xi, out, stream)
+            c1.record(stream)
+            barrier()
+            ms = c0.elapsed_time(c1) / ksteps
+            comp[f"cdf53i/{scheme}/i32/L{a.levels}"] = {"gpx_s": n * n / (ms * 1e-3) / 1e9, "ms": ms}
+            p.close()
+            del out, xi
+        line["compare"] = comp
+
+    if rank == 0 and not a.no_cpu:
+        per_s, runs, secs, threads = time_oracle(4096, a.levels, budget_s=10.0)
+        line["cpu_baseline"] = {"value": per_s / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                "sample": f"oracle (C, FP64 separable lifting, OpenMP) on a 4096x4096 image "
+                                          f"of the same recipe, {a.levels} levels, {runs} runs in {secs:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.barrier()
+        pg.destroy_process_group()
+
+
+def main():
+    a = parse_args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

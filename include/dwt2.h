@@ -1,0 +1,163 @@
+/*
+ * dwt2.h -- C ABI of libdwt2: the 2-D discrete wavelet transform computed by
+ * the non-separable lifting schemes of Barina, Kula, Matysek and Zemcik,
+ * "Accelerating Discrete Wavelet Transforms on Parallel Architectures"
+ * (arXiv:1704.08657), on NVIDIA GB300 (sm_103a).
+ *
+ * Operation (Background and Proposed Schemes sections).  One level splits an
+ * image into 2x2 polyphase quads (c1, c2, c3, c4) = (x[2i][2j], x[2i][2j+1],
+ * x[2i+1][2j], x[2i+1][2j+1]) and applies, for each lifting pair (P, U) of
+ * Eq. 2, the spatial predict T_P then the spatial update S_U (the
+ * non-separable lifting "S_U | T_P"), then scaling.  CDF 9/7 has two pairs
+ * (alpha, beta), (gamma, delta) with P = a(1 + z), U = b(1 + z^-1) and scaling
+ * zeta; the integer-reversible CDF 5/3 has one pair with floor rounding.
+ * All schemes compute the same values (Proposed Schemes); the scheme only
+ * selects the kernel:
+ *   DWT2_NONSEP          spatial predict / update, all terms in one step;
+ *   DWT2_NONSEP_REDUCED  the Optimization Approach: the constant parts P0, U0
+ *                        applied as separable lifting inside the quad right
+ *                        after the non-separable parts P1, U1 (CDF 9/7 only);
+ *   DWT2_SEP_LIFTING     the separable lifting T^H, T^V, S^H, S^V per pair.
+ *
+ * Conventions (readings where the paper is silent):
+ *   - odd sample x[2n+1] is predicted from x[2n], x[2n+2]; even sample x[2n]
+ *     is updated from x[2n-1], x[2n+1];
+ *   - boundary: whole-sample symmetric extension (x[-1] = x[1],
+ *     x[n] = x[n-2]) in every step;
+ *   - CDF 9/7 scaling: low-pass times zeta and high-pass divided by zeta per
+ *     axis (LL * zeta^2, HL and LH * 1, HH / zeta^2);
+ *   - integer 5/3: d = x_o - floor((x_l + x_r)/2), s = x_e +
+ *     floor((d_l + d_r + 2)/4), steps in the order T^H, T^V, S^H, S^V; values
+ *     must stay below 2^28 in magnitude (int32 arithmetic);
+ *   - layout: Mallat.  Level 1 writes, within the h x w image, LL to
+ *     [0, ceil(h/2)) x [0, ceil(w/2)), HL (c2) to the top-right, LH (c3) to the
+ *     bottom-left and HH (c4) to the bottom-right; level k+1 transforms the
+ *     LL region of level k in place of it.  Every level's input needs both
+ *     sides >= 2.
+ *
+ * Memory and ownership.  The caller owns every device buffer and the stream.
+ * A plan owns its device status word and its batch tables; calls are
+ * asynchronous on the given stream and allocate nothing after the plan is
+ * made.  A plan must not be used on two streams at the same time.
+ *
+ * Errors.  Every function returns DWT2_OK (0) or a negative DWT2_ERR_* code;
+ * nothing aborts or traps.  dwt2_strerror() names a code.
+ */
+#ifndef DWT2_H
+#define DWT2_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dwt2_plan_s* dwt2_plan_t;
+
+enum dwt2_wavelet { DWT2_CDF97 = 0, DWT2_CDF53_INT = 1 };
+enum dwt2_dtype { DWT2_F32 = 0, DWT2_F16 = 1, DWT2_BF16 = 2, DWT2_I32 = 3 };
+enum dwt2_scheme { DWT2_NONSEP = 0, DWT2_NONSEP_REDUCED = 1, DWT2_SEP_LIFTING = 2 };
+enum dwt2_boundary { DWT2_SYMMETRIC = 0 };
+
+#define DWT2_OK 0
+#define DWT2_ERR_INVALID_ARG (-1)     /* null pointer, bad enum, bad size      */
+#define DWT2_ERR_UNSUPPORTED (-2)     /* wavelet / dtype / scheme combination  */
+#define DWT2_ERR_LEVELS_TOO_DEEP (-3) /* some level's input side would be < 2  */
+#define DWT2_ERR_MISALIGNED (-4)      /* pointer, offset or pitch alignment    */
+#define DWT2_ERR_CUDA (-5)            /* a CUDA runtime call failed            */
+#define DWT2_ERR_TIMEOUT (-6)         /* a bounded device wait expired         */
+#define DWT2_ERR_DEVICE_CHECK (-7)    /* a device-side bounds check tripped    */
+
+/* plan flags */
+#define DWT2_FLAG_PERSISTENT 0x1u /* batch: one persistent launch for all levels */
+
+/* One image of a batch: element offset of its first pixel from the base
+ * pointer, its size, and its row pitch in elements (pitch >= w).  The same
+ * offset and pitch address its coefficients in the coefficient buffer. */
+typedef struct {
+    int64_t offset_elems;
+    int32_t h, w;
+    int64_t pitch_elems;
+} dwt2_image_desc;
+
+/*
+ * dwt2_plan -- validate a transform and prepare its launches.
+ *   out        receives the plan (set to NULL on error).
+ *   wavelet    DWT2_CDF97 or DWT2_CDF53_INT.
+ *   levels     number of pyramid levels, >= 1.
+ *   boundary   DWT2_SYMMETRIC.
+ *   in_dtype   image element type: DWT2_F32 for CDF 9/7, DWT2_I32 for 5/3.
+ *   coef_dtype coefficient element type: F32, F16 or BF16 for CDF 9/7 (the
+ *              lifting always runs in FP32 and intermediate LL bands are kept
+ *              in FP32), I32 for CDF 5/3.
+ *   scheme     DWT2_NONSEP, DWT2_NONSEP_REDUCED (CDF 9/7 only) or
+ *              DWT2_SEP_LIFTING.
+ *   n_images   number of images (>= 1); images is a host array of that many
+ *              descriptors, copied into the plan.
+ *   flags      0 or DWT2_FLAG_PERSISTENT.
+ * Alignment: the image (input) buffer's base pointer must be 16-byte aligned
+ * and offset_elems and pitch_elems multiples of 4 (16 bytes of 4-byte
+ * elements), else DWT2_ERR_MISALIGNED; coefficient buffers need only natural
+ * element alignment.  The plan allocates its device status word and batch
+ * tables on the current device.
+ */
+int dwt2_plan(dwt2_plan_t* out, int wavelet, int levels, int boundary, int in_dtype,
+              int coef_dtype, int scheme, int n_images, const dwt2_image_desc* images,
+              unsigned flags);
+
+/* Bytes of device workspace the caller passes to every transform call of this
+ * plan (intermediate low-low bands); 256-byte alignment is required. */
+size_t dwt2_workspace_bytes(dwt2_plan_t plan);
+
+/*
+ * dwt2_forward -- coef = W(in), the forward pyramid (Proposed Schemes; the
+ * paper's Optimization Approach for DWT2_NONSEP_REDUCED).
+ *   in         device pointer to the images (in_dtype), read only.
+ *   coef       device pointer to the coefficients (coef_dtype), written; must
+ *              not overlap in.
+ *   workspace  device pointer to dwt2_workspace_bytes(plan) bytes (may be
+ *              NULL when that is 0).
+ *   stream     a cudaStream_t (NULL for the legacy default stream).
+ */
+int dwt2_forward(dwt2_plan_t plan, const void* in, void* coef, void* workspace, void* stream);
+
+/* dwt2_inverse -- out = W^-1(coef): every step undone in reverse order
+ * (each lifting step is inverted by negating its filter, Eq. 2).
+ *   coef (coef_dtype) read only; out (in_dtype) written; no overlap. */
+int dwt2_inverse(dwt2_plan_t plan, const void* coef, void* out, void* workspace, void* stream);
+
+/* dwt2_adjoint -- in_grad = W^T(coef_grad), the transpose of the forward
+ * operator (not in the paper): the transposed steps in reverse order, with the
+ * transposed boundary weights.  CDF 9/7 only; both buffers FP32 and laid out
+ * like the image / the coefficients. */
+int dwt2_adjoint(dwt2_plan_t plan, const void* coef_grad, void* in_grad, void* workspace,
+                 void* stream);
+
+/* dwt2_status -- synchronise the stream, return and clear the plan's device
+ * status word: DWT2_OK, DWT2_ERR_TIMEOUT or DWT2_ERR_DEVICE_CHECK. */
+int dwt2_status(dwt2_plan_t plan, void* stream);
+
+/* dwt2_profile -- when enable != 0, every later transform call of this plan
+ * records a CUDA event pair on its stream around the launches of each pyramid
+ * level (all images of a batch together), in a ring of the last 256 calls;
+ * enabling resets the ring.  The events belong to the plan.  Not in the
+ * paper: a measurement hook. */
+int dwt2_profile(dwt2_plan_t plan, int enable);
+
+/* dwt2_profile_read -- wait for the recorded calls' events and write, for each
+ * of the first n levels (finest first), the mean elapsed milliseconds over the
+ * calls in the ring to ms[0 .. n-1]; n <= the plan's levels.
+ * DWT2_ERR_INVALID_ARG if nothing was recorded. */
+int dwt2_profile_read(dwt2_plan_t plan, float* ms, int n);
+
+/* dwt2_destroy -- free the plan (NULL is accepted). */
+void dwt2_destroy(dwt2_plan_t plan);
+
+/* dwt2_strerror -- static description of an error code. */
+const char* dwt2_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DWT2_H */

@@ -1,0 +1,425 @@
+// api.cu -- the C ABI of libdwt2 (include/dwt2.h): plan validation,
+// workspace layout, tensor-map encoding and the per-level launches.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/dwt2.h"
+#include "internal.h"
+
+using namespace dwt2;
+
+namespace {
+
+constexpr int OUT_Q_H = 60;  // output quads per strip (kernels.cuh)
+
+struct LevelGeom {
+    int h, w, hq, wq, hh, wh;
+};
+
+LevelGeom level_geom(int h, int w) {
+    LevelGeom g;
+    g.h = h;
+    g.w = w;
+    g.hq = (h + 1) / 2;
+    g.wq = (w + 1) / 2;
+    g.hh = h / 2;
+    g.wh = w / 2;
+    return g;
+}
+
+int64_t round4(int64_t v) { return (v + 3) / 4 * 4; }
+size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+size_t dtype_size(int dt) { return (dt == DT_F16 || dt == DT_BF16) ? 2 : 4; }
+
+struct ImagePlan {
+    dwt2_image_desc d;
+    std::vector<LevelGeom> lv;  // lv[l] = input geometry of level l (0-based)
+    size_t ws_off[2];           // workspace offsets of the two LL buffers
+};
+
+// decomposition of one level into (strip, segment) units
+struct Decomp {
+    int n_strips, seg_rows, n_segs, n_units;
+};
+
+Decomp decompose(const LevelGeom& g, int sm_count, int warps_per_sm, int seg_override) {
+    Decomp d;
+    d.n_strips = (g.wq + OUT_Q_H - 1) / OUT_Q_H;
+    int rows;
+    if (seg_override > 0) {
+        rows = seg_override;
+    } else {
+        // about three waves of warps: long segments amortise the 4-row warm-up
+        const int64_t target = int64_t(sm_count) * warps_per_sm * 3;
+        const int64_t total = int64_t(g.hq) * d.n_strips;
+        rows = int((total + target - 1) / target);
+        rows = std::min(std::max(rows, 8), 512);
+    }
+    d.seg_rows = std::min(rows, g.hq);
+    d.n_segs = (g.hq + d.seg_rows - 1) / d.seg_rows;
+    d.n_units = d.n_segs * d.n_strips;
+    return d;
+}
+
+// driver entry point for TMA descriptors
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn get_encode() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+// 2-D map over a w x h array of 4-byte elements with row pitch `pitch`
+// elements; box = 128 x box_rows.
+int encode_map(CUtensorMap* m, const void* base, int w, int h, int64_t pitch, int box_rows, bool is_int) {
+    EncodeTiledFn enc = get_encode();
+    if (!enc) return DWT2_ERR_CUDA;
+    cuuint64_t dims[2] = {cuuint64_t(w), cuuint64_t(h)};
+    cuuint64_t strides[1] = {cuuint64_t(pitch) * 4};
+    cuuint32_t box[2] = {128u, cuuint32_t(box_rows)};
+    cuuint32_t estr[2] = {1u, 1u};
+    CUresult r = enc(m, is_int ? CU_TENSOR_MAP_DATA_TYPE_INT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                     const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? DWT2_OK : DWT2_ERR_MISALIGNED;
+}
+
+int env_int(const char* name, int dflt) {
+    const char* v = getenv(name);
+    return (v && *v) ? atoi(v) : dflt;
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+}  // namespace
+
+struct dwt2_plan_s {
+    int wavelet, levels, in_dtype, coef_dtype, scheme, n_images;
+    unsigned flags;
+    std::vector<ImagePlan> imgs;
+    size_t ws_bytes;
+    unsigned* d_status;
+    int device, sm_count;
+    FwdCfg cfg;
+    int seg_override;
+    uint64_t timeout_ns;
+    // profiling: a ring of PROF_RING calls, one event pair per level each
+    std::vector<cudaEvent_t> ev0, ev1;  // [slot * levels + level]
+    bool prof_on;
+    int prof_calls;  // calls recorded since profiling was enabled
+};
+
+namespace {
+constexpr int PROF_RING = 256;
+void prof_mark(dwt2_plan_t p, int level, bool start, cudaStream_t s) {
+    if (!p->prof_on) return;
+    const int slot = p->prof_calls % PROF_RING;
+    cudaEventRecord(start ? p->ev0[slot * p->levels + level] : p->ev1[slot * p->levels + level], s);
+}
+}  // namespace
+
+extern "C" {
+
+const char* dwt2_strerror(int code) {
+    switch (code) {
+        case DWT2_OK: return "ok";
+        case DWT2_ERR_INVALID_ARG: return "invalid argument";
+        case DWT2_ERR_UNSUPPORTED: return "unsupported wavelet / dtype / scheme combination";
+        case DWT2_ERR_LEVELS_TOO_DEEP: return "too many levels for the image size (a level input side would be < 2)";
+        case DWT2_ERR_MISALIGNED: return "misaligned pointer, offset or pitch";
+        case DWT2_ERR_CUDA: return "CUDA runtime error";
+        case DWT2_ERR_TIMEOUT: return "a bounded device wait expired";
+        case DWT2_ERR_DEVICE_CHECK: return "a device-side bounds check tripped";
+        default: return "unknown error";
+    }
+}
+
+int dwt2_plan(dwt2_plan_t* out, int wavelet, int levels, int boundary, int in_dtype, int coef_dtype, int scheme,
+              int n_images, const dwt2_image_desc* images, unsigned flags) {
+    if (!out) return DWT2_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!images || n_images < 1 || levels < 1 || levels > 30) return DWT2_ERR_INVALID_ARG;
+    if (boundary != DWT2_SYMMETRIC) return DWT2_ERR_INVALID_ARG;
+    if (wavelet != DWT2_CDF97 && wavelet != DWT2_CDF53_INT) return DWT2_ERR_INVALID_ARG;
+    if (scheme < DWT2_NONSEP || scheme > DWT2_SEP_LIFTING) return DWT2_ERR_INVALID_ARG;
+    if (in_dtype < DWT2_F32 || in_dtype > DWT2_I32 || coef_dtype < DWT2_F32 || coef_dtype > DWT2_I32)
+        return DWT2_ERR_INVALID_ARG;
+    if (flags & ~(DWT2_FLAG_PERSISTENT)) return DWT2_ERR_INVALID_ARG;
+    if (wavelet == DWT2_CDF97) {
+        if (in_dtype != DWT2_F32 || coef_dtype == DWT2_I32) return DWT2_ERR_UNSUPPORTED;
+    } else {
+        if (in_dtype != DWT2_I32 || coef_dtype != DWT2_I32) return DWT2_ERR_UNSUPPORTED;
+        if (scheme == DWT2_NONSEP_REDUCED) return DWT2_ERR_UNSUPPORTED;  // floor does not split
+    }
+    std::vector<ImagePlan> imgs(n_images);
+    size_t ws = 0;
+    for (int i = 0; i < n_images; ++i) {
+        const dwt2_image_desc& d = images[i];
+        if (d.h < 1 || d.w < 1 || d.pitch_elems < d.w || d.offset_elems < 0) return DWT2_ERR_INVALID_ARG;
+        if (d.offset_elems % 4 != 0 || d.pitch_elems % 4 != 0) return DWT2_ERR_MISALIGNED;
+        ImagePlan& ip = imgs[i];
+        ip.d = d;
+        int h = d.h, w = d.w;
+        for (int l = 0; l < levels; ++l) {
+            if (h < 2 || w < 2) return DWT2_ERR_LEVELS_TOO_DEEP;
+            ip.lv.push_back(level_geom(h, w));
+            h = (h + 1) / 2;
+            w = (w + 1) / 2;
+        }
+        // LL of level l (0-based, l < levels-1) goes to buffer l % 2
+        size_t need[2] = {0, 0};
+        for (int l = 0; l + 1 < levels; ++l) {
+            const LevelGeom& g = ip.lv[l];
+            need[l % 2] = std::max(need[l % 2], size_t(g.hq) * size_t(round4(g.wq)) * 4);
+        }
+        ip.ws_off[0] = ws;
+        ws += align256(need[0]);
+        ip.ws_off[1] = ws;
+        ws += align256(need[1]);
+    }
+    dwt2_plan_s* p = new (std::nothrow) dwt2_plan_s();
+    if (!p) return DWT2_ERR_INVALID_ARG;
+    p->wavelet = wavelet;
+    p->levels = levels;
+    p->in_dtype = in_dtype;
+    p->coef_dtype = coef_dtype;
+    p->scheme = scheme;
+    p->n_images = n_images;
+    p->flags = flags;
+    p->imgs.swap(imgs);
+    p->ws_bytes = ws;
+    p->d_status = nullptr;
+    p->prof_on = false;
+    p->prof_calls = 0;
+    p->timeout_ns = uint64_t(env_int("DWT2_TIMEOUT_MS", 2000)) * 1000000ull;
+    p->seg_override = env_int("DWT2_SEG_ROWS", 0);
+    int ci = env_int("DWT2_FWD_CFG", 0);
+    if (ci < 0 || ci >= N_FWD_CFGS) ci = 0;
+    p->cfg = FWD_CFGS[ci];
+    if (cudaGetDevice(&p->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess ||
+        cudaMalloc(&p->d_status, sizeof(unsigned)) != cudaSuccess ||
+        cudaMemset(p->d_status, 0, sizeof(unsigned)) != cudaSuccess) {
+        if (p->d_status) cudaFree(p->d_status);
+        delete p;
+        cudaGetLastError();
+        return DWT2_ERR_CUDA;
+    }
+    *out = p;
+    return DWT2_OK;
+}
+
+size_t dwt2_workspace_bytes(dwt2_plan_t p) { return p ? p->ws_bytes : 0; }
+
+void dwt2_destroy(dwt2_plan_t p) {
+    if (!p) return;
+    if (p->d_status) cudaFree(p->d_status);
+    for (cudaEvent_t e : p->ev0) cudaEventDestroy(e);
+    for (cudaEvent_t e : p->ev1) cudaEventDestroy(e);
+    delete p;
+}
+
+int dwt2_profile(dwt2_plan_t p, int enable) {
+    if (!p) return DWT2_ERR_INVALID_ARG;
+    if (enable && p->ev0.empty()) {
+        const size_t n = size_t(PROF_RING) * p->levels;
+        p->ev0.assign(n, nullptr);
+        p->ev1.assign(n, nullptr);
+        for (size_t i = 0; i < n; ++i) {
+            if (cudaEventCreate(&p->ev0[i]) != cudaSuccess || cudaEventCreate(&p->ev1[i]) != cudaSuccess)
+                return DWT2_ERR_CUDA;
+        }
+    }
+    p->prof_on = enable != 0;
+    p->prof_calls = 0;
+    return DWT2_OK;
+}
+
+int dwt2_profile_read(dwt2_plan_t p, float* ms, int n) {
+    if (!p || !ms || n < 0 || n > p->levels || p->ev0.empty() || p->prof_calls == 0) return DWT2_ERR_INVALID_ARG;
+    const int calls = std::min(p->prof_calls, PROF_RING);
+    for (int l = 0; l < n; ++l) {
+        double sum = 0.0;
+        for (int c = 0; c < calls; ++c) {
+            const int slot = (p->prof_calls - 1 - c) % PROF_RING;
+            float t = 0.f;
+            if (cudaEventSynchronize(p->ev1[slot * p->levels + l]) != cudaSuccess ||
+                cudaEventElapsedTime(&t, p->ev0[slot * p->levels + l], p->ev1[slot * p->levels + l]) != cudaSuccess)
+                return DWT2_ERR_CUDA;
+            sum += t;
+        }
+        ms[l] = float(sum / calls);
+    }
+    return DWT2_OK;
+}
+
+int dwt2_status(dwt2_plan_t p, void* stream) {
+    if (!p) return DWT2_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned h = 0;
+    if (cudaMemcpyAsync(&h, p->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess || cudaMemsetAsync(p->d_status, 0, sizeof(unsigned), s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return DWT2_ERR_CUDA;
+    if (h & DEV_TIMEOUT) return DWT2_ERR_TIMEOUT;
+    if (h & DEV_CHECK) return DWT2_ERR_DEVICE_CHECK;
+    return DWT2_OK;
+}
+
+int dwt2_forward(dwt2_plan_t p, const void* in, void* coef, void* workspace, void* stream) {
+    if (!p || !in || !coef) return DWT2_ERR_INVALID_ARG;
+    if (p->ws_bytes && !workspace) return DWT2_ERR_INVALID_ARG;
+    if (!aligned(in, 16) || (workspace && !aligned(workspace, 256))) return DWT2_ERR_MISALIGNED;
+    const size_t csz = dtype_size(p->coef_dtype);
+    if (!aligned(coef, csz)) return DWT2_ERR_MISALIGNED;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const bool is_int = p->wavelet == DWT2_CDF53_INT;
+    const int warps_per_sm = 24;
+    for (int l = 0; l < p->levels; ++l) {
+        prof_mark(p, l, true, s);
+        for (const ImagePlan& ip : p->imgs) {
+            const char* in_img = static_cast<const char*>(in) + ip.d.offset_elems * 4;
+            char* coef_img = static_cast<char*>(coef) + ip.d.offset_elems * csz;
+            char* wsb = static_cast<char*>(workspace);
+            const LevelGeom& g = ip.lv[l];
+            const void* src = (l == 0) ? static_cast<const void*>(in_img)
+                                       : static_cast<const void*>(wsb + ip.ws_off[(l - 1) % 2]);
+            const int64_t src_pitch = (l == 0) ? ip.d.pitch_elems : round4(ip.lv[l - 1].wq);
+            CUtensorMap box, row;
+            int rc = encode_map(&box, src, g.w, g.h, src_pitch, 2 * p->cfg.qr, is_int);
+            if (rc == DWT2_OK) rc = encode_map(&row, src, g.w, g.h, src_pitch, 1, is_int);
+            if (rc != DWT2_OK) return rc;
+            FwdParams fp;
+            fp.h = g.h, fp.w = g.w, fp.hq = g.hq, fp.wq = g.wq, fp.hh = g.hh, fp.wh = g.wh;
+            const Decomp dc = decompose(g, p->sm_count, warps_per_sm, p->seg_override);
+            fp.n_strips = dc.n_strips, fp.seg_rows = dc.seg_rows, fp.n_segs = dc.n_segs, fp.n_units = dc.n_units;
+            fp.coef = coef_img;
+            fp.coef_pitch = ip.d.pitch_elems;
+            const bool last = (l == p->levels - 1);
+            if (last) {
+                fp.ll = coef_img;
+                fp.ll_pitch = ip.d.pitch_elems;
+                fp.ll_is_ct = 0;
+            } else {
+                fp.ll = wsb + ip.ws_off[l % 2];
+                fp.ll_pitch = round4(g.wq);
+                fp.ll_is_ct = 1;
+            }
+            const size_t pair = 2 * csz;
+            const bool coef_vec = (ip.d.pitch_elems % 2 == 0) && aligned(coef_img, pair);
+            fp.vec_lo = coef_vec;
+            fp.vec_hi = coef_vec && (g.wq % 2 == 0);
+            fp.vec_ll = last ? coef_vec : 1;
+            fp.status = p->d_status;
+            fp.timeout_ns = p->timeout_ns;
+            const int grid = (dc.n_units + p->cfg.nw - 1) / p->cfg.nw;
+            int e;
+            switch (p->coef_dtype) {
+                case DWT2_F32: e = launch_forward_f32(p->wavelet, p->scheme, box, row, fp, grid, p->cfg, s); break;
+                case DWT2_F16: e = launch_forward_f16(p->wavelet, p->scheme, box, row, fp, grid, p->cfg, s); break;
+                case DWT2_BF16: e = launch_forward_bf16(p->wavelet, p->scheme, box, row, fp, grid, p->cfg, s); break;
+                default: e = launch_forward_i32(p->wavelet, p->scheme, box, row, fp, grid, p->cfg, s); break;
+            }
+            if (e != cudaSuccess) return DWT2_ERR_CUDA;
+        }
+        prof_mark(p, l, false, s);
+    }
+    if (p->prof_on) ++p->prof_calls;
+    return DWT2_OK;
+}
+
+// shared by the inverse and the adjoint: levels from the coarsest down
+static int run_inverse_like(dwt2_plan_t p, const void* coef, void* out, void* workspace, void* stream, bool adj) {
+    if (!p || !coef || !out) return DWT2_ERR_INVALID_ARG;
+    if (p->ws_bytes && !workspace) return DWT2_ERR_INVALID_ARG;
+    if (workspace && !aligned(workspace, 256)) return DWT2_ERR_MISALIGNED;
+    if (adj && p->wavelet != DWT2_CDF97) return DWT2_ERR_UNSUPPORTED;
+    const size_t csz = adj ? 4 : dtype_size(p->coef_dtype);
+    if (!aligned(coef, csz) || !aligned(out, 4)) return DWT2_ERR_MISALIGNED;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int warps_per_sm = 16;
+    for (int l = p->levels - 1; l >= 0; --l) {
+        prof_mark(p, l, true, s);
+        for (const ImagePlan& ip : p->imgs) {
+            const char* coef_img = static_cast<const char*>(coef) + ip.d.offset_elems * csz;
+            char* out_img = static_cast<char*>(out) + ip.d.offset_elems * 4;
+            char* wsb = static_cast<char*>(workspace);
+            const LevelGeom& g = ip.lv[l];
+            InvParams ipm;
+            ipm.h = g.h, ipm.w = g.w, ipm.hq = g.hq, ipm.wq = g.wq, ipm.hh = g.hh, ipm.wh = g.wh;
+            const Decomp dc = decompose(g, p->sm_count, warps_per_sm, p->seg_override);
+            ipm.n_strips = dc.n_strips, ipm.seg_rows = dc.seg_rows, ipm.n_segs = dc.n_segs, ipm.n_units = dc.n_units;
+            ipm.coef = coef_img;
+            ipm.coef_pitch = ip.d.pitch_elems;
+            const bool coarsest = (l == p->levels - 1);
+            if (coarsest) {
+                ipm.ll = coef_img;
+                ipm.ll_pitch = ip.d.pitch_elems;
+                ipm.ll_is_ct = 0;
+            } else {
+                ipm.ll = wsb + ip.ws_off[l % 2];
+                ipm.ll_pitch = round4(g.wq);
+                ipm.ll_is_ct = 1;
+            }
+            if (l == 0) {
+                ipm.out = out_img;
+                ipm.out_pitch = ip.d.pitch_elems;
+            } else {
+                ipm.out = wsb + ip.ws_off[(l - 1) % 2];
+                ipm.out_pitch = round4(g.w);  // = round4(wq of level l-1)
+            }
+            const size_t pair = 2 * csz;
+            const bool cvec = (ip.d.pitch_elems % 2 == 0) && aligned(coef_img, pair);
+            ipm.vec_in_lo = cvec;
+            ipm.vec_in_hi = cvec && (g.wq % 2 == 0);
+            ipm.vec_ll = coarsest ? cvec : 1;
+            ipm.vec_out = (ipm.out_pitch % 4 == 0) && aligned(ipm.out, 16);
+            ipm.status = p->d_status;
+            const int grid = (dc.n_units + INV_NW - 1) / INV_NW;
+            int e;
+            if (adj) {
+                e = launch_adjoint_f32(ipm, grid, s);
+            } else {
+                switch (p->coef_dtype) {
+                    case DWT2_F32: e = launch_inverse_f32(p->wavelet, p->scheme, ipm, grid, s); break;
+                    case DWT2_F16: e = launch_inverse_f16(p->wavelet, p->scheme, ipm, grid, s); break;
+                    case DWT2_BF16: e = launch_inverse_bf16(p->wavelet, p->scheme, ipm, grid, s); break;
+                    default: e = launch_inverse_i32(p->wavelet, p->scheme, ipm, grid, s); break;
+                }
+            }
+            if (e != cudaSuccess) return DWT2_ERR_CUDA;
+        }
+        prof_mark(p, l, false, s);
+    }
+    if (p->prof_on) ++p->prof_calls;
+    return DWT2_OK;
+}
+
+int dwt2_inverse(dwt2_plan_t p, const void* coef, void* out, void* workspace, void* stream) {
+    return run_inverse_like(p, coef, out, workspace, stream, false);
+}
+
+int dwt2_adjoint(dwt2_plan_t p, const void* coef_grad, void* in_grad, void* workspace, void* stream) {
+    return run_inverse_like(p, coef_grad, in_grad, workspace, stream, true);
+}
+
+}  // extern "C"

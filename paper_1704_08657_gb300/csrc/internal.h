@@ -1,0 +1,80 @@
+// internal.h -- host/device parameter blocks and the launcher interface
+// between the C ABI (api.cu) and the kernel translation units.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dwt2 {
+
+// device status word bits
+enum : unsigned { DEV_TIMEOUT = 1u, DEV_CHECK = 2u };
+
+enum { SCHEME_NONSEP = 0, SCHEME_REDUCED = 1, SCHEME_SEP = 2 };
+enum { WAV_CDF97 = 0, WAV_CDF53I = 1 };
+enum { DT_F32 = 0, DT_F16 = 1, DT_BF16 = 2, DT_I32 = 3 };
+
+// One forward level.  Input pixels come through the two tensor maps; the
+// output is written in Mallat layout: LL to `ll` (compute type when ll_is_ct,
+// i.e. an intermediate band in the workspace, else the coefficient type), HL
+// to coef[row][wq + j], LH to coef[hq + row][j], HH to coef[hq + row][wq + j].
+struct FwdParams {
+    int h, w;                  // level input size in pixels (>= 2)
+    int hq, wq, hh, wh;        // ceil and floor halves
+    int n_strips, seg_rows, n_segs, n_units;
+    void* coef;                // top-left of the level's region, coefficient type
+    int64_t coef_pitch;        // elements
+    void* ll;                  // LL destination
+    int64_t ll_pitch;
+    int ll_is_ct;
+    int vec_lo, vec_hi, vec_ll;  // pair-store alignment: LH, HL / HH, LL
+    unsigned* status;          // device status word (may be null)
+    uint64_t timeout_ns;       // bounded-wait limit
+};
+
+// One inverse or adjoint level: bands in, pixels (compute type) out.
+struct InvParams {
+    int h, w;
+    int hq, wq, hh, wh;
+    int n_strips, seg_rows, n_segs, n_units;
+    const void* coef;          // detail bands (coefficient type), level origin
+    int64_t coef_pitch;
+    const void* ll;            // LL band: compute type when ll_is_ct
+    int64_t ll_pitch;
+    int ll_is_ct;
+    void* out;                 // output pixels, compute type
+    int64_t out_pitch;
+    int vec_in_lo, vec_in_hi, vec_ll, vec_out;
+    unsigned* status;
+};
+
+// forward launch configuration
+struct FwdCfg {
+    int qr, nst, nw;  // quad rows per stage, stages per warp, warps per block
+};
+
+// kernel launchers, one translation unit per coefficient type; they return a
+// cudaError_t value
+int launch_forward_f32(int wav, int scheme, const CUtensorMap& box, const CUtensorMap& row, const FwdParams& p,
+                       int grid, const FwdCfg& cfg, cudaStream_t s);
+int launch_forward_f16(int wav, int scheme, const CUtensorMap& box, const CUtensorMap& row, const FwdParams& p,
+                       int grid, const FwdCfg& cfg, cudaStream_t s);
+int launch_forward_bf16(int wav, int scheme, const CUtensorMap& box, const CUtensorMap& row, const FwdParams& p,
+                        int grid, const FwdCfg& cfg, cudaStream_t s);
+int launch_forward_i32(int wav, int scheme, const CUtensorMap& box, const CUtensorMap& row, const FwdParams& p,
+                       int grid, const FwdCfg& cfg, cudaStream_t s);
+
+int launch_inverse_f32(int wav, int scheme, const InvParams& p, int grid, cudaStream_t s);
+int launch_inverse_f16(int wav, int scheme, const InvParams& p, int grid, cudaStream_t s);
+int launch_inverse_bf16(int wav, int scheme, const InvParams& p, int grid, cudaStream_t s);
+int launch_inverse_i32(int wav, int scheme, const InvParams& p, int grid, cudaStream_t s);
+int launch_adjoint_f32(const InvParams& p, int grid, cudaStream_t s);
+
+// the forward configurations compiled in (index 0 is the default)
+constexpr int N_FWD_CFGS = 3;
+extern const FwdCfg FWD_CFGS[N_FWD_CFGS];
+size_t fwd_smem_bytes_of(const FwdCfg& c);
+constexpr int INV_NW = 4;
+
+}  // namespace dwt2

@@ -1,0 +1,15 @@
+// k_f16.cu -- kernels whose coefficients are stored as __half.
+#include "launch.cuh"
+
+namespace dwt2 {
+
+int launch_forward_f16(int wav, int scheme, const CUtensorMap& box, const CUtensorMap& row, const FwdParams& p,
+                   int grid, const FwdCfg& cfg, cudaStream_t s) {
+    return launch_forward_t<__half>(wav, scheme, box, row, p, grid, cfg, s);
+}
+
+int launch_inverse_f16(int wav, int scheme, const InvParams& p, int grid, cudaStream_t s) {
+    return launch_inverse_t<__half>(wav, scheme, p, grid, s);
+}
+
+}  // namespace dwt2

@@ -1,0 +1,621 @@
+// schemes.cuh -- the lifting steps of every scheme, applied to one quad row of
+// one lane, and the row pipelines that stream quad rows through them.
+//
+// Notation (Barina et al., arXiv:1704.08657, Background and Proposed
+// Schemes): a quad is (c1, c2, c3, c4) = (x[2i][2j], x[2i][2j+1],
+// x[2i+1][2j], x[2i+1][2j+1]).  P acts horizontally, P* vertically.
+// Predict P = a(1 + z) reads the quad itself and the quad to the right (or
+// below for P*); update U = b(1 + z^-1) reads the quad itself and the quad to
+// the left (or above).
+//
+//   spatial predict T_P:  c2 += P c1;  c3 += P* c1;  c4 += PP* c1 + P* c2 + P c3
+//   spatial update  S_U:  c1 += U c2 + U* c3 + UU* c4;  c2 += U* c4;  c3 += U c4
+//
+// with all operands taken before the step.  Quad rows stream top to bottom
+// through the registers of a lane: a step that reads the row below runs one
+// row later than the step before it; a step that reads the row above takes
+// that row's pre-step values from a carry saved when the step ran on it.
+// Horizontal neighbours come from the next / previous lane by shuffle.
+#pragma once
+
+#include "dev_common.cuh"
+
+namespace dwt2 {
+
+// CDF 9/7 lifting constants (alpha, beta, gamma, delta) and scaling zeta.
+struct C97 {
+    static constexpr double Ad = -1.586134342, Bd = -0.052980119, Gd = 0.882911076, Dd = 0.443506852,
+                            Zd = 1.149604398;
+    static constexpr float A = float(Ad), B = float(Bd), G = float(Gd), D = float(Dd);
+    static constexpr float AA = float(Ad * Ad), BB = float(Bd * Bd), GG = float(Gd * Gd), DD = float(Dd * Dd);
+    static constexpr float ZZ = float(Zd * Zd), IZZ = float(1.0 / (Zd * Zd));
+};
+
+// carries of an update step: the row above, before the step
+struct Carry3 {
+    float c3[QL], c4[QL], l4[QL];  // c3, c4 and the c4 of the quad to the left
+};
+template <class CT>
+struct Carry2 {
+    CT c3[QL], c4[QL];
+};
+
+__device__ __forceinline__ void zero_carry(Carry3& c) {
+#pragma unroll
+    for (int q = 0; q < QL; ++q) c.c3[q] = c.c4[q] = c.l4[q] = 0.f;
+}
+template <class CT>
+__device__ __forceinline__ void zero_carry(Carry2<CT>& c) {
+#pragma unroll
+    for (int q = 0; q < QL; ++q) c.c3[q] = c.c4[q] = CT(0);
+}
+
+// ============================================================ CDF 9/7 float
+
+// --- non-separable lifting (Proposed Schemes) ------------------------------
+// T_P on row X with the row below D, P = a(1 + z): every operand pre-step.
+__device__ __forceinline__ void ns_predict(Row<float>& X, const Row<float>& D, float a, float aa) {
+    float r1[QL], r3[QL], dr1[QL];
+    right_of(X.c1, r1);
+    right_of(X.c3, r3);
+    right_of(D.c1, dr1);
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+        const float s1 = X.c1[q] + r1[q];                         // P c1
+        const float sd = D.c1[q] + dr1[q];                        // P c1 of the row below
+        const float t = (X.c3[q] + r3[q]) + (X.c2[q] + D.c2[q]);  // P c3 + P* c2
+        const float c4 = fmaf(a, t, X.c4[q]);
+        X.c4[q] = fmaf(aa, s1 + sd, c4);                          // + PP* c1
+        X.c2[q] = fmaf(a, s1, X.c2[q]);
+        X.c3[q] = fmaf(a, X.c1[q] + D.c1[q], X.c3[q]);            // P* c1
+    }
+}
+
+// S_U on row X with the carry C of the row above, U = b(1 + z^-1).
+__device__ __forceinline__ void ns_update(Row<float>& X, Carry3& C, float b, float bb) {
+    float l2[QL], l4[QL];
+    left_of(X.c2, l2);
+    left_of(X.c4, l4);
+    Carry3 n;
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+        n.c3[q] = X.c3[q];
+        n.c4[q] = X.c4[q];
+        n.l4[q] = l4[q];
+        const float h = l2[q] + X.c2[q];                                   // U c2
+        const float v = C.c3[q] + X.c3[q];                                 // U* c3
+        const float dg = (C.l4[q] + C.c4[q]) + (l4[q] + X.c4[q]);          // UU* c4
+        X.c1[q] = fmaf(b, h + v, fmaf(bb, dg, X.c1[q]));
+        X.c2[q] = fmaf(b, C.c4[q] + X.c4[q], X.c2[q]);                     // U* c4
+        X.c3[q] = fmaf(b, l4[q] + X.c4[q], X.c3[q]);                       // U c4
+    }
+    C = n;
+}
+
+// --- reduced operations (Optimization Approach) -----------------------------
+// P = P0 + P1 with P0 = a (own quad) and P1 = a z (neighbour).  T_{P1} first,
+// on pre-step values, then T_{P0}^H and T_{P0}^V inside the quad.
+__device__ __forceinline__ void rd_predict(Row<float>& X, const Row<float>& D, float a, float aa) {
+    float r1[QL], r3[QL], dr1[QL];
+    right_of(X.c1, r1);
+    right_of(X.c3, r3);
+    right_of(D.c1, dr1);
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+        float c2 = fmaf(a, r1[q], X.c2[q]);       // P1 c1
+        float c3 = fmaf(a, D.c1[q], X.c3[q]);     // P1* c1
+        float c4 = fmaf(a, r3[q], X.c4[q]);       // P1 c3
+        c4 = fmaf(a, D.c2[q], c4);                // P1* c2
+        c4 = fmaf(aa, dr1[q], c4);                // P1 P1* c1
+        c2 = fmaf(a, X.c1[q], c2);                // T_{P0}^H
+        c4 = fmaf(a, c3, c4);
+        c3 = fmaf(a, X.c1[q], c3);                // T_{P0}^V
+        c4 = fmaf(a, c2, c4);
+        X.c2[q] = c2;
+        X.c3[q] = c3;
+        X.c4[q] = c4;
+    }
+}
+
+// U = U0 + U1 with U0 = b and U1 = b z^-1: S_{U1}, then S_{U0}^H, S_{U0}^V.
+__device__ __forceinline__ void rd_update(Row<float>& X, Carry3& C, float b, float bb) {
+    float l2[QL], l4[QL];
+    left_of(X.c2, l2);
+    left_of(X.c4, l4);
+    Carry3 n;
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+        n.c3[q] = X.c3[q];
+        n.c4[q] = X.c4[q];
+        n.l4[q] = l4[q];
+        float c1 = fmaf(b, l2[q], X.c1[q]);       // U1 c2
+        c1 = fmaf(b, C.c3[q], c1);                // U1* c3
+        c1 = fmaf(bb, C.l4[q], c1);               // U1 U1* c4
+        float c2 = fmaf(b, C.c4[q], X.c2[q]);     // U1* c4
+        float c3 = fmaf(b, l4[q], X.c3[q]);       // U1 c4
+        c1 = fmaf(b, c2, c1);                     // S_{U0}^H
+        c3 = fmaf(b, X.c4[q], c3);
+        c1 = fmaf(b, c3, c1);                     // S_{U0}^V
+        c2 = fmaf(b, X.c4[q], c2);
+        X.c1[q] = c1;
+        X.c2[q] = c2;
+        X.c3[q] = c3;
+    }
+    C = n;
+}
+
+// inverse of rd_update: undo S_{U0}^V, S_{U0}^H inside the quad, then S_{-U1}
+// (its pre-step operands are the post-undo values of the neighbours).
+__device__ __forceinline__ void rdi_update(Row<float>& X, Carry3& C, float b, float bb) {
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+        X.c1[q] = fmaf(-b, X.c3[q], X.c1[q]);
+        X.c2[q] = fmaf(-b, X.c4[q], X.c2[q]);
+        X.c1[q] = fmaf(-b, X.c2[q], X.c1[q]);
+        X.c3[q] = fmaf(-b, X.c4[q], X.c3[q]);
+    }
+    float l2[QL], l4[QL];
+    left_of(X.c2, l2);
+    left_of(X.c4, l4);
+    Carry3 n;
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+        n.c3[q] = X.c3[q];
+        n.c4[q] = X.c4[q];
+        n.l4[q] = l4[q];
+        float c1 = fmaf(-b, l2[q], X.c1[q]);
+        c1 = fmaf(-b, C.c3[q], c1);
+        X.c1[q] = fmaf(bb, C.l4[q], c1);
+        X.c2[q] = fmaf(-b, C.c4[q], X.c2[q]);
+        X.c3[q] = fmaf(-b, l4[q], X.c3[q]);
+    }
+    C = n;
+}
+
+// inverse of rd_predict, part 1 (inside the quad): undo T_{P0}^V, T_{P0}^H.
+__device__ __forceinline__ void rdi_predict_local(Row<float>& X, float a) {
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+        X.c4[q] = fmaf(-a, X.c2[q], X.c4[q]);
+        X.c3[q] = fmaf(-a, X.c1[q], X.c3[q]);
+        X.c4[q] = fmaf(-a, X.c3[q], X.c4[q]);
+        X.c2[q] = fmaf(-a, X.c1[q], X.c2[q]);
+    }
+}
+
+// inverse of rd_predict, part 2: T_{-P1}; the row below must have had part 1.
+__device__ __forceinline__ void rdi_predict_exch(Row<float>& X, const Row<float>& D, float a, float aa) {
+    float r1[QL], r3[QL], dr1[QL];
+    right_of(X.c1, r1);
+    right_of(X.c3, r3);
+    right_of(D.c1, dr1);
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+        float c4 = fmaf(-a, r3[q], X.c4[q]);
+        c4 = fmaf(-a, D.c2[q], c4);
+        X.c4[q] = fmaf(aa, dr1[q], c4);
+        X.c2[q] = fmaf(-a, r1[q], X.c2[q]);
+        X.c3[q] = fmaf(-a, D.c1[q], X.c3[q]);
+    }
+}
+
+// --- separable lifting (Background) -----------------------------------------
+template <class CT>
+__device__ __forceinline__ void sp_th(Row<CT>& X, float a) {  // T_P^H
+    float r1[QL], r3[QL];
+    right_of(X.c1, r1);
+    right_of(X.c3, r3);
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+        X.c2[q] = fmaf(a, X.c1[q] + r1[q], X.c2[q]);
+        X.c4[q] = fmaf(a, X.c3[q] + r3[q], X.c4[q]);
+    }
+}
+__device__ __forceinline__ void sp_tv(Row<float>& X, const Row<float>& D, float a) {  // T_P^V
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+        X.c3[q] = fmaf(a, X.c1[q] + D.c1[q], X.c3[q]);
+        X.c4[q] = fmaf(a, X.c2[q] + D.c2[q], X.c4[q]);
+    }
+}
+__device__ __forceinline__ void sp_sh(Row<float>& X, float b) {  // S_U^H
+    float l2[QL], l4[QL];
+    left_of(X.c2, l2);
+    left_of(X.c4, l4);
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+        X.c1[q] = fmaf(b, l2[q] + X.c2[q], X.c1[q]);
+        X.c3[q] = fmaf(b, l4[q] + X.c4[q], X.c3[q]);
+    }
+}
+__device__ __forceinline__ void sp_sv(Row<float>& X, Carry2<float>& C, float b) {  // S_U^V
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+        X.c1[q] = fmaf(b, C.c3[q] + X.c3[q], X.c1[q]);
+        X.c2[q] = fmaf(b, C.c4[q] + X.c4[q], X.c2[q]);
+        C.c3[q] = X.c3[q];
+        C.c4[q] = X.c4[q];
+    }
+}
+
+// scaling: per axis low * zeta, high / zeta
+__device__ __forceinline__ void scale97(Row<float>& X) {
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+        X.c1[q] *= C97::ZZ;
+        X.c4[q] *= C97::IZZ;
+    }
+}
+__device__ __forceinline__ void unscale97(Row<float>& X) {
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+        X.c1[q] *= C97::IZZ;
+        X.c4[q] *= C97::ZZ;
+    }
+}
+
+// ---------------------------------------------------------- 9/7 pipelines
+// arrive(r0) takes the newest quad row and returns the finished row LAG
+// quad rows above it.
+template <int SCHEME>
+struct Fwd97 {
+    static constexpr int LAG = 2;
+    using CT = float;
+    Row<float> r1, r2;
+    Carry3 k0, k1;
+    Carry2<float> s0, s1;
+    __device__ __forceinline__ void init() {
+        zero_row(r1);
+        zero_row(r2);
+        zero_carry(k0);
+        zero_carry(k1);
+        zero_carry(s0);
+        zero_carry(s1);
+    }
+    __device__ __forceinline__ Row<float> arrive(const Row<float>& r0in, int /*row*/) {
+        Row<float> r0 = r0in;
+        if (SCHEME == SCHEME_NONSEP) {
+            ns_predict(r1, r0, C97::A, C97::AA);
+            ns_update(r1, k0, C97::B, C97::BB);
+            ns_predict(r2, r1, C97::G, C97::GG);
+            ns_update(r2, k1, C97::D, C97::DD);
+        } else if (SCHEME == SCHEME_REDUCED) {
+            rd_predict(r1, r0, C97::A, C97::AA);
+            rd_update(r1, k0, C97::B, C97::BB);
+            rd_predict(r2, r1, C97::G, C97::GG);
+            rd_update(r2, k1, C97::D, C97::DD);
+        } else {
+            sp_th(r0, C97::A);
+            sp_tv(r1, r0, C97::A);
+            sp_sh(r1, C97::B);
+            sp_sv(r1, s0, C97::B);
+            sp_th(r1, C97::G);
+            sp_tv(r2, r1, C97::G);
+            sp_sh(r2, C97::D);
+            sp_sv(r2, s1, C97::D);
+        }
+        Row<float> out = r2;
+        scale97(out);
+        r2 = r1;
+        r1 = r0;
+        return out;
+    }
+};
+
+// inverse: unscale, then for each pair in reverse order S_{-U}, T_{-P}
+template <int SCHEME>
+struct Inv97 {
+    static constexpr int LAG = 2;
+    using CT = float;
+    Row<float> r1, r2;
+    Carry3 k0, k1;
+    Carry2<float> s0, s1;
+    __device__ __forceinline__ void init() {
+        zero_row(r1);
+        zero_row(r2);
+        zero_carry(k0);
+        zero_carry(k1);
+        zero_carry(s0);
+        zero_carry(s1);
+    }
+    __device__ __forceinline__ Row<float> arrive(const Row<float>& r0in, int /*row*/) {
+        Row<float> r0 = r0in;
+        unscale97(r0);
+        if (SCHEME == SCHEME_NONSEP) {
+            ns_update(r0, k1, -C97::D, C97::DD);
+            ns_predict(r1, r0, -C97::G, C97::GG);
+            ns_update(r1, k0, -C97::B, C97::BB);
+            ns_predict(r2, r1, -C97::A, C97::AA);
+        } else if (SCHEME == SCHEME_REDUCED) {
+            rdi_update(r0, k1, C97::D, C97::DD);
+            rdi_predict_local(r0, C97::G);
+            rdi_predict_exch(r1, r0, C97::G, C97::GG);
+            rdi_update(r1, k0, C97::B, C97::BB);
+            rdi_predict_local(r1, C97::A);
+            rdi_predict_exch(r2, r1, C97::A, C97::AA);
+        } else {
+            sp_sv(r0, s1, -C97::D);
+            sp_sh(r0, -C97::D);
+            sp_tv(r1, r0, -C97::G);
+            sp_th(r1, -C97::G);
+            sp_sv(r1, s0, -C97::B);
+            sp_sh(r1, -C97::B);
+            sp_tv(r2, r1, -C97::A);
+            sp_th(r2, -C97::A);
+        }
+        Row<float> out = r2;
+        r2 = r1;
+        r1 = r0;
+        return out;
+    }
+};
+
+// ==================================================== adjoint of CDF 9/7
+// The transpose of the forward operator: scaling (symmetric), then for each
+// pair in reverse order S_U^T (reads right / below) and T_P^T (reads left /
+// above).  With the symmetric boundary the transposed 1-D filters carry
+// position-dependent weights:
+//   (U^T s)[k] = b (wO(k) s[k] + wR(k) s[k+1]),  k over odd samples
+//   (P^T d)[m] = a (vL(m) d[m-1] + vO(m) d[m]),  m over even samples
+// wO(0) = 2; wR(nd-1) = 0 (n even) or 2 (n odd); vL(0) = 0; vO(ns-1) = 2
+// (n even) or 0 (n odd); 1 elsewhere, 0 for targets outside the signal.
+struct AxisW {
+    float uO, uR, pL, pO;
+};
+
+__device__ __forceinline__ AxisW axis_weights(int j, int n) {
+    const int ns = (n + 1) >> 1, nd = n >> 1;
+    AxisW w;
+    const bool od = (j >= 0) && (j < nd);   // odd sample j exists
+    const bool ev = (j >= 0) && (j < ns);   // even sample j exists
+    w.uO = od ? (j == 0 ? 2.f : 1.f) : 0.f;
+    w.uR = (od && j + 1 <= ns - 1) ? (((n & 1) && j == nd - 1) ? 2.f : 1.f) : 0.f;
+    w.pL = (ev && j >= 1) ? 1.f : 0.f;
+    w.pO = (ev && j <= nd - 1) ? ((!(n & 1) && j == ns - 1) ? 2.f : 1.f) : 0.f;
+    return w;
+}
+
+// S_U^T on row X (row index i) with the row below D: predict-shaped.
+__device__ __forceinline__ void adj_st(Row<float>& X, const Row<float>& D, float b, float bb,
+                                       const AxisW (&hw)[QL], const AxisW& vw) {
+    float r1[QL], r3[QL], dr1[QL];
+    right_of(X.c1, r1);
+    right_of(X.c3, r3);
+    right_of(D.c1, dr1);
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+        const float hc1 = hw[q].uO * X.c1[q] + hw[q].uR * r1[q];   // U^T c1 along the row
+        const float hd1 = hw[q].uO * D.c1[q] + hw[q].uR * dr1[q];  // same for the row below
+        const float t4 = vw.uO * hc1 + vw.uR * hd1;                 // U*^T U^T c1
+        const float v2 = vw.uO * X.c2[q] + vw.uR * D.c2[q];         // U*^T c2
+        const float h3 = hw[q].uO * X.c3[q] + hw[q].uR * r3[q];     // U^T c3
+        const float v1 = vw.uO * X.c1[q] + vw.uR * D.c1[q];         // U*^T c1
+        X.c4[q] = fmaf(bb, t4, fmaf(b, v2 + h3, X.c4[q]));
+        X.c2[q] = fmaf(b, hc1, X.c2[q]);
+        X.c3[q] = fmaf(b, v1, X.c3[q]);
+    }
+}
+
+// T_P^T on row X with the carry C of the row above: update-shaped.
+__device__ __forceinline__ void adj_tt(Row<float>& X, Carry3& C, float a, float aa, const AxisW (&hw)[QL],
+                                       const AxisW& vw) {
+    float l2[QL], l4[QL];
+    left_of(X.c2, l2);
+    left_of(X.c4, l4);
+    Carry3 n;
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+        n.c3[q] = X.c3[q];
+        n.c4[q] = X.c4[q];
+        n.l4[q] = l4[q];
+        const float h2 = hw[q].pL * l2[q] + hw[q].pO * X.c2[q];      // P^T c2
+        const float v3 = vw.pL * C.c3[q] + vw.pO * X.c3[q];          // P*^T c3
+        const float hu4 = hw[q].pL * C.l4[q] + hw[q].pO * C.c4[q];   // P^T c4, row above
+        const float hx4 = hw[q].pL * l4[q] + hw[q].pO * X.c4[q];     // P^T c4
+        const float t1 = vw.pL * hu4 + vw.pO * hx4;                  // P*^T P^T c4
+        const float v4 = vw.pL * C.c4[q] + vw.pO * X.c4[q];          // P*^T c4
+        X.c1[q] = fmaf(aa, t1, fmaf(a, h2 + v3, X.c1[q]));
+        X.c2[q] = fmaf(a, v4, X.c2[q]);
+        X.c3[q] = fmaf(a, hx4, X.c3[q]);
+    }
+    C = n;
+}
+
+struct Adj97 {
+    static constexpr int LAG = 2;
+    using CT = float;
+    Row<float> r1, r2;
+    Carry3 k0, k1;
+    AxisW hw[QL];  // horizontal weights of the lane's quads
+    int h;         // image height of this level
+    __device__ __forceinline__ void init() {
+        zero_row(r1);
+        zero_row(r2);
+        zero_carry(k0);
+        zero_carry(k1);
+    }
+    // `row` is the quad-row index of r0in
+    __device__ __forceinline__ Row<float> arrive(const Row<float>& r0in, int row) {
+        Row<float> r0 = r0in;
+        scale97(r0);
+        const AxisW v1 = axis_weights(row - 1, h), v2 = axis_weights(row - 2, h);
+        adj_st(r1, r0, C97::D, C97::DD, hw, v1);
+        adj_tt(r1, k0, C97::G, C97::GG, hw, v1);
+        adj_st(r2, r1, C97::B, C97::BB, hw, v2);
+        adj_tt(r2, k1, C97::A, C97::AA, hw, v2);
+        Row<float> out = r2;
+        r2 = r1;
+        r1 = r0;
+        return out;
+    }
+};
+
+// ====================================================== integer CDF 5/3
+// Reversible 5/3: d -= floor((s_l + s_r)/2), s += floor((d_l + d_r + 2)/4),
+// in the separable order T^H, T^V, S^H, S^V (arithmetic shifts are floor).
+
+// fused T_P = T_P^V T_P^H in one step: the neighbour below has its c2 taken
+// after T^H, recomputed here from its pre-step values (the analogue of PP*).
+__device__ __forceinline__ void int_ns_predict(Row<int>& X, const Row<int>& D) {
+    int r1[QL], r3[QL], dr1[QL];
+    right_of(X.c1, r1);
+    right_of(X.c3, r3);
+    right_of(D.c1, dr1);
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+        const int c2n = X.c2[q] - ((X.c1[q] + r1[q]) >> 1);
+        const int d2n = D.c2[q] - ((D.c1[q] + dr1[q]) >> 1);
+        const int c4a = X.c4[q] - ((X.c3[q] + r3[q]) >> 1);
+        X.c3[q] = X.c3[q] - ((X.c1[q] + D.c1[q]) >> 1);
+        X.c4[q] = c4a - ((c2n + d2n) >> 1);
+        X.c2[q] = c2n;
+    }
+}
+
+// fused S_U = S_U^V S_U^H; the carry holds the row above after its update.
+__device__ __forceinline__ void int_ns_update(Row<int>& X, Carry2<int>& C) {
+    int l2[QL], l4[QL];
+    left_of(X.c2, l2);
+    left_of(X.c4, l4);
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+        int c1 = X.c1[q] + ((l2[q] + X.c2[q] + 2) >> 2);
+        const int c3 = X.c3[q] + ((l4[q] + X.c4[q] + 2) >> 2);
+        c1 += (C.c3[q] + c3 + 2) >> 2;
+        const int c2 = X.c2[q] + ((C.c4[q] + X.c4[q] + 2) >> 2);
+        X.c1[q] = c1;
+        X.c2[q] = c2;
+        X.c3[q] = c3;
+        C.c3[q] = c3;
+        C.c4[q] = X.c4[q];
+    }
+}
+
+__device__ __forceinline__ void int_ns_update_inv(Row<int>& X, Carry2<int>& C) {
+    Carry2<int> n;
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+        n.c3[q] = X.c3[q];
+        n.c4[q] = X.c4[q];
+        X.c2[q] -= (C.c4[q] + X.c4[q] + 2) >> 2;
+        X.c1[q] -= (C.c3[q] + X.c3[q] + 2) >> 2;
+    }
+    int l2[QL], l4[QL];
+    left_of(X.c2, l2);
+    left_of(X.c4, l4);
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+        X.c1[q] -= (l2[q] + X.c2[q] + 2) >> 2;
+        X.c3[q] -= (l4[q] + X.c4[q] + 2) >> 2;
+    }
+    C = n;
+}
+
+__device__ __forceinline__ void int_ns_predict_inv(Row<int>& X, const Row<int>& D) {
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+        X.c4[q] += (X.c2[q] + D.c2[q]) >> 1;
+        X.c3[q] += (X.c1[q] + D.c1[q]) >> 1;
+    }
+    int r1[QL], r3[QL];
+    right_of(X.c1, r1);
+    right_of(X.c3, r3);
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+        X.c4[q] += (X.c3[q] + r3[q]) >> 1;
+        X.c2[q] += (X.c1[q] + r1[q]) >> 1;
+    }
+}
+
+__device__ __forceinline__ void int_sp_th(Row<int>& X, int sgn) {
+    int r1[QL], r3[QL];
+    right_of(X.c1, r1);
+    right_of(X.c3, r3);
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+        X.c2[q] -= sgn * ((X.c1[q] + r1[q]) >> 1);
+        X.c4[q] -= sgn * ((X.c3[q] + r3[q]) >> 1);
+    }
+}
+__device__ __forceinline__ void int_sp_tv(Row<int>& X, const Row<int>& D, int sgn) {
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+        X.c3[q] -= sgn * ((X.c1[q] + D.c1[q]) >> 1);
+        X.c4[q] -= sgn * ((X.c2[q] + D.c2[q]) >> 1);
+    }
+}
+__device__ __forceinline__ void int_sp_sh(Row<int>& X, int sgn) {
+    int l2[QL], l4[QL];
+    left_of(X.c2, l2);
+    left_of(X.c4, l4);
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+        X.c1[q] += sgn * ((l2[q] + X.c2[q] + 2) >> 2);
+        X.c3[q] += sgn * ((l4[q] + X.c4[q] + 2) >> 2);
+    }
+}
+__device__ __forceinline__ void int_sp_sv(Row<int>& X, Carry2<int>& C, int sgn) {
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+        X.c1[q] += sgn * ((C.c3[q] + X.c3[q] + 2) >> 2);
+        X.c2[q] += sgn * ((C.c4[q] + X.c4[q] + 2) >> 2);
+        C.c3[q] = X.c3[q];
+        C.c4[q] = X.c4[q];
+    }
+}
+
+template <int SCHEME>
+struct Fwd53 {
+    static constexpr int LAG = 1;
+    using CT = int;
+    Row<int> r1;
+    Carry2<int> k0;
+    __device__ __forceinline__ void init() {
+        zero_row(r1);
+        zero_carry(k0);
+    }
+    __device__ __forceinline__ Row<int> arrive(const Row<int>& r0in, int /*row*/) {
+        Row<int> r0 = r0in;
+        if (SCHEME == SCHEME_SEP) {
+            int_sp_th(r0, 1);
+            int_sp_tv(r1, r0, 1);
+            int_sp_sh(r1, 1);
+            int_sp_sv(r1, k0, 1);
+        } else {
+            int_ns_predict(r1, r0);
+            int_ns_update(r1, k0);
+        }
+        Row<int> out = r1;
+        r1 = r0;
+        return out;
+    }
+};
+
+template <int SCHEME>
+struct Inv53 {
+    static constexpr int LAG = 1;
+    using CT = int;
+    Row<int> r1;
+    Carry2<int> k0;
+    __device__ __forceinline__ void init() {
+        zero_row(r1);
+        zero_carry(k0);
+    }
+    __device__ __forceinline__ Row<int> arrive(const Row<int>& r0in, int /*row*/) {
+        Row<int> r0 = r0in;
+        if (SCHEME == SCHEME_SEP) {
+            int_sp_sv(r0, k0, -1);
+            int_sp_sh(r0, -1);
+            int_sp_tv(r1, r0, -1);
+            int_sp_th(r1, -1);
+        } else {
+            int_ns_update_inv(r0, k0);
+            int_ns_predict_inv(r1, r0);
+        }
+        Row<int> out = r1;
+        r1 = r0;
+        return out;
+    }
+};
+
+}  // namespace dwt2

@@ -1,0 +1,145 @@
+"""PyTorch-facing helpers over the libdwt2 C ABI.
+
+PyTorch provides device memory and streams only; every transform step runs in
+the CUDA kernels of libdwt2.so (see ``abi``).  A ``Plan`` wraps one C plan and
+owns a workspace tensor; ``DWT2Function`` exposes the forward transform to
+autograd with the hand-written adjoint kernel as its backward.
+"""
+from __future__ import annotations
+
+from typing import List, Optional, Sequence, Tuple
+
+import torch
+
+from . import abi
+
+WAVELETS = {"cdf97": abi.DWT2_CDF97, "cdf53": abi.DWT2_CDF53_INT}
+SCHEMES = {"nonsep": abi.DWT2_NONSEP, "reduced": abi.DWT2_NONSEP_REDUCED, "sep": abi.DWT2_SEP_LIFTING}
+DTYPES = {torch.float32: abi.DWT2_F32, torch.float16: abi.DWT2_F16, torch.bfloat16: abi.DWT2_BF16,
+          torch.int32: abi.DWT2_I32}
+
+
+def _stream_handle(stream: Optional[torch.cuda.Stream]) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def round_up(v: int, m: int) -> int:
+    return (v + m - 1) // m * m
+
+
+class Plan:
+    """One transform plan (wavelet, levels, scheme, dtypes, image layout).
+
+    ``images`` is a list of (offset_elems, h, w, pitch_elems); for a single
+    image use ``Plan.single(h, w, ...)``.  Buffers passed to the transform
+    calls are flat or 2-D CUDA tensors addressed by those offsets and pitches.
+    """
+
+    def __init__(self, images: Sequence[Tuple[int, int, int, int]], levels: int, wavelet: str = "cdf97",
+                 scheme: str = "nonsep", coef_dtype: torch.dtype = torch.float32, flags: int = 0,
+                 device: Optional[torch.device] = None):
+        self.images = [tuple(int(v) for v in d) for d in images]
+        self.levels = int(levels)
+        self.wavelet = wavelet
+        self.scheme = scheme
+        self.in_dtype = torch.float32 if wavelet == "cdf97" else torch.int32
+        self.coef_dtype = coef_dtype
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        with torch.cuda.device(self.device):
+            self.handle = abi.dwt2_plan(WAVELETS[wavelet], self.levels, abi.DWT2_SYMMETRIC,
+                                        DTYPES[self.in_dtype], DTYPES[coef_dtype], SCHEMES[scheme],
+                                        self.images, flags)
+        self.ws_bytes = abi.dwt2_workspace_bytes(self.handle)
+        self._ws: Optional[torch.Tensor] = None
+        self.n_elems = max(o + h * p for (o, h, w, p) in self.images)
+
+    @classmethod
+    def single(cls, h: int, w: int, levels: int, pitch: Optional[int] = None, **kw) -> "Plan":
+        return cls([(0, h, w, pitch if pitch is not None else w)], levels, **kw)
+
+    @property
+    def workspace(self) -> torch.Tensor:
+        if self._ws is None:
+            self._ws = torch.empty(max(self.ws_bytes, 256), dtype=torch.uint8, device=self.device)
+        return self._ws
+
+    def _check(self, t: torch.Tensor, dtype: torch.dtype, name: str):
+        if not t.is_cuda or t.dtype != dtype:
+            raise TypeError(f"{name}: expected a CUDA {dtype} tensor, got {t.dtype} on {t.device}")
+        if t.storage_offset() < 0 or t.untyped_storage().nbytes() < (t.storage_offset() + self.n_elems) * t.element_size():
+            raise ValueError(f"{name}: buffer smaller than the plan's layout")
+
+    def forward(self, x: torch.Tensor, out: Optional[torch.Tensor] = None,
+                stream: Optional[torch.cuda.Stream] = None) -> torch.Tensor:
+        self._check(x, self.in_dtype, "x")
+        if out is None:
+            out = torch.empty_like(x, dtype=self.coef_dtype)
+        self._check(out, self.coef_dtype, "out")
+        abi.dwt2_forward(self.handle, x.data_ptr(), out.data_ptr(), self.workspace.data_ptr(),
+                         _stream_handle(stream))
+        return out
+
+    def inverse(self, c: torch.Tensor, out: Optional[torch.Tensor] = None,
+                stream: Optional[torch.cuda.Stream] = None) -> torch.Tensor:
+        self._check(c, self.coef_dtype, "coef")
+        if out is None:
+            out = torch.empty_like(c, dtype=self.in_dtype)
+        self._check(out, self.in_dtype, "out")
+        abi.dwt2_inverse(self.handle, c.data_ptr(), out.data_ptr(), self.workspace.data_ptr(),
+                         _stream_handle(stream))
+        return out
+
+    def adjoint(self, g: torch.Tensor, out: Optional[torch.Tensor] = None,
+                stream: Optional[torch.cuda.Stream] = None) -> torch.Tensor:
+        self._check(g, torch.float32, "coef_grad")
+        if out is None:
+            out = torch.empty_like(g)
+        self._check(out, torch.float32, "out")
+        abi.dwt2_adjoint(self.handle, g.data_ptr(), out.data_ptr(), self.workspace.data_ptr(),
+                         _stream_handle(stream))
+        return out
+
+    def status(self, stream: Optional[torch.cuda.Stream] = None) -> int:
+        return abi.dwt2_status(self.handle, _stream_handle(stream))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            abi.dwt2_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class DWT2Function(torch.autograd.Function):
+    """coef = W(x) with backward dL/dx = W^T(dL/dcoef) from the adjoint kernel."""
+
+    @staticmethod
+    def forward(ctx, x: torch.Tensor, plan: Plan) -> torch.Tensor:
+        ctx.plan = plan
+        return plan.forward(x.contiguous() if x.stride(-1) != 1 else x)
+
+    @staticmethod
+    def backward(ctx, g: torch.Tensor):
+        return ctx.plan.adjoint(g.contiguous()), None
+
+
+def dwt2(x: torch.Tensor, plan: Plan) -> torch.Tensor:
+    return DWT2Function.apply(x, plan)
+
+
+def band_slices(h: int, w: int, levels: int) -> List[Tuple[int, str, slice, slice]]:
+    """Mallat band rectangles (level, name, rows, cols); level 1 is the finest."""
+    out = []
+    for lev in range(1, levels + 1):
+        hl, wl = (h + 1) // 2, (w + 1) // 2
+        out.append((lev, "HL", slice(0, hl), slice(wl, w)))
+        out.append((lev, "LH", slice(hl, h), slice(0, wl)))
+        out.append((lev, "HH", slice(hl, h), slice(wl, w)))
+        h, w = hl, wl
+    out.append((levels, "LL", slice(0, h), slice(0, w)))
+    return out

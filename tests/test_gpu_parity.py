@@ -1,0 +1,173 @@
+"""GPU kernels vs the oracle, element by element, through the C ABI.
+
+Sizes span several strips (120 pixels) and segments plus ragged tails, odd
+sides and the smallest legal images; every output buffer carries a guard band
+(padding columns and rows) that must stay untouched.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1704_08657_gb300 import synth
+from paper_1704_08657_gb300.dwt import Plan, round_up
+from tests.util import assert_fp32_close, assert_lowp_close
+
+pytestmark = pytest.mark.gpu
+
+SENT = -12345.0
+SCHEMES97 = ["nonsep", "reduced", "sep"]
+
+
+def _levels_max(h, w, cap):
+    lv = 0
+    while lv < cap and h >= 2 and w >= 2:
+        lv += 1
+        h, w = (h + 1) // 2, (w + 1) // 2
+    return lv
+
+
+def _padded(x: np.ndarray, dtype, guard_rows=3):
+    """Device buffer with pitch rounded to 4 and guard rows, filled with SENT."""
+    h, w = x.shape
+    pitch = round_up(w + 1, 4)  # at least one padding column
+    buf = torch.full((h + guard_rows, pitch), SENT, dtype=dtype, device="cuda")
+    buf[:h, :w] = torch.from_numpy(np.ascontiguousarray(x)).to(dtype)
+    return buf, pitch
+
+
+def _guard_ok(buf: torch.Tensor, h, w):
+    b = buf.float().cpu().numpy()
+    return bool(np.all(b[:h, w:] == np.float32(SENT)) and np.all(b[h:, :] == np.float32(SENT)))
+
+
+def gpu_forward(x, levels, scheme="nonsep", coef_dtype=torch.float32, wavelet="cdf97"):
+    h, w = x.shape
+    in_dt = torch.float32 if wavelet == "cdf97" else torch.int32
+    xin, pitch = _padded(x, in_dt)
+    out = torch.full_like(xin, SENT, dtype=coef_dtype)
+    plan = Plan.single(h, w, levels, pitch=pitch, wavelet=wavelet, scheme=scheme, coef_dtype=coef_dtype)
+    plan.forward(xin, out)
+    assert plan.status() == 0
+    torch.cuda.synchronize()
+    assert _guard_ok(out, h, w), "forward wrote outside the coefficient region"
+    return out[:h, :w].float().cpu().numpy() if coef_dtype != torch.int32 else out[:h, :w].cpu().numpy()
+
+
+def gpu_inverse(c, levels, scheme="nonsep", coef_dtype=torch.float32, wavelet="cdf97"):
+    h, w = c.shape
+    out_dt = torch.float32 if wavelet == "cdf97" else torch.int32
+    cin, pitch = _padded(c, coef_dtype)
+    out = torch.full_like(cin, SENT, dtype=out_dt)
+    plan = Plan.single(h, w, levels, pitch=pitch, wavelet=wavelet, scheme=scheme, coef_dtype=coef_dtype)
+    plan.inverse(cin, out)
+    assert plan.status() == 0
+    torch.cuda.synchronize()
+    assert _guard_ok(out, h, w), "inverse wrote outside the image"
+    return out[:h, :w].cpu().numpy()
+
+
+def gpu_adjoint(g, levels):
+    h, w = g.shape
+    gin, pitch = _padded(g, torch.float32)
+    out = torch.full_like(gin, SENT)
+    plan = Plan.single(h, w, levels, pitch=pitch)
+    plan.adjoint(gin, out)
+    assert plan.status() == 0
+    torch.cuda.synchronize()
+    assert _guard_ok(out, h, w), "adjoint wrote outside the image"
+    return out[:h, :w].cpu().numpy()
+
+
+SHAPES = [(512, 512), (33, 65), (7, 5), (2, 2), (3, 3), (2, 9), (9, 2), (130, 250), (257, 129),
+          (64, 1000), (1000, 64), (121, 241), (244, 124)]
+
+
+@pytest.mark.parametrize("scheme", SCHEMES97)
+@pytest.mark.parametrize("h,w", SHAPES)
+def test_forward97_fp32(h, w, scheme):
+    x = synth.uniform(h, w, seed=1 + h * 7 + w)
+    for levels in sorted({1, _levels_max(h, w, 5)}):
+        if levels == 0:
+            continue
+        ref = oracle.forward97(x.astype(np.float64), levels)
+        got = gpu_forward(x, levels, scheme)
+        assert_fp32_close(got, ref, levels, 255.0, f"{scheme} {h}x{w} L{levels}")
+
+
+@pytest.mark.parametrize("scheme", SCHEMES97)
+@pytest.mark.parametrize("h,w", [(512, 512), (33, 65), (7, 5), (2, 2), (130, 250), (257, 129)])
+def test_inverse97_fp32(h, w, scheme):
+    levels = _levels_max(h, w, 4)
+    x = synth.uniform(h, w, seed=11)
+    c = oracle.forward97(x.astype(np.float64), levels)
+    got = gpu_inverse(c.astype(np.float32), levels, scheme)
+    ref = oracle.inverse97(c.astype(np.float32).astype(np.float64), levels)
+    assert np.abs(got - ref).max() <= 1e-3 * 255.0 / 255.0 * 2, f"max err {np.abs(got - ref).max()}"
+    # and forward then inverse on the GPU reconstructs the image
+    rec = gpu_inverse(gpu_forward(x, levels, scheme), levels, scheme)
+    assert np.abs(rec - x).max() <= 2e-3
+
+
+@pytest.mark.parametrize("scheme", ["nonsep", "sep"])
+@pytest.mark.parametrize("h,w", [(512, 512), (33, 65), (7, 5), (2, 2), (3, 2), (130, 250), (257, 129), (64, 1000)])
+def test_int53_bit_exact(h, w, scheme):
+    levels = _levels_max(h, w, 5)
+    x = synth.to_int(synth.gradient(h, w, seed=2)) - 128
+    ref = oracle.forward53i(x.astype(np.int64), levels)
+    got = gpu_forward(x, levels, scheme, torch.int32, "cdf53")
+    assert np.array_equal(got.astype(np.int64), ref), f"{int((got != ref).sum())} coefficients differ"
+    back = gpu_inverse(ref.astype(np.int32), levels, scheme, torch.int32, "cdf53")
+    assert np.array_equal(back.astype(np.int64), x.astype(np.int64))
+
+
+@pytest.mark.parametrize("dtype,rel", [(torch.float16, 1e-3), (torch.bfloat16, 8e-3)])
+@pytest.mark.parametrize("h,w", [(512, 512), (130, 250)])
+def test_lowp_storage(h, w, dtype, rel):
+    levels = _levels_max(h, w, 5)
+    x = synth.noisy(h, w, seed=3)
+    ref = oracle.forward97(x.astype(np.float64), levels)
+    for scheme in SCHEMES97:
+        got = gpu_forward(x, levels, scheme, dtype)
+        assert_lowp_close(got, ref, levels, rel, f"{dtype} {scheme}")
+    # the inverse reads the low-precision coefficients
+    c = ref.astype(np.float32)
+    got = gpu_inverse(torch.from_numpy(c).to(dtype).float().numpy(), levels, "nonsep", dtype)
+    ref_i = oracle.inverse97(torch.from_numpy(c).to(dtype).double().numpy(), levels)
+    assert np.abs(got - ref_i).max() <= 2e-3 * np.abs(ref_i).max() / 255.0 * 2
+
+
+@pytest.mark.parametrize("h,w", [(512, 512), (33, 65), (7, 5), (2, 2), (3, 3), (130, 250), (257, 129)])
+def test_adjoint_matches_oracle(h, w):
+    levels = _levels_max(h, w, 4)
+    rng = np.random.default_rng(h * 1000 + w)
+    g = rng.standard_normal((h, w)).astype(np.float32)
+    ref = oracle.adjoint97(g.astype(np.float64), levels)
+    got = gpu_adjoint(g, levels)
+    assert np.abs(got - ref).max() <= 1e-5 * max(1.0, np.abs(ref).max()) * 2 ** levels
+
+
+def test_schemes_agree_with_each_other():
+    x = synth.gradient(300, 260, seed=2)
+    outs = [gpu_forward(x, 3, s) for s in SCHEMES97]
+    for o in outs[1:]:
+        assert np.abs(o - outs[0]).max() <= 2e-3
+
+
+def test_plan_errors_on_gpu():
+    from paper_1704_08657_gb300 import abi
+    with pytest.raises(abi.Dwt2Error) as e:
+        Plan.single(64, 64, 1, pitch=66)
+    assert e.value.code == abi.DWT2_ERR_MISALIGNED
+    with pytest.raises(abi.Dwt2Error) as e:
+        Plan.single(64, 64, 7)
+    assert e.value.code == abi.DWT2_ERR_LEVELS_TOO_DEEP
+    with pytest.raises(abi.Dwt2Error) as e:
+        Plan.single(64, 64, 1, wavelet="cdf53", scheme="reduced", coef_dtype=torch.int32)
+    assert e.value.code == abi.DWT2_ERR_UNSUPPORTED
+    # misaligned input pointer is rejected before any launch
+    p = Plan.single(64, 64, 1)
+    x = torch.zeros(64 * 64 + 1, device="cuda")
+    rc = abi.raw_call("dwt2_forward", p.handle, x.data_ptr() + 4, torch.empty(64 * 64, device="cuda").data_ptr(),
+                      p.workspace.data_ptr(), 0)
+    assert rc == abi.DWT2_ERR_MISALIGNED
