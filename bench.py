@@ -436,7 +436,7 @@ def run_ours(a):
             del out, xi
         line["compare"] = comp
 
-    if rank == 0 and not a.no_cpu:
+    if rank == 0 and world == 1 and not a.no_cpu:
         per_s, runs, secs, threads = time_oracle(4096, a.levels, budget_s=10.0)
         line["cpu_baseline"] = {"value": per_s / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
                                 "sample": f"oracle (C, FP64 separable lifting, OpenMP) on a 4096x4096 image "

@@ -38,7 +38,8 @@ def _padded(x: np.ndarray, dtype, guard_rows=3):
 
 def _guard_ok(buf: torch.Tensor, h, w):
     b = buf.float().cpu().numpy()
-    return bool(np.all(b[:h, w:] == np.float32(SENT)) and np.all(b[h:, :] == np.float32(SENT)))
+    sent = float(torch.tensor(SENT, dtype=buf.dtype))  # the sentinel as stored in this dtype
+    return bool(np.all(b[:h, w:] == sent) and np.all(b[h:, :] == sent))
 
 
 def gpu_forward(x, levels, scheme="nonsep", coef_dtype=torch.float32, wavelet="cdf97"):
