@@ -68,6 +68,7 @@ enum dwt2_boundary { DWT2_SYMMETRIC = 0 };
 #define DWT2_ERR_CUDA (-5)            /* a CUDA runtime call failed            */
 #define DWT2_ERR_TIMEOUT (-6)         /* a bounded device wait expired         */
 #define DWT2_ERR_DEVICE_CHECK (-7)    /* a device-side bounds check tripped    */
+#define DWT2_ERR_TOO_LARGE (-8)       /* beyond dwt2_forward_noalloc's scratch */
 
 /* plan flags */
 #define DWT2_FLAG_PERSISTENT 0x1u /* batch: one persistent launch for all levels */
@@ -150,6 +151,29 @@ int dwt2_profile(dwt2_plan_t plan, int enable);
  * calls in the ring to ms[0 .. n-1]; n <= the plan's levels.
  * DWT2_ERR_INVALID_ARG if nothing was recorded. */
 int dwt2_profile_read(dwt2_plan_t plan, float* ms, int n);
+
+/*
+ * dwt2_forward_noalloc -- the forward pyramid of one image, allocating no
+ * device memory (the paper has no counterpart: this is a service for callers
+ * that cannot allocate when they transform, e.g. code running during a CUDA
+ * graph capture that forbids cudaMalloc, real-time pipelines that allow no
+ * allocation after start-up, or plug-ins whose host owns all device memory).
+ *   wavelet, levels, scheme, coef_dtype  as for dwt2_plan (in_dtype follows
+ *              the wavelet: F32 for CDF 9/7, I32 for CDF 5/3).
+ *   h, w, pitch_elems  the image; pitch a multiple of 4 elements.
+ *   in         device pointer to the image, 16-byte aligned, read only.
+ *   coef       device pointer to the coefficients (Mallat layout, same pitch).
+ *   stream     a cudaStream_t (NULL for the legacy default stream).
+ * The intermediate low-low bands live in a static 32 MiB device array inside
+ * the library (held by every GPU that loads it until exit): enough for a
+ * 4096 x 4096 image; larger requests return DWT2_ERR_TOO_LARGE.  The first
+ * call on a device looks up that array's device address; make it before any
+ * stream capture.  All calls share the array, so calls that overlap on the
+ * GPU race; order them on one stream.  There is no status word: a device-side
+ * timeout is not reported by this entry point.  Same results as dwt2_forward.
+ */
+int dwt2_forward_noalloc(int wavelet, int levels, int scheme, int coef_dtype, int h, int w,
+                         int64_t pitch_elems, const void* in, void* coef, void* stream);
 
 /* dwt2_destroy -- free the plan (NULL is accepted). */
 void dwt2_destroy(dwt2_plan_t plan);

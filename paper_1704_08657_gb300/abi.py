@@ -24,11 +24,13 @@ DWT2_ERR_MISALIGNED = -4
 DWT2_ERR_CUDA = -5
 DWT2_ERR_TIMEOUT = -6
 DWT2_ERR_DEVICE_CHECK = -7
+DWT2_ERR_TOO_LARGE = -8
 DWT2_FLAG_PERSISTENT = 0x1
 
 # the functions the header declares (checked by the CPU test suite)
 EXPORTS = ("dwt2_plan", "dwt2_workspace_bytes", "dwt2_forward", "dwt2_inverse", "dwt2_adjoint",
-           "dwt2_status", "dwt2_profile", "dwt2_profile_read", "dwt2_destroy", "dwt2_strerror")
+           "dwt2_status", "dwt2_profile", "dwt2_profile_read", "dwt2_forward_noalloc", "dwt2_destroy",
+           "dwt2_strerror")
 
 
 class dwt2_image_desc(ctypes.Structure):
@@ -70,6 +72,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.dwt2_profile.restype = ctypes.c_int
     lib.dwt2_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int]
     lib.dwt2_profile_read.restype = ctypes.c_int
+    lib.dwt2_forward_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int, ctypes.c_int64, vp, vp, vp]
+    lib.dwt2_forward_noalloc.restype = ctypes.c_int
     lib.dwt2_destroy.argtypes = [vp]
     lib.dwt2_destroy.restype = None
     lib.dwt2_strerror.argtypes = [ctypes.c_int]
@@ -137,6 +142,15 @@ def dwt2_profile_read(plan: int, n: int):
     if rc != DWT2_OK:
         raise Dwt2Error(rc, "dwt2_profile_read")
     return [float(arr[i]) for i in range(n)]
+
+
+def dwt2_forward_noalloc(wavelet: int, levels: int, scheme: int, coef_dtype: int, h: int, w: int,
+                         pitch_elems: int, in_ptr: int, coef_ptr: int, stream: int = 0) -> int:
+    """Forward pyramid of one image without any device allocation (the
+    intermediate bands use the library's static scratch); returns the code."""
+    return int(load().dwt2_forward_noalloc(int(wavelet), int(levels), int(scheme), int(coef_dtype), int(h),
+                                           int(w), int(pitch_elems), ctypes.c_void_p(in_ptr),
+                                           ctypes.c_void_p(coef_ptr), ctypes.c_void_p(stream)))
 
 
 def dwt2_destroy(plan: int) -> None:

@@ -149,6 +149,8 @@ const char* dwt2_strerror(int code) {
         case DWT2_ERR_CUDA: return "CUDA runtime error";
         case DWT2_ERR_TIMEOUT: return "a bounded device wait expired";
         case DWT2_ERR_DEVICE_CHECK: return "a device-side bounds check tripped";
+        case DWT2_ERR_TOO_LARGE:
+            return "image too large for dwt2_forward_noalloc (its static scratch holds 32 MiB of low-low bands)";
         default: return "unknown error";
     }
 }

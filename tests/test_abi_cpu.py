@@ -31,7 +31,7 @@ def test_exports_every_declared_function(lib):
 
 
 def test_strerror_names_every_code(lib):
-    for code in (0, -1, -2, -3, -4, -5, -6, -7):
+    for code in (0, -1, -2, -3, -4, -5, -6, -7, -8):
         assert abi.dwt2_strerror(code) and abi.dwt2_strerror(code) != "unknown error"
     assert abi.dwt2_strerror(-99) == "unknown error"
 
