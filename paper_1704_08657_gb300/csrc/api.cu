@@ -17,8 +17,6 @@ using namespace dwt2;
 
 namespace {
 
-constexpr int OUT_Q_H = 60;  // output quads per strip (kernels.cuh)
-
 struct LevelGeom {
     int h, w, hq, wq, hh, wh;
 };
@@ -50,22 +48,47 @@ struct Decomp {
     int n_strips, seg_rows, n_segs, n_units;
 };
 
-Decomp decompose(const LevelGeom& g, int sm_count, int warps_per_sm, int seg_override) {
+// Work decomposition of one level into units of seg_rows quad rows of one
+// strip, dealt round-robin in segment-major order so that the warps at work
+// at any moment cover one compact band of image rows (DRAM page and TLB
+// locality; contiguous per-warp ranges that spread the warps over the whole
+// image measured ~2x slower).  The segment height is chosen to minimise
+// rounds x (rows + 4 rows of warm-up), where a round is one unit for every
+// resident warp, over heights up to SEG_MAX so that the band stays small
+// (heights of 32-56 rows measured best on 16384^2; 64-256 were 5-30 % slower).
+// seg_override > 0 forces a height; balanced_env selects contiguous ranges.
+constexpr int SEG_MIN = 8, SEG_MAX = 48, MIN_ROWS = 16;
+
+Decomp decompose(const LevelGeom& g, int out_q, int sm_count, int blocks_per_sm, int nw, int seg_override,
+                 int balanced_env, int* grid, int* balanced) {
     Decomp d;
-    d.n_strips = (g.wq + OUT_Q_H - 1) / OUT_Q_H;
-    int rows;
-    if (seg_override > 0) {
-        rows = seg_override;
-    } else {
-        // about three waves of warps: long segments amortise the 4-row warm-up
-        const int64_t target = int64_t(sm_count) * warps_per_sm * 3;
-        const int64_t total = int64_t(g.hq) * d.n_strips;
-        rows = int((total + target - 1) / target);
-        rows = std::min(std::max(rows, 8), 512);
+    d.n_strips = (g.wq + out_q - 1) / out_q;
+    const int64_t total = int64_t(g.hq) * d.n_strips;
+    const int64_t max_warps = int64_t(sm_count) * std::max(blocks_per_sm, 1) * nw;
+    if (balanced_env) {
+        const int64_t warps = std::max<int64_t>(1, std::min(max_warps, (total + MIN_ROWS - 1) / MIN_ROWS));
+        *grid = int((warps + nw - 1) / nw);
+        *balanced = 1;
+        d.seg_rows = g.hq;
+        d.n_segs = 1;
+        d.n_units = d.n_strips;
+        return d;
     }
-    d.seg_rows = std::min(rows, g.hq);
+    int best = std::min(seg_override > 0 ? seg_override : SEG_MAX, g.hq);
+    if (seg_override <= 0) {
+        int64_t best_cost = INT64_MAX;
+        for (int seg = std::min(SEG_MIN, g.hq); seg <= std::min(SEG_MAX, g.hq); ++seg) {
+            const int64_t units = int64_t((g.hq + seg - 1) / seg) * d.n_strips;
+            const int64_t rounds = (units + max_warps - 1) / max_warps;
+            const int64_t cost = rounds * (seg + 4);
+            if (cost < best_cost) best_cost = cost, best = seg;
+        }
+    }
+    d.seg_rows = best;
     d.n_segs = (g.hq + d.seg_rows - 1) / d.seg_rows;
     d.n_units = d.n_segs * d.n_strips;
+    *grid = (d.n_units + nw - 1) / nw;
+    *balanced = 0;
     return d;
 }
 
@@ -89,13 +112,14 @@ EncodeTiledFn get_encode() {
 }
 
 // 2-D map over a w x h array of 4-byte elements with row pitch `pitch`
-// elements; box = 128 x box_rows.
-int encode_map(CUtensorMap* m, const void* base, int w, int h, int64_t pitch, int box_rows, bool is_int) {
+// elements; box = box_w x box_rows.
+int encode_map(CUtensorMap* m, const void* base, int w, int h, int64_t pitch, int box_w, int box_rows,
+               bool is_int) {
     EncodeTiledFn enc = get_encode();
     if (!enc) return DWT2_ERR_CUDA;
     cuuint64_t dims[2] = {cuuint64_t(w), cuuint64_t(h)};
     cuuint64_t strides[1] = {cuuint64_t(pitch) * 4};
-    cuuint32_t box[2] = {128u, cuuint32_t(box_rows)};
+    cuuint32_t box[2] = {cuuint32_t(box_w), cuuint32_t(box_rows)};
     cuuint32_t estr[2] = {1u, 1u};
     CUresult r = enc(m, is_int ? CU_TENSOR_MAP_DATA_TYPE_INT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
                      const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -120,7 +144,8 @@ struct dwt2_plan_s {
     unsigned* d_status;
     int device, sm_count;
     FwdCfg cfg;
-    int seg_override;
+    int fwd_bps, inv_bps;  // resident blocks per SM of the forward / inverse kernels
+    int seg_override, balanced_env;
     uint64_t timeout_ns;
     // profiling: a ring of PROF_RING calls, one event pair per level each
     std::vector<cudaEvent_t> ev0, ev1;  // [slot * levels + level]
@@ -214,9 +239,12 @@ int dwt2_plan(dwt2_plan_t* out, int wavelet, int levels, int boundary, int in_dt
     p->prof_calls = 0;
     p->timeout_ns = uint64_t(env_int("DWT2_TIMEOUT_MS", 2000)) * 1000000ull;
     p->seg_override = env_int("DWT2_SEG_ROWS", 0);
+    p->balanced_env = env_int("DWT2_BALANCED", 0);
     int ci = env_int("DWT2_FWD_CFG", 0);
     if (ci < 0 || ci >= N_FWD_CFGS) ci = 0;
     p->cfg = FWD_CFGS[ci];
+    p->fwd_bps = forward_blocks_per_sm(wavelet, scheme, coef_dtype, p->cfg);
+    p->inv_bps = inverse_blocks_per_sm(wavelet, scheme, coef_dtype, false);
     if (cudaGetDevice(&p->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess ||
         cudaMalloc(&p->d_status, sizeof(unsigned)) != cudaSuccess ||
@@ -295,7 +323,6 @@ int dwt2_forward(dwt2_plan_t p, const void* in, void* coef, void* workspace, voi
     if (!aligned(coef, csz)) return DWT2_ERR_MISALIGNED;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const bool is_int = p->wavelet == DWT2_CDF53_INT;
-    const int warps_per_sm = 24;
     for (int l = 0; l < p->levels; ++l) {
         prof_mark(p, l, true, s);
         for (const ImagePlan& ip : p->imgs) {
@@ -307,13 +334,17 @@ int dwt2_forward(dwt2_plan_t p, const void* in, void* coef, void* workspace, voi
                                        : static_cast<const void*>(wsb + ip.ws_off[(l - 1) % 2]);
             const int64_t src_pitch = (l == 0) ? ip.d.pitch_elems : round4(ip.lv[l - 1].wq);
             CUtensorMap box, row;
-            int rc = encode_map(&box, src, g.w, g.h, src_pitch, 2 * p->cfg.qr, is_int);
-            if (rc == DWT2_OK) rc = encode_map(&row, src, g.w, g.h, src_pitch, 1, is_int);
+            const int bw = fwd_strip_px(p->cfg);
+            int rc = encode_map(&box, src, g.w, g.h, src_pitch, bw, 2 * p->cfg.qr, is_int);
+            if (rc == DWT2_OK) rc = encode_map(&row, src, g.w, g.h, src_pitch, bw, 1, is_int);
             if (rc != DWT2_OK) return rc;
             FwdParams fp;
             fp.h = g.h, fp.w = g.w, fp.hq = g.hq, fp.wq = g.wq, fp.hh = g.hh, fp.wh = g.wh;
-            const Decomp dc = decompose(g, p->sm_count, warps_per_sm, p->seg_override);
+            int grid = 0, balanced = 0;
+            const Decomp dc = decompose(g, fwd_out_quads(p->cfg), p->sm_count, p->fwd_bps, p->cfg.nw,
+                                        p->seg_override, p->balanced_env, &grid, &balanced);
             fp.n_strips = dc.n_strips, fp.seg_rows = dc.seg_rows, fp.n_segs = dc.n_segs, fp.n_units = dc.n_units;
+            fp.balanced = balanced;
             fp.coef = coef_img;
             fp.coef_pitch = ip.d.pitch_elems;
             const bool last = (l == p->levels - 1);
@@ -333,7 +364,6 @@ int dwt2_forward(dwt2_plan_t p, const void* in, void* coef, void* workspace, voi
             fp.vec_ll = last ? coef_vec : 1;
             fp.status = p->d_status;
             fp.timeout_ns = p->timeout_ns;
-            const int grid = (dc.n_units + p->cfg.nw - 1) / p->cfg.nw;
             int e;
             switch (p->coef_dtype) {
                 case DWT2_F32: e = launch_forward_f32(p->wavelet, p->scheme, box, row, fp, grid, p->cfg, s); break;
@@ -358,7 +388,7 @@ static int run_inverse_like(dwt2_plan_t p, const void* coef, void* out, void* wo
     const size_t csz = adj ? 4 : dtype_size(p->coef_dtype);
     if (!aligned(coef, csz) || !aligned(out, 4)) return DWT2_ERR_MISALIGNED;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const int warps_per_sm = 16;
+    const int inv_bps = adj ? inverse_blocks_per_sm(p->wavelet, p->scheme, p->coef_dtype, true) : p->inv_bps;
     for (int l = p->levels - 1; l >= 0; --l) {
         prof_mark(p, l, true, s);
         for (const ImagePlan& ip : p->imgs) {
@@ -368,8 +398,12 @@ static int run_inverse_like(dwt2_plan_t p, const void* coef, void* out, void* wo
             const LevelGeom& g = ip.lv[l];
             InvParams ipm;
             ipm.h = g.h, ipm.w = g.w, ipm.hq = g.hq, ipm.wq = g.wq, ipm.hh = g.hh, ipm.wh = g.wh;
-            const Decomp dc = decompose(g, p->sm_count, warps_per_sm, p->seg_override);
+            int grid = 0, balanced = 0;
+            const Decomp dc =
+                decompose(g, INV_OUT_Q, p->sm_count, inv_bps, INV_NW, p->seg_override, p->balanced_env, &grid,
+                          &balanced);
             ipm.n_strips = dc.n_strips, ipm.seg_rows = dc.seg_rows, ipm.n_segs = dc.n_segs, ipm.n_units = dc.n_units;
+            ipm.balanced = balanced;
             ipm.coef = coef_img;
             ipm.coef_pitch = ip.d.pitch_elems;
             const bool coarsest = (l == p->levels - 1);
@@ -396,7 +430,6 @@ static int run_inverse_like(dwt2_plan_t p, const void* coef, void* out, void* wo
             ipm.vec_ll = coarsest ? cvec : 1;
             ipm.vec_out = (ipm.out_pitch % 4 == 0) && aligned(ipm.out, 16);
             ipm.status = p->d_status;
-            const int grid = (dc.n_units + INV_NW - 1) / INV_NW;
             int e;
             if (adj) {
                 e = launch_adjoint_f32(ipm, grid, s);

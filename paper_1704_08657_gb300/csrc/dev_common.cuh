@@ -17,14 +17,11 @@ namespace dwt2 {
 constexpr unsigned FULL = 0xffffffffu;
 
 // ----------------------------------------------------------------- geometry
-// A warp owns a strip of 64 quads (128 pixels) per quad row: lane l holds the
-// quads 2l and 2l+1 of the strip.  Two quads on each side are halo: after the
-// lifting steps only quads 2..61 are exact, so a strip outputs 60 quads
-// (120 pixels) and neighbouring strips overlap by 8 pixels.
-constexpr int QL = 2;             // quads per lane
-constexpr int STRIP_PX = 128;     // pixels loaded per strip row
-constexpr int OUT_Q = 60;         // quads output per strip
-constexpr int HALO_Q = 2;         // halo quads on each side
+// A warp owns a strip of 32*QL quads (64*QL pixels) per quad row: lane l
+// holds the quads QL*l .. QL*l+QL-1 of the strip.  Two quads on each side are
+// halo: after the lifting steps only the inner 32*QL-4 quads are exact, so a
+// strip outputs that many quads and neighbouring strips overlap by 8 pixels.
+constexpr int HALO_Q = 2;  // halo quads on each side
 
 // whole-sample symmetric index fold for any integer k and n >= 2:
 // ... 2 1 | 0 1 2 ... n-1 | n-2 n-3 ...
@@ -101,35 +98,6 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, in
 
 __device__ __forceinline__ void tma_prefetch_desc(const CUtensorMap* tm) {
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tm)) : "memory");
-}
-
-// ----------------------------------------------------------- quad rows
-// The lane's two quads of one quad row: c1..c4 are (even row, even col),
-// (even row, odd col), (odd row, even col), (odd row, odd col).
-template <class CT>
-struct Row {
-    CT c1[QL], c2[QL], c3[QL], c4[QL];
-};
-
-template <class CT>
-__device__ __forceinline__ void zero_row(Row<CT>& r) {
-#pragma unroll
-    for (int q = 0; q < QL; ++q) r.c1[q] = r.c2[q] = r.c3[q] = r.c4[q] = CT(0);
-}
-
-// values of the quad to the right / left of each of the lane's quads
-template <class CT>
-__device__ __forceinline__ void right_of(const CT (&x)[QL], CT (&r)[QL]) {
-    const CT nxt = __shfl_down_sync(FULL, x[0], 1);
-    r[0] = x[1];
-    r[1] = nxt;
-}
-
-template <class CT>
-__device__ __forceinline__ void left_of(const CT (&x)[QL], CT (&l)[QL]) {
-    const CT prv = __shfl_up_sync(FULL, x[QL - 1], 1);
-    l[0] = prv;
-    l[1] = x[0];
 }
 
 // ---------------------------------------------------------- conversions

@@ -23,6 +23,7 @@ struct FwdParams {
     int h, w;                  // level input size in pixels (>= 2)
     int hq, wq, hh, wh;        // ceil and floor halves
     int n_strips, seg_rows, n_segs, n_units;
+    int balanced;              // 1: each warp takes one contiguous range of strip-major quad rows
     void* coef;                // top-left of the level's region, coefficient type
     int64_t coef_pitch;        // elements
     void* ll;                  // LL destination
@@ -38,6 +39,7 @@ struct InvParams {
     int h, w;
     int hq, wq, hh, wh;
     int n_strips, seg_rows, n_segs, n_units;
+    int balanced;
     const void* coef;          // detail bands (coefficient type), level origin
     int64_t coef_pitch;
     const void* ll;            // LL band: compute type when ll_is_ct
@@ -51,8 +53,12 @@ struct InvParams {
 
 // forward launch configuration
 struct FwdCfg {
-    int qr, nst, nw;  // quad rows per stage, stages per warp, warps per block
+    int ql, qr, nst, nw;  // quads per lane, quad rows per stage, stages per warp, warps per block
 };
+
+// geometry of a strip: 64*ql pixels loaded, 32*ql - 4 quads output
+inline int fwd_out_quads(const FwdCfg& c) { return 32 * c.ql - 4; }
+inline int fwd_strip_px(const FwdCfg& c) { return 64 * c.ql; }
 
 // kernel launchers, one translation unit per coefficient type; they return a
 // cudaError_t value
@@ -71,10 +77,16 @@ int launch_inverse_bf16(int wav, int scheme, const InvParams& p, int grid, cudaS
 int launch_inverse_i32(int wav, int scheme, const InvParams& p, int grid, cudaStream_t s);
 int launch_adjoint_f32(const InvParams& p, int grid, cudaStream_t s);
 
+// resident blocks per SM of a forward / inverse launch (0 on error)
+int forward_blocks_per_sm(int wav, int scheme, int coef_dtype, const FwdCfg& cfg);
+int inverse_blocks_per_sm(int wav, int scheme, int coef_dtype, bool adjoint);
+
 // the forward configurations compiled in (index 0 is the default)
-constexpr int N_FWD_CFGS = 3;
+constexpr int N_FWD_CFGS = 5;
 extern const FwdCfg FWD_CFGS[N_FWD_CFGS];
 size_t fwd_smem_bytes_of(const FwdCfg& c);
 constexpr int INV_NW = 4;
+constexpr int INV_QL = 2;
+constexpr int INV_OUT_Q = 32 * INV_QL - 4;
 
 }  // namespace dwt2

@@ -12,22 +12,52 @@ int launch_inverse_f32(int wav, int scheme, const InvParams& p, int grid, cudaSt
     return launch_inverse_t<float>(wav, scheme, p, grid, s);
 }
 
+int occupancy_forward_f32(int wav, int scheme, const FwdCfg& cfg) { return occupancy_forward_t<float>(wav, scheme, cfg); }
+int occupancy_inverse_f32(int scheme) { return occupancy_inverse_t<float>(scheme); }
+
 }  // namespace dwt2
 
 namespace dwt2 {
 
 int launch_adjoint_f32(const InvParams& p, int grid, cudaStream_t s) {
-    return launch_inv_one<Adj97, float, true>(p, grid, s);
+    return launch_inv_one<Adj97<INV_QL>, float, true>(p, grid, s);
+}
+
+int occupancy_forward_f16(int wav, int scheme, const FwdCfg& cfg);
+int occupancy_forward_bf16(int wav, int scheme, const FwdCfg& cfg);
+int occupancy_forward_i32(int wav, int scheme, const FwdCfg& cfg);
+int occupancy_inverse_f16(int scheme);
+int occupancy_inverse_bf16(int scheme);
+int occupancy_inverse_i32(int scheme);
+
+int forward_blocks_per_sm(int wav, int scheme, int coef_dtype, const FwdCfg& cfg) {
+    switch (coef_dtype) {
+        case DT_F32: return occupancy_forward_f32(wav, scheme, cfg);
+        case DT_F16: return occupancy_forward_f16(wav, scheme, cfg);
+        case DT_BF16: return occupancy_forward_bf16(wav, scheme, cfg);
+        default: return occupancy_forward_i32(wav, scheme, cfg);
+    }
+}
+
+int inverse_blocks_per_sm(int wav, int scheme, int coef_dtype, bool adjoint) {
+    (void)wav;
+    if (adjoint) return occupancy_inv_one<Adj97<INV_QL>, float, true>();
+    switch (coef_dtype) {
+        case DT_F32: return occupancy_inverse_f32(scheme);
+        case DT_F16: return occupancy_inverse_f16(scheme);
+        case DT_BF16: return occupancy_inverse_bf16(scheme);
+        default: return occupancy_inverse_i32(scheme);
+    }
 }
 
 const FwdCfg FWD_CFGS[N_FWD_CFGS] = {
-#define DWT2_X(I_, QR_, NST_, NW_) {QR_, NST_, NW_},
+#define DWT2_X(I_, QL_, QR_, NST_, NW_) {QL_, QR_, NST_, NW_},
     DWT2_FWD_CFG_LIST(DWT2_X)
 #undef DWT2_X
 };
 
 size_t fwd_smem_bytes_of(const FwdCfg& c) {
-    return size_t(c.nw) * c.nst * (2 * c.qr * STRIP_PX * 4) + size_t(c.nw) * c.nst * 8;
+    return size_t(c.nw) * c.nst * (2 * c.qr * 64 * c.ql * 4) + size_t(c.nw) * c.nst * 8;
 }
 
 }  // namespace dwt2

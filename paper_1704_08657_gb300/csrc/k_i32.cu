@@ -12,4 +12,7 @@ int launch_inverse_i32(int wav, int scheme, const InvParams& p, int grid, cudaSt
     return launch_inverse_t<int>(wav, scheme, p, grid, s);
 }
 
+int occupancy_forward_i32(int wav, int scheme, const FwdCfg& cfg) { return occupancy_forward_t<int>(wav, scheme, cfg); }
+int occupancy_inverse_i32(int scheme) { return occupancy_inverse_t<int>(scheme); }
+
 }  // namespace dwt2

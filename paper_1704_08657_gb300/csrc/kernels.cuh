@@ -1,17 +1,17 @@
 // kernels.cuh -- the transform kernels of one pyramid level.
 //
-// Work decomposition: the level is cut into vertical strips of 60 output
-// quads (120 pixels; a warp loads 128 pixels, 4 on each side are halo) and
+// Work decomposition: the level is cut into vertical strips of 32*QL - 4
+// output quads (a warp loads 64*QL pixels; 4 on each side are halo) and
 // horizontal segments of seg_rows output quad rows.  One (strip, segment)
 // pair is a unit of work for one warp.  A warp streams the quad rows of its
 // unit top to bottom through the row pipeline of the scheme (schemes.cuh),
 // starting two quad rows above the segment (warm-up) and running LAG rows
-// past it.
+// past it, in groups of PHASES arrivals unrolled at compile time.
 //
 // Forward: each warp owns a ring of NST shared-memory stages of QR quad rows
-// (2*QR pixel rows x 128 pixels) filled by 2-D TMA loads that complete on one
-// mbarrier per stage; lane 0 refills a stage once the warp has read it.  Rows
-// outside the image are fetched from their whole-sample mirror rows (one
+// (2*QR pixel rows x 64*QL pixels) filled by 2-D TMA loads that complete on
+// one mbarrier per stage; lane 0 refills a stage once the warp has read it.
+// Rows outside the image are fetched from their whole-sample mirror rows (one
 // single-row TMA box per pixel row); columns outside the image are mirrored in
 // shared memory by the edge strips.  With the symmetric extension in place the
 // lifting needs no boundary cases: every step preserves the symmetry, so the
@@ -24,49 +24,128 @@
 // weights of Adj97 instead.
 #pragma once
 
+#include <type_traits>
+#include <utility>
+
 #include "schemes.cuh"
 
 namespace dwt2 {
 
-template <class CT>
-__device__ __forceinline__ void ld4_smem(const CT* p, CT (&v)[4]);
-template <>
-__device__ __forceinline__ void ld4_smem<float>(const float* p, float (&v)[4]) {
-    const float4 t = *reinterpret_cast<const float4*>(p);
-    v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
+// compile-time loop: f(std::integral_constant<int, 0>) ... f(<N-1>)
+template <class F, int... I>
+__device__ __forceinline__ void static_for_impl(F&& f, std::integer_sequence<int, I...>) {
+    (f(std::integral_constant<int, I>{}), ...);
 }
-template <>
-__device__ __forceinline__ void ld4_smem<int>(const int* p, int (&v)[4]) {
-    const int4 t = *reinterpret_cast<const int4*>(p);
-    v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
+template <int N, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+    static_for_impl(f, std::make_integer_sequence<int, N>{});
 }
 
 template <class CT>
-__device__ __forceinline__ void st4(CT* p, CT a, CT b, CT c, CT d);
-template <>
-__device__ __forceinline__ void st4<float>(float* p, float a, float b, float c, float d) {
-    *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+__device__ __forceinline__ void ld4_smem(const CT* p, CT* v) {
+    if constexpr (std::is_same<CT, float>::value) {
+        const float4 t = *reinterpret_cast<const float4*>(p);
+        v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
+    } else {
+        const int4 t = *reinterpret_cast<const int4*>(p);
+        v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
+    }
 }
-template <>
-__device__ __forceinline__ void st4<int>(int* p, int a, int b, int c, int d) {
-    *reinterpret_cast<int4*>(p) = make_int4(a, b, c, d);
+
+template <class CT>
+__device__ __forceinline__ void st4(CT* p, CT a, CT b, CT c, CT d) {
+    if constexpr (std::is_same<CT, float>::value)
+        *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+    else
+        *reinterpret_cast<int4*>(p) = make_int4(a, b, c, d);
 }
+
+// The pieces of work of one warp, as (strip, first quad row, end quad row):
+// balanced mode gives each warp one contiguous range of the strip-major quad
+// rows (split where it crosses a strip end); otherwise fixed units of
+// seg_rows rows are dealt round-robin.
+template <class P>
+struct Pieces {
+    int64_t rb, re;
+    int unit, stride;
+    __device__ __forceinline__ Pieces(const P& p, int wg, int nwarps) {
+        const int64_t T = int64_t(p.n_strips) * p.hq;
+        rb = T * wg / nwarps;
+        re = T * (wg + 1) / nwarps;
+        unit = wg;
+        stride = nwarps;
+    }
+    __device__ __forceinline__ bool next(const P& p, int& s, int& R0, int& R1) {
+        if (p.balanced) {
+            if (rb >= re) return false;
+            s = int(rb / p.hq);
+            R0 = int(rb - int64_t(s) * p.hq);
+            R1 = int(min(int64_t(p.hq), R0 + (re - rb)));
+            rb += R1 - R0;
+            return true;
+        }
+        if (unit >= p.n_units) return false;
+        s = unit % p.n_strips;
+        R0 = (unit / p.n_strips) * p.seg_rows;
+        R1 = min(R0 + p.seg_rows, p.hq);
+        unit += stride;
+        return true;
+    }
+};
 
 // shared-memory bytes of a forward launch
-template <int QR, int NST, int NW>
+template <int QL, int QR, int NST, int NW>
 constexpr size_t fwd_smem_bytes() {
-    return size_t(NW) * NST * (2 * QR * STRIP_PX * 4) + size_t(NW) * NST * 8;
+    return size_t(NW) * NST * (2 * QR * 64 * QL * 4) + size_t(NW) * NST * 8;
+}
+
+// One quad row (two pixel rows) of the lane from a shared-memory stage; edge
+// strips replace pixels outside [0, w) by their mirror images.
+template <class CT, int QL>
+__device__ __forceinline__ void load_quad_row(const CT* s0, Row<CT, QL>& r, int lane, bool edge, int x0, int w) {
+    constexpr int SPX = 64 * QL;
+    const CT* s1 = s0 + SPX;
+    CT e[2 * QL], o[2 * QL];
+#pragma unroll
+    for (int k = 0; k < 2 * QL; k += 4) {
+        ld4_smem<CT>(s0 + 2 * QL * lane + k, e + k);
+        ld4_smem<CT>(s1 + 2 * QL * lane + k, o + k);
+    }
+    if (edge) {
+#pragma unroll
+        for (int k = 0; k < 2 * QL; ++k) {
+            const int px = x0 + 2 * QL * lane + k;
+            if (px < 0 || px >= w) {
+                const int src = fold_ws(px, w) - x0;
+                const bool in = (src >= 0) && (src < SPX);
+                e[k] = in ? s0[src] : CT(0);
+                o[k] = in ? s1[src] : CT(0);
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+        r.c1[q] = e[2 * q];
+        r.c2[q] = e[2 * q + 1];
+        r.c3[q] = o[2 * q];
+        r.c4[q] = o[2 * q + 1];
+    }
 }
 
 // ------------------------------------------------------------------ forward
-template <class Pipe, class OutT, int QR, int NST, int NW>
+template <class Pipe, class OutT, int QL, int QR, int NST, int NW>
 __global__ void __launch_bounds__(NW * 32)
     fwd_tma_kernel(const __grid_constant__ CUtensorMap tm_box, const __grid_constant__ CUtensorMap tm_row,
                    const FwdParams p) {
     using CT = typename Pipe::CT;
+    using R = Row<CT, QL>;
+    constexpr int SPX = 64 * QL;
+    constexpr int OUTQ = 32 * QL - 2 * HALO_Q;
     constexpr int ROWS = 2 * QR;
-    constexpr int STAGE_ELEMS = ROWS * STRIP_PX;
+    constexpr int STAGE_ELEMS = ROWS * SPX;
     constexpr unsigned STAGE_BYTES = STAGE_ELEMS * 4u;
+    static_assert(PHASES % QR == 0, "a group of arrivals must cover whole stages");
+    static_assert(QL % 2 == 0, "band stores go in pairs");
     extern __shared__ __align__(128) unsigned char smem[];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -83,16 +162,36 @@ __global__ void __launch_bounds__(NW * 32)
     __syncwarp();
 
     uint32_t gstage = 0;  // stages consumed by this warp so far (slot / phase)
-    for (int unit = blockIdx.x * NW + warp; unit < p.n_units; unit += gridDim.x * NW) {
-        const int s = unit % p.n_strips, g = unit / p.n_strips;
-        const int R0 = g * p.seg_rows;
-        const int R1 = min(R0 + p.seg_rows, p.hq);
-        const int A0 = R0 - 2;                           // first quad row streamed
-        const int n_arr = (R1 - R0) + 2 + Pipe::LAG;     // quad rows streamed
-        const int NT = (n_arr + QR - 1) / QR;            // stages
-        const int x0 = s * (2 * OUT_Q) - 2 * HALO_Q;     // first pixel column (multiple of 4)
-        const int jb = x0 / 2 + 2 * lane;                // first quad column of this lane
-        const bool edge = (x0 < 0) || (x0 + STRIP_PX > p.w);
+    Pieces<FwdParams> pieces(p, blockIdx.x * NW + warp, gridDim.x * NW);
+    int s, R0, R1;
+    while (pieces.next(p, s, R0, R1)) {
+        const int A0 = R0 - 2;                         // first quad row streamed
+        const int n_arr = (R1 - R0) + 2 + Pipe::LAG;   // quad rows streamed
+        const int n_grp = (n_arr + PHASES - 1) / PHASES;  // groups of arrivals (the last may stop early)
+        const int NT = (n_arr + QR - 1) / QR;          // stages
+        const int x0 = s * (2 * OUTQ) - 2 * HALO_Q;                          // first pixel (multiple of 4)
+        const int jb = x0 / 2 + QL * lane;                                   // first quad column of the lane
+        const bool edge = (x0 < 0) || (x0 + SPX > p.w);
+
+        // which of the lane's quads this strip outputs, per band parity
+        bool ev[QL], dv[QL], mp[QL];
+#pragma unroll
+        for (int q = 0; q < QL; ++q) {
+            const int lq = QL * lane + q;
+            mp[q] = (lq >= HALO_Q) && (lq < 32 * QL - HALO_Q);
+            ev[q] = mp[q] && (jb + q < p.wq);
+            dv[q] = mp[q] && (jb + q < p.wh);
+        }
+        // warp-uniform: every output quad of the strip exists in all four bands
+        // and every band row takes paired stores
+        const bool fast = p.vec_lo && p.vec_hi && (p.ll_is_ct || p.vec_ll) &&
+                          (x0 / 2 + 32 * QL - HALO_Q <= p.wh);
+        // band pointers at output row R0, advanced one pitch per stored row
+        OutT* hl = reinterpret_cast<OutT*>(p.coef) + int64_t(R0) * p.coef_pitch + p.wq + jb;
+        OutT* lh = reinterpret_cast<OutT*>(p.coef) + int64_t(p.hq + R0) * p.coef_pitch + jb;
+        OutT* hh = lh + p.wq;
+        CT* llc = reinterpret_cast<CT*>(p.ll) + int64_t(R0) * p.ll_pitch + jb;
+        OutT* llo = reinterpret_cast<OutT*>(p.ll) + int64_t(R0) * p.ll_pitch + jb;
 
         auto issue = [&](int t, int slot) {
             const int y0 = 2 * (A0 + t * QR);
@@ -103,7 +202,7 @@ __global__ void __launch_bounds__(NW * 32)
             } else {
 #pragma unroll 1
                 for (int r = 0; r < ROWS; ++r)
-                    tma_load_2d(dst + r * STRIP_PX, &tm_row, x0, fold_ws(y0 + r, p.h), &bars[slot]);
+                    tma_load_2d(dst + r * SPX, &tm_row, x0, fold_ws(y0 + r, p.h), &bars[slot]);
             }
         };
 
@@ -114,67 +213,75 @@ __global__ void __launch_bounds__(NW * 32)
         Pipe pipe;
         pipe.init();
         bool ok = true;
-        for (int t = 0; t < NT; ++t) {
-            const uint32_t gs = gstage + t;
-            const int slot = gs % NST;
-            if (!mbar_wait_bounded(&bars[slot], (gs / NST) & 1u, p.status, p.timeout_ns)) {
-                // give the copies still in flight a bounded time to land
-                for (int u = t + 1; u < NT && u < t + NST; ++u) {
-                    const uint32_t gu = gstage + u;
-                    mbar_wait_bounded(&bars[gu % NST], (gu / NST) & 1u, nullptr, p.timeout_ns);
+        int t = 0, slot = 0;
+        const CT* stage = bufs;
+        for (int gi = 0; gi < n_grp && ok; ++gi) {
+            static_for<PHASES>([&](auto ph) {
+                constexpr int PH = decltype(ph)::value;
+                constexpr int QI = PH % QR;
+                if (gi * PHASES + PH >= QR * NT) return;  // past the unit's last stage
+                if constexpr (QI == 0) {
+                    if (!ok) return;
+                    const uint32_t gs = gstage + t;
+                    slot = gs % NST;
+                    if (!mbar_wait_bounded(&bars[slot], (gs / NST) & 1u, p.status, p.timeout_ns)) {
+                        // give the copies still in flight a bounded time to land
+                        for (int u = t + 1; u < NT && u < t + NST; ++u) {
+                            const uint32_t gu = gstage + u;
+                            mbar_wait_bounded(&bars[gu % NST], (gu / NST) & 1u, nullptr, p.timeout_ns);
+                        }
+                        ok = false;
+                        return;
+                    }
+                    stage = bufs + slot * STAGE_ELEMS;
                 }
-                ok = false;
-                break;
-            }
-            const CT* stage = bufs + slot * STAGE_ELEMS;
+                const int vi = A0 + gi * PHASES + PH;  // quad row streamed now
+                load_quad_row<CT, QL>(stage + (2 * QI) * SPX, pipe.template slot<PH>(), lane, edge, x0, p.w);
+                const R& out = pipe.template step<PH>(vi);
+                const int oi = vi - Pipe::LAG;
+                const bool row_on = (oi >= R0) & (oi < R1);
+                const bool orow = row_on & (oi < p.hh);
+                if (fast) {
 #pragma unroll
-            for (int qr = 0; qr < QR; ++qr) {
-                const int vi = A0 + t * QR + qr;  // quad row streamed now
-                const CT* s0 = stage + (2 * qr) * STRIP_PX;
-                const CT* s1 = s0 + STRIP_PX;
-                CT e[4], o[4];
-                ld4_smem<CT>(s0 + 4 * lane, e);
-                ld4_smem<CT>(s1 + 4 * lane, o);
-                if (edge) {
+                    for (int q = 0; q < QL; q += 2) {
+                        const bool on = row_on & mp[q] & mp[q + 1];
+                        const bool oo = orow & mp[q] & mp[q + 1];
+                        if (p.ll_is_ct) {
+                            if (on) st_pair<CT>(llc + q, out.c1[q], out.c1[q + 1]);
+                        } else {
+                            if (on) st_pair<OutT>(llo + q, Cvt<OutT>::to(out.c1[q]), Cvt<OutT>::to(out.c1[q + 1]));
+                        }
+                        if (on) st_pair<OutT>(hl + q, Cvt<OutT>::to(out.c2[q]), Cvt<OutT>::to(out.c2[q + 1]));
+                        if (oo) st_pair<OutT>(lh + q, Cvt<OutT>::to(out.c3[q]), Cvt<OutT>::to(out.c3[q + 1]));
+                        if (oo) st_pair<OutT>(hh + q, Cvt<OutT>::to(out.c4[q]), Cvt<OutT>::to(out.c4[q + 1]));
+                    }
+                } else if (row_on) {
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const int px = x0 + 4 * lane + k;
-                        if (px < 0 || px >= p.w) {
-                            const int src = fold_ws(px, p.w) - x0;
-                            const bool in = (src >= 0) && (src < STRIP_PX);
-                            e[k] = in ? s0[src] : CT(0);
-                            o[k] = in ? s1[src] : CT(0);
+                    for (int q = 0; q < QL; q += 2) {
+                        if (p.ll_is_ct)
+                            store_pair<CT, CT>(llc, q, out.c1[q], out.c1[q + 1], ev[q], ev[q + 1], true);
+                        else
+                            store_pair<OutT, CT>(llo, q, out.c1[q], out.c1[q + 1], ev[q], ev[q + 1], p.vec_ll);
+                        store_pair<OutT, CT>(hl, q, out.c2[q], out.c2[q + 1], dv[q], dv[q + 1], p.vec_hi);
+                        if (orow) {
+                            store_pair<OutT, CT>(lh, q, out.c3[q], out.c3[q + 1], ev[q], ev[q + 1], p.vec_lo);
+                            store_pair<OutT, CT>(hh, q, out.c4[q], out.c4[q + 1], dv[q], dv[q + 1], p.vec_hi);
                         }
                     }
                 }
-                Row<CT> in;
-                in.c1[0] = e[0], in.c2[0] = e[1], in.c1[1] = e[2], in.c2[1] = e[3];
-                in.c3[0] = o[0], in.c4[0] = o[1], in.c3[1] = o[2], in.c4[1] = o[3];
-                const Row<CT> out = pipe.arrive(in, vi);
-                const int oi = vi - Pipe::LAG;
-                if (oi >= R0 && oi < R1) {
-                    const bool lo = (lane >= 1) && (lane <= 30);
-                    const bool e0 = lo && jb < p.wq, e1 = lo && jb + 1 < p.wq;
-                    const bool d0 = lo && jb < p.wh, d1 = lo && jb + 1 < p.wh;
-                    const bool odd_row = oi < p.hh;
-                    OutT* crow = reinterpret_cast<OutT*>(p.coef) + int64_t(oi) * p.coef_pitch;
-                    OutT* crow_b = reinterpret_cast<OutT*>(p.coef) + int64_t(p.hq + oi) * p.coef_pitch;
-                    if (p.ll_is_ct) {
-                        CT* lrow = reinterpret_cast<CT*>(p.ll) + int64_t(oi) * p.ll_pitch;
-                        store_pair<CT, CT>(lrow, jb, out.c1[0], out.c1[1], e0, e1, p.vec_ll);
-                    } else {
-                        OutT* lrow = reinterpret_cast<OutT*>(p.ll) + int64_t(oi) * p.ll_pitch;
-                        store_pair<OutT, CT>(lrow, jb, out.c1[0], out.c1[1], e0, e1, p.vec_ll);
-                    }
-                    store_pair<OutT, CT>(crow + p.wq, jb, out.c2[0], out.c2[1], d0, d1, p.vec_hi);
-                    if (odd_row) {
-                        store_pair<OutT, CT>(crow_b, jb, out.c3[0], out.c3[1], e0, e1, p.vec_lo);
-                        store_pair<OutT, CT>(crow_b + p.wq, jb, out.c4[0], out.c4[1], d0, d1, p.vec_hi);
-                    }
+                const int64_t cstep = row_on ? p.coef_pitch : 0;
+                const int64_t lstep = row_on ? p.ll_pitch : 0;
+                hl += cstep;
+                lh += cstep;
+                hh += cstep;
+                llc += lstep;
+                llo += lstep;
+                if constexpr (QI == QR - 1) {
+                    __syncwarp();
+                    if (lane == 0 && ok && t + NST < NT) issue(t + NST, slot);
+                    ++t;
                 }
-            }
-            __syncwarp();
-            if (lane == 0 && t + NST < NT) issue(t + NST, slot);
+            });
         }
         if (!ok) return;
         gstage += NT;
@@ -215,28 +322,30 @@ __device__ __forceinline__ CT ld_one(const T* p) {
     return CT(Cvt<T>::from(*p));
 }
 
-// One quad row of the lane's two quads from the four bands.  MIRROR: positions
+// One quad row of the lane's quads from the four bands.  MIRROR: positions
 // outside the image read their mirror images; otherwise they read zero.
-template <class CT, class BT, bool MIRROR>
-__device__ __forceinline__ Row<CT> load_bands(const InvParams& p, int vi, int jb, bool fast) {
-    Row<CT> r;
+template <class CT, class BT, bool MIRROR, int QL>
+__device__ __forceinline__ void load_bands(const InvParams& p, int vi, int jb, bool fast, Row<CT, QL>& r) {
     const BT* coef = reinterpret_cast<const BT*>(p.coef);
     if (fast) {  // whole strip and row inside the bands: direct pair loads
         const int64_t re = vi, ro = vi;
-        const BT* hl = coef + re * p.coef_pitch + p.wq;
-        const BT* lh = coef + (p.hq + ro) * p.coef_pitch;
+        const BT* hl = coef + re * p.coef_pitch + p.wq + jb;
+        const BT* lh = coef + (p.hq + ro) * p.coef_pitch + jb;
         const BT* hh = lh + p.wq;
-        if (p.ll_is_ct) {
-            const CT* ll = reinterpret_cast<const CT*>(p.ll) + re * p.ll_pitch;
-            ld_pair(ll + jb, r.c1[0], r.c1[1], p.vec_ll);
-        } else {
-            const BT* ll = reinterpret_cast<const BT*>(p.ll) + re * p.ll_pitch;
-            ld_pair(ll + jb, r.c1[0], r.c1[1], p.vec_ll);
+#pragma unroll
+        for (int q = 0; q < QL; q += 2) {
+            if (p.ll_is_ct) {
+                const CT* ll = reinterpret_cast<const CT*>(p.ll) + re * p.ll_pitch + jb;
+                ld_pair(ll + q, r.c1[q], r.c1[q + 1], p.vec_ll);
+            } else {
+                const BT* ll = reinterpret_cast<const BT*>(p.ll) + re * p.ll_pitch + jb;
+                ld_pair(ll + q, r.c1[q], r.c1[q + 1], p.vec_ll);
+            }
+            ld_pair(hl + q, r.c2[q], r.c2[q + 1], p.vec_in_hi);
+            ld_pair(lh + q, r.c3[q], r.c3[q + 1], p.vec_in_lo);
+            ld_pair(hh + q, r.c4[q], r.c4[q + 1], p.vec_in_hi);
         }
-        ld_pair(hl + jb, r.c2[0], r.c2[1], p.vec_in_hi);
-        ld_pair(lh + jb, r.c3[0], r.c3[1], p.vec_in_lo);
-        ld_pair(hh + jb, r.c4[0], r.c4[1], p.vec_in_hi);
-        return r;
+        return;
     }
     int re, ro;
     bool rev, rov;
@@ -283,27 +392,34 @@ __device__ __forceinline__ Row<CT> load_bands(const InvParams& p, int vi, int jb
         r.c3[q] = (rov && cev) ? v3 : CT(0);
         r.c4[q] = (rov && cov) ? v4 : CT(0);
     }
-    return r;
 }
 
 // --------------------------------------------------------- inverse / adjoint
-// Pipe: Inv97<S>, Inv53<S> or Adj97.  BT: coefficient element type.
-template <class Pipe, class BT, bool ADJ, int NW>
+// Pipe: Inv97<S, QL>, Inv53<S, QL> or Adj97<QL>.  BT: coefficient element type.
+template <class Pipe, class BT, bool ADJ, int QL, int NW>
 __global__ void __launch_bounds__(NW * 32) inv_kernel(const InvParams p) {
     using CT = typename Pipe::CT;
+    using R = Row<CT, QL>;
     constexpr bool MIRROR = !ADJ;
+    constexpr int OUTQ = 32 * QL - 2 * HALO_Q;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-    for (int unit = blockIdx.x * NW + warp; unit < p.n_units; unit += gridDim.x * NW) {
-        const int s = unit % p.n_strips, g = unit / p.n_strips;
-        const int R0 = g * p.seg_rows;
-        const int R1 = min(R0 + p.seg_rows, p.hq);
+    Pieces<InvParams> pieces(p, blockIdx.x * NW + warp, gridDim.x * NW);
+    int s, R0, R1;
+    while (pieces.next(p, s, R0, R1)) {
         const int A0 = R0 - 2;
         const int n_arr = (R1 - R0) + 2 + Pipe::LAG;
-        const int x0 = s * (2 * OUT_Q) - 2 * HALO_Q;
-        const int jb = x0 / 2 + 2 * lane;
+        const int n_grp = (n_arr + PHASES - 1) / PHASES;
+        const int x0 = s * (2 * OUTQ) - 2 * HALO_Q;
+        const int jb = x0 / 2 + QL * lane;
         // the whole strip reads only existing band columns
-        const bool fast_cols = (x0 >= 0) && (x0 / 2 + 2 * 32 <= p.wh);
+        const bool fast_cols = (x0 >= 0) && (x0 / 2 + 32 * QL <= p.wh);
+        bool mine[QL];
+#pragma unroll
+        for (int q = 0; q < QL; ++q) {
+            const int lq = QL * lane + q;
+            mine[q] = (lq >= HALO_Q) && (lq < 32 * QL - HALO_Q);
+        }
 
         Pipe pipe;
         pipe.init();
@@ -314,35 +430,43 @@ __global__ void __launch_bounds__(NW * 32) inv_kernel(const InvParams p) {
         }
         auto fast_row = [&](int vi) { return fast_cols && vi >= 0 && 2 * vi + 1 < p.h; };
 
-        Row<CT> n1 = load_bands<CT, BT, MIRROR>(p, A0, jb, fast_row(A0));
-        Row<CT> n2 = load_bands<CT, BT, MIRROR>(p, A0 + 1, jb, fast_row(A0 + 1));
-        for (int a = 0; a < n_arr; ++a) {
-            const int vi = A0 + a;
-            const Row<CT> cur = n1;
-            n1 = n2;
-            if (a + 2 < n_arr) n2 = load_bands<CT, BT, MIRROR>(p, vi + 2, jb, fast_row(vi + 2));
-            const Row<CT> out = pipe.arrive(cur, vi);
-            const int oi = vi - Pipe::LAG;
-            if (oi < R0 || oi >= R1) continue;
-            const bool lo = (lane >= 1) && (lane <= 30);
-            const int px = 2 * jb;  // first pixel column of the lane
-            CT* row_e = reinterpret_cast<CT*>(p.out) + int64_t(2 * oi) * p.out_pitch;
-            CT* row_o = row_e + p.out_pitch;
-            const bool has_o = 2 * oi + 1 < p.h;
-            if (lo && p.vec_out && px + 3 < p.w) {
-                st4<CT>(row_e + px, out.c1[0], out.c2[0], out.c1[1], out.c2[1]);
-                if (has_o) st4<CT>(row_o + px, out.c3[0], out.c4[0], out.c3[1], out.c4[1]);
-            } else if (lo) {
-                const CT ev[4] = {out.c1[0], out.c2[0], out.c1[1], out.c2[1]};
-                const CT od[4] = {out.c3[0], out.c4[0], out.c3[1], out.c4[1]};
+        R pf[2];  // rows vi+1 and vi+2 in flight
+        load_bands<CT, BT, MIRROR, QL>(p, A0, jb, fast_row(A0), pf[0]);
+        load_bands<CT, BT, MIRROR, QL>(p, A0 + 1, jb, fast_row(A0 + 1), pf[1]);
+        CT* row_e = reinterpret_cast<CT*>(p.out) + int64_t(2 * R0) * p.out_pitch;
+        const int px = 2 * jb;  // first pixel column of the lane
+        for (int gi = 0; gi < n_grp; ++gi) {
+            static_for<PHASES>([&](auto ph) {
+                constexpr int PH = decltype(ph)::value;
+                if (gi * PHASES + PH >= n_arr) return;
+                const int vi = A0 + gi * PHASES + PH;
+                pipe.template slot<PH>() = pf[PH % 2];
+                load_bands<CT, BT, MIRROR, QL>(p, vi + 2, jb, fast_row(vi + 2), pf[PH % 2]);
+                const R& out = pipe.template step<PH>(vi);
+                const int oi = vi - Pipe::LAG;
+                if (oi < R0 || oi >= R1) return;
+                CT* row_o = row_e + p.out_pitch;
+                const bool has_o = 2 * oi + 1 < p.h;
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    if (px + k < p.w) {
-                        row_e[px + k] = ev[k];
-                        if (has_o) row_o[px + k] = od[k];
+                for (int q = 0; q < QL; q += 2) {
+                    const int c = px + 2 * q;
+                    if (mine[q] && mine[q + 1] && p.vec_out && c + 3 < p.w) {
+                        st4<CT>(row_e + c, out.c1[q], out.c2[q], out.c1[q + 1], out.c2[q + 1]);
+                        if (has_o) st4<CT>(row_o + c, out.c3[q], out.c4[q], out.c3[q + 1], out.c4[q + 1]);
+                    } else {
+                        const CT ev[4] = {out.c1[q], out.c2[q], out.c1[q + 1], out.c2[q + 1]};
+                        const CT od[4] = {out.c3[q], out.c4[q], out.c3[q + 1], out.c4[q + 1]};
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            if (mine[q + (k >> 1)] && c + k < p.w) {
+                                row_e[c + k] = ev[k];
+                                if (has_o) row_o[c + k] = od[k];
+                            }
+                        }
                     }
                 }
-            }
+                row_e += 2 * p.out_pitch;
+            });
         }
     }
 }

@@ -8,10 +8,10 @@
 
 namespace dwt2 {
 
-template <class Pipe, class OutT, int QR, int NST, int NW>
+template <class Pipe, class OutT, int QL, int QR, int NST, int NW>
 int launch_fwd_one(const CUtensorMap& box, const CUtensorMap& row, const FwdParams& p, int grid, cudaStream_t s) {
-    auto k = fwd_tma_kernel<Pipe, OutT, QR, NST, NW>;
-    constexpr size_t smem = fwd_smem_bytes<QR, NST, NW>();
+    auto k = fwd_tma_kernel<Pipe, OutT, QL, QR, NST, NW>;
+    constexpr size_t smem = fwd_smem_bytes<QL, QR, NST, NW>();
     if (smem > 48 * 1024) {
         static bool done = false;
         if (!done) {
@@ -24,15 +24,72 @@ int launch_fwd_one(const CUtensorMap& box, const CUtensorMap& row, const FwdPara
     return cudaGetLastError();
 }
 
-// the compiled forward configurations (quad rows per stage, stages, warps)
-#define DWT2_FWD_CFG_LIST(X) X(0, 2, 4, 4) X(1, 3, 3, 4) X(2, 1, 8, 4)
+// the compiled forward configurations (quads per lane, quad rows per stage,
+// stages, warps per block); the first is the default
+#define DWT2_FWD_CFG_LIST(X) X(0, 2, 3, 3, 4) X(1, 2, 2, 4, 4) X(2, 2, 1, 6, 4) X(3, 2, 2, 4, 8) X(4, 4, 2, 4, 4)
 
-template <class Pipe, class OutT>
+template <class Pipe, class OutT, int QL, int QR, int NST, int NW>
+int occupancy_fwd_one() {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fwd_tma_kernel<Pipe, OutT, QL, QR, NST, NW>, NW * 32,
+                                                      fwd_smem_bytes<QL, QR, NST, NW>()) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+template <template <int, int> class PipeT, int S, class OutT>
+int occupancy_fwd_cfgs(const FwdCfg& c) {
+#define DWT2_X(I_, QL_, QR_, NST_, NW_)                                \
+    if (c.ql == QL_ && c.qr == QR_ && c.nst == NST_ && c.nw == NW_) \
+        return occupancy_fwd_one<PipeT<S, QL_>, OutT, QL_, QR_, NST_, NW_>();
+    DWT2_FWD_CFG_LIST(DWT2_X)
+#undef DWT2_X
+    return 0;
+}
+
+template <class OutT>
+int occupancy_forward_t(int wav, int scheme, const FwdCfg& c) {
+    if constexpr (std::is_same<OutT, int>::value) {
+        if (scheme == SCHEME_SEP) return occupancy_fwd_cfgs<Fwd53, SCHEME_SEP, int>(c);
+        return occupancy_fwd_cfgs<Fwd53, SCHEME_NONSEP, int>(c);
+    } else {
+        if (scheme == SCHEME_NONSEP) return occupancy_fwd_cfgs<Fwd97, SCHEME_NONSEP, OutT>(c);
+        if (scheme == SCHEME_REDUCED) return occupancy_fwd_cfgs<Fwd97, SCHEME_REDUCED, OutT>(c);
+        return occupancy_fwd_cfgs<Fwd97, SCHEME_SEP, OutT>(c);
+    }
+}
+
+template <class Pipe, class BT, bool ADJ>
+int occupancy_inv_one() {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, inv_kernel<Pipe, BT, ADJ, INV_QL, INV_NW>, INV_NW * 32, 0) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+template <class BT>
+int occupancy_inverse_t(int scheme) {
+    if constexpr (std::is_same<BT, int>::value) {
+        if (scheme == SCHEME_SEP) return occupancy_inv_one<Inv53<SCHEME_SEP, INV_QL>, int, false>();
+        return occupancy_inv_one<Inv53<SCHEME_NONSEP, INV_QL>, int, false>();
+    } else {
+        if (scheme == SCHEME_NONSEP) return occupancy_inv_one<Inv97<SCHEME_NONSEP, INV_QL>, BT, false>();
+        if (scheme == SCHEME_REDUCED) return occupancy_inv_one<Inv97<SCHEME_REDUCED, INV_QL>, BT, false>();
+        return occupancy_inv_one<Inv97<SCHEME_SEP, INV_QL>, BT, false>();
+    }
+}
+
+template <template <int, int> class PipeT, int S, class OutT>
 int launch_fwd_cfgs(const CUtensorMap& box, const CUtensorMap& row, const FwdParams& p, int grid,
                     const FwdCfg& c, cudaStream_t s) {
-#define DWT2_X(I_, QR_, NST_, NW_)                      \
-    if (c.qr == QR_ && c.nst == NST_ && c.nw == NW_) \
-        return launch_fwd_one<Pipe, OutT, QR_, NST_, NW_>(box, row, p, grid, s);
+#define DWT2_X(I_, QL_, QR_, NST_, NW_)                                   \
+    if (c.ql == QL_ && c.qr == QR_ && c.nst == NST_ && c.nw == NW_)    \
+        return launch_fwd_one<PipeT<S, QL_>, OutT, QL_, QR_, NST_, NW_>(box, row, p, grid, s);
     DWT2_FWD_CFG_LIST(DWT2_X)
 #undef DWT2_X
     return cudaErrorInvalidValue;
@@ -43,21 +100,21 @@ int launch_forward_t(int wav, int scheme, const CUtensorMap& box, const CUtensor
                      int grid, const FwdCfg& c, cudaStream_t s) {
     if constexpr (std::is_same<OutT, int>::value) {
         if (wav != WAV_CDF53I) return cudaErrorInvalidValue;
-        if (scheme == SCHEME_SEP) return launch_fwd_cfgs<Fwd53<SCHEME_SEP>, int>(box, row, p, grid, c, s);
-        if (scheme == SCHEME_NONSEP) return launch_fwd_cfgs<Fwd53<SCHEME_NONSEP>, int>(box, row, p, grid, c, s);
+        if (scheme == SCHEME_SEP) return launch_fwd_cfgs<Fwd53, SCHEME_SEP, int>(box, row, p, grid, c, s);
+        if (scheme == SCHEME_NONSEP) return launch_fwd_cfgs<Fwd53, SCHEME_NONSEP, int>(box, row, p, grid, c, s);
         return cudaErrorInvalidValue;
     } else {
         if (wav != WAV_CDF97) return cudaErrorInvalidValue;
-        if (scheme == SCHEME_NONSEP) return launch_fwd_cfgs<Fwd97<SCHEME_NONSEP>, OutT>(box, row, p, grid, c, s);
-        if (scheme == SCHEME_REDUCED) return launch_fwd_cfgs<Fwd97<SCHEME_REDUCED>, OutT>(box, row, p, grid, c, s);
-        if (scheme == SCHEME_SEP) return launch_fwd_cfgs<Fwd97<SCHEME_SEP>, OutT>(box, row, p, grid, c, s);
+        if (scheme == SCHEME_NONSEP) return launch_fwd_cfgs<Fwd97, SCHEME_NONSEP, OutT>(box, row, p, grid, c, s);
+        if (scheme == SCHEME_REDUCED) return launch_fwd_cfgs<Fwd97, SCHEME_REDUCED, OutT>(box, row, p, grid, c, s);
+        if (scheme == SCHEME_SEP) return launch_fwd_cfgs<Fwd97, SCHEME_SEP, OutT>(box, row, p, grid, c, s);
         return cudaErrorInvalidValue;
     }
 }
 
 template <class Pipe, class BT, bool ADJ>
 int launch_inv_one(const InvParams& p, int grid, cudaStream_t s) {
-    inv_kernel<Pipe, BT, ADJ, INV_NW><<<grid, INV_NW * 32, 0, s>>>(p);
+    inv_kernel<Pipe, BT, ADJ, INV_QL, INV_NW><<<grid, INV_NW * 32, 0, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -65,14 +122,14 @@ template <class BT>
 int launch_inverse_t(int wav, int scheme, const InvParams& p, int grid, cudaStream_t s) {
     if constexpr (std::is_same<BT, int>::value) {
         if (wav != WAV_CDF53I) return cudaErrorInvalidValue;
-        if (scheme == SCHEME_SEP) return launch_inv_one<Inv53<SCHEME_SEP>, int, false>(p, grid, s);
-        if (scheme == SCHEME_NONSEP) return launch_inv_one<Inv53<SCHEME_NONSEP>, int, false>(p, grid, s);
+        if (scheme == SCHEME_SEP) return launch_inv_one<Inv53<SCHEME_SEP, INV_QL>, int, false>(p, grid, s);
+        if (scheme == SCHEME_NONSEP) return launch_inv_one<Inv53<SCHEME_NONSEP, INV_QL>, int, false>(p, grid, s);
         return cudaErrorInvalidValue;
     } else {
         if (wav != WAV_CDF97) return cudaErrorInvalidValue;
-        if (scheme == SCHEME_NONSEP) return launch_inv_one<Inv97<SCHEME_NONSEP>, BT, false>(p, grid, s);
-        if (scheme == SCHEME_REDUCED) return launch_inv_one<Inv97<SCHEME_REDUCED>, BT, false>(p, grid, s);
-        if (scheme == SCHEME_SEP) return launch_inv_one<Inv97<SCHEME_SEP>, BT, false>(p, grid, s);
+        if (scheme == SCHEME_NONSEP) return launch_inv_one<Inv97<SCHEME_NONSEP, INV_QL>, BT, false>(p, grid, s);
+        if (scheme == SCHEME_REDUCED) return launch_inv_one<Inv97<SCHEME_REDUCED, INV_QL>, BT, false>(p, grid, s);
+        if (scheme == SCHEME_SEP) return launch_inv_one<Inv97<SCHEME_SEP, INV_QL>, BT, false>(p, grid, s);
         return cudaErrorInvalidValue;
     }
 }

@@ -27,7 +27,6 @@ namespace {
 
 constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(32) << 20;
 constexpr int NOALLOC_MAX_DEVICES = 64;
-constexpr int NOALLOC_OUT_Q = 60;  // output quads per strip of the forward kernel
 
 // The scratch.  In host code this name is only a host-side stand-in for the
 // device array; kernels get the device address from cudaGetSymbolAddress.
@@ -37,6 +36,7 @@ struct NoallocDevice {
     bool ready;
     void* scratch;  // device address of g_noalloc_scratch on this device
     int sm_count;
+    int fwd_bps[4][3];  // resident forward blocks per SM by coefficient type and scheme
 };
 
 std::mutex g_noalloc_mu;
@@ -61,6 +61,10 @@ int noalloc_setup(int dev, NoallocDevice** out) {
         }
         d.scratch = ptr;
         d.sm_count = sms;
+        for (int dt = 0; dt < 4; ++dt)
+            for (int sc = 0; sc < 3; ++sc)
+                d.fwd_bps[dt][sc] = dwt2::forward_blocks_per_sm(dt == DWT2_I32 ? DWT2_CDF53_INT : DWT2_CDF97, sc, dt,
+                                                               dwt2::FWD_CFGS[0]);
         d.ready = true;
     }
     *out = &d;
@@ -86,12 +90,13 @@ NoallocEncodeFn noalloc_encoder() {
     return fn;
 }
 
-int noalloc_map(CUtensorMap* m, const void* base, int w, int h, int64_t pitch, int box_rows, bool is_int) {
+int noalloc_map(CUtensorMap* m, const void* base, int w, int h, int64_t pitch, int box_w, int box_rows,
+                bool is_int) {
     NoallocEncodeFn enc = noalloc_encoder();
     if (!enc) return DWT2_ERR_CUDA;
     cuuint64_t dims[2] = {cuuint64_t(w), cuuint64_t(h)};
     cuuint64_t strides[1] = {cuuint64_t(pitch) * 4};
-    cuuint32_t box[2] = {128u, cuuint32_t(box_rows)};
+    cuuint32_t box[2] = {cuuint32_t(box_w), cuuint32_t(box_rows)};
     cuuint32_t estr[2] = {1u, 1u};
     CUresult r = enc(m, is_int ? CU_TENSOR_MAP_DATA_TYPE_INT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
                      const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -158,21 +163,29 @@ extern "C" int dwt2_forward_noalloc(int wavelet, int levels, int scheme, int coe
         const void* src = (l == 0) ? in : static_cast<const void*>(buf[(l - 1) % 2]);
         const int64_t src_pitch = (l == 0) ? pitch_elems : noalloc_round4(W);  // = round4(wq of level l-1)
         CUtensorMap box, row;
-        rc = noalloc_map(&box, src, W, H, src_pitch, 2 * cfg.qr, is_int);
-        if (rc == DWT2_OK) rc = noalloc_map(&row, src, W, H, src_pitch, 1, is_int);
+        rc = noalloc_map(&box, src, W, H, src_pitch, fwd_strip_px(cfg), 2 * cfg.qr, is_int);
+        if (rc == DWT2_OK) rc = noalloc_map(&row, src, W, H, src_pitch, fwd_strip_px(cfg), 1, is_int);
         if (rc != DWT2_OK) return rc;
         FwdParams fp;
         fp.h = H, fp.w = W, fp.hq = (H + 1) / 2, fp.wq = (W + 1) / 2, fp.hh = H / 2, fp.wh = W / 2;
-        fp.n_strips = (fp.wq + NOALLOC_OUT_Q - 1) / NOALLOC_OUT_Q;
+        // segments of the height dwt2_forward chooses (rounds x (rows + 4) minimal)
+        fp.n_strips = (fp.wq + fwd_out_quads(cfg) - 1) / fwd_out_quads(cfg);
         {
-            const int64_t target = int64_t(st->sm_count) * 24 * 3;
-            const int64_t total = int64_t(fp.hq) * fp.n_strips;
-            int rows = int((total + target - 1) / target);
-            rows = std::min(std::max(rows, 8), 512);
-            fp.seg_rows = std::min(rows, fp.hq);
+            const int64_t max_warps =
+                int64_t(st->sm_count) * std::max(st->fwd_bps[coef_dtype][scheme], 1) * cfg.nw;
+            int best = std::min(48, fp.hq);
+            int64_t best_cost = INT64_MAX;
+            for (int seg = std::min(8, fp.hq); seg <= std::min(48, fp.hq); ++seg) {
+                const int64_t units = int64_t((fp.hq + seg - 1) / seg) * fp.n_strips;
+                const int64_t cost = ((units + max_warps - 1) / max_warps) * (seg + 4);
+                if (cost < best_cost) best_cost = cost, best = seg;
+            }
+            fp.seg_rows = best;
         }
         fp.n_segs = (fp.hq + fp.seg_rows - 1) / fp.seg_rows;
         fp.n_units = fp.n_segs * fp.n_strips;
+        fp.balanced = 0;
+        const int grid = (fp.n_units + cfg.nw - 1) / cfg.nw;
         fp.coef = coef;
         fp.coef_pitch = pitch_elems;
         const bool last = (l == levels - 1);
@@ -191,7 +204,6 @@ extern "C" int dwt2_forward_noalloc(int wavelet, int levels, int scheme, int coe
         fp.vec_ll = last ? coef_vec : 1;
         fp.status = nullptr;  // no status word: device-side timeouts are not reported here
         fp.timeout_ns = 2000000000ull;
-        const int grid = (fp.n_units + cfg.nw - 1) / cfg.nw;
         int e;
         switch (coef_dtype) {
             case DWT2_F32: e = launch_forward_f32(wavelet, scheme, box, row, fp, grid, cfg, s); break;

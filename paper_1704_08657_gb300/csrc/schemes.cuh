@@ -12,10 +12,15 @@
 //   spatial update  S_U:  c1 += U c2 + U* c3 + UU* c4;  c2 += U* c4;  c3 += U c4
 //
 // with all operands taken before the step.  Quad rows stream top to bottom
-// through the registers of a lane: a step that reads the row below runs one
-// row later than the step before it; a step that reads the row above takes
-// that row's pre-step values from a carry saved when the step ran on it.
-// Horizontal neighbours come from the next / previous lane by shuffle.
+// through the registers of a lane (QL quads per lane): a step that reads the
+// row below runs one row later than the step before it; a step that reads the
+// row above takes that row's pre-step values from a carry saved when the step
+// ran on it.  Horizontal neighbours come from the next / previous lane by
+// shuffle.
+//
+// Pipelines are driven by a compile-time phase PH (the arrival index modulo
+// 6): the rows rotate through a ring of LAG+1 slots and the carries through
+// two slots, so that a group of 6 unrolled arrivals needs no register copies.
 #pragma once
 
 #include "dev_common.cuh"
@@ -31,21 +36,53 @@ struct C97 {
     static constexpr float ZZ = float(Zd * Zd), IZZ = float(1.0 / (Zd * Zd));
 };
 
+constexpr int PHASES = 6;  // arrivals per unrolled group
+
+template <class CT, int QL>
+struct Row {
+    CT c1[QL], c2[QL], c3[QL], c4[QL];
+};
+
+template <class CT, int QL>
+__device__ __forceinline__ void zero_row(Row<CT, QL>& r) {
+#pragma unroll
+    for (int q = 0; q < QL; ++q) r.c1[q] = r.c2[q] = r.c3[q] = r.c4[q] = CT(0);
+}
+
+// values of the quad to the right / left of each of the lane's quads
+template <class CT, int QL>
+__device__ __forceinline__ void right_of(const CT (&x)[QL], CT (&r)[QL]) {
+    const CT nxt = __shfl_down_sync(FULL, x[0], 1);
+#pragma unroll
+    for (int q = 0; q + 1 < QL; ++q) r[q] = x[q + 1];
+    r[QL - 1] = nxt;
+}
+
+template <class CT, int QL>
+__device__ __forceinline__ void left_of(const CT (&x)[QL], CT (&l)[QL]) {
+    const CT prv = __shfl_up_sync(FULL, x[QL - 1], 1);
+    l[0] = prv;
+#pragma unroll
+    for (int q = 1; q < QL; ++q) l[q] = x[q - 1];
+}
+
 // carries of an update step: the row above, before the step
+template <int QL>
 struct Carry3 {
     float c3[QL], c4[QL], l4[QL];  // c3, c4 and the c4 of the quad to the left
 };
-template <class CT>
+template <class CT, int QL>
 struct Carry2 {
     CT c3[QL], c4[QL];
 };
 
-__device__ __forceinline__ void zero_carry(Carry3& c) {
+template <int QL>
+__device__ __forceinline__ void zero_carry(Carry3<QL>& c) {
 #pragma unroll
     for (int q = 0; q < QL; ++q) c.c3[q] = c.c4[q] = c.l4[q] = 0.f;
 }
-template <class CT>
-__device__ __forceinline__ void zero_carry(Carry2<CT>& c) {
+template <class CT, int QL>
+__device__ __forceinline__ void zero_carry(Carry2<CT, QL>& c) {
 #pragma unroll
     for (int q = 0; q < QL; ++q) c.c3[q] = c.c4[q] = CT(0);
 }
@@ -54,7 +91,8 @@ __device__ __forceinline__ void zero_carry(Carry2<CT>& c) {
 
 // --- non-separable lifting (Proposed Schemes) ------------------------------
 // T_P on row X with the row below D, P = a(1 + z): every operand pre-step.
-__device__ __forceinline__ void ns_predict(Row<float>& X, const Row<float>& D, float a, float aa) {
+template <int QL>
+__device__ __forceinline__ void ns_predict(Row<float, QL>& X, const Row<float, QL>& D, float a, float aa) {
     float r1[QL], r3[QL], dr1[QL];
     right_of(X.c1, r1);
     right_of(X.c3, r3);
@@ -71,31 +109,33 @@ __device__ __forceinline__ void ns_predict(Row<float>& X, const Row<float>& D, f
     }
 }
 
-// S_U on row X with the carry C of the row above, U = b(1 + z^-1).
-__device__ __forceinline__ void ns_update(Row<float>& X, Carry3& C, float b, float bb) {
+// S_U on row X with the carry C of the row above, U = b(1 + z^-1); the
+// row's own pre-step values become the carry N for the row below.
+template <int QL>
+__device__ __forceinline__ void ns_update(Row<float, QL>& X, const Carry3<QL>& C, Carry3<QL>& N, float b,
+                                          float bb) {
     float l2[QL], l4[QL];
     left_of(X.c2, l2);
     left_of(X.c4, l4);
-    Carry3 n;
 #pragma unroll
     for (int q = 0; q < QL; ++q) {
-        n.c3[q] = X.c3[q];
-        n.c4[q] = X.c4[q];
-        n.l4[q] = l4[q];
-        const float h = l2[q] + X.c2[q];                                   // U c2
-        const float v = C.c3[q] + X.c3[q];                                 // U* c3
-        const float dg = (C.l4[q] + C.c4[q]) + (l4[q] + X.c4[q]);          // UU* c4
+        N.c3[q] = X.c3[q];
+        N.c4[q] = X.c4[q];
+        N.l4[q] = l4[q];
+        const float h = l2[q] + X.c2[q];                              // U c2
+        const float v = C.c3[q] + X.c3[q];                            // U* c3
+        const float dg = (C.l4[q] + C.c4[q]) + (l4[q] + X.c4[q]);     // UU* c4
         X.c1[q] = fmaf(b, h + v, fmaf(bb, dg, X.c1[q]));
-        X.c2[q] = fmaf(b, C.c4[q] + X.c4[q], X.c2[q]);                     // U* c4
-        X.c3[q] = fmaf(b, l4[q] + X.c4[q], X.c3[q]);                       // U c4
+        X.c2[q] = fmaf(b, C.c4[q] + X.c4[q], X.c2[q]);                // U* c4
+        X.c3[q] = fmaf(b, l4[q] + X.c4[q], X.c3[q]);                  // U c4
     }
-    C = n;
 }
 
 // --- reduced operations (Optimization Approach) -----------------------------
 // P = P0 + P1 with P0 = a (own quad) and P1 = a z (neighbour).  T_{P1} first,
 // on pre-step values, then T_{P0}^H and T_{P0}^V inside the quad.
-__device__ __forceinline__ void rd_predict(Row<float>& X, const Row<float>& D, float a, float aa) {
+template <int QL>
+__device__ __forceinline__ void rd_predict(Row<float, QL>& X, const Row<float, QL>& D, float a, float aa) {
     float r1[QL], r3[QL], dr1[QL];
     right_of(X.c1, r1);
     right_of(X.c3, r3);
@@ -118,16 +158,17 @@ __device__ __forceinline__ void rd_predict(Row<float>& X, const Row<float>& D, f
 }
 
 // U = U0 + U1 with U0 = b and U1 = b z^-1: S_{U1}, then S_{U0}^H, S_{U0}^V.
-__device__ __forceinline__ void rd_update(Row<float>& X, Carry3& C, float b, float bb) {
+template <int QL>
+__device__ __forceinline__ void rd_update(Row<float, QL>& X, const Carry3<QL>& C, Carry3<QL>& N, float b,
+                                          float bb) {
     float l2[QL], l4[QL];
     left_of(X.c2, l2);
     left_of(X.c4, l4);
-    Carry3 n;
 #pragma unroll
     for (int q = 0; q < QL; ++q) {
-        n.c3[q] = X.c3[q];
-        n.c4[q] = X.c4[q];
-        n.l4[q] = l4[q];
+        N.c3[q] = X.c3[q];
+        N.c4[q] = X.c4[q];
+        N.l4[q] = l4[q];
         float c1 = fmaf(b, l2[q], X.c1[q]);       // U1 c2
         c1 = fmaf(b, C.c3[q], c1);                // U1* c3
         c1 = fmaf(bb, C.l4[q], c1);               // U1 U1* c4
@@ -141,12 +182,13 @@ __device__ __forceinline__ void rd_update(Row<float>& X, Carry3& C, float b, flo
         X.c2[q] = c2;
         X.c3[q] = c3;
     }
-    C = n;
 }
 
 // inverse of rd_update: undo S_{U0}^V, S_{U0}^H inside the quad, then S_{-U1}
 // (its pre-step operands are the post-undo values of the neighbours).
-__device__ __forceinline__ void rdi_update(Row<float>& X, Carry3& C, float b, float bb) {
+template <int QL>
+__device__ __forceinline__ void rdi_update(Row<float, QL>& X, const Carry3<QL>& C, Carry3<QL>& N, float b,
+                                           float bb) {
 #pragma unroll
     for (int q = 0; q < QL; ++q) {
         X.c1[q] = fmaf(-b, X.c3[q], X.c1[q]);
@@ -157,23 +199,22 @@ __device__ __forceinline__ void rdi_update(Row<float>& X, Carry3& C, float b, fl
     float l2[QL], l4[QL];
     left_of(X.c2, l2);
     left_of(X.c4, l4);
-    Carry3 n;
 #pragma unroll
     for (int q = 0; q < QL; ++q) {
-        n.c3[q] = X.c3[q];
-        n.c4[q] = X.c4[q];
-        n.l4[q] = l4[q];
+        N.c3[q] = X.c3[q];
+        N.c4[q] = X.c4[q];
+        N.l4[q] = l4[q];
         float c1 = fmaf(-b, l2[q], X.c1[q]);
         c1 = fmaf(-b, C.c3[q], c1);
         X.c1[q] = fmaf(bb, C.l4[q], c1);
         X.c2[q] = fmaf(-b, C.c4[q], X.c2[q]);
         X.c3[q] = fmaf(-b, l4[q], X.c3[q]);
     }
-    C = n;
 }
 
 // inverse of rd_predict, part 1 (inside the quad): undo T_{P0}^V, T_{P0}^H.
-__device__ __forceinline__ void rdi_predict_local(Row<float>& X, float a) {
+template <int QL>
+__device__ __forceinline__ void rdi_predict_local(Row<float, QL>& X, float a) {
 #pragma unroll
     for (int q = 0; q < QL; ++q) {
         X.c4[q] = fmaf(-a, X.c2[q], X.c4[q]);
@@ -184,7 +225,8 @@ __device__ __forceinline__ void rdi_predict_local(Row<float>& X, float a) {
 }
 
 // inverse of rd_predict, part 2: T_{-P1}; the row below must have had part 1.
-__device__ __forceinline__ void rdi_predict_exch(Row<float>& X, const Row<float>& D, float a, float aa) {
+template <int QL>
+__device__ __forceinline__ void rdi_predict_exch(Row<float, QL>& X, const Row<float, QL>& D, float a, float aa) {
     float r1[QL], r3[QL], dr1[QL];
     right_of(X.c1, r1);
     right_of(X.c3, r3);
@@ -200,8 +242,8 @@ __device__ __forceinline__ void rdi_predict_exch(Row<float>& X, const Row<float>
 }
 
 // --- separable lifting (Background) -----------------------------------------
-template <class CT>
-__device__ __forceinline__ void sp_th(Row<CT>& X, float a) {  // T_P^H
+template <int QL>
+__device__ __forceinline__ void sp_th(Row<float, QL>& X, float a) {  // T_P^H
     float r1[QL], r3[QL];
     right_of(X.c1, r1);
     right_of(X.c3, r3);
@@ -211,14 +253,16 @@ __device__ __forceinline__ void sp_th(Row<CT>& X, float a) {  // T_P^H
         X.c4[q] = fmaf(a, X.c3[q] + r3[q], X.c4[q]);
     }
 }
-__device__ __forceinline__ void sp_tv(Row<float>& X, const Row<float>& D, float a) {  // T_P^V
+template <int QL>
+__device__ __forceinline__ void sp_tv(Row<float, QL>& X, const Row<float, QL>& D, float a) {  // T_P^V
 #pragma unroll
     for (int q = 0; q < QL; ++q) {
         X.c3[q] = fmaf(a, X.c1[q] + D.c1[q], X.c3[q]);
         X.c4[q] = fmaf(a, X.c2[q] + D.c2[q], X.c4[q]);
     }
 }
-__device__ __forceinline__ void sp_sh(Row<float>& X, float b) {  // S_U^H
+template <int QL>
+__device__ __forceinline__ void sp_sh(Row<float, QL>& X, float b) {  // S_U^H
     float l2[QL], l4[QL];
     left_of(X.c2, l2);
     left_of(X.c4, l4);
@@ -228,25 +272,29 @@ __device__ __forceinline__ void sp_sh(Row<float>& X, float b) {  // S_U^H
         X.c3[q] = fmaf(b, l4[q] + X.c4[q], X.c3[q]);
     }
 }
-__device__ __forceinline__ void sp_sv(Row<float>& X, Carry2<float>& C, float b) {  // S_U^V
+template <int QL>
+__device__ __forceinline__ void sp_sv(Row<float, QL>& X, const Carry2<float, QL>& C, Carry2<float, QL>& N,
+                                      float b) {  // S_U^V
 #pragma unroll
     for (int q = 0; q < QL; ++q) {
         X.c1[q] = fmaf(b, C.c3[q] + X.c3[q], X.c1[q]);
         X.c2[q] = fmaf(b, C.c4[q] + X.c4[q], X.c2[q]);
-        C.c3[q] = X.c3[q];
-        C.c4[q] = X.c4[q];
+        N.c3[q] = X.c3[q];
+        N.c4[q] = X.c4[q];
     }
 }
 
 // scaling: per axis low * zeta, high / zeta
-__device__ __forceinline__ void scale97(Row<float>& X) {
+template <int QL>
+__device__ __forceinline__ void scale97(Row<float, QL>& X) {
 #pragma unroll
     for (int q = 0; q < QL; ++q) {
         X.c1[q] *= C97::ZZ;
         X.c4[q] *= C97::IZZ;
     }
 }
-__device__ __forceinline__ void unscale97(Row<float>& X) {
+template <int QL>
+__device__ __forceinline__ void unscale97(Row<float, QL>& X) {
 #pragma unroll
     for (int q = 0; q < QL; ++q) {
         X.c1[q] *= C97::IZZ;
@@ -255,98 +303,116 @@ __device__ __forceinline__ void unscale97(Row<float>& X) {
 }
 
 // ---------------------------------------------------------- 9/7 pipelines
-// arrive(r0) takes the newest quad row and returns the finished row LAG
-// quad rows above it.
-template <int SCHEME>
+// slot<PH>() is where arrival PH's quad row is loaded; step<PH>(row) runs the
+// steps due at that arrival and returns the finished row LAG rows above it.
+template <int SCHEME, int QL>
 struct Fwd97 {
     static constexpr int LAG = 2;
     using CT = float;
-    Row<float> r1, r2;
-    Carry3 k0, k1;
-    Carry2<float> s0, s1;
+    using R = Row<float, QL>;
+    R rw[3];
+    Carry3<QL> ka[2], kb[2];
+    Carry2<float, QL> sa[2], sb[2];
     __device__ __forceinline__ void init() {
-        zero_row(r1);
-        zero_row(r2);
-        zero_carry(k0);
-        zero_carry(k1);
-        zero_carry(s0);
-        zero_carry(s1);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) zero_row(rw[i]);
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            zero_carry(ka[i]);
+            zero_carry(kb[i]);
+            zero_carry(sa[i]);
+            zero_carry(sb[i]);
+        }
     }
-    __device__ __forceinline__ Row<float> arrive(const Row<float>& r0in, int /*row*/) {
-        Row<float> r0 = r0in;
-        if (SCHEME == SCHEME_NONSEP) {
+    template <int PH>
+    __device__ __forceinline__ R& slot() {
+        return rw[PH % 3];
+    }
+    template <int PH>
+    __device__ __forceinline__ R& step(int /*row*/) {
+        R& r0 = rw[PH % 3];
+        R& r1 = rw[(PH + 2) % 3];
+        R& r2 = rw[(PH + 1) % 3];
+        constexpr int c = PH & 1, n = c ^ 1;
+        if constexpr (SCHEME == SCHEME_NONSEP) {
             ns_predict(r1, r0, C97::A, C97::AA);
-            ns_update(r1, k0, C97::B, C97::BB);
+            ns_update(r1, ka[c], ka[n], C97::B, C97::BB);
             ns_predict(r2, r1, C97::G, C97::GG);
-            ns_update(r2, k1, C97::D, C97::DD);
-        } else if (SCHEME == SCHEME_REDUCED) {
+            ns_update(r2, kb[c], kb[n], C97::D, C97::DD);
+        } else if constexpr (SCHEME == SCHEME_REDUCED) {
             rd_predict(r1, r0, C97::A, C97::AA);
-            rd_update(r1, k0, C97::B, C97::BB);
+            rd_update(r1, ka[c], ka[n], C97::B, C97::BB);
             rd_predict(r2, r1, C97::G, C97::GG);
-            rd_update(r2, k1, C97::D, C97::DD);
+            rd_update(r2, kb[c], kb[n], C97::D, C97::DD);
         } else {
             sp_th(r0, C97::A);
             sp_tv(r1, r0, C97::A);
             sp_sh(r1, C97::B);
-            sp_sv(r1, s0, C97::B);
+            sp_sv(r1, sa[c], sa[n], C97::B);
             sp_th(r1, C97::G);
             sp_tv(r2, r1, C97::G);
             sp_sh(r2, C97::D);
-            sp_sv(r2, s1, C97::D);
+            sp_sv(r2, sb[c], sb[n], C97::D);
         }
-        Row<float> out = r2;
-        scale97(out);
-        r2 = r1;
-        r1 = r0;
-        return out;
+        scale97(r2);
+        return r2;
     }
 };
 
 // inverse: unscale, then for each pair in reverse order S_{-U}, T_{-P}
-template <int SCHEME>
+template <int SCHEME, int QL>
 struct Inv97 {
     static constexpr int LAG = 2;
     using CT = float;
-    Row<float> r1, r2;
-    Carry3 k0, k1;
-    Carry2<float> s0, s1;
+    using R = Row<float, QL>;
+    R rw[3];
+    Carry3<QL> ka[2], kb[2];
+    Carry2<float, QL> sa[2], sb[2];
     __device__ __forceinline__ void init() {
-        zero_row(r1);
-        zero_row(r2);
-        zero_carry(k0);
-        zero_carry(k1);
-        zero_carry(s0);
-        zero_carry(s1);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) zero_row(rw[i]);
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            zero_carry(ka[i]);
+            zero_carry(kb[i]);
+            zero_carry(sa[i]);
+            zero_carry(sb[i]);
+        }
     }
-    __device__ __forceinline__ Row<float> arrive(const Row<float>& r0in, int /*row*/) {
-        Row<float> r0 = r0in;
+    template <int PH>
+    __device__ __forceinline__ R& slot() {
+        return rw[PH % 3];
+    }
+    template <int PH>
+    __device__ __forceinline__ R& step(int /*row*/) {
+        R& r0 = rw[PH % 3];
+        R& r1 = rw[(PH + 2) % 3];
+        R& r2 = rw[(PH + 1) % 3];
+        constexpr int c = PH & 1, n = c ^ 1;
         unscale97(r0);
-        if (SCHEME == SCHEME_NONSEP) {
-            ns_update(r0, k1, -C97::D, C97::DD);
+        if constexpr (SCHEME == SCHEME_NONSEP) {
+            ns_update(r0, kb[c], kb[n], -C97::D, C97::DD);
             ns_predict(r1, r0, -C97::G, C97::GG);
-            ns_update(r1, k0, -C97::B, C97::BB);
+            ns_update(r1, ka[c], ka[n], -C97::B, C97::BB);
             ns_predict(r2, r1, -C97::A, C97::AA);
-        } else if (SCHEME == SCHEME_REDUCED) {
-            rdi_update(r0, k1, C97::D, C97::DD);
+        } else if constexpr (SCHEME == SCHEME_REDUCED) {
+            rdi_update(r0, kb[c], kb[n], C97::D, C97::DD);
             rdi_predict_local(r0, C97::G);
             rdi_predict_exch(r1, r0, C97::G, C97::GG);
-            rdi_update(r1, k0, C97::B, C97::BB);
+            rdi_update(r1, ka[c], ka[n], C97::B, C97::BB);
             rdi_predict_local(r1, C97::A);
             rdi_predict_exch(r2, r1, C97::A, C97::AA);
         } else {
-            sp_sv(r0, s1, -C97::D);
+            sp_sv(r0, sb[c], sb[n], -C97::D);
             sp_sh(r0, -C97::D);
             sp_tv(r1, r0, -C97::G);
             sp_th(r1, -C97::G);
-            sp_sv(r1, s0, -C97::B);
+            sp_sv(r1, sa[c], sa[n], -C97::B);
             sp_sh(r1, -C97::B);
             sp_tv(r2, r1, -C97::A);
             sp_th(r2, -C97::A);
         }
-        Row<float> out = r2;
-        r2 = r1;
-        r1 = r0;
-        return out;
+        return r2;
     }
 };
 
@@ -376,7 +442,8 @@ __device__ __forceinline__ AxisW axis_weights(int j, int n) {
 }
 
 // S_U^T on row X (row index i) with the row below D: predict-shaped.
-__device__ __forceinline__ void adj_st(Row<float>& X, const Row<float>& D, float b, float bb,
+template <int QL>
+__device__ __forceinline__ void adj_st(Row<float, QL>& X, const Row<float, QL>& D, float b, float bb,
                                        const AxisW (&hw)[QL], const AxisW& vw) {
     float r1[QL], r3[QL], dr1[QL];
     right_of(X.c1, r1);
@@ -397,17 +464,17 @@ __device__ __forceinline__ void adj_st(Row<float>& X, const Row<float>& D, float
 }
 
 // T_P^T on row X with the carry C of the row above: update-shaped.
-__device__ __forceinline__ void adj_tt(Row<float>& X, Carry3& C, float a, float aa, const AxisW (&hw)[QL],
-                                       const AxisW& vw) {
+template <int QL>
+__device__ __forceinline__ void adj_tt(Row<float, QL>& X, const Carry3<QL>& C, Carry3<QL>& N, float a, float aa,
+                                       const AxisW (&hw)[QL], const AxisW& vw) {
     float l2[QL], l4[QL];
     left_of(X.c2, l2);
     left_of(X.c4, l4);
-    Carry3 n;
 #pragma unroll
     for (int q = 0; q < QL; ++q) {
-        n.c3[q] = X.c3[q];
-        n.c4[q] = X.c4[q];
-        n.l4[q] = l4[q];
+        N.c3[q] = X.c3[q];
+        N.c4[q] = X.c4[q];
+        N.l4[q] = l4[q];
         const float h2 = hw[q].pL * l2[q] + hw[q].pO * X.c2[q];      // P^T c2
         const float v3 = vw.pL * C.c3[q] + vw.pO * X.c3[q];          // P*^T c3
         const float hu4 = hw[q].pL * C.l4[q] + hw[q].pO * C.c4[q];   // P^T c4, row above
@@ -418,35 +485,44 @@ __device__ __forceinline__ void adj_tt(Row<float>& X, Carry3& C, float a, float 
         X.c2[q] = fmaf(a, v4, X.c2[q]);
         X.c3[q] = fmaf(a, hx4, X.c3[q]);
     }
-    C = n;
 }
 
+template <int QL>
 struct Adj97 {
     static constexpr int LAG = 2;
     using CT = float;
-    Row<float> r1, r2;
-    Carry3 k0, k1;
+    using R = Row<float, QL>;
+    R rw[3];
+    Carry3<QL> ka[2], kb[2];
     AxisW hw[QL];  // horizontal weights of the lane's quads
     int h;         // image height of this level
     __device__ __forceinline__ void init() {
-        zero_row(r1);
-        zero_row(r2);
-        zero_carry(k0);
-        zero_carry(k1);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) zero_row(rw[i]);
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            zero_carry(ka[i]);
+            zero_carry(kb[i]);
+        }
     }
-    // `row` is the quad-row index of r0in
-    __device__ __forceinline__ Row<float> arrive(const Row<float>& r0in, int row) {
-        Row<float> r0 = r0in;
+    template <int PH>
+    __device__ __forceinline__ R& slot() {
+        return rw[PH % 3];
+    }
+    // `row` is the quad-row index of the newest row
+    template <int PH>
+    __device__ __forceinline__ R& step(int row) {
+        R& r0 = rw[PH % 3];
+        R& r1 = rw[(PH + 2) % 3];
+        R& r2 = rw[(PH + 1) % 3];
+        constexpr int c = PH & 1, n = c ^ 1;
         scale97(r0);
         const AxisW v1 = axis_weights(row - 1, h), v2 = axis_weights(row - 2, h);
         adj_st(r1, r0, C97::D, C97::DD, hw, v1);
-        adj_tt(r1, k0, C97::G, C97::GG, hw, v1);
+        adj_tt(r1, ka[c], ka[n], C97::G, C97::GG, hw, v1);
         adj_st(r2, r1, C97::B, C97::BB, hw, v2);
-        adj_tt(r2, k1, C97::A, C97::AA, hw, v2);
-        Row<float> out = r2;
-        r2 = r1;
-        r1 = r0;
-        return out;
+        adj_tt(r2, kb[c], kb[n], C97::A, C97::AA, hw, v2);
+        return r2;
     }
 };
 
@@ -456,7 +532,8 @@ struct Adj97 {
 
 // fused T_P = T_P^V T_P^H in one step: the neighbour below has its c2 taken
 // after T^H, recomputed here from its pre-step values (the analogue of PP*).
-__device__ __forceinline__ void int_ns_predict(Row<int>& X, const Row<int>& D) {
+template <int QL>
+__device__ __forceinline__ void int_ns_predict(Row<int, QL>& X, const Row<int, QL>& D) {
     int r1[QL], r3[QL], dr1[QL];
     right_of(X.c1, r1);
     right_of(X.c3, r3);
@@ -473,7 +550,8 @@ __device__ __forceinline__ void int_ns_predict(Row<int>& X, const Row<int>& D) {
 }
 
 // fused S_U = S_U^V S_U^H; the carry holds the row above after its update.
-__device__ __forceinline__ void int_ns_update(Row<int>& X, Carry2<int>& C) {
+template <int QL>
+__device__ __forceinline__ void int_ns_update(Row<int, QL>& X, const Carry2<int, QL>& C, Carry2<int, QL>& N) {
     int l2[QL], l4[QL];
     left_of(X.c2, l2);
     left_of(X.c4, l4);
@@ -486,17 +564,17 @@ __device__ __forceinline__ void int_ns_update(Row<int>& X, Carry2<int>& C) {
         X.c1[q] = c1;
         X.c2[q] = c2;
         X.c3[q] = c3;
-        C.c3[q] = c3;
-        C.c4[q] = X.c4[q];
+        N.c3[q] = c3;
+        N.c4[q] = X.c4[q];
     }
 }
 
-__device__ __forceinline__ void int_ns_update_inv(Row<int>& X, Carry2<int>& C) {
-    Carry2<int> n;
+template <int QL>
+__device__ __forceinline__ void int_ns_update_inv(Row<int, QL>& X, const Carry2<int, QL>& C, Carry2<int, QL>& N) {
 #pragma unroll
     for (int q = 0; q < QL; ++q) {
-        n.c3[q] = X.c3[q];
-        n.c4[q] = X.c4[q];
+        N.c3[q] = X.c3[q];
+        N.c4[q] = X.c4[q];
         X.c2[q] -= (C.c4[q] + X.c4[q] + 2) >> 2;
         X.c1[q] -= (C.c3[q] + X.c3[q] + 2) >> 2;
     }
@@ -508,10 +586,10 @@ __device__ __forceinline__ void int_ns_update_inv(Row<int>& X, Carry2<int>& C) {
         X.c1[q] -= (l2[q] + X.c2[q] + 2) >> 2;
         X.c3[q] -= (l4[q] + X.c4[q] + 2) >> 2;
     }
-    C = n;
 }
 
-__device__ __forceinline__ void int_ns_predict_inv(Row<int>& X, const Row<int>& D) {
+template <int QL>
+__device__ __forceinline__ void int_ns_predict_inv(Row<int, QL>& X, const Row<int, QL>& D) {
 #pragma unroll
     for (int q = 0; q < QL; ++q) {
         X.c4[q] += (X.c2[q] + D.c2[q]) >> 1;
@@ -527,7 +605,8 @@ __device__ __forceinline__ void int_ns_predict_inv(Row<int>& X, const Row<int>& 
     }
 }
 
-__device__ __forceinline__ void int_sp_th(Row<int>& X, int sgn) {
+template <int QL>
+__device__ __forceinline__ void int_sp_th(Row<int, QL>& X, int sgn) {
     int r1[QL], r3[QL];
     right_of(X.c1, r1);
     right_of(X.c3, r3);
@@ -537,14 +616,16 @@ __device__ __forceinline__ void int_sp_th(Row<int>& X, int sgn) {
         X.c4[q] -= sgn * ((X.c3[q] + r3[q]) >> 1);
     }
 }
-__device__ __forceinline__ void int_sp_tv(Row<int>& X, const Row<int>& D, int sgn) {
+template <int QL>
+__device__ __forceinline__ void int_sp_tv(Row<int, QL>& X, const Row<int, QL>& D, int sgn) {
 #pragma unroll
     for (int q = 0; q < QL; ++q) {
         X.c3[q] -= sgn * ((X.c1[q] + D.c1[q]) >> 1);
         X.c4[q] -= sgn * ((X.c2[q] + D.c2[q]) >> 1);
     }
 }
-__device__ __forceinline__ void int_sp_sh(Row<int>& X, int sgn) {
+template <int QL>
+__device__ __forceinline__ void int_sp_sh(Row<int, QL>& X, int sgn) {
     int l2[QL], l4[QL];
     left_of(X.c2, l2);
     left_of(X.c4, l4);
@@ -554,67 +635,84 @@ __device__ __forceinline__ void int_sp_sh(Row<int>& X, int sgn) {
         X.c3[q] += sgn * ((l4[q] + X.c4[q] + 2) >> 2);
     }
 }
-__device__ __forceinline__ void int_sp_sv(Row<int>& X, Carry2<int>& C, int sgn) {
+template <int QL>
+__device__ __forceinline__ void int_sp_sv(Row<int, QL>& X, const Carry2<int, QL>& C, Carry2<int, QL>& N, int sgn) {
 #pragma unroll
     for (int q = 0; q < QL; ++q) {
         X.c1[q] += sgn * ((C.c3[q] + X.c3[q] + 2) >> 2);
         X.c2[q] += sgn * ((C.c4[q] + X.c4[q] + 2) >> 2);
-        C.c3[q] = X.c3[q];
-        C.c4[q] = X.c4[q];
+        N.c3[q] = X.c3[q];
+        N.c4[q] = X.c4[q];
     }
 }
 
-template <int SCHEME>
+template <int SCHEME, int QL>
 struct Fwd53 {
     static constexpr int LAG = 1;
     using CT = int;
-    Row<int> r1;
-    Carry2<int> k0;
+    using R = Row<int, QL>;
+    R rw[2];
+    Carry2<int, QL> k[2];
     __device__ __forceinline__ void init() {
-        zero_row(r1);
-        zero_carry(k0);
+        zero_row(rw[0]);
+        zero_row(rw[1]);
+        zero_carry(k[0]);
+        zero_carry(k[1]);
     }
-    __device__ __forceinline__ Row<int> arrive(const Row<int>& r0in, int /*row*/) {
-        Row<int> r0 = r0in;
-        if (SCHEME == SCHEME_SEP) {
+    template <int PH>
+    __device__ __forceinline__ R& slot() {
+        return rw[PH % 2];
+    }
+    template <int PH>
+    __device__ __forceinline__ R& step(int /*row*/) {
+        R& r0 = rw[PH % 2];
+        R& r1 = rw[(PH + 1) % 2];
+        constexpr int c = PH & 1, n = c ^ 1;
+        if constexpr (SCHEME == SCHEME_SEP) {
             int_sp_th(r0, 1);
             int_sp_tv(r1, r0, 1);
             int_sp_sh(r1, 1);
-            int_sp_sv(r1, k0, 1);
+            int_sp_sv(r1, k[c], k[n], 1);
         } else {
             int_ns_predict(r1, r0);
-            int_ns_update(r1, k0);
+            int_ns_update(r1, k[c], k[n]);
         }
-        Row<int> out = r1;
-        r1 = r0;
-        return out;
+        return r1;
     }
 };
 
-template <int SCHEME>
+template <int SCHEME, int QL>
 struct Inv53 {
     static constexpr int LAG = 1;
     using CT = int;
-    Row<int> r1;
-    Carry2<int> k0;
+    using R = Row<int, QL>;
+    R rw[2];
+    Carry2<int, QL> k[2];
     __device__ __forceinline__ void init() {
-        zero_row(r1);
-        zero_carry(k0);
+        zero_row(rw[0]);
+        zero_row(rw[1]);
+        zero_carry(k[0]);
+        zero_carry(k[1]);
     }
-    __device__ __forceinline__ Row<int> arrive(const Row<int>& r0in, int /*row*/) {
-        Row<int> r0 = r0in;
-        if (SCHEME == SCHEME_SEP) {
-            int_sp_sv(r0, k0, -1);
+    template <int PH>
+    __device__ __forceinline__ R& slot() {
+        return rw[PH % 2];
+    }
+    template <int PH>
+    __device__ __forceinline__ R& step(int /*row*/) {
+        R& r0 = rw[PH % 2];
+        R& r1 = rw[(PH + 1) % 2];
+        constexpr int c = PH & 1, n = c ^ 1;
+        if constexpr (SCHEME == SCHEME_SEP) {
+            int_sp_sv(r0, k[c], k[n], -1);
             int_sp_sh(r0, -1);
             int_sp_tv(r1, r0, -1);
             int_sp_th(r1, -1);
         } else {
-            int_ns_update_inv(r0, k0);
+            int_ns_update_inv(r0, k[c], k[n]);
             int_ns_predict_inv(r1, r0);
         }
-        Row<int> out = r1;
-        r1 = r0;
-        return out;
+        return r1;
     }
 };
 
