@@ -71,7 +71,10 @@ enum dwt2_boundary { DWT2_SYMMETRIC = 0 };
 #define DWT2_ERR_TOO_LARGE (-8)       /* beyond dwt2_forward_noalloc's scratch */
 
 /* plan flags */
-#define DWT2_FLAG_PERSISTENT 0x1u /* batch: one persistent launch for all levels */
+#define DWT2_FLAG_PERSISTENT 0x1u /* forward: one persistent launch for all images and levels */
+#define DWT2_FLAG_TEST_DROP_SIGNAL 0x100u /* test hook (persistent forward): the first queued
+                                             unit never reports completion, so its dependants
+                                             time out and dwt2_status returns DWT2_ERR_TIMEOUT */
 
 /* One image of a batch: element offset of its first pixel from the base
  * pointer, its size, and its row pitch in elements (pitch >= w).  The same
@@ -96,7 +99,11 @@ typedef struct {
  *              DWT2_SEP_LIFTING.
  *   n_images   number of images (>= 1); images is a host array of that many
  *              descriptors, copied into the plan.
- *   flags      0 or DWT2_FLAG_PERSISTENT.
+ *   flags      0 or DWT2_FLAG_PERSISTENT: dwt2_forward then runs every level of every
+ *              image in one persistent launch whose units take work from a device
+ *              queue and wait (bounded by DWT2_TIMEOUT_MS, default 2000) for the
+ *              segments of the previous level they read; the plan allocates its
+ *              queue tables at creation and the call is CUDA-graph capturable.
  * Alignment: the image (input) buffer's base pointer must be 16-byte aligned
  * and offset_elems and pitch_elems multiples of 4 (16 bytes of 4-byte
  * elements), else DWT2_ERR_MISALIGNED; coefficient buffers need only natural
@@ -134,6 +141,17 @@ int dwt2_inverse(dwt2_plan_t plan, const void* coef, void* out, void* workspace,
  * like the image / the coefficients. */
 int dwt2_adjoint(dwt2_plan_t plan, const void* coef_grad, void* in_grad, void* workspace,
                  void* stream);
+
+/* dwt2_autotune -- choose the plan's launch configuration (not in the paper).
+ * With *choice < 0: run the forward on the given buffers (same arguments as
+ * dwt2_forward) for each candidate configuration (kernel tile shape and
+ * segment height; segment height for persistent plans), a few timed calls
+ * each on the stream, keep the fastest and store its index in *choice.  With
+ * *choice >= 0: apply that candidate without timing (e.g. from a cache of an
+ * earlier run on the same GPU).  The coefficient buffer is overwritten.
+ * Synchronises the stream; not for use during graph capture. */
+int dwt2_autotune(dwt2_plan_t plan, const void* in, void* coef, void* workspace, void* stream,
+                  int* choice);
 
 /* dwt2_status -- synchronise the stream, return and clear the plan's device
  * status word: DWT2_OK, DWT2_ERR_TIMEOUT or DWT2_ERR_DEVICE_CHECK. */

@@ -26,11 +26,12 @@ DWT2_ERR_TIMEOUT = -6
 DWT2_ERR_DEVICE_CHECK = -7
 DWT2_ERR_TOO_LARGE = -8
 DWT2_FLAG_PERSISTENT = 0x1
+DWT2_FLAG_TEST_DROP_SIGNAL = 0x100
 
 # the functions the header declares (checked by the CPU test suite)
 EXPORTS = ("dwt2_plan", "dwt2_workspace_bytes", "dwt2_forward", "dwt2_inverse", "dwt2_adjoint",
-           "dwt2_status", "dwt2_profile", "dwt2_profile_read", "dwt2_forward_noalloc", "dwt2_destroy",
-           "dwt2_strerror")
+           "dwt2_autotune", "dwt2_status", "dwt2_profile", "dwt2_profile_read", "dwt2_forward_noalloc",
+           "dwt2_destroy", "dwt2_strerror")
 
 
 class dwt2_image_desc(ctypes.Structure):
@@ -66,6 +67,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         f = getattr(lib, name)
         f.argtypes = [vp, vp, vp, vp, vp]
         f.restype = ctypes.c_int
+    lib.dwt2_autotune.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int)]
+    lib.dwt2_autotune.restype = ctypes.c_int
     lib.dwt2_status.argtypes = [vp, vp]
     lib.dwt2_status.restype = ctypes.c_int
     lib.dwt2_profile.argtypes = [vp, ctypes.c_int]
@@ -123,6 +126,17 @@ def dwt2_inverse(plan: int, coef_ptr: int, out_ptr: int, ws_ptr: int = 0, stream
 
 def dwt2_adjoint(plan: int, gcoef_ptr: int, gin_ptr: int, ws_ptr: int = 0, stream: int = 0) -> None:
     _call("dwt2_adjoint", plan, gcoef_ptr, gin_ptr, ws_ptr, stream)
+
+
+def dwt2_autotune(plan: int, in_ptr: int, coef_ptr: int, ws_ptr: int = 0, stream: int = 0,
+                  choice: int = -1) -> int:
+    """Time the candidate configurations (choice < 0) or apply one; returns the choice."""
+    c = ctypes.c_int(int(choice))
+    rc = load().dwt2_autotune(ctypes.c_void_p(plan), ctypes.c_void_p(in_ptr), ctypes.c_void_p(coef_ptr),
+                              ctypes.c_void_p(ws_ptr), ctypes.c_void_p(stream), ctypes.byref(c))
+    if rc != DWT2_OK:
+        raise Dwt2Error(rc, "dwt2_autotune")
+    return int(c.value)
 
 
 def dwt2_status(plan: int, stream: int = 0) -> int:

@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -39,8 +40,8 @@ size_t dtype_size(int dt) { return (dt == DT_F16 || dt == DT_BF16) ? 2 : 4; }
 
 struct ImagePlan {
     dwt2_image_desc d;
-    std::vector<LevelGeom> lv;  // lv[l] = input geometry of level l (0-based)
-    size_t ws_off[2];           // workspace offsets of the two LL buffers
+    std::vector<LevelGeom> lv;   // lv[l] = input geometry of level l (0-based)
+    std::vector<size_t> ws_off;  // ws_off[l] = byte offset of level l's LL band (l < levels-1)
 };
 
 // decomposition of one level into (strip, segment) units
@@ -147,6 +148,14 @@ struct dwt2_plan_s {
     int fwd_bps, inv_bps;  // resident blocks per SM of the forward / inverse kernels
     int seg_override, balanced_env;
     uint64_t timeout_ns;
+    // persistent forward: descriptors, queue-ordered units, counters + queue word
+    bool persistent;
+    int pml_bps, pml_seg, pml_force_cpasync;
+    std::vector<PmlDesc> h_descs;  // host copy (TMA maps are encoded per call from it)
+    PmlDesc* d_descs;
+    PmlUnit* d_units;
+    unsigned* d_counters;  // n_counters segment counters followed by the queue word
+    int n_units, n_counters;
     // profiling: a ring of PROF_RING calls, one event pair per level each
     std::vector<cudaEvent_t> ev0, ev1;  // [slot * levels + level]
     bool prof_on;
@@ -160,6 +169,171 @@ void prof_mark(dwt2_plan_t p, int level, bool start, cudaStream_t s) {
     const int slot = p->prof_calls % PROF_RING;
     cudaEventRecord(start ? p->ev0[slot * p->levels + level] : p->ev1[slot * p->levels + level], s);
 }
+}  // namespace
+
+namespace {
+
+// Queue order of the persistent forward.  Units of level 0 keep their natural
+// order (image, segment, strip); a unit of level l gets the latest position of
+// the level l-1 units it reads plus `lag`, about one GPU round of units, so
+// that its inputs are normally complete when it is dequeued.
+constexpr int PML_SEG_DEFAULT = 32;
+
+int build_persistent(dwt2_plan_t p) {
+    const int bps = pml_blocks_per_sm(p->wavelet, p->scheme, p->coef_dtype);
+    if (bps <= 0) return DWT2_ERR_CUDA;
+    p->pml_bps = bps;
+    const int64_t lag = int64_t(p->sm_count) * bps * PML_NW * 5 / 4;
+    const int L = p->levels;
+    const size_t csz = dtype_size(p->coef_dtype);
+    std::vector<PmlDesc> descs;
+    std::vector<PmlUnit> units;
+    std::vector<int64_t> keys;
+    std::vector<int> levels_of;
+    int ctr = 0;
+    for (size_t i = 0; i < p->imgs.size(); ++i) {
+        const ImagePlan& ip = p->imgs[i];
+        std::vector<int64_t> seg_key_prev;  // latest key of each segment of level l-1
+        int prev_base = -1, prev_need = 0, prev_seg = 1;
+        for (int l = 0; l < L; ++l) {
+            const LevelGeom& g = ip.lv[l];
+            PmlDesc d;
+            d.h = g.h, d.w = g.w, d.hq = g.hq, d.wq = g.wq, d.hh = g.hh, d.wh = g.wh;
+            d.n_strips = (g.wq + fwd_out_quads(FwdCfg{PML_QL, PML_QR, PML_NST, PML_NW}) - 1) /
+                         fwd_out_quads(FwdCfg{PML_QL, PML_QR, PML_NST, PML_NW});
+            d.seg_rows = std::min(p->pml_seg, g.hq);
+            const int n_segs = (g.hq + d.seg_rows - 1) / d.seg_rows;
+            d.src_is_ws = l > 0;
+            d.src_off = (l == 0) ? ip.d.offset_elems : int64_t(ip.ws_off[l - 1] / 4);
+            d.src_pitch = (l == 0) ? ip.d.pitch_elems : round4(ip.lv[l - 1].wq);
+            d.coef_off = ip.d.offset_elems;
+            d.coef_pitch = ip.d.pitch_elems;
+            const bool last = (l == L - 1);
+            d.ll_is_ct = !last;
+            d.ll_off = last ? ip.d.offset_elems : int64_t(ip.ws_off[l] / 4);
+            d.ll_pitch = last ? ip.d.pitch_elems : round4(g.wq);
+            const bool cvec = (ip.d.pitch_elems % 2 == 0) && ((ip.d.offset_elems * csz) % (2 * csz) == 0);
+            d.vec_lo = cvec;
+            d.vec_hi = cvec && (g.wq % 2 == 0);
+            d.vec_ll = last ? cvec : 1;
+            d.ctr_base = ctr;
+            d.dep_base = prev_base;
+            d.dep_need = prev_need;
+            const int di = int(descs.size());
+            descs.push_back(d);
+            std::vector<int64_t> seg_key(n_segs, 0);
+            for (int gseg = 0; gseg < n_segs; ++gseg) {
+                const int R0 = gseg * d.seg_rows, R1 = std::min(R0 + d.seg_rows, g.hq);
+                int dlo = 0, dhi = -1;
+                int64_t key = int64_t(keys.size());
+                if (l > 0) {
+                    // input rows this unit can touch (warm-up, pipeline lag, stage
+                    // rounding, mirrored rows), as rows of the level l-1 low-low band
+                    int lo = std::max(0, 2 * R0 - 4);
+                    const int hi = std::min(g.h, 2 * R1 + 8);
+                    if (2 * R1 + 8 > g.h) lo = std::max(0, std::min(lo, g.h - 9));
+                    dlo = lo / prev_seg;
+                    dhi = (hi - 1) / prev_seg;
+                    int64_t kmax = 0;
+                    for (int q = dlo; q <= dhi; ++q) kmax = std::max(kmax, seg_key_prev[q]);
+                    key = kmax + lag;
+                }
+                for (int s = 0; s < d.n_strips; ++s) {
+                    units.push_back(PmlUnit{di, s, gseg, dlo, dhi});
+                    keys.push_back(l == 0 ? int64_t(keys.size()) : key);
+                    levels_of.push_back(l);
+                }
+                seg_key[gseg] = keys.back();
+            }
+            seg_key_prev.swap(seg_key);
+            prev_base = ctr;
+            prev_need = d.n_strips;
+            prev_seg = d.seg_rows;
+            ctr += n_segs;
+        }
+    }
+    // stable sort by key (ties: lower level first)
+    std::vector<int> order(units.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = int(i);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        if (keys[a] != keys[b]) return keys[a] < keys[b];
+        return levels_of[a] < levels_of[b];
+    });
+    std::vector<PmlUnit> sorted(units.size());
+    for (size_t i = 0; i < order.size(); ++i) sorted[i] = units[order[i]];
+    p->n_units = int(sorted.size());
+    p->n_counters = ctr;
+    p->h_descs = descs;
+    if (p->d_descs) cudaFree(p->d_descs);
+    if (p->d_units) cudaFree(p->d_units);
+    if (p->d_counters) cudaFree(p->d_counters);
+    p->d_descs = nullptr;
+    p->d_units = nullptr;
+    p->d_counters = nullptr;
+    if (cudaMalloc(&p->d_descs, descs.size() * sizeof(PmlDesc)) != cudaSuccess ||
+        cudaMalloc(&p->d_units, sorted.size() * sizeof(PmlUnit)) != cudaSuccess ||
+        cudaMalloc(&p->d_counters, (size_t(ctr) + 1) * sizeof(unsigned)) != cudaSuccess ||
+        cudaMemcpy(p->d_descs, descs.data(), descs.size() * sizeof(PmlDesc), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(p->d_units, sorted.data(), sorted.size() * sizeof(PmlUnit), cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        return DWT2_ERR_CUDA;
+    }
+    return DWT2_OK;
+}
+
+int forward_persistent(dwt2_plan_t p, const void* in, void* coef, void* workspace, cudaStream_t s) {
+    const size_t csz = dtype_size(p->coef_dtype);
+    if (cudaMemsetAsync(p->d_counters, 0, (size_t(p->n_counters) + 1) * sizeof(unsigned), s) != cudaSuccess)
+        return DWT2_ERR_CUDA;
+    // the launch block is large (tensor maps); keep it off the stack
+    std::unique_ptr<PmlLaunch> lp(new (std::nothrow) PmlLaunch());
+    if (!lp) return DWT2_ERR_INVALID_ARG;
+    PmlParams& pp = lp->base;
+    pp.in = in;
+    pp.coef = coef;
+    pp.ws = workspace;
+    pp.descs = p->d_descs;
+    pp.units = p->d_units;
+    pp.n_units = p->n_units;
+    pp.counters = p->d_counters;
+    pp.queue = p->d_counters + p->n_counters;
+    pp.coef_vec = aligned(coef, 2 * csz);
+    pp.test_drop_signal = (p->flags & DWT2_FLAG_TEST_DROP_SIGNAL) != 0;
+    pp.status = p->d_status;
+    pp.timeout_ns = p->timeout_ns;
+    lp->use_tma = int(p->h_descs.size()) <= PML_TMA_MAX_DESCS && !p->pml_force_cpasync;
+    if (lp->use_tma) {
+        const bool is_int = p->wavelet == DWT2_CDF53_INT;
+        const int bw = 64 * PML_QL;
+        for (size_t i = 0; i < p->h_descs.size(); ++i) {
+            const PmlDesc& d = p->h_descs[i];
+            const char* base = d.src_is_ws ? static_cast<const char*>(workspace) : static_cast<const char*>(in);
+            const void* src = base + d.src_off * 4;
+            int rc = encode_map(&lp->maps[2 * i], src, d.w, d.h, d.src_pitch, bw, 2 * PML_QR, is_int);
+            if (rc == DWT2_OK) rc = encode_map(&lp->maps[2 * i + 1], src, d.w, d.h, d.src_pitch, bw, 1, is_int);
+            if (rc != DWT2_OK) return rc;
+        }
+    }
+    const int grid = p->sm_count * p->pml_bps;
+    prof_mark(p, 0, true, s);
+    int e;
+    switch (p->coef_dtype) {
+        case DWT2_F32: e = launch_pml_f32(p->wavelet, p->scheme, *lp, grid, s); break;
+        case DWT2_F16: e = launch_pml_f16(p->wavelet, p->scheme, *lp, grid, s); break;
+        case DWT2_BF16: e = launch_pml_bf16(p->wavelet, p->scheme, *lp, grid, s); break;
+        default: e = launch_pml_i32(p->wavelet, p->scheme, *lp, grid, s); break;
+    }
+    // the whole pyramid is one launch: it is timed as level 0; the other levels read 0
+    prof_mark(p, 0, false, s);
+    for (int l = 1; l < p->levels; ++l) {
+        prof_mark(p, l, true, s);
+        prof_mark(p, l, false, s);
+    }
+    if (p->prof_on) ++p->prof_calls;
+    return e == cudaSuccess ? DWT2_OK : DWT2_ERR_CUDA;
+}
+
 }  // namespace
 
 extern "C" {
@@ -190,7 +364,7 @@ int dwt2_plan(dwt2_plan_t* out, int wavelet, int levels, int boundary, int in_dt
     if (scheme < DWT2_NONSEP || scheme > DWT2_SEP_LIFTING) return DWT2_ERR_INVALID_ARG;
     if (in_dtype < DWT2_F32 || in_dtype > DWT2_I32 || coef_dtype < DWT2_F32 || coef_dtype > DWT2_I32)
         return DWT2_ERR_INVALID_ARG;
-    if (flags & ~(DWT2_FLAG_PERSISTENT)) return DWT2_ERR_INVALID_ARG;
+    if (flags & ~(DWT2_FLAG_PERSISTENT | DWT2_FLAG_TEST_DROP_SIGNAL)) return DWT2_ERR_INVALID_ARG;
     if (wavelet == DWT2_CDF97) {
         if (in_dtype != DWT2_F32 || coef_dtype == DWT2_I32) return DWT2_ERR_UNSUPPORTED;
     } else {
@@ -212,16 +386,13 @@ int dwt2_plan(dwt2_plan_t* out, int wavelet, int levels, int boundary, int in_dt
             h = (h + 1) / 2;
             w = (w + 1) / 2;
         }
-        // LL of level l (0-based, l < levels-1) goes to buffer l % 2
-        size_t need[2] = {0, 0};
+        // the LL band of every level but the last has its own buffer, so that
+        // levels may run concurrently (persistent launch)
         for (int l = 0; l + 1 < levels; ++l) {
             const LevelGeom& g = ip.lv[l];
-            need[l % 2] = std::max(need[l % 2], size_t(g.hq) * size_t(round4(g.wq)) * 4);
+            ip.ws_off.push_back(ws);
+            ws += align256(size_t(g.hq) * size_t(round4(g.wq)) * 4);
         }
-        ip.ws_off[0] = ws;
-        ws += align256(need[0]);
-        ip.ws_off[1] = ws;
-        ws += align256(need[1]);
     }
     dwt2_plan_s* p = new (std::nothrow) dwt2_plan_s();
     if (!p) return DWT2_ERR_INVALID_ARG;
@@ -254,6 +425,22 @@ int dwt2_plan(dwt2_plan_t* out, int wavelet, int levels, int boundary, int in_dt
         cudaGetLastError();
         return DWT2_ERR_CUDA;
     }
+    p->persistent = (flags & DWT2_FLAG_PERSISTENT) != 0;
+    p->d_descs = nullptr;
+    p->d_units = nullptr;
+    p->d_counters = nullptr;
+    p->n_units = p->n_counters = 0;
+    p->pml_bps = 0;
+    p->pml_seg = env_int("DWT2_PML_SEG_ROWS", PML_SEG_DEFAULT);
+    p->pml_force_cpasync = env_int("DWT2_PML_CPASYNC", 0);
+    if (p->pml_seg < 4) p->pml_seg = PML_SEG_DEFAULT;
+    if (p->persistent) {
+        const int rc = build_persistent(p);
+        if (rc != DWT2_OK) {
+            dwt2_destroy(p);
+            return rc;
+        }
+    }
     *out = p;
     return DWT2_OK;
 }
@@ -263,6 +450,9 @@ size_t dwt2_workspace_bytes(dwt2_plan_t p) { return p ? p->ws_bytes : 0; }
 void dwt2_destroy(dwt2_plan_t p) {
     if (!p) return;
     if (p->d_status) cudaFree(p->d_status);
+    if (p->d_descs) cudaFree(p->d_descs);
+    if (p->d_units) cudaFree(p->d_units);
+    if (p->d_counters) cudaFree(p->d_counters);
     for (cudaEvent_t e : p->ev0) cudaEventDestroy(e);
     for (cudaEvent_t e : p->ev1) cudaEventDestroy(e);
     delete p;
@@ -322,6 +512,7 @@ int dwt2_forward(dwt2_plan_t p, const void* in, void* coef, void* workspace, voi
     const size_t csz = dtype_size(p->coef_dtype);
     if (!aligned(coef, csz)) return DWT2_ERR_MISALIGNED;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (p->persistent) return forward_persistent(p, in, coef, workspace, s);
     const bool is_int = p->wavelet == DWT2_CDF53_INT;
     for (int l = 0; l < p->levels; ++l) {
         prof_mark(p, l, true, s);
@@ -331,7 +522,7 @@ int dwt2_forward(dwt2_plan_t p, const void* in, void* coef, void* workspace, voi
             char* wsb = static_cast<char*>(workspace);
             const LevelGeom& g = ip.lv[l];
             const void* src = (l == 0) ? static_cast<const void*>(in_img)
-                                       : static_cast<const void*>(wsb + ip.ws_off[(l - 1) % 2]);
+                                       : static_cast<const void*>(wsb + ip.ws_off[l - 1]);
             const int64_t src_pitch = (l == 0) ? ip.d.pitch_elems : round4(ip.lv[l - 1].wq);
             CUtensorMap box, row;
             const int bw = fwd_strip_px(p->cfg);
@@ -353,7 +544,7 @@ int dwt2_forward(dwt2_plan_t p, const void* in, void* coef, void* workspace, voi
                 fp.ll_pitch = ip.d.pitch_elems;
                 fp.ll_is_ct = 0;
             } else {
-                fp.ll = wsb + ip.ws_off[l % 2];
+                fp.ll = wsb + ip.ws_off[l];
                 fp.ll_pitch = round4(g.wq);
                 fp.ll_is_ct = 1;
             }
@@ -412,7 +603,7 @@ static int run_inverse_like(dwt2_plan_t p, const void* coef, void* out, void* wo
                 ipm.ll_pitch = ip.d.pitch_elems;
                 ipm.ll_is_ct = 0;
             } else {
-                ipm.ll = wsb + ip.ws_off[l % 2];
+                ipm.ll = wsb + ip.ws_off[l];
                 ipm.ll_pitch = round4(g.wq);
                 ipm.ll_is_ct = 1;
             }
@@ -420,7 +611,7 @@ static int run_inverse_like(dwt2_plan_t p, const void* coef, void* out, void* wo
                 ipm.out = out_img;
                 ipm.out_pitch = ip.d.pitch_elems;
             } else {
-                ipm.out = wsb + ip.ws_off[(l - 1) % 2];
+                ipm.out = wsb + ip.ws_off[l - 1];
                 ipm.out_pitch = round4(g.w);  // = round4(wq of level l-1)
             }
             const size_t pair = 2 * csz;
@@ -447,6 +638,66 @@ static int run_inverse_like(dwt2_plan_t p, const void* coef, void* out, void* wo
     }
     if (p->prof_on) ++p->prof_calls;
     return DWT2_OK;
+}
+
+// Candidate launch configurations of the forward: per-level plans try every
+// compiled kernel configuration with the automatic segment height and a few
+// fixed heights; persistent plans try a few segment heights.
+static const int TUNE_SEGS[] = {0, 24, 32, 44, 56};
+static const int TUNE_PML_SEGS[] = {16, 24, 32, 48};
+
+static int tune_candidates(dwt2_plan_t p) {
+    return p->persistent ? int(sizeof(TUNE_PML_SEGS) / sizeof(int))
+                         : N_FWD_CFGS * int(sizeof(TUNE_SEGS) / sizeof(int));
+}
+
+static int tune_apply(dwt2_plan_t p, int c) {
+    if (c < 0 || c >= tune_candidates(p)) return DWT2_ERR_INVALID_ARG;
+    if (p->persistent) {
+        p->pml_seg = TUNE_PML_SEGS[c];
+        return build_persistent(p);
+    }
+    const int ns = int(sizeof(TUNE_SEGS) / sizeof(int));
+    p->cfg = FWD_CFGS[c / ns];
+    p->seg_override = TUNE_SEGS[c % ns];
+    p->fwd_bps = forward_blocks_per_sm(p->wavelet, p->scheme, p->coef_dtype, p->cfg);
+    return DWT2_OK;
+}
+
+int dwt2_autotune(dwt2_plan_t p, const void* in, void* coef, void* workspace, void* stream, int* choice) {
+    if (!p || !choice) return DWT2_ERR_INVALID_ARG;
+    if (*choice >= 0) return tune_apply(p, *choice);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return DWT2_ERR_CUDA;
+    }
+    const bool prof = p->prof_on;
+    p->prof_on = false;
+    int best = -1, rc = DWT2_OK;
+    float best_ms = 0.f;
+    for (int c = 0; c < tune_candidates(p) && rc == DWT2_OK; ++c) {
+        rc = tune_apply(p, c);
+        for (int i = 0; i < 2 && rc == DWT2_OK; ++i) rc = dwt2_forward(p, in, coef, workspace, stream);
+        if (rc != DWT2_OK) break;
+        const int reps = 5;
+        cudaEventRecord(e0, s);
+        for (int i = 0; i < reps && rc == DWT2_OK; ++i) rc = dwt2_forward(p, in, coef, workspace, stream);
+        cudaEventRecord(e1, s);
+        float ms = 0.f;
+        if (rc != DWT2_OK || cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            rc = rc != DWT2_OK ? rc : DWT2_ERR_CUDA;
+            break;
+        }
+        if (best < 0 || ms < best_ms) best = c, best_ms = ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    p->prof_on = prof;
+    if (rc != DWT2_OK) return rc;
+    *choice = best;
+    return tune_apply(p, best);
 }
 
 int dwt2_inverse(dwt2_plan_t p, const void* coef, void* out, void* workspace, void* stream) {

@@ -51,6 +51,42 @@ struct InvParams {
     unsigned* status;
 };
 
+// Persistent forward: one descriptor per (image, level), one entry per unit
+// of work in queue order, counters of completed strips per (image, level,
+// segment).  Offsets are in elements from the base pointers of PmlParams.
+struct PmlDesc {
+    int h, w, hq, wq, hh, wh;
+    int n_strips, seg_rows;
+    int src_is_ws;                 // level input: 0 the images, 1 the workspace
+    int64_t src_off, src_pitch;    // compute-type elements
+    int64_t coef_off, coef_pitch;  // coefficient elements (the image's origin)
+    int ll_is_ct;                  // LL to the workspace (1) or the coefficients (0)
+    int64_t ll_off, ll_pitch;
+    int vec_lo, vec_hi, vec_ll;    // pair-store alignment for an aligned coefficient base
+    int ctr_base;                  // first counter of this level's segments
+    int dep_base, dep_need;        // previous level's counters (-1: none) and its strip count
+};
+
+struct PmlUnit {
+    int desc, s, g;      // descriptor, strip, segment
+    int dep_lo, dep_hi;  // segments of the previous level this unit reads
+};
+
+struct PmlParams {
+    const void* in;
+    void* coef;
+    void* ws;
+    const PmlDesc* descs;
+    const PmlUnit* units;
+    int n_units;
+    unsigned* counters;
+    unsigned* queue;
+    int coef_vec;          // the coefficient base allows paired stores
+    int test_drop_signal;  // test hook: queue entry 0 never signals completion
+    unsigned* status;
+    uint64_t timeout_ns;
+};
+
 // forward launch configuration
 struct FwdCfg {
     int ql, qr, nst, nw;  // quads per lane, quad rows per stage, stages per warp, warps per block
@@ -77,14 +113,32 @@ int launch_inverse_bf16(int wav, int scheme, const InvParams& p, int grid, cudaS
 int launch_inverse_i32(int wav, int scheme, const InvParams& p, int grid, cudaStream_t s);
 int launch_adjoint_f32(const InvParams& p, int grid, cudaStream_t s);
 
+// Plans with at most PML_TMA_MAX_DESCS (image, level) descriptors pass a
+// box map and a single-row map per descriptor as kernel parameters and load
+// with TMA; larger batches load with cp.async.
+constexpr int PML_TMA_MAX_DESCS = 16;
+struct PmlLaunch {
+    CUtensorMap maps[2 * PML_TMA_MAX_DESCS];  // [2*desc] box, [2*desc+1] single row
+    PmlParams base;
+    int use_tma;
+};
+
+int launch_pml_f32(int wav, int scheme, const PmlLaunch& p, int grid, cudaStream_t s);
+int launch_pml_f16(int wav, int scheme, const PmlLaunch& p, int grid, cudaStream_t s);
+int launch_pml_bf16(int wav, int scheme, const PmlLaunch& p, int grid, cudaStream_t s);
+int launch_pml_i32(int wav, int scheme, const PmlLaunch& p, int grid, cudaStream_t s);
+int pml_blocks_per_sm(int wav, int scheme, int coef_dtype);
+
 // resident blocks per SM of a forward / inverse launch (0 on error)
 int forward_blocks_per_sm(int wav, int scheme, int coef_dtype, const FwdCfg& cfg);
 int inverse_blocks_per_sm(int wav, int scheme, int coef_dtype, bool adjoint);
 
 // the forward configurations compiled in (index 0 is the default)
-constexpr int N_FWD_CFGS = 5;
+constexpr int N_FWD_CFGS = 3;
 extern const FwdCfg FWD_CFGS[N_FWD_CFGS];
 size_t fwd_smem_bytes_of(const FwdCfg& c);
+// the persistent kernel's fixed configuration
+constexpr int PML_QL = 2, PML_QR = 3, PML_NST = 3, PML_NW = 4;
 constexpr int INV_NW = 4;
 constexpr int INV_QL = 2;
 constexpr int INV_OUT_Q = 32 * INV_QL - 4;

@@ -15,4 +15,9 @@ int launch_inverse_bf16(int wav, int scheme, const InvParams& p, int grid, cudaS
 int occupancy_forward_bf16(int wav, int scheme, const FwdCfg& cfg) { return occupancy_forward_t<__nv_bfloat16>(wav, scheme, cfg); }
 int occupancy_inverse_bf16(int scheme) { return occupancy_inverse_t<__nv_bfloat16>(scheme); }
 
+int launch_pml_bf16(int wav, int scheme, const PmlLaunch& p, int grid, cudaStream_t s) {
+    return launch_pml_t<__nv_bfloat16>(wav, scheme, &p, grid, s, false);
+}
+int occupancy_pml_bf16(int wav, int scheme) { return launch_pml_t<__nv_bfloat16>(wav, scheme, nullptr, 0, nullptr, true); }
+
 }  // namespace dwt2

@@ -15,4 +15,9 @@ int launch_inverse_f16(int wav, int scheme, const InvParams& p, int grid, cudaSt
 int occupancy_forward_f16(int wav, int scheme, const FwdCfg& cfg) { return occupancy_forward_t<__half>(wav, scheme, cfg); }
 int occupancy_inverse_f16(int scheme) { return occupancy_inverse_t<__half>(scheme); }
 
+int launch_pml_f16(int wav, int scheme, const PmlLaunch& p, int grid, cudaStream_t s) {
+    return launch_pml_t<__half>(wav, scheme, &p, grid, s, false);
+}
+int occupancy_pml_f16(int wav, int scheme) { return launch_pml_t<__half>(wav, scheme, nullptr, 0, nullptr, true); }
+
 }  // namespace dwt2

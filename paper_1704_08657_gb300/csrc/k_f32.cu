@@ -15,6 +15,11 @@ int launch_inverse_f32(int wav, int scheme, const InvParams& p, int grid, cudaSt
 int occupancy_forward_f32(int wav, int scheme, const FwdCfg& cfg) { return occupancy_forward_t<float>(wav, scheme, cfg); }
 int occupancy_inverse_f32(int scheme) { return occupancy_inverse_t<float>(scheme); }
 
+int launch_pml_f32(int wav, int scheme, const PmlLaunch& p, int grid, cudaStream_t s) {
+    return launch_pml_t<float>(wav, scheme, &p, grid, s, false);
+}
+int occupancy_pml_f32(int wav, int scheme) { return launch_pml_t<float>(wav, scheme, nullptr, 0, nullptr, true); }
+
 }  // namespace dwt2
 
 namespace dwt2 {
@@ -36,6 +41,19 @@ int forward_blocks_per_sm(int wav, int scheme, int coef_dtype, const FwdCfg& cfg
         case DT_F16: return occupancy_forward_f16(wav, scheme, cfg);
         case DT_BF16: return occupancy_forward_bf16(wav, scheme, cfg);
         default: return occupancy_forward_i32(wav, scheme, cfg);
+    }
+}
+
+int occupancy_pml_f16(int wav, int scheme);
+int occupancy_pml_bf16(int wav, int scheme);
+int occupancy_pml_i32(int wav, int scheme);
+
+int pml_blocks_per_sm(int wav, int scheme, int coef_dtype) {
+    switch (coef_dtype) {
+        case DT_F32: return occupancy_pml_f32(wav, scheme);
+        case DT_F16: return occupancy_pml_f16(wav, scheme);
+        case DT_BF16: return occupancy_pml_bf16(wav, scheme);
+        default: return occupancy_pml_i32(wav, scheme);
     }
 }
 

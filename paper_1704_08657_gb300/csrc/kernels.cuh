@@ -132,159 +132,334 @@ __device__ __forceinline__ void load_quad_row(const CT* s0, Row<CT, QL>& r, int 
     }
 }
 
+// ------------------------------------------------------------------ loaders
+// A loader fills one shared-memory stage (2*QR pixel rows of 64*QL pixels,
+// starting at pixel column x0 and pixel row y0 of the level's input) and
+// makes it complete on the stage's mbarrier.  Rows outside [0, h) are taken
+// from their whole-sample mirror rows; columns outside [0, w) are left as
+// zeros (load_quad_row mirrors them).
+
+// 2-D TMA (cp.async.bulk.tensor) issued by lane 0; one box when every row is
+// inside the image, else one single-row box per pixel row.
+struct TmaLoader {
+    static constexpr unsigned ARRIVALS = 1;
+    const CUtensorMap* box;
+    const CUtensorMap* row;
+    template <class CT, int QL, int QR>
+    __device__ __forceinline__ void issue(CT* dst, uint64_t* bar, int x0, int y0, int h, int /*w*/,
+                                          int lane) const {
+        constexpr int SPX = 64 * QL, ROWS = 2 * QR;
+        if (lane != 0) return;
+        mbar_expect_tx(bar, unsigned(ROWS * SPX * 4));
+        if (y0 >= 0 && y0 + ROWS <= h) {
+            tma_load_2d(dst, box, x0, y0, bar);
+        } else {
+#pragma unroll 1
+            for (int r = 0; r < ROWS; ++r) tma_load_2d(dst + r * SPX, row, x0, fold_ws(y0 + r, h), bar);
+        }
+    }
+};
+
+// 16-byte cp.async by every lane (one 4-pixel chunk per lane per row and QL/2
+// chunks per lane), zero-filling the part of a chunk past the right edge; each
+// lane's copies arrive on the mbarrier when they land.  Needs a 16-byte
+// aligned source row (pitch a multiple of 4 elements).
+template <class CT>
+struct CpAsyncLoader {
+    static constexpr unsigned ARRIVALS = 32;
+    const CT* src;
+    int64_t pitch;
+    template <class CT_, int QL, int QR>
+    __device__ __forceinline__ void issue(CT_* dst, uint64_t* bar, int x0, int y0, int h, int w, int lane) const {
+        constexpr int SPX = 64 * QL, ROWS = 2 * QR;
+        const bool inside = (y0 >= 0) && (y0 + ROWS <= h);
+#pragma unroll
+        for (int r = 0; r < ROWS; ++r) {
+            const int y = inside ? y0 + r : fold_ws(y0 + r, h);
+            const CT* srow = src + int64_t(y) * pitch;
+#pragma unroll
+            for (int k = 0; k < QL / 2; ++k) {
+                const int c = lane + 32 * k;  // chunk index in the strip
+                const int px = x0 + 4 * c;
+                const int n = (px >= 0) ? max(0, min(4, w - px)) : 0;
+                const CT* g = srow + (n > 0 ? px : 0);
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst + r * SPX + 4 * c)),
+                             "l"(g), "r"(4 * n)
+                             : "memory");
+            }
+        }
+        asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+    }
+};
+
 // ------------------------------------------------------------------ forward
-template <class Pipe, class OutT, int QL, int QR, int NST, int NW>
-__global__ void __launch_bounds__(NW * 32)
-    fwd_tma_kernel(const __grid_constant__ CUtensorMap tm_box, const __grid_constant__ CUtensorMap tm_row,
-                   const FwdParams p) {
+// One unit of work: quad rows [R0, R1) of strip s of one level.  P provides
+// the level's geometry and outputs (fields of FwdParams); bufs / bars are the
+// warp's stage ring, gstage the warp's running stage count (slot and mbarrier
+// phase).  Returns false when a stage wait timed out.
+template <class Pipe, class OutT, int QL, int QR, int NST, class P, class Loader>
+__device__ __forceinline__ bool fwd_unit(const P& p, const Loader& ld, int s, int R0, int R1,
+                                         typename Pipe::CT* bufs, uint64_t* bars, uint32_t& gstage, int lane) {
     using CT = typename Pipe::CT;
     using R = Row<CT, QL>;
     constexpr int SPX = 64 * QL;
     constexpr int OUTQ = 32 * QL - 2 * HALO_Q;
     constexpr int ROWS = 2 * QR;
     constexpr int STAGE_ELEMS = ROWS * SPX;
-    constexpr unsigned STAGE_BYTES = STAGE_ELEMS * 4u;
     static_assert(PHASES % QR == 0, "a group of arrivals must cover whole stages");
     static_assert(QL % 2 == 0, "band stores go in pairs");
+
+    const int A0 = R0 - 2;                            // first quad row streamed
+    const int n_arr = (R1 - R0) + 2 + Pipe::LAG;      // quad rows streamed
+    const int n_grp = (n_arr + PHASES - 1) / PHASES;  // groups of arrivals (the last may stop early)
+    const int NT = (n_arr + QR - 1) / QR;             // stages
+    const int x0 = s * (2 * OUTQ) - 2 * HALO_Q;       // first pixel (multiple of 4)
+    const int jb = x0 / 2 + QL * lane;                // first quad column of the lane
+    const bool edge = (x0 < 0) || (x0 + SPX > p.w);
+
+    // which of the lane's quads this strip outputs, per band parity
+    bool ev[QL], dv[QL], mp[QL];
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+        const int lq = QL * lane + q;
+        mp[q] = (lq >= HALO_Q) && (lq < 32 * QL - HALO_Q);
+        ev[q] = mp[q] && (jb + q < p.wq);
+        dv[q] = mp[q] && (jb + q < p.wh);
+    }
+    // warp-uniform: every output quad of the strip exists in all four bands
+    // and every band row takes paired stores
+    const bool fast = p.vec_lo && p.vec_hi && (p.ll_is_ct || p.vec_ll) && (x0 / 2 + 32 * QL - HALO_Q <= p.wh);
+    // band pointers at output row R0, advanced one pitch per stored row
+    OutT* hl = reinterpret_cast<OutT*>(p.coef) + int64_t(R0) * p.coef_pitch + p.wq + jb;
+    OutT* lh = reinterpret_cast<OutT*>(p.coef) + int64_t(p.hq + R0) * p.coef_pitch + jb;
+    OutT* hh = lh + p.wq;
+    CT* llc = reinterpret_cast<CT*>(p.ll) + int64_t(R0) * p.ll_pitch + jb;
+    OutT* llo = reinterpret_cast<OutT*>(p.ll) + int64_t(R0) * p.ll_pitch + jb;
+
+    for (int t = 0; t < NST && t < NT; ++t) {
+        const uint32_t gs = gstage + t;
+        ld.template issue<CT, QL, QR>(bufs + (gs % NST) * STAGE_ELEMS, &bars[gs % NST], x0, 2 * (A0 + t * QR), p.h,
+                                      p.w, lane);
+    }
+
+    Pipe pipe;
+    pipe.init();
+    bool ok = true;
+    int t = 0, slot = 0;
+    const CT* stage = bufs;
+    for (int gi = 0; gi < n_grp && ok; ++gi) {
+        static_for<PHASES>([&](auto ph) {
+            constexpr int PH = decltype(ph)::value;
+            constexpr int QI = PH % QR;
+            if (gi * PHASES + PH >= QR * NT) return;  // past the unit's last stage
+            if constexpr (QI == 0) {
+                if (!ok) return;
+                const uint32_t gs = gstage + t;
+                slot = gs % NST;
+                if (!mbar_wait_bounded(&bars[slot], (gs / NST) & 1u, p.status, p.timeout_ns)) {
+                    // give the copies still in flight a bounded time to land
+                    for (int u = t + 1; u < NT && u < t + NST; ++u) {
+                        const uint32_t gu = gstage + u;
+                        mbar_wait_bounded(&bars[gu % NST], (gu / NST) & 1u, nullptr, p.timeout_ns);
+                    }
+                    ok = false;
+                    return;
+                }
+                stage = bufs + slot * STAGE_ELEMS;
+            }
+            const int vi = A0 + gi * PHASES + PH;  // quad row streamed now
+            load_quad_row<CT, QL>(stage + (2 * QI) * SPX, pipe.template slot<PH>(), lane, edge, x0, p.w);
+            const R& out = pipe.template step<PH>(vi);
+            const int oi = vi - Pipe::LAG;
+            const bool row_on = (oi >= R0) & (oi < R1);
+            const bool orow = row_on & (oi < p.hh);
+            if (fast) {
+#pragma unroll
+                for (int q = 0; q < QL; q += 2) {
+                    const bool on = row_on & mp[q] & mp[q + 1];
+                    const bool oo = orow & mp[q] & mp[q + 1];
+                    if (p.ll_is_ct) {
+                        if (on) st_pair<CT>(llc + q, out.c1[q], out.c1[q + 1]);
+                    } else {
+                        if (on) st_pair<OutT>(llo + q, Cvt<OutT>::to(out.c1[q]), Cvt<OutT>::to(out.c1[q + 1]));
+                    }
+                    if (on) st_pair<OutT>(hl + q, Cvt<OutT>::to(out.c2[q]), Cvt<OutT>::to(out.c2[q + 1]));
+                    if (oo) st_pair<OutT>(lh + q, Cvt<OutT>::to(out.c3[q]), Cvt<OutT>::to(out.c3[q + 1]));
+                    if (oo) st_pair<OutT>(hh + q, Cvt<OutT>::to(out.c4[q]), Cvt<OutT>::to(out.c4[q + 1]));
+                }
+            } else if (row_on) {
+#pragma unroll
+                for (int q = 0; q < QL; q += 2) {
+                    if (p.ll_is_ct)
+                        store_pair<CT, CT>(llc, q, out.c1[q], out.c1[q + 1], ev[q], ev[q + 1], true);
+                    else
+                        store_pair<OutT, CT>(llo, q, out.c1[q], out.c1[q + 1], ev[q], ev[q + 1], p.vec_ll);
+                    store_pair<OutT, CT>(hl, q, out.c2[q], out.c2[q + 1], dv[q], dv[q + 1], p.vec_hi);
+                    if (orow) {
+                        store_pair<OutT, CT>(lh, q, out.c3[q], out.c3[q + 1], ev[q], ev[q + 1], p.vec_lo);
+                        store_pair<OutT, CT>(hh, q, out.c4[q], out.c4[q + 1], dv[q], dv[q + 1], p.vec_hi);
+                    }
+                }
+            }
+            const int64_t cstep = row_on ? p.coef_pitch : 0;
+            const int64_t lstep = row_on ? p.ll_pitch : 0;
+            hl += cstep;
+            lh += cstep;
+            hh += cstep;
+            llc += lstep;
+            llo += lstep;
+            if constexpr (QI == QR - 1) {
+                __syncwarp();
+                if (ok && t + NST < NT)
+                    ld.template issue<CT, QL, QR>(bufs + slot * STAGE_ELEMS, &bars[slot], x0,
+                                                  2 * (A0 + (t + NST) * QR), p.h, p.w, lane);
+                ++t;
+            }
+        });
+    }
+    if (ok) gstage += NT;
+    return ok;
+}
+
+template <class CT, int QL, int QR, int NST, int NW>
+__device__ __forceinline__ void stage_ring(unsigned char* smem, int warp, CT*& bufs, uint64_t*& bars) {
+    constexpr int STAGE_ELEMS = 2 * QR * 64 * QL;
+    bufs = reinterpret_cast<CT*>(smem) + warp * NST * STAGE_ELEMS;
+    bars = reinterpret_cast<uint64_t*>(smem + size_t(NW) * NST * STAGE_ELEMS * 4) + warp * NST;
+}
+
+// One pyramid level, TMA-fed: the warps take their units from Pieces.
+template <class Pipe, class OutT, int QL, int QR, int NST, int NW>
+__global__ void __launch_bounds__(NW * 32)
+    fwd_tma_kernel(const __grid_constant__ CUtensorMap tm_box, const __grid_constant__ CUtensorMap tm_row,
+                   const FwdParams p) {
+    using CT = typename Pipe::CT;
     extern __shared__ __align__(128) unsigned char smem[];
-
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    CT* bufs = reinterpret_cast<CT*>(smem) + warp * NST * STAGE_ELEMS;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + size_t(NW) * NST * STAGE_BYTES) + warp * NST;
-
+    CT* bufs;
+    uint64_t* bars;
+    stage_ring<CT, QL, QR, NST, NW>(smem, warp, bufs, bars);
     if (lane == 0) {
 #pragma unroll
-        for (int i = 0; i < NST; ++i) mbar_init(&bars[i], 1);
+        for (int i = 0; i < NST; ++i) mbar_init(&bars[i], TmaLoader::ARRIVALS);
         fence_mbar_init();
         tma_prefetch_desc(&tm_box);
         tma_prefetch_desc(&tm_row);
     }
     __syncwarp();
-
-    uint32_t gstage = 0;  // stages consumed by this warp so far (slot / phase)
+    const TmaLoader ld{&tm_box, &tm_row};
+    uint32_t gstage = 0;
     Pieces<FwdParams> pieces(p, blockIdx.x * NW + warp, gridDim.x * NW);
     int s, R0, R1;
     while (pieces.next(p, s, R0, R1)) {
-        const int A0 = R0 - 2;                         // first quad row streamed
-        const int n_arr = (R1 - R0) + 2 + Pipe::LAG;   // quad rows streamed
-        const int n_grp = (n_arr + PHASES - 1) / PHASES;  // groups of arrivals (the last may stop early)
-        const int NT = (n_arr + QR - 1) / QR;          // stages
-        const int x0 = s * (2 * OUTQ) - 2 * HALO_Q;                          // first pixel (multiple of 4)
-        const int jb = x0 / 2 + QL * lane;                                   // first quad column of the lane
-        const bool edge = (x0 < 0) || (x0 + SPX > p.w);
+        if (!fwd_unit<Pipe, OutT, QL, QR, NST>(p, ld, s, R0, R1, bufs, bars, gstage, lane)) return;
+    }
+}
 
-        // which of the lane's quads this strip outputs, per band parity
-        bool ev[QL], dv[QL], mp[QL];
+// ------------------------------------------------- persistent (batched) forward
+// All units of all images and levels of a plan in one launch.  Units are taken
+// from a device queue in the plan's order; a unit of level l first waits
+// (bounded) until the level l-1 segments it reads are complete, i.e. their
+// counters reached the strip count; after its stores it bumps the counter of
+// its own segment.  The queue order puts every unit about one GPU round behind
+// the segments it depends on, so waits are rare and the low-low band it reads
+// was written moments before (usually still in L2).
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// the geometry and outputs of one unit's level, with the field names fwd_unit uses
+struct PmlView {
+    int h, w, hq, wq, hh, wh;
+    void* coef;
+    int64_t coef_pitch;
+    void* ll;
+    int64_t ll_pitch;
+    int ll_is_ct;
+    int vec_lo, vec_hi, vec_ll;
+    unsigned* status;
+    uint64_t timeout_ns;
+};
+
+template <class Pipe, class OutT, int QL, int QR, int NST, int NW, bool TMA>
+__global__ void __launch_bounds__(NW * 32) pml_kernel(const __grid_constant__ PmlLaunch L) {
+    using CT = typename Pipe::CT;
+    const PmlParams& P = L.base;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    CT* bufs;
+    uint64_t* bars;
+    stage_ring<CT, QL, QR, NST, NW>(smem, warp, bufs, bars);
+    if (lane == 0) {
 #pragma unroll
-        for (int q = 0; q < QL; ++q) {
-            const int lq = QL * lane + q;
-            mp[q] = (lq >= HALO_Q) && (lq < 32 * QL - HALO_Q);
-            ev[q] = mp[q] && (jb + q < p.wq);
-            dv[q] = mp[q] && (jb + q < p.wh);
-        }
-        // warp-uniform: every output quad of the strip exists in all four bands
-        // and every band row takes paired stores
-        const bool fast = p.vec_lo && p.vec_hi && (p.ll_is_ct || p.vec_ll) &&
-                          (x0 / 2 + 32 * QL - HALO_Q <= p.wh);
-        // band pointers at output row R0, advanced one pitch per stored row
-        OutT* hl = reinterpret_cast<OutT*>(p.coef) + int64_t(R0) * p.coef_pitch + p.wq + jb;
-        OutT* lh = reinterpret_cast<OutT*>(p.coef) + int64_t(p.hq + R0) * p.coef_pitch + jb;
-        OutT* hh = lh + p.wq;
-        CT* llc = reinterpret_cast<CT*>(p.ll) + int64_t(R0) * p.ll_pitch + jb;
-        OutT* llo = reinterpret_cast<OutT*>(p.ll) + int64_t(R0) * p.ll_pitch + jb;
-
-        auto issue = [&](int t, int slot) {
-            const int y0 = 2 * (A0 + t * QR);
-            CT* dst = bufs + slot * STAGE_ELEMS;
-            mbar_expect_tx(&bars[slot], STAGE_BYTES);
-            if (y0 >= 0 && y0 + ROWS <= p.h) {
-                tma_load_2d(dst, &tm_box, x0, y0, &bars[slot]);
-            } else {
-#pragma unroll 1
-                for (int r = 0; r < ROWS; ++r)
-                    tma_load_2d(dst + r * SPX, &tm_row, x0, fold_ws(y0 + r, p.h), &bars[slot]);
+        for (int i = 0; i < NST; ++i) mbar_init(&bars[i], TMA ? TmaLoader::ARRIVALS : CpAsyncLoader<CT>::ARRIVALS);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    uint32_t gstage = 0;
+    for (;;) {
+        int u = 0;
+        if (lane == 0) u = int(atomicAdd(P.queue, 1u));
+        u = __shfl_sync(FULL, u, 0);
+        if (u >= P.n_units) break;
+        const PmlUnit un = P.units[u];
+        const PmlDesc& d = P.descs[un.desc];
+        if (d.dep_base >= 0) {
+            bool waited_ok = true;
+            if (lane == 0) {
+                for (int g = un.dep_lo; g <= un.dep_hi; ++g) {
+                    const unsigned* c = P.counters + d.dep_base + g;
+                    if (ld_acquire(c) >= unsigned(d.dep_need)) continue;
+                    const uint64_t t0 = globaltimer_ns();
+                    while (ld_acquire(c) < unsigned(d.dep_need)) {
+                        if (globaltimer_ns() - t0 > P.timeout_ns) {
+                            waited_ok = false;
+                            break;
+                        }
+                        __nanosleep(256);
+                    }
+                }
+                if (!waited_ok && P.status) atomicOr(P.status, DEV_TIMEOUT);
+                // the level's input was written through the generic proxy by other
+                // warps; TMA reads through the async proxy
+                if (TMA) asm volatile("fence.proxy.async.global;" ::: "memory");
             }
-        };
-
-        if (lane == 0) {
-            for (int t = 0; t < NST && t < NT; ++t) issue(t, (gstage + t) % NST);
+            __syncwarp();
         }
-
-        Pipe pipe;
-        pipe.init();
-        bool ok = true;
-        int t = 0, slot = 0;
-        const CT* stage = bufs;
-        for (int gi = 0; gi < n_grp && ok; ++gi) {
-            static_for<PHASES>([&](auto ph) {
-                constexpr int PH = decltype(ph)::value;
-                constexpr int QI = PH % QR;
-                if (gi * PHASES + PH >= QR * NT) return;  // past the unit's last stage
-                if constexpr (QI == 0) {
-                    if (!ok) return;
-                    const uint32_t gs = gstage + t;
-                    slot = gs % NST;
-                    if (!mbar_wait_bounded(&bars[slot], (gs / NST) & 1u, p.status, p.timeout_ns)) {
-                        // give the copies still in flight a bounded time to land
-                        for (int u = t + 1; u < NT && u < t + NST; ++u) {
-                            const uint32_t gu = gstage + u;
-                            mbar_wait_bounded(&bars[gu % NST], (gu / NST) & 1u, nullptr, p.timeout_ns);
-                        }
-                        ok = false;
-                        return;
-                    }
-                    stage = bufs + slot * STAGE_ELEMS;
-                }
-                const int vi = A0 + gi * PHASES + PH;  // quad row streamed now
-                load_quad_row<CT, QL>(stage + (2 * QI) * SPX, pipe.template slot<PH>(), lane, edge, x0, p.w);
-                const R& out = pipe.template step<PH>(vi);
-                const int oi = vi - Pipe::LAG;
-                const bool row_on = (oi >= R0) & (oi < R1);
-                const bool orow = row_on & (oi < p.hh);
-                if (fast) {
-#pragma unroll
-                    for (int q = 0; q < QL; q += 2) {
-                        const bool on = row_on & mp[q] & mp[q + 1];
-                        const bool oo = orow & mp[q] & mp[q + 1];
-                        if (p.ll_is_ct) {
-                            if (on) st_pair<CT>(llc + q, out.c1[q], out.c1[q + 1]);
-                        } else {
-                            if (on) st_pair<OutT>(llo + q, Cvt<OutT>::to(out.c1[q]), Cvt<OutT>::to(out.c1[q + 1]));
-                        }
-                        if (on) st_pair<OutT>(hl + q, Cvt<OutT>::to(out.c2[q]), Cvt<OutT>::to(out.c2[q + 1]));
-                        if (oo) st_pair<OutT>(lh + q, Cvt<OutT>::to(out.c3[q]), Cvt<OutT>::to(out.c3[q + 1]));
-                        if (oo) st_pair<OutT>(hh + q, Cvt<OutT>::to(out.c4[q]), Cvt<OutT>::to(out.c4[q + 1]));
-                    }
-                } else if (row_on) {
-#pragma unroll
-                    for (int q = 0; q < QL; q += 2) {
-                        if (p.ll_is_ct)
-                            store_pair<CT, CT>(llc, q, out.c1[q], out.c1[q + 1], ev[q], ev[q + 1], true);
-                        else
-                            store_pair<OutT, CT>(llo, q, out.c1[q], out.c1[q + 1], ev[q], ev[q + 1], p.vec_ll);
-                        store_pair<OutT, CT>(hl, q, out.c2[q], out.c2[q + 1], dv[q], dv[q + 1], p.vec_hi);
-                        if (orow) {
-                            store_pair<OutT, CT>(lh, q, out.c3[q], out.c3[q + 1], ev[q], ev[q + 1], p.vec_lo);
-                            store_pair<OutT, CT>(hh, q, out.c4[q], out.c4[q + 1], dv[q], dv[q + 1], p.vec_hi);
-                        }
-                    }
-                }
-                const int64_t cstep = row_on ? p.coef_pitch : 0;
-                const int64_t lstep = row_on ? p.ll_pitch : 0;
-                hl += cstep;
-                lh += cstep;
-                hh += cstep;
-                llc += lstep;
-                llo += lstep;
-                if constexpr (QI == QR - 1) {
-                    __syncwarp();
-                    if (lane == 0 && ok && t + NST < NT) issue(t + NST, slot);
-                    ++t;
-                }
-            });
+        PmlView v;
+        v.h = d.h, v.w = d.w, v.hq = d.hq, v.wq = d.wq, v.hh = d.hh, v.wh = d.wh;
+        v.coef = static_cast<OutT*>(P.coef) + d.coef_off;
+        v.coef_pitch = d.coef_pitch;
+        v.ll = d.ll_is_ct ? static_cast<void*>(static_cast<CT*>(P.ws) + d.ll_off)
+                          : static_cast<void*>(static_cast<OutT*>(P.coef) + d.ll_off);
+        v.ll_pitch = d.ll_pitch;
+        v.ll_is_ct = d.ll_is_ct;
+        v.vec_lo = d.vec_lo && P.coef_vec, v.vec_hi = d.vec_hi && P.coef_vec;
+        v.vec_ll = d.ll_is_ct ? 1 : (d.vec_ll && P.coef_vec);
+        v.status = P.status;
+        v.timeout_ns = P.timeout_ns;
+        const int R0 = un.g * d.seg_rows;
+        const int R1 = min(R0 + d.seg_rows, d.hq);
+        bool ok;
+        if constexpr (TMA) {
+            const TmaLoader ld{&L.maps[2 * un.desc], &L.maps[2 * un.desc + 1]};
+            ok = fwd_unit<Pipe, OutT, QL, QR, NST>(v, ld, un.s, R0, R1, bufs, bars, gstage, lane);
+        } else {
+            const CT* src = d.src_is_ws ? static_cast<const CT*>(P.ws) + d.src_off
+                                        : static_cast<const CT*>(P.in) + d.src_off;
+            const CpAsyncLoader<CT> ld{src, d.src_pitch};
+            ok = fwd_unit<Pipe, OutT, QL, QR, NST>(v, ld, un.s, R0, R1, bufs, bars, gstage, lane);
         }
         if (!ok) return;
-        gstage += NT;
+        // this unit's stores must be visible to the TMA reads of later units
+        if (TMA) asm volatile("fence.proxy.async.global;" ::: "memory");
+        __syncwarp();
+        if (lane == 0 && !(P.test_drop_signal && u == 0)) {
+            __threadfence();
+            atomicAdd(P.counters + d.ctr_base + un.g, 1u);
+        }
     }
 }
 

@@ -26,7 +26,7 @@ int launch_fwd_one(const CUtensorMap& box, const CUtensorMap& row, const FwdPara
 
 // the compiled forward configurations (quads per lane, quad rows per stage,
 // stages, warps per block); the first is the default
-#define DWT2_FWD_CFG_LIST(X) X(0, 2, 3, 3, 4) X(1, 2, 2, 4, 4) X(2, 2, 1, 6, 4) X(3, 2, 2, 4, 8) X(4, 4, 2, 4, 4)
+#define DWT2_FWD_CFG_LIST(X) X(0, 2, 3, 3, 4) X(1, 2, 2, 4, 4) X(2, 2, 2, 4, 8)
 
 template <class Pipe, class OutT, int QL, int QR, int NST, int NW>
 int occupancy_fwd_one() {
@@ -109,6 +109,54 @@ int launch_forward_t(int wav, int scheme, const CUtensorMap& box, const CUtensor
         if (scheme == SCHEME_REDUCED) return launch_fwd_cfgs<Fwd97, SCHEME_REDUCED, OutT>(box, row, p, grid, c, s);
         if (scheme == SCHEME_SEP) return launch_fwd_cfgs<Fwd97, SCHEME_SEP, OutT>(box, row, p, grid, c, s);
         return cudaErrorInvalidValue;
+    }
+}
+
+template <class Pipe, class OutT>
+int launch_pml_one(const PmlLaunch& p, int grid, cudaStream_t s) {
+    constexpr size_t smem = fwd_smem_bytes<PML_QL, PML_QR, PML_NST, PML_NW>();
+    static_assert(smem <= 48 * 1024, "persistent kernel stages fit the default shared-memory limit");
+    if (p.use_tma)
+        pml_kernel<Pipe, OutT, PML_QL, PML_QR, PML_NST, PML_NW, true><<<grid, PML_NW * 32, smem, s>>>(p);
+    else
+        pml_kernel<Pipe, OutT, PML_QL, PML_QR, PML_NST, PML_NW, false><<<grid, PML_NW * 32, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <class Pipe, class OutT>
+int occupancy_pml_one() {
+    int a = 0, b = 0;
+    constexpr size_t smem = fwd_smem_bytes<PML_QL, PML_QR, PML_NST, PML_NW>();
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &a, pml_kernel<Pipe, OutT, PML_QL, PML_QR, PML_NST, PML_NW, true>, PML_NW * 32, smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &b, pml_kernel<Pipe, OutT, PML_QL, PML_QR, PML_NST, PML_NW, false>, PML_NW * 32, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return a < b ? a : b;  // the grid must be resident for either loader
+}
+
+// occupancy != 0: return resident blocks per SM instead of launching
+template <class OutT>
+int launch_pml_t(int wav, int scheme, const PmlLaunch* p, int grid, cudaStream_t s, bool occupancy) {
+    if constexpr (std::is_same<OutT, int>::value) {
+        if (wav != WAV_CDF53I) return occupancy ? 0 : int(cudaErrorInvalidValue);
+        if (scheme == SCHEME_SEP)
+            return occupancy ? occupancy_pml_one<Fwd53<SCHEME_SEP, PML_QL>, int>()
+                             : launch_pml_one<Fwd53<SCHEME_SEP, PML_QL>, int>(*p, grid, s);
+        return occupancy ? occupancy_pml_one<Fwd53<SCHEME_NONSEP, PML_QL>, int>()
+                         : launch_pml_one<Fwd53<SCHEME_NONSEP, PML_QL>, int>(*p, grid, s);
+    } else {
+        if (wav != WAV_CDF97) return occupancy ? 0 : int(cudaErrorInvalidValue);
+        if (scheme == SCHEME_NONSEP)
+            return occupancy ? occupancy_pml_one<Fwd97<SCHEME_NONSEP, PML_QL>, OutT>()
+                             : launch_pml_one<Fwd97<SCHEME_NONSEP, PML_QL>, OutT>(*p, grid, s);
+        if (scheme == SCHEME_REDUCED)
+            return occupancy ? occupancy_pml_one<Fwd97<SCHEME_REDUCED, PML_QL>, OutT>()
+                             : launch_pml_one<Fwd97<SCHEME_REDUCED, PML_QL>, OutT>(*p, grid, s);
+        return occupancy ? occupancy_pml_one<Fwd97<SCHEME_SEP, PML_QL>, OutT>()
+                         : launch_pml_one<Fwd97<SCHEME_SEP, PML_QL>, OutT>(*p, grid, s);
     }
 }
 

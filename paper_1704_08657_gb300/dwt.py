@@ -7,6 +7,9 @@ autograd with the hand-written adjoint kernel as its backward.
 """
 from __future__ import annotations
 
+import hashlib
+import json
+import os
 from typing import List, Optional, Sequence, Tuple
 
 import torch
@@ -45,6 +48,8 @@ class Plan:
         self.scheme = scheme
         self.in_dtype = torch.float32 if wavelet == "cdf97" else torch.int32
         self.coef_dtype = coef_dtype
+        self.flags = int(flags)
+        self.tuned: Optional[int] = None
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         with torch.cuda.device(self.device):
             self.handle = abi.dwt2_plan(WAVELETS[wavelet], self.levels, abi.DWT2_SYMMETRIC,
@@ -99,6 +104,39 @@ class Plan:
         abi.dwt2_adjoint(self.handle, g.data_ptr(), out.data_ptr(), self.workspace.data_ptr(),
                          _stream_handle(stream))
         return out
+
+    def tune_key(self) -> str:
+        """Cache key of this plan's autotuning choice on this GPU and driver."""
+        h = hashlib.sha256(repr(self.images).encode()).hexdigest()[:16]
+        return "|".join([torch.cuda.get_device_name(self.device), str(torch.version.cuda), self.wavelet, self.scheme,
+                         str(self.coef_dtype), str(self.levels), str(self.flags), h])
+
+    def autotune(self, x: torch.Tensor, out: Optional[torch.Tensor] = None,
+                 stream: Optional[torch.cuda.Stream] = None, cache: Optional[str] = None) -> int:
+        """Pick the fastest launch configuration for this plan (dwt2_autotune).
+
+        With ``cache`` (a JSON file, default $DWT2_TUNE_CACHE) an earlier choice
+        for the same GPU, driver and plan is applied without timing, and a new
+        choice is written back.  ``out`` is overwritten.
+        """
+        self._check(x, self.in_dtype, "x")
+        if out is None:
+            out = torch.empty_like(x, dtype=self.coef_dtype)
+        cache = cache if cache is not None else os.environ.get("DWT2_TUNE_CACHE")
+        key = self.tune_key()
+        table = {}
+        if cache and os.path.exists(cache):
+            with open(cache) as f:
+                table = json.load(f)
+        choice = int(table.get(key, -1))
+        choice = abi.dwt2_autotune(self.handle, x.data_ptr(), out.data_ptr(), self.workspace.data_ptr(),
+                                   _stream_handle(stream), choice)
+        if cache and table.get(key) != choice:
+            table[key] = choice
+            with open(cache, "w") as f:
+                json.dump(table, f, indent=1, sort_keys=True)
+        self.tuned = choice
+        return choice
 
     def status(self, stream: Optional[torch.cuda.Stream] = None) -> int:
         return abi.dwt2_status(self.handle, _stream_handle(stream))

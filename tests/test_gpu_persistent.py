@@ -1,0 +1,134 @@
+"""Persistent forward (DWT2_FLAG_PERSISTENT): every level of every image in one
+launch with a device work queue and bounded inter-level waits.
+
+Checked against the oracle per image, against the per-level launches (same
+arithmetic, so identical bits), under CUDA-graph capture, and with a dropped
+completion signal, which must surface as DWT2_ERR_TIMEOUT from dwt2_status
+without hanging, after which the context stays usable.
+"""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1704_08657_gb300 import abi, synth
+from paper_1704_08657_gb300.dwt import Plan
+from tests.util import assert_fp32_close, assert_lowp_close
+
+pytestmark = pytest.mark.gpu
+
+
+def _batch(shapes, seed=5, dtype=np.float32):
+    buf, descs = synth.batch_pack(shapes, seed=seed)
+    return buf.astype(dtype), descs
+
+
+def _unpack(flat: np.ndarray, descs):
+    return [flat[o:o + h * p].reshape(h, p)[:, :w] for (o, h, w, p) in descs]
+
+
+@pytest.mark.parametrize("h,w,levels", [(512, 512, 5), (1000, 764, 4), (130, 250, 3), (7, 5, 2), (2, 2, 1),
+                                        (2048, 96, 5), (33, 4100, 3)])
+@pytest.mark.parametrize("scheme", ["reduced", "nonsep", "sep"])
+@pytest.mark.parametrize("loader", ["tma", "cpasync"])
+def test_persistent_single_image(h, w, levels, scheme, loader, monkeypatch):
+    # single images load with TMA (tensor maps as kernel parameters); the
+    # cp.async loader of large batches is forced here to cover it as well
+    monkeypatch.setenv("DWT2_PML_CPASYNC", "1" if loader == "cpasync" else "0")
+    x = synth.gradient(h, w, seed=2)
+    pitch = (w + 3) // 4 * 4
+    xd = torch.zeros((h, pitch), device="cuda")
+    xd[:, :w] = torch.from_numpy(x).cuda()
+    pp = Plan.single(h, w, levels, pitch=pitch, scheme=scheme, flags=abi.DWT2_FLAG_PERSISTENT)
+    pl = Plan.single(h, w, levels, pitch=pitch, scheme=scheme)
+    cp = pp.forward(xd)
+    cl = pl.forward(xd)
+    torch.cuda.synchronize()
+    assert pp.status() == 0
+    assert torch.equal(cp[:, :w], cl[:, :w]), "persistent and per-level launches differ"
+    ref = oracle.forward97(x.astype(np.float64), levels)
+    assert_fp32_close(cp[:, :w].cpu().numpy(), ref, levels, 255.0, f"persistent {scheme} {h}x{w}")
+
+
+@pytest.mark.parametrize("n,seed", [(40, 4), (512, 4)])
+def test_persistent_batch_uneven_images(n, seed):
+    shapes = synth.batch_shapes(n, seed=seed)
+    if n == 512:  # the full batch: sizes 64..2048, three levels
+        assert min(min(s) for s in shapes) >= 64 and max(max(s) for s in shapes) <= 2048
+    buf, descs = _batch(shapes)
+    xd = torch.from_numpy(buf).cuda()
+    plan = Plan(descs, 3, flags=abi.DWT2_FLAG_PERSISTENT)
+    c = plan.forward(xd)
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    got = _unpack(c.cpu().numpy(), descs)
+    imgs = _unpack(buf, descs)
+    for i, (g, x) in enumerate(zip(got, imgs)):
+        if n == 512 and i % 16 != 0:
+            continue  # the oracle checks every 16th image of the full batch
+        ref = oracle.forward97(x.astype(np.float64), 3)
+        assert_fp32_close(g, ref, 3, 255.0, f"image {i} {x.shape}")
+    # every image also equals the one-launch-per-image path, bit for bit
+    per = Plan(descs, 3).forward(xd)
+    torch.cuda.synchronize()
+    assert torch.equal(per, c)
+
+
+def test_persistent_batch_lowp_and_int():
+    shapes = synth.batch_shapes(24, seed=9)
+    buf, descs = _batch(shapes)
+    xd = torch.from_numpy(buf).cuda()
+    imgs = _unpack(buf, descs)
+    c = Plan(descs, 3, coef_dtype=torch.float16, flags=abi.DWT2_FLAG_PERSISTENT).forward(xd)
+    got = _unpack(c.float().cpu().numpy(), descs)
+    for g, x in zip(got, imgs):
+        assert_lowp_close(g, oracle.forward97(x.astype(np.float64), 3), 3, 1e-3, "fp16 batch")
+    bi = np.rint(buf).astype(np.int32)
+    ci = Plan(descs, 3, wavelet="cdf53", coef_dtype=torch.int32, flags=abi.DWT2_FLAG_PERSISTENT).forward(
+        torch.from_numpy(bi).cuda())
+    goti = _unpack(ci.cpu().numpy(), descs)
+    for g, x in zip(goti, _unpack(bi, descs)):
+        assert np.array_equal(g.astype(np.int64), oracle.forward53i(x.astype(np.int64), 3))
+
+
+def test_persistent_under_cuda_graph():
+    shapes = synth.batch_shapes(64, seed=4)
+    buf, descs = _batch(shapes)
+    xd = torch.from_numpy(buf).cuda()
+    plan = Plan(descs, 3, flags=abi.DWT2_FLAG_PERSISTENT)
+    ws = plan.workspace  # allocated before capture
+    out = torch.zeros_like(xd)  # pitch padding and gaps between images are never written
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        plan.forward(xd, out, stream=s)  # warm-up outside the capture
+    torch.cuda.synchronize()
+    ref = out.clone()
+    g = torch.cuda.CUDAGraph()
+    out.zero_()
+    with torch.cuda.graph(g, stream=s):
+        plan.forward(xd, out, stream=s)
+    for _ in range(3):
+        out.zero_()
+        g.replay()
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    assert torch.equal(out, ref)
+    del ws
+
+
+def test_dropped_signal_times_out_without_hanging(monkeypatch):
+    monkeypatch.setenv("DWT2_TIMEOUT_MS", "30")
+    h = w = 512
+    x = torch.from_numpy(synth.uniform(h, w, seed=1)).cuda()
+    plan = Plan.single(h, w, 3, flags=abi.DWT2_FLAG_PERSISTENT | abi.DWT2_FLAG_TEST_DROP_SIGNAL)
+    plan.forward(x)
+    assert plan.status() == abi.DWT2_ERR_TIMEOUT
+    assert plan.status() == 0  # the status word was cleared
+    # the context is still usable
+    ok = Plan.single(h, w, 3, flags=abi.DWT2_FLAG_PERSISTENT)
+    c = ok.forward(x)
+    assert ok.status() == 0
+    ref = oracle.forward97(x.cpu().numpy().astype(np.float64), 3)
+    assert_fp32_close(c.cpu().numpy(), ref, 3, 255.0, "after timeout")
