@@ -280,6 +280,7 @@ def run_ours(a):
     plan = make(a.scheme)
     coef = torch.empty_like(x)
     ws = plan.workspace
+    tuned = plan.autotune(x, coef)  # untimed: picks the kernel configuration and segment height
 
     def step():
         abi.dwt2_forward(plan.handle, x.data_ptr(), coef.data_ptr(), ws.data_ptr(), stream.cuda_stream)
@@ -349,9 +350,11 @@ def run_ours(a):
             "peak_source": f"{peak_kind} HBM copy bandwidth", "level1_ms": l1,
             "traffic": profiled_traffic(n, n), "algorithmic_bytes": 8 * n * n}
 
+    cfg = config_of(a, world)
+    cfg["autotuned_choice"] = tuned
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_of(a, world),
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
             "roofline": roof, "gpu_launches": a.steps * a.levels, "clocks": clocks}
 
     # end to end through the public API with host buffers
@@ -434,6 +437,7 @@ def run_ours(a):
             comp[f"cdf53i/{scheme}/i32/L{a.levels}"] = {"gpx_s": n * n / (ms * 1e-3) / 1e9, "ms": ms}
             p.close()
             del out, xi
+        comp.update(batch_and_grad(dev, stream, barrier))
         line["compare"] = comp
 
     if rank == 0 and world == 1 and not a.no_cpu:
@@ -446,6 +450,75 @@ def run_ours(a):
     if pg is not None:
         pg.barrier()
         pg.destroy_process_group()
+
+
+def _time(fn, steps, stream, barrier):
+    import torch
+    for _ in range(3):
+        fn()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    barrier()
+    return e0.elapsed_time(e1) / steps
+
+
+def batch_and_grad(dev, stream, barrier):
+    """The batching and differentiation forms on their own workloads."""
+    import torch
+
+    from paper_1704_08657_gb300 import abi, synth
+    from paper_1704_08657_gb300.dwt import Plan
+    out = {}
+    # 512 uneven images, sides log-uniform in [64, 2048], three levels
+    shapes = synth.batch_shapes(512, seed=4)
+    buf, descs = synth.batch_pack(shapes, seed=5)
+    px = sum(h * w for h, w in shapes)
+    xb = torch.from_numpy(buf).to(dev)
+    cb = torch.empty_like(xb)
+    per = Plan(descs, 3, device=dev)
+    ms_per = _time(lambda: per.forward(xb, cb, stream), 5, stream, barrier)
+    per.close()
+    pp = Plan(descs, 3, flags=abi.DWT2_FLAG_PERSISTENT, device=dev)
+    choice = pp.autotune(xb, cb, stream)
+    pp.forward(xb, cb, stream)
+    barrier()
+    g = torch.cuda.CUDAGraph()
+    s2 = torch.cuda.Stream(dev)
+    s2.wait_stream(stream)
+    with torch.cuda.graph(g, stream=s2):
+        pp.forward(xb, cb, s2)
+    ms_graph = _time(lambda: g.replay(), 50, stream, barrier)
+    assert pp.status() == 0
+    out["batch512/L3/persistent_graph"] = {"gpx_s": px / (ms_graph * 1e-3) / 1e9, "ms": ms_graph, "pixels": px,
+                                           "autotuned_choice": choice, "launches": 1}
+    out["batch512/L3/launch_per_image"] = {"gpx_s": px / (ms_per * 1e-3) / 1e9, "ms": ms_per,
+                                           "launches": 3 * len(shapes)}
+    del g, xb, cb
+    pp.close()
+    # 16 x 4096^2, four levels: forward + adjoint of the L1 detail loss
+    side, nimg, levels = 4096, 16, 4
+    descs = [(i * side * side, side, side, side) for i in range(nimg)]
+    pg = Plan(descs, levels, scheme="reduced", device=dev)
+    x = torch.randint(0, 256, (nimg * side * side,), device=dev, generator=torch.Generator(dev).manual_seed(6)).float()
+    cbuf = torch.empty_like(x)
+    gin = torch.empty_like(x)
+    scale = 1.0 / pg.n_detail()
+
+    def fwd_bwd():
+        pg.forward(x, cbuf, stream)
+        pg.adjoint_l1(cbuf, scale, gin, stream)
+    ms = _time(fwd_bwd, 20, stream, barrier)
+    ms_f = _time(lambda: pg.forward(x, cbuf, stream), 20, stream, barrier)
+    npx = nimg * side * side
+    out["grad16x4096/L4/forward+adjoint_l1"] = {"gpx_s": npx / (ms * 1e-3) / 1e9, "ms": ms, "forward_ms": ms_f,
+                                                 "adjoint_ms": ms - ms_f}
+    pg.close()
+    return out
 
 
 def main():

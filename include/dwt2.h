@@ -142,6 +142,16 @@ int dwt2_inverse(dwt2_plan_t plan, const void* coef, void* out, void* workspace,
 int dwt2_adjoint(dwt2_plan_t plan, const void* coef_grad, void* in_grad, void* workspace,
                  void* stream);
 
+/* dwt2_adjoint_l1 -- in_grad = W^T(scale * sign(detail(coef))): the gradient
+ * with respect to the image of scale * (sum of |c| over every detail band),
+ * the coarsest LL band excluded, where coef = W(image) (not in the paper; a
+ * wavelet-domain L1 loss for training and regularised reconstruction).  The
+ * sign is taken inside the adjoint's band loads, so no gradient array is
+ * written.  scale = 1 / (number of detail coefficients) gives the mean.  CDF
+ * 9/7 with FP32 coefficients; coef and in_grad as for dwt2_adjoint. */
+int dwt2_adjoint_l1(dwt2_plan_t plan, const void* coef, void* in_grad, float scale, void* workspace,
+                    void* stream);
+
 /* dwt2_autotune -- choose the plan's launch configuration (not in the paper).
  * With *choice < 0: run the forward on the given buffers (same arguments as
  * dwt2_forward) for each candidate configuration (kernel tile shape and

@@ -29,7 +29,7 @@ DWT2_FLAG_PERSISTENT = 0x1
 DWT2_FLAG_TEST_DROP_SIGNAL = 0x100
 
 # the functions the header declares (checked by the CPU test suite)
-EXPORTS = ("dwt2_plan", "dwt2_workspace_bytes", "dwt2_forward", "dwt2_inverse", "dwt2_adjoint",
+EXPORTS = ("dwt2_plan", "dwt2_workspace_bytes", "dwt2_forward", "dwt2_inverse", "dwt2_adjoint", "dwt2_adjoint_l1",
            "dwt2_autotune", "dwt2_status", "dwt2_profile", "dwt2_profile_read", "dwt2_forward_noalloc",
            "dwt2_destroy", "dwt2_strerror")
 
@@ -67,6 +67,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         f = getattr(lib, name)
         f.argtypes = [vp, vp, vp, vp, vp]
         f.restype = ctypes.c_int
+    lib.dwt2_adjoint_l1.argtypes = [vp, vp, vp, ctypes.c_float, vp, vp]
+    lib.dwt2_adjoint_l1.restype = ctypes.c_int
     lib.dwt2_autotune.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int)]
     lib.dwt2_autotune.restype = ctypes.c_int
     lib.dwt2_status.argtypes = [vp, vp]
@@ -126,6 +128,13 @@ def dwt2_inverse(plan: int, coef_ptr: int, out_ptr: int, ws_ptr: int = 0, stream
 
 def dwt2_adjoint(plan: int, gcoef_ptr: int, gin_ptr: int, ws_ptr: int = 0, stream: int = 0) -> None:
     _call("dwt2_adjoint", plan, gcoef_ptr, gin_ptr, ws_ptr, stream)
+
+
+def dwt2_adjoint_l1(plan: int, coef_ptr: int, gin_ptr: int, scale: float, ws_ptr: int = 0, stream: int = 0) -> None:
+    rc = load().dwt2_adjoint_l1(ctypes.c_void_p(plan), ctypes.c_void_p(coef_ptr), ctypes.c_void_p(gin_ptr),
+                                ctypes.c_float(scale), ctypes.c_void_p(ws_ptr), ctypes.c_void_p(stream))
+    if rc != DWT2_OK:
+        raise Dwt2Error(rc, "dwt2_adjoint_l1")
 
 
 def dwt2_autotune(plan: int, in_ptr: int, coef_ptr: int, ws_ptr: int = 0, stream: int = 0,

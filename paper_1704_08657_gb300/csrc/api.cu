@@ -570,12 +570,15 @@ int dwt2_forward(dwt2_plan_t p, const void* in, void* coef, void* workspace, voi
     return DWT2_OK;
 }
 
-// shared by the inverse and the adjoint: levels from the coarsest down
-static int run_inverse_like(dwt2_plan_t p, const void* coef, void* out, void* workspace, void* stream, bool adj) {
+// shared by the inverse and the adjoint: levels from the coarsest down.
+// l1: adjoint of l1_scale * sum |detail coefficients| (coef holds coefficients).
+static int run_inverse_like(dwt2_plan_t p, const void* coef, void* out, void* workspace, void* stream, bool adj,
+                            bool l1 = false, float l1_scale = 0.f) {
     if (!p || !coef || !out) return DWT2_ERR_INVALID_ARG;
     if (p->ws_bytes && !workspace) return DWT2_ERR_INVALID_ARG;
     if (workspace && !aligned(workspace, 256)) return DWT2_ERR_MISALIGNED;
     if (adj && p->wavelet != DWT2_CDF97) return DWT2_ERR_UNSUPPORTED;
+    if (l1 && p->coef_dtype != DWT2_F32) return DWT2_ERR_UNSUPPORTED;
     const size_t csz = adj ? 4 : dtype_size(p->coef_dtype);
     if (!aligned(coef, csz) || !aligned(out, 4)) return DWT2_ERR_MISALIGNED;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -621,6 +624,8 @@ static int run_inverse_like(dwt2_plan_t p, const void* coef, void* out, void* wo
             ipm.vec_ll = coarsest ? cvec : 1;
             ipm.vec_out = (ipm.out_pitch % 4 == 0) && aligned(ipm.out, 16);
             ipm.status = p->d_status;
+            ipm.l1 = l1;
+            ipm.l1_scale = l1_scale;
             int e;
             if (adj) {
                 e = launch_adjoint_f32(ipm, grid, s);
@@ -706,6 +711,10 @@ int dwt2_inverse(dwt2_plan_t p, const void* coef, void* out, void* workspace, vo
 
 int dwt2_adjoint(dwt2_plan_t p, const void* coef_grad, void* in_grad, void* workspace, void* stream) {
     return run_inverse_like(p, coef_grad, in_grad, workspace, stream, true);
+}
+
+int dwt2_adjoint_l1(dwt2_plan_t p, const void* coef, void* in_grad, float scale, void* workspace, void* stream) {
+    return run_inverse_like(p, coef, in_grad, workspace, stream, true, true, scale);
 }
 
 }  // extern "C"

@@ -49,6 +49,10 @@ struct InvParams {
     int64_t out_pitch;
     int vec_in_lo, vec_in_hi, vec_ll, vec_out;
     unsigned* status;
+    // adjoint of an L1 loss on the detail bands: band values v read from the
+    // coefficients become l1_scale * sign(v) (detail bands) or 0 (coarsest LL)
+    int l1;
+    float l1_scale;
 };
 
 // Persistent forward: one descriptor per (image, level), one entry per unit

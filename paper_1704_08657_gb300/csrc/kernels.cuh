@@ -569,6 +569,19 @@ __device__ __forceinline__ void load_bands(const InvParams& p, int vi, int jb, b
     }
 }
 
+// L1 adjoint: the gradient of l1_scale * sum |detail| w.r.t. the coefficients
+template <class CT, int QL>
+__device__ __forceinline__ void l1_transform(const InvParams& p, Row<CT, QL>& r) {
+    const float s = p.l1_scale;
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+        if (!p.ll_is_ct) r.c1[q] = CT(0);  // the coarsest LL is not in the loss
+        r.c2[q] = CT(r.c2[q] > 0 ? s : (r.c2[q] < 0 ? -s : 0.f));
+        r.c3[q] = CT(r.c3[q] > 0 ? s : (r.c3[q] < 0 ? -s : 0.f));
+        r.c4[q] = CT(r.c4[q] > 0 ? s : (r.c4[q] < 0 ? -s : 0.f));
+    }
+}
+
 // --------------------------------------------------------- inverse / adjoint
 // Pipe: Inv97<S, QL>, Inv53<S, QL> or Adj97<QL>.  BT: coefficient element type.
 template <class Pipe, class BT, bool ADJ, int QL, int NW>
@@ -608,6 +621,12 @@ __global__ void __launch_bounds__(NW * 32) inv_kernel(const InvParams p) {
         R pf[2];  // rows vi+1 and vi+2 in flight
         load_bands<CT, BT, MIRROR, QL>(p, A0, jb, fast_row(A0), pf[0]);
         load_bands<CT, BT, MIRROR, QL>(p, A0 + 1, jb, fast_row(A0 + 1), pf[1]);
+        if constexpr (ADJ) {
+            if (p.l1) {
+                l1_transform(p, pf[0]);
+                l1_transform(p, pf[1]);
+            }
+        }
         CT* row_e = reinterpret_cast<CT*>(p.out) + int64_t(2 * R0) * p.out_pitch;
         const int px = 2 * jb;  // first pixel column of the lane
         for (int gi = 0; gi < n_grp; ++gi) {
@@ -617,6 +636,9 @@ __global__ void __launch_bounds__(NW * 32) inv_kernel(const InvParams p) {
                 const int vi = A0 + gi * PHASES + PH;
                 pipe.template slot<PH>() = pf[PH % 2];
                 load_bands<CT, BT, MIRROR, QL>(p, vi + 2, jb, fast_row(vi + 2), pf[PH % 2]);
+                if constexpr (ADJ) {
+                    if (p.l1) l1_transform(p, pf[PH % 2]);
+                }
                 const R& out = pipe.template step<PH>(vi);
                 const int oi = vi - Pipe::LAG;
                 if (oi < R0 || oi >= R1) return;

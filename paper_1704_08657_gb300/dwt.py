@@ -105,6 +105,31 @@ class Plan:
                          _stream_handle(stream))
         return out
 
+    def adjoint_l1(self, coef: torch.Tensor, scale: float, out: Optional[torch.Tensor] = None,
+                   stream: Optional[torch.cuda.Stream] = None) -> torch.Tensor:
+        """Gradient of scale * sum|detail coefficients| w.r.t. the image, where
+        coef = forward(image) (dwt2_adjoint_l1)."""
+        self._check(coef, torch.float32, "coef")
+        if out is None:
+            out = torch.empty_like(coef)
+        self._check(out, torch.float32, "out")
+        abi.dwt2_adjoint_l1(self.handle, coef.data_ptr(), out.data_ptr(), float(scale), self.workspace.data_ptr(),
+                            _stream_handle(stream))
+        return out
+
+    def coarsest_ll(self):
+        """(offset, h, w, pitch) of every image's coarsest low-low band."""
+        out = []
+        for (o, h, w, p) in self.images:
+            for _ in range(self.levels):
+                h, w = (h + 1) // 2, (w + 1) // 2
+            out.append((o, h, w, p))
+        return out
+
+    def n_detail(self) -> int:
+        """Number of detail coefficients over all images and levels."""
+        return sum(h * w for (_, h, w, _) in self.images) - sum(h * w for (_, h, w, _) in self.coarsest_ll())
+
     def tune_key(self) -> str:
         """Cache key of this plan's autotuning choice on this GPU and driver."""
         h = hashlib.sha256(repr(self.images).encode()).hexdigest()[:16]
@@ -168,6 +193,39 @@ class DWT2Function(torch.autograd.Function):
 
 def dwt2(x: torch.Tensor, plan: Plan) -> torch.Tensor:
     return DWT2Function.apply(x, plan)
+
+
+def _abs_sum_images(c: torch.Tensor, regions) -> torch.Tensor:
+    flat = c.reshape(-1)
+    tot = torch.zeros((), dtype=torch.float64, device=c.device)
+    for (o, h, w, p) in regions:
+        tot = tot + flat[o:o + h * p].view(h, p)[:, :w].abs().sum(dtype=torch.float64)
+    return tot
+
+
+class L1DetailLoss(torch.autograd.Function):
+    """mean |detail coefficients| of W(x) (every level, the coarsest LL
+    excluded).  The backward is one dwt2_adjoint_l1 call: the sign of the
+    coefficients is taken inside the adjoint kernel."""
+
+    @staticmethod
+    def forward(ctx, x: torch.Tensor, plan: Plan) -> torch.Tensor:
+        c = plan.forward(x)
+        ctx.plan = plan
+        ctx.save_for_backward(c)
+        n = plan.n_detail()
+        total = _abs_sum_images(c, plan.images) - _abs_sum_images(c, plan.coarsest_ll())
+        return (total / n).to(torch.float32)
+
+    @staticmethod
+    def backward(ctx, gout: torch.Tensor):
+        (c,) = ctx.saved_tensors
+        plan = ctx.plan
+        return plan.adjoint_l1(c, float(gout) / plan.n_detail()), None
+
+
+def l1_detail_loss(x: torch.Tensor, plan: Plan) -> torch.Tensor:
+    return L1DetailLoss.apply(x, plan)
 
 
 def band_slices(h: int, w: int, levels: int) -> List[Tuple[int, str, slice, slice]]:

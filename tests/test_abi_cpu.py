@@ -20,7 +20,7 @@ def lib():
 def _declared_functions():
     txt = open(os.path.join(ROOT, "include", "dwt2.h")).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"\b(dwt2_[a-z_]+)\s*\(", txt)))
+    return sorted(set(re.findall(r"\b(dwt2_[a-z_0-9]+)\s*\(", txt)))
 
 
 def test_exports_every_declared_function(lib):

@@ -71,9 +71,9 @@ def test_persistent_batch_uneven_images(n, seed):
         ref = oracle.forward97(x.astype(np.float64), 3)
         assert_fp32_close(g, ref, 3, 255.0, f"image {i} {x.shape}")
     # every image also equals the one-launch-per-image path, bit for bit
-    per = Plan(descs, 3).forward(xd)
-    torch.cuda.synchronize()
-    assert torch.equal(per, c)
+    per = _unpack(Plan(descs, 3).forward(xd).cpu().numpy(), descs)
+    for i, (a, b) in enumerate(zip(per, got)):
+        assert np.array_equal(a, b), f"image {i}"  # padding between images is never written
 
 
 def test_persistent_batch_lowp_and_int():

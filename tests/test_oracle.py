@@ -259,3 +259,21 @@ def test_int53_close_to_linear_filter_bank(h, w):
     # rounding: each predict adds [0, 1/2], each update (-1/2, 3/4]; two axes
     assert np.abs(d).max() <= 2.5
     assert abs(d.mean()) < 0.5
+
+
+def test_oracle_adjoint_is_the_gradient_fp64():
+    """gradcheck (FP64, 32x32, three levels): the oracle's adjoint is the
+    Jacobian transpose of its forward transform."""
+    import torch
+
+    class F(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, x):
+            return torch.from_numpy(oracle.forward97(x.detach().numpy(), 3))
+
+        @staticmethod
+        def backward(ctx, g):
+            return torch.from_numpy(oracle.adjoint97(g.detach().numpy(), 3))
+
+    x = torch.from_numpy(RNG.standard_normal((32, 32))).requires_grad_(True)
+    assert torch.autograd.gradcheck(F.apply, (x,), eps=1e-6, atol=1e-8, rtol=1e-6, fast_mode=True)
