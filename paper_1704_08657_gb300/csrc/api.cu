@@ -150,8 +150,12 @@ struct dwt2_plan_s {
     uint64_t timeout_ns;
     // persistent forward: descriptors, queue-ordered units, counters + queue word
     bool persistent;
-    int pml_bps, pml_seg, pml_force_cpasync;
+    int pml_bps, pml_seg, pml_force_cpasync, pml_lag_pct;
     std::vector<PmlDesc> h_descs;  // host copy (TMA maps are encoded per call from it)
+    // batched inverse / adjoint (several images): descriptors, units by level
+    InvDesc* d_inv_descs;
+    InvUnit* d_inv_units;
+    std::vector<int> inv_level_start;  // units of level l: [start[l], start[l+1])
     PmlDesc* d_descs;
     PmlUnit* d_units;
     unsigned* d_counters;  // n_counters segment counters followed by the queue word
@@ -183,7 +187,7 @@ int build_persistent(dwt2_plan_t p) {
     const int bps = pml_blocks_per_sm(p->wavelet, p->scheme, p->coef_dtype);
     if (bps <= 0) return DWT2_ERR_CUDA;
     p->pml_bps = bps;
-    const int64_t lag = int64_t(p->sm_count) * bps * PML_NW * 5 / 4;
+    const int64_t lag = int64_t(p->sm_count) * bps * PML_NW * std::max(10, p->pml_lag_pct) / 100;
     const int L = p->levels;
     const size_t csz = dtype_size(p->coef_dtype);
     std::vector<PmlDesc> descs;
@@ -279,6 +283,98 @@ int build_persistent(dwt2_plan_t p) {
         cudaGetLastError();
         return DWT2_ERR_CUDA;
     }
+    return DWT2_OK;
+}
+
+// Tables of the batched inverse / adjoint: per (image, level) a descriptor,
+// per level the units of every image (segments of INV_BATCH_SEG quad rows).
+constexpr int INV_BATCH_SEG = 32;
+
+int build_inverse_batch(dwt2_plan_t p) {
+    const int L = p->levels;
+    std::vector<InvDesc> descs;
+    std::vector<std::vector<InvUnit>> by_level(L);
+    for (size_t i = 0; i < p->imgs.size(); ++i) {
+        const ImagePlan& ip = p->imgs[i];
+        const int64_t off = ip.d.offset_elems, pitch = ip.d.pitch_elems;
+        const bool cvec = (pitch % 2 == 0);  // offsets are multiples of 4 elements
+        for (int l = 0; l < L; ++l) {
+            const LevelGeom& g = ip.lv[l];
+            InvDesc d;
+            d.h = g.h, d.w = g.w, d.hq = g.hq, d.wq = g.wq, d.hh = g.hh, d.wh = g.wh;
+            d.n_strips = (g.wq + INV_OUT_Q - 1) / INV_OUT_Q;
+            d.seg_rows = std::min(INV_BATCH_SEG, g.hq);
+            d.coef_off = off;
+            d.coef_pitch = pitch;
+            const bool coarsest = (l == L - 1);
+            d.ll_is_ct = !coarsest;
+            d.ll_off = coarsest ? off : int64_t(ip.ws_off[l] / 4);
+            d.ll_pitch = coarsest ? pitch : round4(g.wq);
+            d.out_is_ws = l > 0;
+            d.out_off = (l == 0) ? off : int64_t(ip.ws_off[l - 1] / 4);
+            d.out_pitch = (l == 0) ? pitch : round4(g.w);
+            d.vec_in_lo = cvec;
+            d.vec_in_hi = cvec && (g.wq % 2 == 0);
+            d.vec_ll = coarsest ? cvec : 1;
+            d.vec_out = (d.out_pitch % 4 == 0);
+            const int di = int(descs.size());
+            descs.push_back(d);
+            const int n_segs = (g.hq + d.seg_rows - 1) / d.seg_rows;
+            for (int gseg = 0; gseg < n_segs; ++gseg)
+                for (int s = 0; s < d.n_strips; ++s) by_level[l].push_back(InvUnit{di, s, gseg});
+        }
+    }
+    std::vector<InvUnit> units;
+    p->inv_level_start.assign(1, 0);
+    for (int l = 0; l < L; ++l) {
+        units.insert(units.end(), by_level[l].begin(), by_level[l].end());
+        p->inv_level_start.push_back(int(units.size()));
+    }
+    if (cudaMalloc(&p->d_inv_descs, descs.size() * sizeof(InvDesc)) != cudaSuccess ||
+        cudaMalloc(&p->d_inv_units, std::max<size_t>(1, units.size()) * sizeof(InvUnit)) != cudaSuccess ||
+        cudaMemcpy(p->d_inv_descs, descs.data(), descs.size() * sizeof(InvDesc), cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(p->d_inv_units, units.data(), units.size() * sizeof(InvUnit), cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        return DWT2_ERR_CUDA;
+    }
+    return DWT2_OK;
+}
+
+int inverse_batch(dwt2_plan_t p, const void* coef, void* out, void* workspace, cudaStream_t s, bool adj, bool l1,
+                  float l1_scale) {
+    const size_t csz = adj ? 4 : dtype_size(p->coef_dtype);
+    InvBatchParams b;
+    b.coef = coef;
+    b.out = out;
+    b.ws = workspace;
+    b.descs = p->d_inv_descs;
+    b.coef_vec = aligned(coef, 2 * csz);
+    b.out_vec = aligned(out, 16);
+    b.l1 = l1;
+    b.l1_scale = l1_scale;
+    b.status = p->d_status;
+    for (int l = p->levels - 1; l >= 0; --l) {
+        prof_mark(p, l, true, s);
+        b.units = p->d_inv_units + p->inv_level_start[l];
+        b.n_units = p->inv_level_start[l + 1] - p->inv_level_start[l];
+        const int grid = (b.n_units + INV_NW - 1) / INV_NW;
+        int e;
+        if (adj) {
+            e = launch_adj_batch_f32(b, grid, s);
+        } else {
+            switch (p->coef_dtype) {
+                case DWT2_F32: e = launch_inv_batch_f32(p->wavelet, p->scheme, b, grid, s); break;
+                case DWT2_F16: e = launch_inv_batch_f16(p->wavelet, p->scheme, b, grid, s); break;
+                case DWT2_BF16: e = launch_inv_batch_bf16(p->wavelet, p->scheme, b, grid, s); break;
+                default: e = launch_inv_batch_i32(p->wavelet, p->scheme, b, grid, s); break;
+            }
+        }
+        if (e != cudaSuccess) return DWT2_ERR_CUDA;
+        prof_mark(p, l, false, s);
+    }
+    if (p->prof_on) ++p->prof_calls;
     return DWT2_OK;
 }
 
@@ -433,9 +529,19 @@ int dwt2_plan(dwt2_plan_t* out, int wavelet, int levels, int boundary, int in_dt
     p->pml_bps = 0;
     p->pml_seg = env_int("DWT2_PML_SEG_ROWS", PML_SEG_DEFAULT);
     p->pml_force_cpasync = env_int("DWT2_PML_CPASYNC", 0);
+    p->pml_lag_pct = env_int("DWT2_PML_LAG_PCT", 300);
     if (p->pml_seg < 4) p->pml_seg = PML_SEG_DEFAULT;
+    p->d_inv_descs = nullptr;
+    p->d_inv_units = nullptr;
     if (p->persistent) {
         const int rc = build_persistent(p);
+        if (rc != DWT2_OK) {
+            dwt2_destroy(p);
+            return rc;
+        }
+    }
+    if (n_images > 1) {
+        const int rc = build_inverse_batch(p);
         if (rc != DWT2_OK) {
             dwt2_destroy(p);
             return rc;
@@ -453,6 +559,8 @@ void dwt2_destroy(dwt2_plan_t p) {
     if (p->d_descs) cudaFree(p->d_descs);
     if (p->d_units) cudaFree(p->d_units);
     if (p->d_counters) cudaFree(p->d_counters);
+    if (p->d_inv_descs) cudaFree(p->d_inv_descs);
+    if (p->d_inv_units) cudaFree(p->d_inv_units);
     for (cudaEvent_t e : p->ev0) cudaEventDestroy(e);
     for (cudaEvent_t e : p->ev1) cudaEventDestroy(e);
     delete p;
@@ -582,6 +690,7 @@ static int run_inverse_like(dwt2_plan_t p, const void* coef, void* out, void* wo
     const size_t csz = adj ? 4 : dtype_size(p->coef_dtype);
     if (!aligned(coef, csz) || !aligned(out, 4)) return DWT2_ERR_MISALIGNED;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (p->n_images > 1) return inverse_batch(p, coef, out, workspace, s, adj, l1, l1_scale);
     const int inv_bps = adj ? inverse_blocks_per_sm(p->wavelet, p->scheme, p->coef_dtype, true) : p->inv_bps;
     for (int l = p->levels - 1; l >= 0; --l) {
         prof_mark(p, l, true, s);

@@ -12,6 +12,10 @@ int launch_inverse_f32(int wav, int scheme, const InvParams& p, int grid, cudaSt
     return launch_inverse_t<float>(wav, scheme, p, grid, s);
 }
 
+int launch_inv_batch_f32(int wav, int scheme, const InvBatchParams& p, int grid, cudaStream_t s) {
+    return launch_inv_batch_t<float>(wav, scheme, p, grid, s);
+}
+
 int occupancy_forward_f32(int wav, int scheme, const FwdCfg& cfg) { return occupancy_forward_t<float>(wav, scheme, cfg); }
 int occupancy_inverse_f32(int scheme) { return occupancy_inverse_t<float>(scheme); }
 
@@ -42,6 +46,10 @@ int forward_blocks_per_sm(int wav, int scheme, int coef_dtype, const FwdCfg& cfg
         case DT_BF16: return occupancy_forward_bf16(wav, scheme, cfg);
         default: return occupancy_forward_i32(wav, scheme, cfg);
     }
+}
+
+int launch_adj_batch_f32(const InvBatchParams& p, int grid, cudaStream_t s) {
+    return launch_inv_batch_one<Adj97<INV_QL>, float, true>(p, grid, s);
 }
 
 int occupancy_pml_f16(int wav, int scheme);

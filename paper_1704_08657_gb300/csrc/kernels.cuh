@@ -583,88 +583,125 @@ __device__ __forceinline__ void l1_transform(const InvParams& p, Row<CT, QL>& r)
 }
 
 // --------------------------------------------------------- inverse / adjoint
+// One unit (strip s, quad rows [R0, R1)) of one inverse or adjoint level.
 // Pipe: Inv97<S, QL>, Inv53<S, QL> or Adj97<QL>.  BT: coefficient element type.
-template <class Pipe, class BT, bool ADJ, int QL, int NW>
-__global__ void __launch_bounds__(NW * 32) inv_kernel(const InvParams p) {
+template <class Pipe, class BT, bool ADJ, int QL>
+__device__ __forceinline__ void inv_unit(const InvParams& p, int s, int R0, int R1, int lane) {
     using CT = typename Pipe::CT;
     using R = Row<CT, QL>;
     constexpr bool MIRROR = !ADJ;
     constexpr int OUTQ = 32 * QL - 2 * HALO_Q;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-    Pieces<InvParams> pieces(p, blockIdx.x * NW + warp, gridDim.x * NW);
-    int s, R0, R1;
-    while (pieces.next(p, s, R0, R1)) {
-        const int A0 = R0 - 2;
-        const int n_arr = (R1 - R0) + 2 + Pipe::LAG;
-        const int n_grp = (n_arr + PHASES - 1) / PHASES;
-        const int x0 = s * (2 * OUTQ) - 2 * HALO_Q;
-        const int jb = x0 / 2 + QL * lane;
-        // the whole strip reads only existing band columns
-        const bool fast_cols = (x0 >= 0) && (x0 / 2 + 32 * QL <= p.wh);
-        bool mine[QL];
+    const int A0 = R0 - 2;
+    const int n_arr = (R1 - R0) + 2 + Pipe::LAG;
+    const int n_grp = (n_arr + PHASES - 1) / PHASES;
+    const int x0 = s * (2 * OUTQ) - 2 * HALO_Q;
+    const int jb = x0 / 2 + QL * lane;
+    // the whole strip reads only existing band columns
+    const bool fast_cols = (x0 >= 0) && (x0 / 2 + 32 * QL <= p.wh);
+    bool mine[QL];
 #pragma unroll
-        for (int q = 0; q < QL; ++q) {
-            const int lq = QL * lane + q;
-            mine[q] = (lq >= HALO_Q) && (lq < 32 * QL - HALO_Q);
-        }
+    for (int q = 0; q < QL; ++q) {
+        const int lq = QL * lane + q;
+        mine[q] = (lq >= HALO_Q) && (lq < 32 * QL - HALO_Q);
+    }
 
-        Pipe pipe;
-        pipe.init();
-        if constexpr (ADJ) {
+    Pipe pipe;
+    pipe.init();
+    if constexpr (ADJ) {
 #pragma unroll
-            for (int q = 0; q < QL; ++q) pipe.hw[q] = axis_weights(jb + q, p.w);
-            pipe.h = p.h;
-        }
-        auto fast_row = [&](int vi) { return fast_cols && vi >= 0 && 2 * vi + 1 < p.h; };
+        for (int q = 0; q < QL; ++q) pipe.hw[q] = axis_weights(jb + q, p.w);
+        pipe.h = p.h;
+    }
+    auto fast_row = [&](int vi) { return fast_cols && vi >= 0 && 2 * vi + 1 < p.h; };
 
-        R pf[2];  // rows vi+1 and vi+2 in flight
-        load_bands<CT, BT, MIRROR, QL>(p, A0, jb, fast_row(A0), pf[0]);
-        load_bands<CT, BT, MIRROR, QL>(p, A0 + 1, jb, fast_row(A0 + 1), pf[1]);
-        if constexpr (ADJ) {
-            if (p.l1) {
-                l1_transform(p, pf[0]);
-                l1_transform(p, pf[1]);
+    R pf[2];  // rows vi+1 and vi+2 in flight
+    load_bands<CT, BT, MIRROR, QL>(p, A0, jb, fast_row(A0), pf[0]);
+    load_bands<CT, BT, MIRROR, QL>(p, A0 + 1, jb, fast_row(A0 + 1), pf[1]);
+    if constexpr (ADJ) {
+        if (p.l1) {
+            l1_transform(p, pf[0]);
+            l1_transform(p, pf[1]);
+        }
+    }
+    CT* row_e = reinterpret_cast<CT*>(p.out) + int64_t(2 * R0) * p.out_pitch;
+    const int px = 2 * jb;  // first pixel column of the lane
+    for (int gi = 0; gi < n_grp; ++gi) {
+        static_for<PHASES>([&](auto ph) {
+            constexpr int PH = decltype(ph)::value;
+            if (gi * PHASES + PH >= n_arr) return;
+            const int vi = A0 + gi * PHASES + PH;
+            pipe.template slot<PH>() = pf[PH % 2];
+            load_bands<CT, BT, MIRROR, QL>(p, vi + 2, jb, fast_row(vi + 2), pf[PH % 2]);
+            if constexpr (ADJ) {
+                if (p.l1) l1_transform(p, pf[PH % 2]);
             }
-        }
-        CT* row_e = reinterpret_cast<CT*>(p.out) + int64_t(2 * R0) * p.out_pitch;
-        const int px = 2 * jb;  // first pixel column of the lane
-        for (int gi = 0; gi < n_grp; ++gi) {
-            static_for<PHASES>([&](auto ph) {
-                constexpr int PH = decltype(ph)::value;
-                if (gi * PHASES + PH >= n_arr) return;
-                const int vi = A0 + gi * PHASES + PH;
-                pipe.template slot<PH>() = pf[PH % 2];
-                load_bands<CT, BT, MIRROR, QL>(p, vi + 2, jb, fast_row(vi + 2), pf[PH % 2]);
-                if constexpr (ADJ) {
-                    if (p.l1) l1_transform(p, pf[PH % 2]);
-                }
-                const R& out = pipe.template step<PH>(vi);
-                const int oi = vi - Pipe::LAG;
-                if (oi < R0 || oi >= R1) return;
-                CT* row_o = row_e + p.out_pitch;
-                const bool has_o = 2 * oi + 1 < p.h;
+            const R& out = pipe.template step<PH>(vi);
+            const int oi = vi - Pipe::LAG;
+            if (oi < R0 || oi >= R1) return;
+            CT* row_o = row_e + p.out_pitch;
+            const bool has_o = 2 * oi + 1 < p.h;
 #pragma unroll
-                for (int q = 0; q < QL; q += 2) {
-                    const int c = px + 2 * q;
-                    if (mine[q] && mine[q + 1] && p.vec_out && c + 3 < p.w) {
-                        st4<CT>(row_e + c, out.c1[q], out.c2[q], out.c1[q + 1], out.c2[q + 1]);
-                        if (has_o) st4<CT>(row_o + c, out.c3[q], out.c4[q], out.c3[q + 1], out.c4[q + 1]);
-                    } else {
-                        const CT ev[4] = {out.c1[q], out.c2[q], out.c1[q + 1], out.c2[q + 1]};
-                        const CT od[4] = {out.c3[q], out.c4[q], out.c3[q + 1], out.c4[q + 1]};
+            for (int q = 0; q < QL; q += 2) {
+                const int c = px + 2 * q;
+                if (mine[q] && mine[q + 1] && p.vec_out && c + 3 < p.w) {
+                    st4<CT>(row_e + c, out.c1[q], out.c2[q], out.c1[q + 1], out.c2[q + 1]);
+                    if (has_o) st4<CT>(row_o + c, out.c3[q], out.c4[q], out.c3[q + 1], out.c4[q + 1]);
+                } else {
+                    const CT ev[4] = {out.c1[q], out.c2[q], out.c1[q + 1], out.c2[q + 1]};
+                    const CT od[4] = {out.c3[q], out.c4[q], out.c3[q + 1], out.c4[q + 1]};
 #pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            if (mine[q + (k >> 1)] && c + k < p.w) {
-                                row_e[c + k] = ev[k];
-                                if (has_o) row_o[c + k] = od[k];
-                            }
+                    for (int k = 0; k < 4; ++k) {
+                        if (mine[q + (k >> 1)] && c + k < p.w) {
+                            row_e[c + k] = ev[k];
+                            if (has_o) row_o[c + k] = od[k];
                         }
                     }
                 }
-                row_e += 2 * p.out_pitch;
-            });
-        }
+            }
+            row_e += 2 * p.out_pitch;
+        });
+    }
+}
+
+// One level of one image: the warps take their units from Pieces.
+template <class Pipe, class BT, bool ADJ, int QL, int NW>
+__global__ void __launch_bounds__(NW * 32) inv_kernel(const InvParams p) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    Pieces<InvParams> pieces(p, blockIdx.x * NW + warp, gridDim.x * NW);
+    int s, R0, R1;
+    while (pieces.next(p, s, R0, R1)) inv_unit<Pipe, BT, ADJ, QL>(p, s, R0, R1, lane);
+}
+
+// One level of every image of a batch in one launch: units from the plan's
+// table, dealt round-robin; geometry and offsets from per-image descriptors.
+template <class Pipe, class BT, bool ADJ, int QL, int NW>
+__global__ void __launch_bounds__(NW * 32) inv_batch_kernel(const InvBatchParams B) {
+    using CT = typename Pipe::CT;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int u = blockIdx.x * NW + warp; u < B.n_units; u += gridDim.x * NW) {
+        const InvUnit un = B.units[u];
+        const InvDesc& d = B.descs[un.desc];
+        InvParams p;
+        p.h = d.h, p.w = d.w, p.hq = d.hq, p.wq = d.wq, p.hh = d.hh, p.wh = d.wh;
+        p.n_strips = d.n_strips, p.seg_rows = d.seg_rows, p.n_segs = 0, p.n_units = 0, p.balanced = 0;
+        p.coef = static_cast<const BT*>(B.coef) + d.coef_off;
+        p.coef_pitch = d.coef_pitch;
+        p.ll = d.ll_is_ct ? static_cast<const void*>(static_cast<const CT*>(B.ws) + d.ll_off)
+                          : static_cast<const void*>(static_cast<const BT*>(B.coef) + d.ll_off);
+        p.ll_pitch = d.ll_pitch;
+        p.ll_is_ct = d.ll_is_ct;
+        p.out = d.out_is_ws ? static_cast<void*>(static_cast<CT*>(B.ws) + d.out_off)
+                            : static_cast<void*>(static_cast<CT*>(B.out) + d.out_off);
+        p.out_pitch = d.out_pitch;
+        p.vec_in_lo = d.vec_in_lo && B.coef_vec;
+        p.vec_in_hi = d.vec_in_hi && B.coef_vec;
+        p.vec_ll = d.ll_is_ct ? 1 : (d.vec_ll && B.coef_vec);
+        p.vec_out = d.out_is_ws ? 1 : (d.vec_out && B.out_vec);
+        p.status = B.status;
+        p.l1 = B.l1;
+        p.l1_scale = B.l1_scale;
+        const int R0 = un.g * d.seg_rows;
+        inv_unit<Pipe, BT, ADJ, QL>(p, un.s, R0, min(R0 + d.seg_rows, d.hq), lane);
     }
 }
 

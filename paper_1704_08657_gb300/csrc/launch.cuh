@@ -166,6 +166,27 @@ int launch_inv_one(const InvParams& p, int grid, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+template <class Pipe, class BT, bool ADJ>
+int launch_inv_batch_one(const InvBatchParams& p, int grid, cudaStream_t s) {
+    inv_batch_kernel<Pipe, BT, ADJ, INV_QL, INV_NW><<<grid, INV_NW * 32, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <class BT>
+int launch_inv_batch_t(int wav, int scheme, const InvBatchParams& p, int grid, cudaStream_t s) {
+    if constexpr (std::is_same<BT, int>::value) {
+        if (wav != WAV_CDF53I) return cudaErrorInvalidValue;
+        if (scheme == SCHEME_SEP) return launch_inv_batch_one<Inv53<SCHEME_SEP, INV_QL>, int, false>(p, grid, s);
+        return launch_inv_batch_one<Inv53<SCHEME_NONSEP, INV_QL>, int, false>(p, grid, s);
+    } else {
+        if (wav != WAV_CDF97) return cudaErrorInvalidValue;
+        if (scheme == SCHEME_NONSEP) return launch_inv_batch_one<Inv97<SCHEME_NONSEP, INV_QL>, BT, false>(p, grid, s);
+        if (scheme == SCHEME_REDUCED)
+            return launch_inv_batch_one<Inv97<SCHEME_REDUCED, INV_QL>, BT, false>(p, grid, s);
+        return launch_inv_batch_one<Inv97<SCHEME_SEP, INV_QL>, BT, false>(p, grid, s);
+    }
+}
+
 template <class BT>
 int launch_inverse_t(int wav, int scheme, const InvParams& p, int grid, cudaStream_t s) {
     if constexpr (std::is_same<BT, int>::value) {

@@ -132,3 +132,42 @@ def test_dropped_signal_times_out_without_hanging(monkeypatch):
     assert ok.status() == 0
     ref = oracle.forward97(x.cpu().numpy().astype(np.float64), 3)
     assert_fp32_close(c.cpu().numpy(), ref, 3, 255.0, "after timeout")
+
+
+def test_batch_inverse_adjoint_and_l1():
+    """Multi-image plans run the inverse and adjoint as one launch per level
+    for all images (plan-time descriptor tables)."""
+    shapes = synth.batch_shapes(30, seed=11)
+    buf, descs = _batch(shapes)
+    xd = torch.from_numpy(buf).cuda()
+    plan = Plan(descs, 3, scheme="reduced")
+    c = plan.forward(xd)
+    rec = plan.inverse(c)
+    g = torch.randn_like(xd)
+    gin = plan.adjoint(g)
+    gl1 = plan.adjoint_l1(c, 0.5)
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    imgs = _unpack(buf, descs)
+    cs = _unpack(c.cpu().numpy(), descs)
+    for x, r, ci, gi, gref, gl in zip(imgs, _unpack(rec.cpu().numpy(), descs), cs, _unpack(g.cpu().numpy(), descs),
+                                     _unpack(gin.cpu().numpy(), descs), _unpack(gl1.cpu().numpy(), descs)):
+        assert np.abs(r - x).max() <= 2e-3
+        ref = oracle.inverse97(ci.astype(np.float64), 3)
+        assert np.abs(r - ref).max() <= 2e-3
+        aref = oracle.adjoint97(gi.astype(np.float64), 3)
+        assert np.abs(gref - aref).max() <= 1e-4 * max(1.0, np.abs(aref).max())
+        sg = 0.5 * np.sign(ci.astype(np.float64))
+        hl, wl = ci.shape
+        for _ in range(3):
+            hl, wl = (hl + 1) // 2, (wl + 1) // 2
+        sg[:hl, :wl] = 0.0
+        lref = oracle.adjoint97(sg, 3)
+        assert np.abs(gl - lref).max() <= 1e-4 * max(1.0, np.abs(lref).max())
+    # integer 5/3: the batched inverse is exact
+    bi = np.rint(buf).astype(np.int32)
+    pi = Plan(descs, 3, wavelet="cdf53", coef_dtype=torch.int32)
+    ci = pi.forward(torch.from_numpy(bi).cuda())
+    back = pi.inverse(ci)
+    for x, r in zip(_unpack(bi, descs), _unpack(back.cpu().numpy(), descs)):
+        assert np.array_equal(x, r)
