@@ -181,6 +181,7 @@ size_t fwd_smem_bytes_of(const FwdCfg& c);
 constexpr int PML_QL = 2, PML_QR = 3, PML_NST = 3, PML_NW = 4;
 constexpr int INV_NW = 4;
 constexpr int INV_QL = 2;
+constexpr int INV_QR = 3, INV_NST = 3;  // staged inverse / adjoint ring
 constexpr int INV_OUT_Q = 32 * INV_QL - 4;
 
 }  // namespace dwt2

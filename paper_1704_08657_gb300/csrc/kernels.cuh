@@ -663,21 +663,231 @@ __device__ __forceinline__ void inv_unit(const InvParams& p, int s, int R0, int 
     }
 }
 
+// cp.async of `bytes` (4 or 8) from global to shared memory; src_bytes 0
+// zero-fills the destination.
+template <int BYTES>
+__device__ __forceinline__ void cp_async_small(void* dst, const void* src, bool valid) {
+    static_assert(BYTES == 4 || BYTES == 8, "cp.async.ca copies 4, 8 or 16 bytes");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(smem_u32(dst)), "l"(src), "n"(BYTES),
+                 "r"(valid ? BYTES : 0)
+                 : "memory");
+}
+
+template <class T, class CT>
+__device__ __forceinline__ void ld_pair_smem(const unsigned char* p, CT& a, CT& b) {
+    if constexpr (std::is_same<T, float>::value) {
+        const float2 v = *reinterpret_cast<const float2*>(p);
+        a = v.x, b = v.y;
+    } else if constexpr (std::is_same<T, int>::value) {
+        const int2 v = *reinterpret_cast<const int2*>(p);
+        a = v.x, b = v.y;
+    } else if constexpr (std::is_same<T, __half>::value) {
+        const __half2 v = *reinterpret_cast<const __half2*>(p);
+        a = __low2float(v), b = __high2float(v);
+    } else {
+        const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162*>(p);
+        a = __low2float(v), b = __high2float(v);
+    }
+}
+
+// Shared-memory ring of the staged inverse / adjoint: per stage QR quad rows
+// of the four bands, 256 bytes per band row (the lane's two quads as one pair).
+template <int QR, int NST, int NW>
+constexpr size_t inv_smem_bytes() {
+    return size_t(NW) * NST * QR * 4 * 256 + size_t(NW) * NST * 8;
+}
+
+// One unit of an interior strip whose band rows take paired copies: the bands
+// stream through a ring of NST stages of QR quad rows filled by cp.async
+// (mirrored rows for the inverse, zero rows for the adjoint at the top and
+// bottom).  Returns false when a stage wait timed out.
+template <class Pipe, class BT, bool ADJ, int QR, int NST>
+__device__ __forceinline__ bool inv_unit_staged(const InvParams& p, int s, int R0, int R1, int lane,
+                                                unsigned char* ring, uint64_t* bars, uint32_t& gstage) {
+    using CT = typename Pipe::CT;
+    using R = Row<CT, 2>;
+    constexpr int QL = 2, OUTQ = 32 * QL - 2 * HALO_Q;
+    constexpr int BAND = 256, ROWB = 4 * BAND, STAGEB = QR * ROWB;
+    constexpr int PB = 2 * int(sizeof(BT));  // bytes of a coefficient pair
+    static_assert(PHASES % QR == 0, "a group of arrivals must cover whole stages");
+    const int A0 = R0 - 2;
+    const int n_arr = (R1 - R0) + 2 + Pipe::LAG;
+    const int n_grp = (n_arr + PHASES - 1) / PHASES;
+    const int NT = (n_arr + QR - 1) / QR;
+    const int x0 = s * (2 * OUTQ) - 2 * HALO_Q;
+    const int jb = x0 / 2 + QL * lane;
+    const bool mine = (lane >= 1) && (lane <= 30);
+    const BT* coef = reinterpret_cast<const BT*>(p.coef);
+
+    auto issue = [&](int t, int slot) {
+        unsigned char* st = ring + slot * STAGEB;
+#pragma unroll
+        for (int r = 0; r < QR; ++r) {
+            const int vi = A0 + t * QR + r;
+            int re, ro;
+            bool rev, rov;
+            if (ADJ) {
+                rev = (vi >= 0) && (vi < p.hq);
+                rov = (vi >= 0) && (vi < p.hh);
+                re = rev ? vi : 0;
+                ro = rov ? vi : 0;
+            } else {
+                const bool in = (vi >= 0) && (2 * vi + 1 < p.h);
+                re = in ? vi : (fold_ws(2 * vi, p.h) >> 1);
+                ro = in ? vi : (fold_ws(2 * vi + 1, p.h) >> 1);
+                rev = rov = true;
+            }
+            unsigned char* d = st + r * ROWB;
+            if (p.ll_is_ct)
+                cp_async_small<8>(d + lane * 8, reinterpret_cast<const CT*>(p.ll) + int64_t(re) * p.ll_pitch + jb, rev);
+            else
+                cp_async_small<PB>(d + lane * PB, reinterpret_cast<const BT*>(p.ll) + int64_t(re) * p.ll_pitch + jb,
+                                   rev);
+            cp_async_small<PB>(d + BAND + lane * PB, coef + int64_t(re) * p.coef_pitch + p.wq + jb, rev);
+            cp_async_small<PB>(d + 2 * BAND + lane * PB, coef + int64_t(p.hq + ro) * p.coef_pitch + jb, rov);
+            cp_async_small<PB>(d + 3 * BAND + lane * PB, coef + int64_t(p.hq + ro) * p.coef_pitch + p.wq + jb, rov);
+        }
+        asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&bars[slot]))
+                     : "memory");
+    };
+    for (int t = 0; t < NST && t < NT; ++t) issue(t, (gstage + t) % NST);
+
+    Pipe pipe;
+    pipe.init();
+    if constexpr (ADJ && !std::is_same<Pipe, AdjInner97<2>>::value) {
+#pragma unroll
+        for (int q = 0; q < QL; ++q) pipe.hw[q] = axis_weights(jb + q, p.w);
+        pipe.h = p.h;
+    }
+    bool ok = true;
+    int t = 0, slot = 0;
+    const unsigned char* stage = ring;
+    CT* row_e = reinterpret_cast<CT*>(p.out) + int64_t(2 * R0) * p.out_pitch;
+    const int px = 2 * jb;
+    for (int gi = 0; gi < n_grp && ok; ++gi) {
+        static_for<PHASES>([&](auto ph) {
+            constexpr int PH = decltype(ph)::value;
+            constexpr int QI = PH % QR;
+            if (gi * PHASES + PH >= QR * NT) return;
+            if constexpr (QI == 0) {
+                if (!ok) return;
+                const uint32_t gs = gstage + t;
+                slot = gs % NST;
+                if (!mbar_wait_bounded(&bars[slot], (gs / NST) & 1u, p.status, 2000000000ull)) {
+                    for (int u = t + 1; u < NT && u < t + NST; ++u) {
+                        const uint32_t gu = gstage + u;
+                        mbar_wait_bounded(&bars[gu % NST], (gu / NST) & 1u, nullptr, 2000000000ull);
+                    }
+                    ok = false;
+                    return;
+                }
+                stage = ring + slot * STAGEB;
+            }
+            const int vi = A0 + gi * PHASES + PH;
+            R& in = pipe.template slot<PH>();
+            const unsigned char* d = stage + QI * ROWB;
+            if (p.ll_is_ct)
+                ld_pair_smem<CT, CT>(d + lane * 8, in.c1[0], in.c1[1]);
+            else
+                ld_pair_smem<BT, CT>(d + lane * PB, in.c1[0], in.c1[1]);
+            ld_pair_smem<BT, CT>(d + BAND + lane * PB, in.c2[0], in.c2[1]);
+            ld_pair_smem<BT, CT>(d + 2 * BAND + lane * PB, in.c3[0], in.c3[1]);
+            ld_pair_smem<BT, CT>(d + 3 * BAND + lane * PB, in.c4[0], in.c4[1]);
+            if constexpr (ADJ) {
+                if (p.l1) l1_transform(p, in);
+            }
+            const R& out = pipe.template step<PH>(vi);
+            const int oi = vi - Pipe::LAG;
+            if (oi >= R0 && oi < R1) {
+                CT* row_o = row_e + p.out_pitch;
+                const bool has_o = 2 * oi + 1 < p.h;
+                if (mine && p.vec_out && px + 3 < p.w) {
+                    st4<CT>(row_e + px, out.c1[0], out.c2[0], out.c1[1], out.c2[1]);
+                    if (has_o) st4<CT>(row_o + px, out.c3[0], out.c4[0], out.c3[1], out.c4[1]);
+                } else if (mine) {
+                    const CT ev[4] = {out.c1[0], out.c2[0], out.c1[1], out.c2[1]};
+                    const CT od[4] = {out.c3[0], out.c4[0], out.c3[1], out.c4[1]};
+#pragma unroll
+                    for (int k2 = 0; k2 < 4; ++k2) {
+                        if (px + k2 < p.w) {
+                            row_e[px + k2] = ev[k2];
+                            if (has_o) row_o[px + k2] = od[k2];
+                        }
+                    }
+                }
+                row_e += 2 * p.out_pitch;
+            }
+            if constexpr (QI == QR - 1) {
+                __syncwarp();
+                if (ok && t + NST < NT) issue(t + NST, slot);
+                ++t;
+            }
+        });
+    }
+    if (ok) gstage += NT;
+    return ok;
+}
+
+// inverse / adjoint unit: staged when the strip is interior and every band
+// row takes paired copies, else direct loads.  Adjoint units away from the
+// boundary (every quad of the strip and every row the steps weight in
+// [1, half - 2]) run the unweighted pipeline.
+template <class Pipe, class BT, bool ADJ, int QR, int NST>
+__device__ __forceinline__ bool inv_unit_any(const InvParams& p, int s, int R0, int R1, int lane,
+                                             unsigned char* ring, uint64_t* bars, uint32_t& gstage) {
+    constexpr int OUTQ = 32 * 2 - 2 * HALO_Q;
+    const int x0 = s * (2 * OUTQ) - 2 * HALO_Q;
+    const bool staged = (x0 >= 0) && (x0 / 2 + 64 <= p.wh) && p.vec_in_lo && p.vec_in_hi && p.vec_ll;
+    if constexpr (ADJ) {
+        // the steps weight rows R0-4 .. R1+1 (see Adj97::step) and quads x0/2 .. x0/2+63
+        const bool inner = staged && (x0 / 2 >= 1) && (x0 / 2 + 63 <= p.wh - 2) && (R0 - 4 >= 1) &&
+                           (R1 + 1 <= p.hh - 2);
+        if (inner) return inv_unit_staged<AdjInner97<2>, BT, true, QR, NST>(p, s, R0, R1, lane, ring, bars, gstage);
+    }
+    if (staged) return inv_unit_staged<Pipe, BT, ADJ, QR, NST>(p, s, R0, R1, lane, ring, bars, gstage);
+    inv_unit<Pipe, BT, ADJ, 2>(p, s, R0, R1, lane);
+    return true;
+}
+
+template <int QR, int NST, int NW>
+__device__ __forceinline__ void inv_ring(unsigned char* smem, int warp, int lane, unsigned char*& ring,
+                                         uint64_t*& bars) {
+    ring = smem + size_t(warp) * NST * QR * 4 * 256;
+    bars = reinterpret_cast<uint64_t*>(smem + size_t(NW) * NST * QR * 4 * 256) + warp * NST;
+    if (lane == 0) {
+#pragma unroll
+        for (int i = 0; i < NST; ++i) mbar_init(&bars[i], 32);
+        fence_mbar_init();
+    }
+    __syncwarp();
+}
+
 // One level of one image: the warps take their units from Pieces.
 template <class Pipe, class BT, bool ADJ, int QL, int NW>
 __global__ void __launch_bounds__(NW * 32) inv_kernel(const InvParams p) {
+    extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char* ring;
+    uint64_t* bars;
+    inv_ring<INV_QR, INV_NST, NW>(smem, warp, lane, ring, bars);
+    uint32_t gstage = 0;
     Pieces<InvParams> pieces(p, blockIdx.x * NW + warp, gridDim.x * NW);
     int s, R0, R1;
-    while (pieces.next(p, s, R0, R1)) inv_unit<Pipe, BT, ADJ, QL>(p, s, R0, R1, lane);
+    while (pieces.next(p, s, R0, R1))
+        if (!inv_unit_any<Pipe, BT, ADJ, INV_QR, INV_NST>(p, s, R0, R1, lane, ring, bars, gstage)) return;
 }
 
 // One level of every image of a batch in one launch: units from the plan's
 // table, dealt round-robin; geometry and offsets from per-image descriptors.
 template <class Pipe, class BT, bool ADJ, int QL, int NW>
-__global__ void __launch_bounds__(NW * 32) inv_batch_kernel(const InvBatchParams B) {
+__global__ void __launch_bounds__(NW * 32, 4) inv_batch_kernel(const InvBatchParams B) {
     using CT = typename Pipe::CT;
+    extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char* ring;
+    uint64_t* bars;
+    inv_ring<INV_QR, INV_NST, NW>(smem, warp, lane, ring, bars);
+    uint32_t gstage = 0;
     for (int u = blockIdx.x * NW + warp; u < B.n_units; u += gridDim.x * NW) {
         const InvUnit un = B.units[u];
         const InvDesc& d = B.descs[un.desc];
@@ -701,7 +911,9 @@ __global__ void __launch_bounds__(NW * 32) inv_batch_kernel(const InvBatchParams
         p.l1 = B.l1;
         p.l1_scale = B.l1_scale;
         const int R0 = un.g * d.seg_rows;
-        inv_unit<Pipe, BT, ADJ, QL>(p, un.s, R0, min(R0 + d.seg_rows, d.hq), lane);
+        if (!inv_unit_any<Pipe, BT, ADJ, INV_QR, INV_NST>(p, un.s, R0, min(R0 + d.seg_rows, d.hq), lane, ring, bars,
+                                                          gstage))
+            return;
     }
 }
 

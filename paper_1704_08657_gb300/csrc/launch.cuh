@@ -64,8 +64,8 @@ int occupancy_forward_t(int wav, int scheme, const FwdCfg& c) {
 template <class Pipe, class BT, bool ADJ>
 int occupancy_inv_one() {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, inv_kernel<Pipe, BT, ADJ, INV_QL, INV_NW>, INV_NW * 32, 0) !=
-        cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, inv_kernel<Pipe, BT, ADJ, INV_QL, INV_NW>, INV_NW * 32,
+                                                      inv_smem_bytes<INV_QR, INV_NST, INV_NW>()) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -162,13 +162,14 @@ int launch_pml_t(int wav, int scheme, const PmlLaunch* p, int grid, cudaStream_t
 
 template <class Pipe, class BT, bool ADJ>
 int launch_inv_one(const InvParams& p, int grid, cudaStream_t s) {
-    inv_kernel<Pipe, BT, ADJ, INV_QL, INV_NW><<<grid, INV_NW * 32, 0, s>>>(p);
+    inv_kernel<Pipe, BT, ADJ, INV_QL, INV_NW><<<grid, INV_NW * 32, inv_smem_bytes<INV_QR, INV_NST, INV_NW>(), s>>>(p);
     return cudaGetLastError();
 }
 
 template <class Pipe, class BT, bool ADJ>
 int launch_inv_batch_one(const InvBatchParams& p, int grid, cudaStream_t s) {
-    inv_batch_kernel<Pipe, BT, ADJ, INV_QL, INV_NW><<<grid, INV_NW * 32, 0, s>>>(p);
+    inv_batch_kernel<Pipe, BT, ADJ, INV_QL, INV_NW>
+        <<<grid, INV_NW * 32, inv_smem_bytes<INV_QR, INV_NST, INV_NW>(), s>>>(p);
     return cudaGetLastError();
 }
 

@@ -526,6 +526,45 @@ struct Adj97 {
     }
 };
 
+// Away from the image boundary every weight is 1: U^T = b(1 + z) and
+// P^T = a(1 + z^-1), so S_U^T is a spatial predict with coefficient b and
+// T_P^T a spatial update with coefficient a (the reduced split applies).  A
+// unit whose strip and rows are all interior runs this pipeline.
+template <int QL>
+struct AdjInner97 {
+    static constexpr int LAG = 2;
+    using CT = float;
+    using R = Row<float, QL>;
+    R rw[3];
+    Carry3<QL> ka[2], kb[2];
+    __device__ __forceinline__ void init() {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) zero_row(rw[i]);
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            zero_carry(ka[i]);
+            zero_carry(kb[i]);
+        }
+    }
+    template <int PH>
+    __device__ __forceinline__ R& slot() {
+        return rw[PH % 3];
+    }
+    template <int PH>
+    __device__ __forceinline__ R& step(int /*row*/) {
+        R& r0 = rw[PH % 3];
+        R& r1 = rw[(PH + 2) % 3];
+        R& r2 = rw[(PH + 1) % 3];
+        constexpr int c = PH & 1, n = c ^ 1;
+        scale97(r0);
+        rd_predict(r1, r0, C97::D, C97::DD);
+        rd_update(r1, ka[c], ka[n], C97::G, C97::GG);
+        rd_predict(r2, r1, C97::B, C97::BB);
+        rd_update(r2, kb[c], kb[n], C97::A, C97::AA);
+        return r2;
+    }
+};
+
 // ====================================================== integer CDF 5/3
 // Reversible 5/3: d -= floor((s_l + s_r)/2), s += floor((d_l + d_r + 2)/4),
 // in the separable order T^H, T^V, S^H, S^V (arithmetic shifts are floor).
