@@ -50,6 +50,7 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--profile", action="store_true",
                     help="warm-up and K steps only (for ncu captures); prints a minimal line")
+    ap.add_argument("--persistent", action="store_true", help="one persistent launch for the whole pyramid")
     return ap.parse_args()
 
 
@@ -274,10 +275,11 @@ def run_ours(a):
     x = torch.from_numpy(x_host).to(dev)
     stream = torch.cuda.current_stream(dev)
 
-    def make(scheme, coef_dtype=torch.float32, levels=a.levels, wavelet="cdf97"):
-        return Plan.single(n, n, levels, scheme=scheme, coef_dtype=coef_dtype, wavelet=wavelet, device=dev)
+    def make(scheme, coef_dtype=torch.float32, levels=a.levels, wavelet="cdf97", flags=0):
+        return Plan.single(n, n, levels, scheme=scheme, coef_dtype=coef_dtype, wavelet=wavelet, flags=flags,
+                           device=dev)
 
-    plan = make(a.scheme)
+    plan = make(a.scheme, flags=abi.DWT2_FLAG_PERSISTENT if a.persistent else 0)
     coef = torch.empty_like(x)
     ws = plan.workspace
     tuned = plan.autotune(x, coef)  # untimed: picks the kernel configuration and segment height
