@@ -19,7 +19,7 @@
  *     T_P^H adds P(c1) to c2 and P(c3) to c4 along rows, T_P^V adds P*(c1) to
  *     c3 and P*(c2) to c4 along columns, S_U^H / S_U^V likewise for U.
  *
- * Readings where the paper is silent (each is listed in the design doc):
+ * Readings where the paper is silent:
  *   - CDF 9/7 lifting constants alpha..zeta (not printed in the paper): the
  *     standard values below.  Scaling: low-pass samples times zeta, high-pass
  *     samples divided by zeta, per axis.

@@ -147,6 +147,9 @@ struct dwt2_plan_s {
     FwdCfg cfg;
     int fwd_bps, inv_bps;  // resident blocks per SM of the forward / inverse kernels
     int seg_override, balanced_env;
+    // fused level pairs: segment height in level l+1 quad rows (0: off) and
+    // how many pairs, from level 0 on, may run fused
+    int fuse_seg, fuse_pairs, fused_bps;
     uint64_t timeout_ns;
     // persistent forward: descriptors, queue-ordered units, counters + queue word
     bool persistent;
@@ -430,6 +433,105 @@ int forward_persistent(dwt2_plan_t p, const void* in, void* coef, void* workspac
     return e == cudaSuccess ? DWT2_OK : DWT2_ERR_CUDA;
 }
 
+// The output fields of one forward level of one image (geometry, band
+// pointers, pair-store alignment); the work decomposition is left to the caller.
+FwdParams level_outputs(dwt2_plan_t p, const ImagePlan& ip, int l, void* coef, void* workspace) {
+    const size_t csz = dtype_size(p->coef_dtype);
+    char* coef_img = static_cast<char*>(coef) + ip.d.offset_elems * csz;
+    char* wsb = static_cast<char*>(workspace);
+    const LevelGeom& g = ip.lv[l];
+    FwdParams fp;
+    memset(&fp, 0, sizeof(fp));
+    fp.h = g.h, fp.w = g.w, fp.hq = g.hq, fp.wq = g.wq, fp.hh = g.hh, fp.wh = g.wh;
+    fp.coef = coef_img;
+    fp.coef_pitch = ip.d.pitch_elems;
+    const bool last = (l == p->levels - 1);
+    if (last) {
+        fp.ll = coef_img;
+        fp.ll_pitch = ip.d.pitch_elems;
+        fp.ll_is_ct = 0;
+    } else {
+        fp.ll = wsb + ip.ws_off[l];
+        fp.ll_pitch = round4(g.wq);
+        fp.ll_is_ct = 1;
+    }
+    const bool coef_vec = (ip.d.pitch_elems % 2 == 0) && aligned(coef_img, 2 * csz);
+    fp.vec_lo = coef_vec;
+    fp.vec_hi = coef_vec && (g.wq % 2 == 0);
+    fp.vec_ll = last ? coef_vec : 1;
+    fp.status = p->d_status;
+    fp.timeout_ns = p->timeout_ns;
+    return fp;
+}
+
+// tensor maps over the input of level l of one image: a box of 2*qr rows and
+// a single row, both 64*ql pixels wide
+int level_maps(dwt2_plan_t p, const ImagePlan& ip, int l, const void* in, void* workspace, int ql, int qr,
+               CUtensorMap* box, CUtensorMap* row) {
+    const LevelGeom& g = ip.lv[l];
+    const void* src = (l == 0) ? static_cast<const void*>(static_cast<const char*>(in) + ip.d.offset_elems * 4)
+                               : static_cast<const void*>(static_cast<const char*>(workspace) + ip.ws_off[l - 1]);
+    const int64_t src_pitch = (l == 0) ? ip.d.pitch_elems : round4(ip.lv[l - 1].wq);
+    const bool is_int = p->wavelet == DWT2_CDF53_INT;
+    int rc = encode_map(box, src, g.w, g.h, src_pitch, 64 * ql, 2 * qr, is_int);
+    if (rc == DWT2_OK) rc = encode_map(row, src, g.w, g.h, src_pitch, 64 * ql, 1, is_int);
+    return rc;
+}
+
+int forward_level(dwt2_plan_t p, const ImagePlan& ip, int l, const void* in, void* coef, void* workspace,
+                  cudaStream_t s) {
+    CUtensorMap box, row;
+    const int rc = level_maps(p, ip, l, in, workspace, p->cfg.ql, p->cfg.qr, &box, &row);
+    if (rc != DWT2_OK) return rc;
+    FwdParams fp = level_outputs(p, ip, l, coef, workspace);
+    int grid = 0, balanced = 0;
+    const Decomp dc = decompose(ip.lv[l], fwd_out_quads(p->cfg), p->sm_count, p->fwd_bps, p->cfg.nw, p->seg_override,
+                                p->balanced_env, &grid, &balanced);
+    fp.n_strips = dc.n_strips, fp.seg_rows = dc.seg_rows, fp.n_segs = dc.n_segs, fp.n_units = dc.n_units;
+    fp.balanced = balanced;
+    int e;
+    switch (p->coef_dtype) {
+        case DWT2_F32: e = launch_forward_f32(p->wavelet, p->scheme, box, row, fp, grid, p->cfg, s); break;
+        case DWT2_F16: e = launch_forward_f16(p->wavelet, p->scheme, box, row, fp, grid, p->cfg, s); break;
+        case DWT2_BF16: e = launch_forward_bf16(p->wavelet, p->scheme, box, row, fp, grid, p->cfg, s); break;
+        default: e = launch_forward_i32(p->wavelet, p->scheme, box, row, fp, grid, p->cfg, s); break;
+    }
+    return e == cudaSuccess ? DWT2_OK : DWT2_ERR_CUDA;
+}
+
+// Levels l and l+1 in one launch need a level-l input of at least 64 x 64
+// (mirror rows of the low-low band stay inside a block's ring).
+bool fused_eligible(const LevelGeom& g) { return g.h >= 64 && g.w >= 64; }
+
+int forward_fused(dwt2_plan_t p, const ImagePlan& ip, int l, const void* in, void* coef, void* workspace,
+                  cudaStream_t s) {
+    CUtensorMap box, row;
+    const int rc = level_maps(p, ip, l, in, workspace, 2, FUSED_QR, &box, &row);
+    if (rc != DWT2_OK) return rc;
+    FusedParams fp;
+    fp.l1 = level_outputs(p, ip, l, coef, workspace);
+    fp.l1.ll = nullptr;  // the low-low band stays on chip
+    fp.l2 = level_outputs(p, ip, l + 1, coef, workspace);
+    const LevelGeom& g2 = ip.lv[l + 1];
+    fp.n_cols = (g2.w + FUSED_OWN_MAX - 1) / FUSED_OWN_MAX;
+    fp.own = int(round4((g2.w + fp.n_cols - 1) / fp.n_cols));
+    fp.seg2 = std::max(2, std::min(p->fuse_seg, g2.hq));  // the ring protocol needs segments of >= 2 rows
+    fp.n_segs = (g2.hq + fp.seg2 - 1) / fp.seg2;
+    if (fp.n_segs > 1 && g2.hq - (fp.n_segs - 1) * fp.seg2 < 2) --fp.n_segs;  // no one-row last segment
+    fp.n_items = fp.n_cols * fp.n_segs;
+    fp.status = p->d_status;
+    fp.timeout_ns = p->timeout_ns;
+    const int grid = std::min(fp.n_items, p->sm_count * p->fused_bps);
+    int e;
+    switch (p->coef_dtype) {
+        case DWT2_F32: e = launch_fused_f32(p->wavelet, p->scheme, box, row, fp, grid, s); break;
+        case DWT2_F16: e = launch_fused_f16(p->wavelet, p->scheme, box, row, fp, grid, s); break;
+        case DWT2_BF16: e = launch_fused_bf16(p->wavelet, p->scheme, box, row, fp, grid, s); break;
+        default: e = launch_fused_i32(p->wavelet, p->scheme, box, row, fp, grid, s); break;
+    }
+    return e == cudaSuccess ? DWT2_OK : DWT2_ERR_CUDA;
+}
+
 }  // namespace
 
 extern "C" {
@@ -506,6 +608,9 @@ int dwt2_plan(dwt2_plan_t* out, int wavelet, int levels, int boundary, int in_dt
     p->prof_calls = 0;
     p->timeout_ns = uint64_t(env_int("DWT2_TIMEOUT_MS", 2000)) * 1000000ull;
     p->seg_override = env_int("DWT2_SEG_ROWS", 0);
+    p->fuse_seg = std::max(0, env_int("DWT2_FUSE_SEG", 0));
+    p->fuse_pairs = std::max(0, env_int("DWT2_FUSE_PAIRS", 1));
+    p->fused_bps = fused_blocks_per_sm(wavelet, scheme, coef_dtype);
     p->balanced_env = env_int("DWT2_BALANCED", 0);
     int ci = env_int("DWT2_FWD_CFG", 0);
     if (ci < 0 || ci >= N_FWD_CFGS) ci = 0;
@@ -621,58 +726,21 @@ int dwt2_forward(dwt2_plan_t p, const void* in, void* coef, void* workspace, voi
     if (!aligned(coef, csz)) return DWT2_ERR_MISALIGNED;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (p->persistent) return forward_persistent(p, in, coef, workspace, s);
-    const bool is_int = p->wavelet == DWT2_CDF53_INT;
-    for (int l = 0; l < p->levels; ++l) {
+    for (int l = 0; l < p->levels;) {
+        bool fuse = p->fuse_seg > 0 && l / 2 < p->fuse_pairs && l % 2 == 0 && l + 1 < p->levels && p->fused_bps > 0;
+        for (const ImagePlan& ip : p->imgs) fuse = fuse && fused_eligible(ip.lv[l]);
         prof_mark(p, l, true, s);
         for (const ImagePlan& ip : p->imgs) {
-            const char* in_img = static_cast<const char*>(in) + ip.d.offset_elems * 4;
-            char* coef_img = static_cast<char*>(coef) + ip.d.offset_elems * csz;
-            char* wsb = static_cast<char*>(workspace);
-            const LevelGeom& g = ip.lv[l];
-            const void* src = (l == 0) ? static_cast<const void*>(in_img)
-                                       : static_cast<const void*>(wsb + ip.ws_off[l - 1]);
-            const int64_t src_pitch = (l == 0) ? ip.d.pitch_elems : round4(ip.lv[l - 1].wq);
-            CUtensorMap box, row;
-            const int bw = fwd_strip_px(p->cfg);
-            int rc = encode_map(&box, src, g.w, g.h, src_pitch, bw, 2 * p->cfg.qr, is_int);
-            if (rc == DWT2_OK) rc = encode_map(&row, src, g.w, g.h, src_pitch, bw, 1, is_int);
+            const int rc = fuse ? forward_fused(p, ip, l, in, coef, workspace, s)
+                                : forward_level(p, ip, l, in, coef, workspace, s);
             if (rc != DWT2_OK) return rc;
-            FwdParams fp;
-            fp.h = g.h, fp.w = g.w, fp.hq = g.hq, fp.wq = g.wq, fp.hh = g.hh, fp.wh = g.wh;
-            int grid = 0, balanced = 0;
-            const Decomp dc = decompose(g, fwd_out_quads(p->cfg), p->sm_count, p->fwd_bps, p->cfg.nw,
-                                        p->seg_override, p->balanced_env, &grid, &balanced);
-            fp.n_strips = dc.n_strips, fp.seg_rows = dc.seg_rows, fp.n_segs = dc.n_segs, fp.n_units = dc.n_units;
-            fp.balanced = balanced;
-            fp.coef = coef_img;
-            fp.coef_pitch = ip.d.pitch_elems;
-            const bool last = (l == p->levels - 1);
-            if (last) {
-                fp.ll = coef_img;
-                fp.ll_pitch = ip.d.pitch_elems;
-                fp.ll_is_ct = 0;
-            } else {
-                fp.ll = wsb + ip.ws_off[l];
-                fp.ll_pitch = round4(g.wq);
-                fp.ll_is_ct = 1;
-            }
-            const size_t pair = 2 * csz;
-            const bool coef_vec = (ip.d.pitch_elems % 2 == 0) && aligned(coef_img, pair);
-            fp.vec_lo = coef_vec;
-            fp.vec_hi = coef_vec && (g.wq % 2 == 0);
-            fp.vec_ll = last ? coef_vec : 1;
-            fp.status = p->d_status;
-            fp.timeout_ns = p->timeout_ns;
-            int e;
-            switch (p->coef_dtype) {
-                case DWT2_F32: e = launch_forward_f32(p->wavelet, p->scheme, box, row, fp, grid, p->cfg, s); break;
-                case DWT2_F16: e = launch_forward_f16(p->wavelet, p->scheme, box, row, fp, grid, p->cfg, s); break;
-                case DWT2_BF16: e = launch_forward_bf16(p->wavelet, p->scheme, box, row, fp, grid, p->cfg, s); break;
-                default: e = launch_forward_i32(p->wavelet, p->scheme, box, row, fp, grid, p->cfg, s); break;
-            }
-            if (e != cudaSuccess) return DWT2_ERR_CUDA;
         }
         prof_mark(p, l, false, s);
+        if (fuse) {  // the pair is one launch, timed as level l; level l+1 reads 0
+            prof_mark(p, l + 1, true, s);
+            prof_mark(p, l + 1, false, s);
+        }
+        l += fuse ? 2 : 1;
     }
     if (p->prof_on) ++p->prof_calls;
     return DWT2_OK;
@@ -759,10 +827,14 @@ static int run_inverse_like(dwt2_plan_t p, const void* coef, void* out, void* wo
 // fixed heights; persistent plans try a few segment heights.
 static const int TUNE_SEGS[] = {0, 24, 32, 44, 56};
 static const int TUNE_PML_SEGS[] = {16, 24, 32, 48};
+constexpr int N_TUNE_SEGS = int(sizeof(TUNE_SEGS) / sizeof(TUNE_SEGS[0]));
+// Fused level pairs are not among the candidates: on 16384^2 they measured
+// 2.3x slower than the two per-level launches (the row pipeline is bound by
+// instruction issue as much as by DRAM, and the fused kernel executes ~1.5x
+// the instructions).  Plans enable them with DWT2_FUSE_SEG.
 
 static int tune_candidates(dwt2_plan_t p) {
-    return p->persistent ? int(sizeof(TUNE_PML_SEGS) / sizeof(int))
-                         : N_FWD_CFGS * int(sizeof(TUNE_SEGS) / sizeof(int));
+    return p->persistent ? int(sizeof(TUNE_PML_SEGS) / sizeof(int)) : N_FWD_CFGS * N_TUNE_SEGS;
 }
 
 static int tune_apply(dwt2_plan_t p, int c) {
@@ -771,9 +843,8 @@ static int tune_apply(dwt2_plan_t p, int c) {
         p->pml_seg = TUNE_PML_SEGS[c];
         return build_persistent(p);
     }
-    const int ns = int(sizeof(TUNE_SEGS) / sizeof(int));
-    p->cfg = FWD_CFGS[c / ns];
-    p->seg_override = TUNE_SEGS[c % ns];
+    p->cfg = FWD_CFGS[c / N_TUNE_SEGS];
+    p->seg_override = TUNE_SEGS[c % N_TUNE_SEGS];
     p->fwd_bps = forward_blocks_per_sm(p->wavelet, p->scheme, p->coef_dtype, p->cfg);
     return DWT2_OK;
 }

@@ -127,6 +127,31 @@ int launch_inv_batch_bf16(int wav, int scheme, const InvBatchParams& p, int grid
 int launch_inv_batch_i32(int wav, int scheme, const InvBatchParams& p, int grid, cudaStream_t s);
 int launch_adj_batch_f32(const InvBatchParams& p, int grid, cudaStream_t s);
 
+// Two forward levels in one launch (fused.cuh): level l comes through the
+// tensor maps, level l+1 reads the level-l low-low band from a ring of rows in
+// shared memory, so that band never reaches global memory.  A block owns `own`
+// low-low columns (level l+1 input columns) and seg2 level l+1 quad rows; the
+// last segment has at least two rows.
+struct FusedParams {
+    FwdParams l1, l2;  // l1.ll is not written
+    int own, n_cols, seg2, n_segs, n_items;
+    unsigned* status;
+    uint64_t timeout_ns;
+};
+constexpr int FUSED_W1 = 9, FUSED_W2 = 5;           // producer (level l) and consumer (level l+1) warps
+constexpr int FUSED_OWN_MAX = 60 * FUSED_W1 - 8;    // 4 halo columns each side
+constexpr int FUSED_QR = 3, FUSED_NST = 3;          // producer stage ring
+
+int launch_fused_f32(int wav, int scheme, const CUtensorMap& box, const CUtensorMap& row, const FusedParams& p,
+                     int grid, cudaStream_t s);
+int launch_fused_f16(int wav, int scheme, const CUtensorMap& box, const CUtensorMap& row, const FusedParams& p,
+                     int grid, cudaStream_t s);
+int launch_fused_bf16(int wav, int scheme, const CUtensorMap& box, const CUtensorMap& row, const FusedParams& p,
+                      int grid, cudaStream_t s);
+int launch_fused_i32(int wav, int scheme, const CUtensorMap& box, const CUtensorMap& row, const FusedParams& p,
+                     int grid, cudaStream_t s);
+int fused_blocks_per_sm(int wav, int scheme, int coef_dtype);
+
 // forward launch configuration
 struct FwdCfg {
     int ql, qr, nst, nw;  // quads per lane, quad rows per stage, stages per warp, warps per block

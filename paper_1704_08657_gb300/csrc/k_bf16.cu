@@ -24,4 +24,12 @@ int launch_pml_bf16(int wav, int scheme, const PmlLaunch& p, int grid, cudaStrea
 }
 int occupancy_pml_bf16(int wav, int scheme) { return launch_pml_t<__nv_bfloat16>(wav, scheme, nullptr, 0, nullptr, true); }
 
+int launch_fused_bf16(int wav, int scheme, const CUtensorMap& box, const CUtensorMap& row, const FusedParams& p,
+                      int grid, cudaStream_t s) {
+    return launch_fused_t<__nv_bfloat16>(wav, scheme, &box, &row, &p, grid, s, false);
+}
+int occupancy_fused_bf16(int wav, int scheme) {
+    return launch_fused_t<__nv_bfloat16>(wav, scheme, nullptr, nullptr, nullptr, 0, nullptr, true);
+}
+
 }  // namespace dwt2

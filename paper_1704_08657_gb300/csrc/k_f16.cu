@@ -24,4 +24,12 @@ int launch_pml_f16(int wav, int scheme, const PmlLaunch& p, int grid, cudaStream
 }
 int occupancy_pml_f16(int wav, int scheme) { return launch_pml_t<__half>(wav, scheme, nullptr, 0, nullptr, true); }
 
+int launch_fused_f16(int wav, int scheme, const CUtensorMap& box, const CUtensorMap& row, const FusedParams& p,
+                     int grid, cudaStream_t s) {
+    return launch_fused_t<__half>(wav, scheme, &box, &row, &p, grid, s, false);
+}
+int occupancy_fused_f16(int wav, int scheme) {
+    return launch_fused_t<__half>(wav, scheme, nullptr, nullptr, nullptr, 0, nullptr, true);
+}
+
 }  // namespace dwt2

@@ -24,6 +24,14 @@ int launch_pml_f32(int wav, int scheme, const PmlLaunch& p, int grid, cudaStream
 }
 int occupancy_pml_f32(int wav, int scheme) { return launch_pml_t<float>(wav, scheme, nullptr, 0, nullptr, true); }
 
+int launch_fused_f32(int wav, int scheme, const CUtensorMap& box, const CUtensorMap& row, const FusedParams& p,
+                     int grid, cudaStream_t s) {
+    return launch_fused_t<float>(wav, scheme, &box, &row, &p, grid, s, false);
+}
+int occupancy_fused_f32(int wav, int scheme) {
+    return launch_fused_t<float>(wav, scheme, nullptr, nullptr, nullptr, 0, nullptr, true);
+}
+
 }  // namespace dwt2
 
 namespace dwt2 {
@@ -62,6 +70,19 @@ int pml_blocks_per_sm(int wav, int scheme, int coef_dtype) {
         case DT_F16: return occupancy_pml_f16(wav, scheme);
         case DT_BF16: return occupancy_pml_bf16(wav, scheme);
         default: return occupancy_pml_i32(wav, scheme);
+    }
+}
+
+int occupancy_fused_f16(int wav, int scheme);
+int occupancy_fused_bf16(int wav, int scheme);
+int occupancy_fused_i32(int wav, int scheme);
+
+int fused_blocks_per_sm(int wav, int scheme, int coef_dtype) {
+    switch (coef_dtype) {
+        case DT_F32: return occupancy_fused_f32(wav, scheme);
+        case DT_F16: return occupancy_fused_f16(wav, scheme);
+        case DT_BF16: return occupancy_fused_bf16(wav, scheme);
+        default: return occupancy_fused_i32(wav, scheme);
     }
 }
 

@@ -4,6 +4,7 @@
 
 #include <type_traits>
 
+#include "fused.cuh"
 #include "kernels.cuh"
 
 namespace dwt2 {
@@ -201,6 +202,58 @@ int launch_inverse_t(int wav, int scheme, const InvParams& p, int grid, cudaStre
         if (scheme == SCHEME_REDUCED) return launch_inv_one<Inv97<SCHEME_REDUCED, INV_QL>, BT, false>(p, grid, s);
         if (scheme == SCHEME_SEP) return launch_inv_one<Inv97<SCHEME_SEP, INV_QL>, BT, false>(p, grid, s);
         return cudaErrorInvalidValue;
+    }
+}
+
+// ------------------------------------------------------ fused level pairs
+template <class Pipe, class OutT>
+int fused_prepare() {
+    static bool done = false;
+    if (!done) {
+        cudaError_t e = cudaFuncSetAttribute(fused2_kernel<Pipe, OutT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             int(fused_smem_bytes()));
+        if (e != cudaSuccess) return e;
+        done = true;
+    }
+    return cudaSuccess;
+}
+
+// occupancy: return resident blocks per SM instead of launching
+template <class Pipe, class OutT>
+int launch_fused_one(const CUtensorMap* box, const CUtensorMap* row, const FusedParams* p, int grid, cudaStream_t s,
+                     bool occupancy) {
+    const int e = fused_prepare<Pipe, OutT>();
+    if (occupancy) {
+        int n = 0;
+        if (e != cudaSuccess || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fused2_kernel<Pipe, OutT>,
+                                                                              FUSED_THREADS, fused_smem_bytes()) !=
+                                    cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        return n;
+    }
+    if (e != cudaSuccess) return e;
+    fused2_kernel<Pipe, OutT><<<grid, FUSED_THREADS, fused_smem_bytes(), s>>>(*box, *row, *p);
+    return cudaGetLastError();
+}
+
+template <class OutT>
+int launch_fused_t(int wav, int scheme, const CUtensorMap* box, const CUtensorMap* row, const FusedParams* p,
+                   int grid, cudaStream_t s, bool occ) {
+    const int bad = occ ? 0 : int(cudaErrorInvalidValue);
+    if constexpr (std::is_same<OutT, int>::value) {
+        if (wav != WAV_CDF53I) return bad;
+        if (scheme == SCHEME_SEP) return launch_fused_one<Fwd53<SCHEME_SEP, 2>, int>(box, row, p, grid, s, occ);
+        if (scheme == SCHEME_NONSEP) return launch_fused_one<Fwd53<SCHEME_NONSEP, 2>, int>(box, row, p, grid, s, occ);
+        return bad;
+    } else {
+        if (wav != WAV_CDF97) return bad;
+        if (scheme == SCHEME_NONSEP) return launch_fused_one<Fwd97<SCHEME_NONSEP, 2>, OutT>(box, row, p, grid, s, occ);
+        if (scheme == SCHEME_REDUCED)
+            return launch_fused_one<Fwd97<SCHEME_REDUCED, 2>, OutT>(box, row, p, grid, s, occ);
+        if (scheme == SCHEME_SEP) return launch_fused_one<Fwd97<SCHEME_SEP, 2>, OutT>(box, row, p, grid, s, occ);
+        return bad;
     }
 }
 

@@ -20,7 +20,7 @@ def band_errors(got: np.ndarray, ref: np.ndarray, levels: int):
 def assert_fp32_close(got: np.ndarray, ref: np.ndarray, levels: int, x_max: float, what: str = ""):
     """FP32 lifting vs the FP64 oracle.
 
-    Criterion (FP32 tolerance): a level-k band, divided by 2^k
+    Criterion: a level-k band, divided by 2^k
     (the DC gain of k levels, so that every band lives on the input's [0, 255]
     scale), must be within 1e-3 * x_max / 255 of the oracle; equivalently the
     raw error is at most 1e-3 * 2^k * x_max / 255.
