@@ -155,11 +155,16 @@ int dwt2_adjoint_l1(dwt2_plan_t plan, const void* coef, void* in_grad, float sca
 /* dwt2_autotune -- choose the plan's launch configuration (not in the paper).
  * With *choice < 0: run the forward on the given buffers (same arguments as
  * dwt2_forward) for each candidate configuration (kernel tile shape and
- * segment height; segment height for persistent plans), a few timed calls
- * each on the stream, keep the fastest and store its index in *choice.  With
- * *choice >= 0: apply that candidate without timing (e.g. from a cache of an
- * earlier run on the same GPU).  The coefficient buffer is overwritten.
- * Synchronises the stream; not for use during graph capture. */
+ * segment height; segment height for persistent plans), a few calls each on
+ * the stream timed per level with the plan's profile events, keep the fastest
+ * candidate of every level (of the whole launch for persistent plans) and
+ * store the choice in *choice: 5 bits per level for the first six levels,
+ * deeper levels sharing the sixth field (persistent plans: the candidate
+ * index).  With *choice >= 0: apply that choice without timing (e.g. from a
+ * cache of an earlier run on the same GPU); DWT2_ERR_INVALID_ARG if it is not
+ * a valid choice for this plan.  The coefficient buffer is overwritten and the
+ * plan's profile ring is reset.  Synchronises the stream; not for use during
+ * graph capture. */
 int dwt2_autotune(dwt2_plan_t plan, const void* in, void* coef, void* workspace, void* stream,
                   int* choice);
 

@@ -144,9 +144,12 @@ struct dwt2_plan_s {
     size_t ws_bytes;
     unsigned* d_status;
     int device, sm_count;
-    FwdCfg cfg;
-    int fwd_bps, inv_bps;  // resident blocks per SM of the forward / inverse kernels
-    int seg_override, balanced_env;
+    int cfg_env, seg_env;           // DWT2_FWD_CFG, DWT2_SEG_ROWS
+    int cfg_bps[N_FWD_CFGS];        // resident blocks per SM of each forward configuration
+    std::vector<int> lvl_cand;      // per level: tuning candidate, or -1 for cfg_env / seg_env
+    int inv_bps;                    // resident blocks per SM of the inverse kernel
+    int pdl;                        // per-level forward launches as programmatic dependents (DWT2_PDL)
+    int balanced_env;
     // fused level pairs: segment height in level l+1 quad rows (0: off) and
     // how many pairs, from level 0 on, may run fused
     int fuse_seg, fuse_pairs, fused_bps;
@@ -478,23 +481,39 @@ int level_maps(dwt2_plan_t p, const ImagePlan& ip, int l, const void* in, void* 
     return rc;
 }
 
+// Tuning candidates of one per-level forward launch: every compiled kernel
+// configuration with the automatic segment height and a few fixed heights.
+const int TUNE_SEGS[] = {0, 2, 4, 8, 12, 16, 24, 32, 44};
+constexpr int N_TUNE_SEGS = int(sizeof(TUNE_SEGS) / sizeof(TUNE_SEGS[0]));
+constexpr int N_LVL_CANDS = N_FWD_CFGS * N_TUNE_SEGS;
+constexpr int TUNE_BITS = 5, TUNE_LEVELS = 6;  // a plan's choice: 5 bits per level, levels >= 5 share one
+static_assert(N_LVL_CANDS <= (1 << TUNE_BITS), "candidates fit the choice field");
+
 int forward_level(dwt2_plan_t p, const ImagePlan& ip, int l, const void* in, void* coef, void* workspace,
                   cudaStream_t s) {
+    int ci = p->cfg_env, seg = p->seg_env;
+    const int cand = p->lvl_cand[l];
+    if (cand >= 0) {
+        ci = cand / N_TUNE_SEGS;
+        seg = TUNE_SEGS[cand % N_TUNE_SEGS];
+    }
+    const FwdCfg& cfg = FWD_CFGS[ci];
     CUtensorMap box, row;
-    const int rc = level_maps(p, ip, l, in, workspace, p->cfg.ql, p->cfg.qr, &box, &row);
+    const int rc = level_maps(p, ip, l, in, workspace, cfg.ql, cfg.qr, &box, &row);
     if (rc != DWT2_OK) return rc;
     FwdParams fp = level_outputs(p, ip, l, coef, workspace);
     int grid = 0, balanced = 0;
-    const Decomp dc = decompose(ip.lv[l], fwd_out_quads(p->cfg), p->sm_count, p->fwd_bps, p->cfg.nw, p->seg_override,
+    const Decomp dc = decompose(ip.lv[l], fwd_out_quads(cfg), p->sm_count, p->cfg_bps[ci], cfg.nw, seg,
                                 p->balanced_env, &grid, &balanced);
     fp.n_strips = dc.n_strips, fp.seg_rows = dc.seg_rows, fp.n_segs = dc.n_segs, fp.n_units = dc.n_units;
     fp.balanced = balanced;
+    fp.pdl = p->pdl;
     int e;
     switch (p->coef_dtype) {
-        case DWT2_F32: e = launch_forward_f32(p->wavelet, p->scheme, box, row, fp, grid, p->cfg, s); break;
-        case DWT2_F16: e = launch_forward_f16(p->wavelet, p->scheme, box, row, fp, grid, p->cfg, s); break;
-        case DWT2_BF16: e = launch_forward_bf16(p->wavelet, p->scheme, box, row, fp, grid, p->cfg, s); break;
-        default: e = launch_forward_i32(p->wavelet, p->scheme, box, row, fp, grid, p->cfg, s); break;
+        case DWT2_F32: e = launch_forward_f32(p->wavelet, p->scheme, box, row, fp, grid, cfg, s); break;
+        case DWT2_F16: e = launch_forward_f16(p->wavelet, p->scheme, box, row, fp, grid, cfg, s); break;
+        case DWT2_BF16: e = launch_forward_bf16(p->wavelet, p->scheme, box, row, fp, grid, cfg, s); break;
+        default: e = launch_forward_i32(p->wavelet, p->scheme, box, row, fp, grid, cfg, s); break;
     }
     return e == cudaSuccess ? DWT2_OK : DWT2_ERR_CUDA;
 }
@@ -607,15 +626,16 @@ int dwt2_plan(dwt2_plan_t* out, int wavelet, int levels, int boundary, int in_dt
     p->prof_on = false;
     p->prof_calls = 0;
     p->timeout_ns = uint64_t(env_int("DWT2_TIMEOUT_MS", 2000)) * 1000000ull;
-    p->seg_override = env_int("DWT2_SEG_ROWS", 0);
+    p->seg_env = env_int("DWT2_SEG_ROWS", 0);
+    p->pdl = env_int("DWT2_PDL", 1) != 0;
+    p->lvl_cand.assign(levels, -1);
     p->fuse_seg = std::max(0, env_int("DWT2_FUSE_SEG", 0));
     p->fuse_pairs = std::max(0, env_int("DWT2_FUSE_PAIRS", 1));
     p->fused_bps = fused_blocks_per_sm(wavelet, scheme, coef_dtype);
     p->balanced_env = env_int("DWT2_BALANCED", 0);
-    int ci = env_int("DWT2_FWD_CFG", 0);
-    if (ci < 0 || ci >= N_FWD_CFGS) ci = 0;
-    p->cfg = FWD_CFGS[ci];
-    p->fwd_bps = forward_blocks_per_sm(wavelet, scheme, coef_dtype, p->cfg);
+    p->cfg_env = env_int("DWT2_FWD_CFG", 0);
+    if (p->cfg_env < 0 || p->cfg_env >= N_FWD_CFGS) p->cfg_env = 0;
+    for (int c = 0; c < N_FWD_CFGS; ++c) p->cfg_bps[c] = forward_blocks_per_sm(wavelet, scheme, coef_dtype, FWD_CFGS[c]);
     p->inv_bps = inverse_blocks_per_sm(wavelet, scheme, coef_dtype, false);
     if (cudaGetDevice(&p->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess ||
@@ -771,7 +791,7 @@ static int run_inverse_like(dwt2_plan_t p, const void* coef, void* out, void* wo
             ipm.h = g.h, ipm.w = g.w, ipm.hq = g.hq, ipm.wq = g.wq, ipm.hh = g.hh, ipm.wh = g.wh;
             int grid = 0, balanced = 0;
             const Decomp dc =
-                decompose(g, INV_OUT_Q, p->sm_count, inv_bps, INV_NW, p->seg_override, p->balanced_env, &grid,
+                decompose(g, INV_OUT_Q, p->sm_count, inv_bps, INV_NW, p->seg_env, p->balanced_env, &grid,
                           &balanced);
             ipm.n_strips = dc.n_strips, ipm.seg_rows = dc.seg_rows, ipm.n_segs = dc.n_segs, ipm.n_units = dc.n_units;
             ipm.balanced = balanced;
@@ -822,65 +842,77 @@ static int run_inverse_like(dwt2_plan_t p, const void* coef, void* out, void* wo
     return DWT2_OK;
 }
 
-// Candidate launch configurations of the forward: per-level plans try every
-// compiled kernel configuration with the automatic segment height and a few
-// fixed heights; persistent plans try a few segment heights.
-static const int TUNE_SEGS[] = {0, 24, 32, 44, 56};
+// Autotuning.  Per-level plans time every candidate of TUNE_SEGS x the
+// compiled configurations on the whole pyramid, read each level's time from
+// the plan's profile events and keep, level by level, the fastest candidate
+// (the launches of different levels are independent).  The choice packs
+// TUNE_BITS bits per level for the first TUNE_LEVELS levels; deeper levels use
+// the last field.  Persistent plans try a few segment heights.
 static const int TUNE_PML_SEGS[] = {16, 24, 32, 48};
-constexpr int N_TUNE_SEGS = int(sizeof(TUNE_SEGS) / sizeof(TUNE_SEGS[0]));
+constexpr int N_TUNE_PML = int(sizeof(TUNE_PML_SEGS) / sizeof(TUNE_PML_SEGS[0]));
 // Fused level pairs are not among the candidates: on 16384^2 they measured
 // 2.3x slower than the two per-level launches (the row pipeline is bound by
 // instruction issue as much as by DRAM, and the fused kernel executes ~1.5x
 // the instructions).  Plans enable them with DWT2_FUSE_SEG.
 
-static int tune_candidates(dwt2_plan_t p) {
-    return p->persistent ? int(sizeof(TUNE_PML_SEGS) / sizeof(int)) : N_FWD_CFGS * N_TUNE_SEGS;
-}
+static int tune_fields(dwt2_plan_t p) { return std::min(p->levels, TUNE_LEVELS); }
 
-static int tune_apply(dwt2_plan_t p, int c) {
-    if (c < 0 || c >= tune_candidates(p)) return DWT2_ERR_INVALID_ARG;
+static int tune_apply(dwt2_plan_t p, int choice) {
+    if (choice < 0) return DWT2_ERR_INVALID_ARG;
     if (p->persistent) {
-        p->pml_seg = TUNE_PML_SEGS[c];
+        if (choice >= N_TUNE_PML) return DWT2_ERR_INVALID_ARG;
+        p->pml_seg = TUNE_PML_SEGS[choice];
         return build_persistent(p);
     }
-    p->cfg = FWD_CFGS[c / N_TUNE_SEGS];
-    p->seg_override = TUNE_SEGS[c % N_TUNE_SEGS];
-    p->fwd_bps = forward_blocks_per_sm(p->wavelet, p->scheme, p->coef_dtype, p->cfg);
+    const int nf = tune_fields(p);
+    if (nf * TUNE_BITS < 31 && choice >= (1 << (nf * TUNE_BITS))) return DWT2_ERR_INVALID_ARG;
+    for (int f = 0; f < nf; ++f)
+        if (((choice >> (f * TUNE_BITS)) & ((1 << TUNE_BITS) - 1)) >= N_LVL_CANDS) return DWT2_ERR_INVALID_ARG;
+    for (int l = 0; l < p->levels; ++l) p->lvl_cand[l] = (choice >> (std::min(l, nf - 1) * TUNE_BITS)) & ((1 << TUNE_BITS) - 1);
     return DWT2_OK;
 }
 
 int dwt2_autotune(dwt2_plan_t p, const void* in, void* coef, void* workspace, void* stream, int* choice) {
     if (!p || !choice) return DWT2_ERR_INVALID_ARG;
     if (*choice >= 0) return tune_apply(p, *choice);
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
-        if (e0) cudaEventDestroy(e0);
-        return DWT2_ERR_CUDA;
-    }
     const bool prof = p->prof_on;
-    p->prof_on = false;
-    int best = -1, rc = DWT2_OK;
-    float best_ms = 0.f;
-    for (int c = 0; c < tune_candidates(p) && rc == DWT2_OK; ++c) {
-        rc = tune_apply(p, c);
-        for (int i = 0; i < 2 && rc == DWT2_OK; ++i) rc = dwt2_forward(p, in, coef, workspace, stream);
-        if (rc != DWT2_OK) break;
-        const int reps = 5;
-        cudaEventRecord(e0, s);
-        for (int i = 0; i < reps && rc == DWT2_OK; ++i) rc = dwt2_forward(p, in, coef, workspace, stream);
-        cudaEventRecord(e1, s);
-        float ms = 0.f;
-        if (rc != DWT2_OK || cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-            rc = rc != DWT2_OK ? rc : DWT2_ERR_CUDA;
-            break;
+    int rc = DWT2_OK;
+    const int L = p->levels;
+    const int n_cand = p->persistent ? N_TUNE_PML : N_LVL_CANDS;
+    std::vector<float> ms(size_t(n_cand) * L, 0.f);
+    for (int c = 0; c < n_cand && rc == DWT2_OK; ++c) {
+        if (p->persistent) {
+            rc = tune_apply(p, c);
+        } else {
+            for (int l = 0; l < L; ++l) p->lvl_cand[l] = c;
         }
-        if (best < 0 || ms < best_ms) best = c, best_ms = ms;
+        for (int i = 0; i < 2 && rc == DWT2_OK; ++i) rc = dwt2_forward(p, in, coef, workspace, stream);
+        if (rc == DWT2_OK) rc = dwt2_profile(p, 1);
+        for (int i = 0; i < 5 && rc == DWT2_OK; ++i) rc = dwt2_forward(p, in, coef, workspace, stream);
+        if (rc == DWT2_OK) rc = dwt2_profile_read(p, &ms[size_t(c) * L], L);
+        p->prof_on = false;
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     p->prof_on = prof;
+    p->prof_calls = 0;
     if (rc != DWT2_OK) return rc;
+    int best = 0;
+    if (p->persistent) {
+        for (int c = 1; c < n_cand; ++c)
+            if (ms[size_t(c) * L] < ms[size_t(best) * L]) best = c;
+    } else {
+        const int nf = tune_fields(p);
+        for (int f = 0; f < nf; ++f) {
+            // the last field covers every deeper level: sum their times
+            int bc = 0;
+            float bt = 0.f;
+            for (int c = 0; c < n_cand; ++c) {
+                float t = 0.f;
+                for (int l = f; l < (f == nf - 1 ? L : f + 1); ++l) t += ms[size_t(c) * L + l];
+                if (c == 0 || t < bt) bc = c, bt = t;
+            }
+            best |= bc << (f * TUNE_BITS);
+        }
+    }
     *choice = best;
     return tune_apply(p, best);
 }

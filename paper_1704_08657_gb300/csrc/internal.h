@@ -32,6 +32,7 @@ struct FwdParams {
     int vec_lo, vec_hi, vec_ll;  // pair-store alignment: LH, HL / HH, LL
     unsigned* status;          // device status word (may be null)
     uint64_t timeout_ns;       // bounded-wait limit
+    int pdl;                   // host side: launch as a programmatic dependent of the previous kernel
 };
 
 // One inverse or adjoint level: bands in, pixels (compute type) out.

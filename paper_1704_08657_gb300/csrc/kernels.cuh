@@ -347,6 +347,10 @@ __global__ void __launch_bounds__(NW * 32)
         tma_prefetch_desc(&tm_row);
     }
     __syncwarp();
+    // the input (the previous level's low-low band) and the outputs are only
+    // touched after the previous grid in the stream has completed
+    griddep_wait();
+    griddep_launch_dependents();
     const TmaLoader ld{&tm_box, &tm_row};
     uint32_t gstage = 0;
     Pieces<FwdParams> pieces(p, blockIdx.x * NW + warp, gridDim.x * NW);

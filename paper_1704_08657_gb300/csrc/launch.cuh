@@ -21,8 +21,21 @@ int launch_fwd_one(const CUtensorMap& box, const CUtensorMap& row, const FwdPara
             done = true;
         }
     }
-    k<<<grid, NW * 32, smem, s>>>(box, row, p);
-    return cudaGetLastError();
+    if (!p.pdl) {
+        k<<<grid, NW * 32, smem, s>>>(box, row, p);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(grid);
+    lc.blockDim = dim3(NW * 32);
+    lc.dynamicSmemBytes = smem;
+    lc.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    return cudaLaunchKernelEx(&lc, k, box, row, p);
 }
 
 // the compiled forward configurations (quads per lane, quad rows per stage,

@@ -185,6 +185,7 @@ extern "C" int dwt2_forward_noalloc(int wavelet, int levels, int scheme, int coe
         fp.n_segs = (fp.hq + fp.seg_rows - 1) / fp.seg_rows;
         fp.n_units = fp.n_segs * fp.n_strips;
         fp.balanced = 0;
+        fp.pdl = 0;
         const int grid = (fp.n_units + cfg.nw - 1) / cfg.nw;
         fp.coef = coef;
         fp.coef_pitch = pitch_elems;
