@@ -87,6 +87,21 @@ def kernel_hash() -> str:
     return h.hexdigest()[:16]
 
 
+TUNE_SEGS = (0, 2, 4, 8, 12, 16, 24, 32, 44)  # candidate segment heights of dwt2_autotune
+FWD_CFGS = ((2, 3, 3, 4), (2, 2, 4, 4), (2, 2, 4, 8))  # compiled (ql, qr, nst, nw)
+
+
+def tuned_levels(choice, levels, persistent):
+    """(ql, qr, nst, nw, seg_rows) of each level from a per-level tuning choice."""
+    if persistent or choice is None or choice < 0:
+        return []
+    out = []
+    for lev in range(levels):
+        f = (choice >> (5 * min(lev, 5))) & 31
+        out.append(FWD_CFGS[f // len(TUNE_SEGS)] + (TUNE_SEGS[f % len(TUNE_SEGS)],))
+    return out
+
+
 def profiled_traffic(h, w):
     """Per-launch DRAM bytes of the level-1 kernel from the committed ncu
     summary, when it was taken on the current kernel sources."""
@@ -317,8 +332,7 @@ def run_ours(a):
             step()
         torch.cuda.synchronize(dev)
 
-    # timed region: exactly K steps; the level-1 kernel timed by the plan's events
-    abi.dwt2_profile(plan.handle, True)
+    # timed region: exactly K steps (no per-level events inside it)
     barrier()
     t_wall0 = time.time()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -330,10 +344,16 @@ def run_ours(a):
     barrier()
     t_wall1 = time.time()
     ms_total = e0.elapsed_time(e1)
-    l1 = abi.dwt2_profile_read(plan.handle, 1)[0]  # mean over the last (up to 256) steps
+    # then the per-level kernel times from the plan's event pairs (mean over
+    # up to 256 further steps)
+    abi.dwt2_profile(plan.handle, True)
+    for _ in range(max(3, min(a.steps, 256))):
+        step()
+    levels_ms = abi.dwt2_profile_read(plan.handle, a.levels)
     abi.dwt2_profile(plan.handle, False)
+    l1 = levels_ms[0]
     sampler.stop()
-    clocks = sampler.summary(t_soak, t_wall1)
+    clocks = sampler.summary(t_soak, time.time())
     assert plan.status() == 0, "device status word set during the bench"
 
     if pg is not None:
@@ -347,36 +367,64 @@ def run_ours(a):
     # roofline of the level-1 kernel: 4 B read + 4 B written per pixel
     peak, peak_kind = measured_peaks()
     achieved = 8.0 * n * n / (l1 * 1e-3) / 1e9
-    roof = {"bound": "hbm", "kernel": f"fwd_tma_kernel<Fwd97<{a.scheme}>, float> (level 1)",
+    lvl_cfg = tuned_levels(tuned, a.levels, a.persistent)
+    ql, qr, nst, nw, seg = lvl_cfg[0] if lvl_cfg else (2, 3, 3, 4, 0)
+    kname = (f"pml_kernel<Fwd97<{a.scheme}>, float> (whole pyramid)" if a.persistent else
+             f"fwd_tma_kernel<Fwd97<{a.scheme}, {ql}>, float, {ql}, {qr}, {nst}, {nw}> (level 1)")
+    roof = {"bound": "hbm", "kernel": kname,
             "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "peak_source": f"{peak_kind} HBM copy bandwidth", "level1_ms": l1,
+            "peak_source": f"{peak_kind} HBM copy bandwidth (burst; the kernel is timed inside the pyramid)",
+            "level1_ms": l1, "levels_ms": levels_ms,
             "traffic": profiled_traffic(n, n), "algorithmic_bytes": 8 * n * n}
 
     cfg = config_of(a, world)
     cfg["autotuned_choice"] = tuned
+    cfg["per_level_config"] = [{"ql": c[0], "qr": c[1], "nst": c[2], "nw": c[3], "seg_rows": c[4] or "auto"}
+                               for c in lvl_cfg]
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
             "roofline": roof, "gpu_launches": a.steps * a.levels, "clocks": clocks}
 
-    # end to end through the public API with host buffers
+    # end to end through the public API with host buffers: every step copies
+    # its input from pinned host memory, runs dwt2_forward and copies the
+    # coefficients back to pinned host memory.  Steps are pipelined over two
+    # device buffer sets and three streams (host-to-device, compute,
+    # device-to-host), so one step's copies overlap its neighbours' work.
     if rank == 0 or True:
         hin = torch.from_numpy(x_host).pin_memory()
-        hout = torch.empty_like(hin).pin_memory()
-        xd = torch.empty_like(x)
-        cd = torch.empty_like(x)
-        for _ in range(2):
-            xd.copy_(hin, non_blocking=True)
-            plan.forward(xd, cd, stream)
-            hout.copy_(cd, non_blocking=True)
+        hout = [torch.empty_like(hin).pin_memory() for _ in range(2)]
+        xd = [torch.empty_like(x) for _ in range(2)]
+        cd = [torch.empty_like(x) for _ in range(2)]
+        s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+        ev = {k: [torch.cuda.Event() for _ in range(2)] for k in ("in", "fwd", "out")}
+
+        def e2e_steps(k):
+            for i in range(k):
+                b = i % 2
+                if i >= 2:
+                    s_in.wait_event(ev["fwd"][b])  # xd[b] free once step i-2 has read it
+                with torch.cuda.stream(s_in):
+                    xd[b].copy_(hin, non_blocking=True)
+                ev["in"][b].record(s_in)
+                stream.wait_event(ev["in"][b])
+                if i >= 2:
+                    stream.wait_event(ev["out"][b])  # cd[b] free once step i-2 was copied out
+                plan.forward(xd[b], cd[b], stream)
+                ev["fwd"][b].record(stream)
+                s_out.wait_event(ev["fwd"][b])
+                with torch.cuda.stream(s_out):
+                    hout[b].copy_(cd[b], non_blocking=True)
+                ev["out"][b].record(s_out)
+            stream.wait_stream(s_in)
+            stream.wait_stream(s_out)
+        e2e_steps(2)
         barrier()
         ee0 = torch.cuda.Event(enable_timing=True)
         ee1 = torch.cuda.Event(enable_timing=True)
         ee0.record(stream)
-        for _ in range(a.e2e_steps):
-            xd.copy_(hin, non_blocking=True)
-            plan.forward(xd, cd, stream)
-            hout.copy_(cd, non_blocking=True)
+        s_in.wait_stream(stream)
+        e2e_steps(a.e2e_steps)
         ee1.record(stream)
         barrier()
         e2e_ms = ee0.elapsed_time(ee1) / a.e2e_steps
@@ -384,9 +432,11 @@ def run_ours(a):
             t = torch.tensor([e2e_ms], device=dev)
             pg.all_reduce(t, op=pg.ReduceOp.MAX)
             e2e_ms = float(t.item())
+        ok = bool(torch.equal(hout[(a.e2e_steps - 1) % 2], coef.cpu()))
         line["e2e"] = {"value": px / (e2e_ms * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": 4 * n * n,
-                       "d2h_bytes_per_step": 4 * n * n, "steps": a.e2e_steps,
-                       "path": "pinned host -> dwt2_forward -> pinned host"}
+                       "d2h_bytes_per_step": 4 * n * n, "steps": a.e2e_steps, "ms_per_step": e2e_ms,
+                       "path": "pinned host -> dwt2_forward -> pinned host, pipelined over 2 buffer sets "
+                               "and 3 streams", "result_matches_device_run": ok}
         del hin, hout, xd, cd
 
     # schemes and precisions on the same image (level-1 kernel and whole pyramid)
@@ -401,6 +451,7 @@ def run_ours(a):
             for levels in (1, a.levels):
                 p = make(scheme, cdt, levels)
                 out = torch.empty_like(x, dtype=cdt)
+                p.autotune(x, out, stream)
                 for _ in range(3):
                     p.forward(x, out, stream)
                 abi.dwt2_profile(p.handle, True)
@@ -425,6 +476,7 @@ def run_ours(a):
             xi = torch.from_numpy(synth.to_int(x_host)).to(dev)
             p = make(scheme, torch.int32, a.levels, "cdf53")
             out = torch.empty_like(xi)
+            p.autotune(xi, out, stream)
             for _ in range(3):
                 p.forward(xi, out, stream)
             barrier()
@@ -521,6 +573,19 @@ def batch_and_grad(dev, stream, barrier):
                                                  "adjoint_ms": ms - ms_f,
                                                  "launches": "forward: 1 persistent; adjoint: 1 per level"}
     pg.close()
+    # the same with the per-level forward (autotuned; one launch per image and level)
+    pl = Plan(descs, levels, scheme="reduced", device=dev)
+    pl.autotune(x, cbuf, stream)
+
+    def fwd_bwd_pl():
+        pl.forward(x, cbuf, stream)
+        pl.adjoint_l1(cbuf, scale, gin, stream)
+    ms = _time(fwd_bwd_pl, 20, stream, barrier)
+    ms_f = _time(lambda: pl.forward(x, cbuf, stream), 20, stream, barrier)
+    out["grad16x4096/L4/forward+adjoint_l1/per_level_forward"] = {
+        "gpx_s": npx / (ms * 1e-3) / 1e9, "ms": ms, "forward_ms": ms_f, "adjoint_ms": ms - ms_f,
+        "launches": "forward: 1 per image and level; adjoint: 1 per level"}
+    pl.close()
     return out
 
 
