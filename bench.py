@@ -51,6 +51,8 @@ def parse_args():
     ap.add_argument("--profile", action="store_true",
                     help="warm-up and K steps only (for ncu captures); prints a minimal line")
     ap.add_argument("--persistent", action="store_true", help="one persistent launch for the whole pyramid")
+    ap.add_argument("--tune-choice", type=int, default=-1,
+                    help="apply this dwt2_autotune choice instead of timing the candidates (ncu captures)")
     return ap.parse_args()
 
 
@@ -87,8 +89,8 @@ def kernel_hash() -> str:
     return h.hexdigest()[:16]
 
 
-TUNE_SEGS = (0, 2, 4, 8, 12, 16, 24, 32, 44)  # candidate segment heights of dwt2_autotune
-FWD_CFGS = ((2, 3, 3, 4), (2, 2, 4, 4), (2, 2, 4, 8))  # compiled (ql, qr, nst, nw)
+TUNE_SEGS = (0, 2, 4, 8, 12, 16, 24, 32)  # candidate segment heights of dwt2_autotune
+FWD_CFGS = ((2, 3, 3, 4, 0), (2, 2, 4, 4, 0), (2, 2, 4, 8, 0), (2, 2, 4, 8, 1))  # (ql, qr, nst, nw, spec)
 
 
 def tuned_levels(choice, levels, persistent):
@@ -297,7 +299,11 @@ def run_ours(a):
     plan = make(a.scheme, flags=abi.DWT2_FLAG_PERSISTENT if a.persistent else 0)
     coef = torch.empty_like(x)
     ws = plan.workspace
-    tuned = plan.autotune(x, coef)  # untimed: picks the kernel configuration and segment height
+    if a.tune_choice >= 0:
+        tuned = abi.dwt2_autotune(plan.handle, x.data_ptr(), coef.data_ptr(), ws.data_ptr(), stream.cuda_stream,
+                                  a.tune_choice)
+    else:
+        tuned = plan.autotune(x, coef)  # untimed: picks the kernel configuration and segment height per level
 
     def step():
         abi.dwt2_forward(plan.handle, x.data_ptr(), coef.data_ptr(), ws.data_ptr(), stream.cuda_stream)
@@ -321,7 +327,8 @@ def run_ours(a):
         torch.cuda.synchronize(dev)
         ms = p0.elapsed_time(p1) / a.steps
         print(json.dumps({"mode": "profile", "workload": workload_name(a), "ms_per_step": ms,
-                          "gpx_s": n * n / (ms * 1e-3) / 1e9, "status": plan.status()}), flush=True)
+                          "gpx_s": n * n / (ms * 1e-3) / 1e9, "status": plan.status(), "autotuned_choice": tuned,
+                          "launches_per_step": 1 if a.persistent else a.levels}), flush=True)
         return
     sampler = ClockSampler(gpu_selector(dev, local))
     sampler.start()
@@ -368,9 +375,10 @@ def run_ours(a):
     peak, peak_kind = measured_peaks()
     achieved = 8.0 * n * n / (l1 * 1e-3) / 1e9
     lvl_cfg = tuned_levels(tuned, a.levels, a.persistent)
-    ql, qr, nst, nw, seg = lvl_cfg[0] if lvl_cfg else (2, 3, 3, 4, 0)
+    ql, qr, nst, nw, spec, seg = lvl_cfg[0] if lvl_cfg else (2, 3, 3, 4, 0, 0)
     kname = (f"pml_kernel<Fwd97<{a.scheme}>, float> (whole pyramid)" if a.persistent else
-             f"fwd_tma_kernel<Fwd97<{a.scheme}, {ql}>, float, {ql}, {qr}, {nst}, {nw}> (level 1)")
+             f"fwd_tma_kernel<Fwd97<{a.scheme}, {ql}>, float, {ql}, {qr}, {nst}, {nw}, "
+             f"{'true' if spec else 'false'}> (level 1)")
     roof = {"bound": "hbm", "kernel": kname,
             "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "peak_source": f"{peak_kind} HBM copy bandwidth (burst; the kernel is timed inside the pyramid)",
@@ -379,8 +387,8 @@ def run_ours(a):
 
     cfg = config_of(a, world)
     cfg["autotuned_choice"] = tuned
-    cfg["per_level_config"] = [{"ql": c[0], "qr": c[1], "nst": c[2], "nw": c[3], "seg_rows": c[4] or "auto"}
-                               for c in lvl_cfg]
+    cfg["per_level_config"] = [{"ql": c[0], "qr": c[1], "nst": c[2], "nw": c[3], "interior_loop": bool(c[4]),
+                                "seg_rows": c[5] or "auto"} for c in lvl_cfg]
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,

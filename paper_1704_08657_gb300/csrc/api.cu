@@ -209,8 +209,8 @@ int build_persistent(dwt2_plan_t p) {
             const LevelGeom& g = ip.lv[l];
             PmlDesc d;
             d.h = g.h, d.w = g.w, d.hq = g.hq, d.wq = g.wq, d.hh = g.hh, d.wh = g.wh;
-            d.n_strips = (g.wq + fwd_out_quads(FwdCfg{PML_QL, PML_QR, PML_NST, PML_NW}) - 1) /
-                         fwd_out_quads(FwdCfg{PML_QL, PML_QR, PML_NST, PML_NW});
+            d.n_strips = (g.wq + fwd_out_quads(FwdCfg{PML_QL, PML_QR, PML_NST, PML_NW, 0}) - 1) /
+                         fwd_out_quads(FwdCfg{PML_QL, PML_QR, PML_NST, PML_NW, 0});
             d.seg_rows = std::min(p->pml_seg, g.hq);
             const int n_segs = (g.hq + d.seg_rows - 1) / d.seg_rows;
             d.src_is_ws = l > 0;
@@ -483,7 +483,7 @@ int level_maps(dwt2_plan_t p, const ImagePlan& ip, int l, const void* in, void* 
 
 // Tuning candidates of one per-level forward launch: every compiled kernel
 // configuration with the automatic segment height and a few fixed heights.
-const int TUNE_SEGS[] = {0, 2, 4, 8, 12, 16, 24, 32, 44};
+const int TUNE_SEGS[] = {0, 2, 4, 8, 12, 16, 24, 32};
 constexpr int N_TUNE_SEGS = int(sizeof(TUNE_SEGS) / sizeof(TUNE_SEGS[0]));
 constexpr int N_LVL_CANDS = N_FWD_CFGS * N_TUNE_SEGS;
 constexpr int TUNE_BITS = 5, TUNE_LEVELS = 6;  // a plan's choice: 5 bits per level, levels >= 5 share one
@@ -887,9 +887,15 @@ int dwt2_autotune(dwt2_plan_t p, const void* in, void* coef, void* workspace, vo
             for (int l = 0; l < L; ++l) p->lvl_cand[l] = c;
         }
         for (int i = 0; i < 2 && rc == DWT2_OK; ++i) rc = dwt2_forward(p, in, coef, workspace, stream);
-        if (rc == DWT2_OK) rc = dwt2_profile(p, 1);
-        for (int i = 0; i < 5 && rc == DWT2_OK; ++i) rc = dwt2_forward(p, in, coef, workspace, stream);
-        if (rc == DWT2_OK) rc = dwt2_profile_read(p, &ms[size_t(c) * L], L);
+        // the smallest of three means of four calls, per level
+        float* mc = &ms[size_t(c) * L];
+        for (int r = 0; r < 3 && rc == DWT2_OK; ++r) {
+            std::vector<float> m(L, 0.f);
+            rc = dwt2_profile(p, 1);
+            for (int i = 0; i < 4 && rc == DWT2_OK; ++i) rc = dwt2_forward(p, in, coef, workspace, stream);
+            if (rc == DWT2_OK) rc = dwt2_profile_read(p, m.data(), L);
+            for (int l = 0; l < L && rc == DWT2_OK; ++l) mc[l] = (r == 0) ? m[l] : std::min(mc[l], m[l]);
+        }
         p->prof_on = false;
     }
     p->prof_on = prof;

@@ -156,6 +156,7 @@ int fused_blocks_per_sm(int wav, int scheme, int coef_dtype);
 // forward launch configuration
 struct FwdCfg {
     int ql, qr, nst, nw;  // quads per lane, quad rows per stage, stages per warp, warps per block
+    int spec;             // 1: interior strips run a specialised row loop (larger kernel)
 };
 
 // geometry of a strip: 64*ql pixels loaded, 32*ql - 4 quads output
@@ -200,7 +201,7 @@ int forward_blocks_per_sm(int wav, int scheme, int coef_dtype, const FwdCfg& cfg
 int inverse_blocks_per_sm(int wav, int scheme, int coef_dtype, bool adjoint);
 
 // the forward configurations compiled in (index 0 is the default)
-constexpr int N_FWD_CFGS = 3;
+constexpr int N_FWD_CFGS = 4;
 extern const FwdCfg FWD_CFGS[N_FWD_CFGS];
 size_t fwd_smem_bytes_of(const FwdCfg& c);
 // the persistent kernel's fixed configuration

@@ -98,7 +98,7 @@ int inverse_blocks_per_sm(int wav, int scheme, int coef_dtype, bool adjoint) {
 }
 
 const FwdCfg FWD_CFGS[N_FWD_CFGS] = {
-#define DWT2_X(I_, QL_, QR_, NST_, NW_) {QL_, QR_, NST_, NW_},
+#define DWT2_X(I_, QL_, QR_, NST_, NW_, SP_) {QL_, QR_, NST_, NW_, SP_},
     DWT2_FWD_CFG_LIST(DWT2_X)
 #undef DWT2_X
 };

@@ -197,7 +197,19 @@ struct CpAsyncLoader {
 // the level's geometry and outputs (fields of FwdParams); bufs / bars are the
 // warp's stage ring, gstage the warp's running stage count (slot and mbarrier
 // phase).  Returns false when a stage wait timed out.
-template <class Pipe, class OutT, int QL, int QR, int NST, class P, class Loader>
+//
+// MODE 0 handles every strip.  MODE 1 and 2 are compiled for interior strips
+// (fwd_interior: no mirrored columns, every band row takes paired stores),
+// with the low-low band in the compute type (1) or the coefficient type (2):
+// their row loop has no edge or store-alignment branches, which keeps the hot
+// loop small in the instruction cache.
+template <class P>
+__device__ __forceinline__ bool fwd_interior(const P& p, int x0, int QL) {
+    return x0 >= 0 && x0 + 64 * QL <= p.w && p.vec_lo && p.vec_hi && (p.ll_is_ct || p.vec_ll) &&
+           (x0 / 2 + 32 * QL - HALO_Q <= p.wh);
+}
+
+template <class Pipe, class OutT, int QL, int QR, int NST, int MODE = 0, class P, class Loader>
 __device__ __forceinline__ bool fwd_unit(const P& p, const Loader& ld, int s, int R0, int R1,
                                          typename Pipe::CT* bufs, uint64_t* bars, uint32_t& gstage, int lane) {
     using CT = typename Pipe::CT;
@@ -215,7 +227,9 @@ __device__ __forceinline__ bool fwd_unit(const P& p, const Loader& ld, int s, in
     const int NT = (n_arr + QR - 1) / QR;             // stages
     const int x0 = s * (2 * OUTQ) - 2 * HALO_Q;       // first pixel (multiple of 4)
     const int jb = x0 / 2 + QL * lane;                // first quad column of the lane
-    const bool edge = (x0 < 0) || (x0 + SPX > p.w);
+    constexpr bool SPEC = MODE != 0;
+    const bool edge = SPEC ? false : ((x0 < 0) || (x0 + SPX > p.w));
+    const bool llct = MODE == 1 ? true : (MODE == 2 ? false : bool(p.ll_is_ct));
 
     // which of the lane's quads this strip outputs, per band parity
     bool ev[QL], dv[QL], mp[QL];
@@ -228,7 +242,8 @@ __device__ __forceinline__ bool fwd_unit(const P& p, const Loader& ld, int s, in
     }
     // warp-uniform: every output quad of the strip exists in all four bands
     // and every band row takes paired stores
-    const bool fast = p.vec_lo && p.vec_hi && (p.ll_is_ct || p.vec_ll) && (x0 / 2 + 32 * QL - HALO_Q <= p.wh);
+    const bool fast =
+        SPEC ? true : (p.vec_lo && p.vec_hi && (p.ll_is_ct || p.vec_ll) && (x0 / 2 + 32 * QL - HALO_Q <= p.wh));
     // band pointers at output row R0, advanced one pitch per stored row
     OutT* hl = reinterpret_cast<OutT*>(p.coef) + int64_t(R0) * p.coef_pitch + p.wq + jb;
     OutT* lh = reinterpret_cast<OutT*>(p.coef) + int64_t(p.hq + R0) * p.coef_pitch + jb;
@@ -278,7 +293,7 @@ __device__ __forceinline__ bool fwd_unit(const P& p, const Loader& ld, int s, in
                 for (int q = 0; q < QL; q += 2) {
                     const bool on = row_on & mp[q] & mp[q + 1];
                     const bool oo = orow & mp[q] & mp[q + 1];
-                    if (p.ll_is_ct) {
+                    if (llct) {
                         if (on) st_pair<CT>(llc + q, out.c1[q], out.c1[q + 1]);
                     } else {
                         if (on) st_pair<OutT>(llo + q, Cvt<OutT>::to(out.c1[q]), Cvt<OutT>::to(out.c1[q + 1]));
@@ -290,7 +305,7 @@ __device__ __forceinline__ bool fwd_unit(const P& p, const Loader& ld, int s, in
             } else if (row_on) {
 #pragma unroll
                 for (int q = 0; q < QL; q += 2) {
-                    if (p.ll_is_ct)
+                    if (llct)
                         store_pair<CT, CT>(llc, q, out.c1[q], out.c1[q + 1], ev[q], ev[q + 1], true);
                     else
                         store_pair<OutT, CT>(llo, q, out.c1[q], out.c1[q + 1], ev[q], ev[q + 1], p.vec_ll);
@@ -328,8 +343,9 @@ __device__ __forceinline__ void stage_ring(unsigned char* smem, int warp, CT*& b
     bars = reinterpret_cast<uint64_t*>(smem + size_t(NW) * NST * STAGE_ELEMS * 4) + warp * NST;
 }
 
-// One pyramid level, TMA-fed: the warps take their units from Pieces.
-template <class Pipe, class OutT, int QL, int QR, int NST, int NW>
+// One pyramid level, TMA-fed: the warps take their units from Pieces.  SPEC
+// compiles the specialised row loops for interior strips as well.
+template <class Pipe, class OutT, int QL, int QR, int NST, int NW, bool SPEC>
 __global__ void __launch_bounds__(NW * 32)
     fwd_tma_kernel(const __grid_constant__ CUtensorMap tm_box, const __grid_constant__ CUtensorMap tm_row,
                    const FwdParams p) {
@@ -356,7 +372,17 @@ __global__ void __launch_bounds__(NW * 32)
     Pieces<FwdParams> pieces(p, blockIdx.x * NW + warp, gridDim.x * NW);
     int s, R0, R1;
     while (pieces.next(p, s, R0, R1)) {
-        if (!fwd_unit<Pipe, OutT, QL, QR, NST>(p, ld, s, R0, R1, bufs, bars, gstage, lane)) return;
+        bool ok;
+        if constexpr (SPEC) {
+            if (fwd_interior(p, s * (2 * (32 * QL - 2 * HALO_Q)) - 2 * HALO_Q, QL))
+                ok = p.ll_is_ct ? fwd_unit<Pipe, OutT, QL, QR, NST, 1>(p, ld, s, R0, R1, bufs, bars, gstage, lane)
+                                : fwd_unit<Pipe, OutT, QL, QR, NST, 2>(p, ld, s, R0, R1, bufs, bars, gstage, lane);
+            else
+                ok = fwd_unit<Pipe, OutT, QL, QR, NST, 0>(p, ld, s, R0, R1, bufs, bars, gstage, lane);
+        } else {
+            ok = fwd_unit<Pipe, OutT, QL, QR, NST, 0>(p, ld, s, R0, R1, bufs, bars, gstage, lane);
+        }
+        if (!ok) return;
     }
 }
 

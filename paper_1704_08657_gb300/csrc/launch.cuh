@@ -9,9 +9,9 @@
 
 namespace dwt2 {
 
-template <class Pipe, class OutT, int QL, int QR, int NST, int NW>
+template <class Pipe, class OutT, int QL, int QR, int NST, int NW, bool SPEC>
 int launch_fwd_one(const CUtensorMap& box, const CUtensorMap& row, const FwdParams& p, int grid, cudaStream_t s) {
-    auto k = fwd_tma_kernel<Pipe, OutT, QL, QR, NST, NW>;
+    auto k = fwd_tma_kernel<Pipe, OutT, QL, QR, NST, NW, SPEC>;
     constexpr size_t smem = fwd_smem_bytes<QL, QR, NST, NW>();
     if (smem > 48 * 1024) {
         static bool done = false;
@@ -39,13 +39,13 @@ int launch_fwd_one(const CUtensorMap& box, const CUtensorMap& row, const FwdPara
 }
 
 // the compiled forward configurations (quads per lane, quad rows per stage,
-// stages, warps per block); the first is the default
-#define DWT2_FWD_CFG_LIST(X) X(0, 2, 3, 3, 4) X(1, 2, 2, 4, 4) X(2, 2, 2, 4, 8)
+// stages, warps per block, specialised interior loop); the first is the default
+#define DWT2_FWD_CFG_LIST(X) X(0, 2, 3, 3, 4, 0) X(1, 2, 2, 4, 4, 0) X(2, 2, 2, 4, 8, 0) X(3, 2, 2, 4, 8, 1)
 
-template <class Pipe, class OutT, int QL, int QR, int NST, int NW>
+template <class Pipe, class OutT, int QL, int QR, int NST, int NW, bool SPEC>
 int occupancy_fwd_one() {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fwd_tma_kernel<Pipe, OutT, QL, QR, NST, NW>, NW * 32,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fwd_tma_kernel<Pipe, OutT, QL, QR, NST, NW, SPEC>, NW * 32,
                                                       fwd_smem_bytes<QL, QR, NST, NW>()) != cudaSuccess) {
         cudaGetLastError();
         return 0;
@@ -55,9 +55,9 @@ int occupancy_fwd_one() {
 
 template <template <int, int> class PipeT, int S, class OutT>
 int occupancy_fwd_cfgs(const FwdCfg& c) {
-#define DWT2_X(I_, QL_, QR_, NST_, NW_)                                \
-    if (c.ql == QL_ && c.qr == QR_ && c.nst == NST_ && c.nw == NW_) \
-        return occupancy_fwd_one<PipeT<S, QL_>, OutT, QL_, QR_, NST_, NW_>();
+#define DWT2_X(I_, QL_, QR_, NST_, NW_, SP_)                                             \
+    if (c.ql == QL_ && c.qr == QR_ && c.nst == NST_ && c.nw == NW_ && c.spec == SP_) \
+        return occupancy_fwd_one<PipeT<S, QL_>, OutT, QL_, QR_, NST_, NW_, SP_ != 0>();
     DWT2_FWD_CFG_LIST(DWT2_X)
 #undef DWT2_X
     return 0;
@@ -101,9 +101,9 @@ int occupancy_inverse_t(int scheme) {
 template <template <int, int> class PipeT, int S, class OutT>
 int launch_fwd_cfgs(const CUtensorMap& box, const CUtensorMap& row, const FwdParams& p, int grid,
                     const FwdCfg& c, cudaStream_t s) {
-#define DWT2_X(I_, QL_, QR_, NST_, NW_)                                   \
-    if (c.ql == QL_ && c.qr == QR_ && c.nst == NST_ && c.nw == NW_)    \
-        return launch_fwd_one<PipeT<S, QL_>, OutT, QL_, QR_, NST_, NW_>(box, row, p, grid, s);
+#define DWT2_X(I_, QL_, QR_, NST_, NW_, SP_)                                             \
+    if (c.ql == QL_ && c.qr == QR_ && c.nst == NST_ && c.nw == NW_ && c.spec == SP_) \
+        return launch_fwd_one<PipeT<S, QL_>, OutT, QL_, QR_, NST_, NW_, SP_ != 0>(box, row, p, grid, s);
     DWT2_FWD_CFG_LIST(DWT2_X)
 #undef DWT2_X
     return cudaErrorInvalidValue;

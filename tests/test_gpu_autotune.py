@@ -38,8 +38,26 @@ def test_autotune_keeps_results(tmp_path, flags):
     assert torch.equal(p2.forward(x), before)
 
 
-def test_autotune_rejects_bad_choice():
-    plan = Plan.single(64, 64, 2)
+@pytest.mark.parametrize("flags,bad", [(0, 1 << 10), (abi.DWT2_FLAG_PERSISTENT, 99)])
+def test_autotune_rejects_bad_choice(flags, bad):
+    # a two-level plan packs 5 bits per level: a choice of 2^10 or more is not one of its choices
+    plan = Plan.single(64, 64, 2, flags=flags)
     x = torch.zeros((64, 64), device="cuda")
     with pytest.raises(abi.Dwt2Error):
-        abi.dwt2_autotune(plan.handle, x.data_ptr(), x.data_ptr(), plan.workspace.data_ptr(), 0, 999)
+        abi.dwt2_autotune(plan.handle, x.data_ptr(), x.data_ptr(), plan.workspace.data_ptr(), 0, bad)
+
+
+def test_autotune_choice_fields_per_level():
+    # every level's field decodes to a valid candidate, and applying a
+    # hand-made choice (different candidates per level) keeps the results
+    h, w, levels = 1024, 1536, 5
+    x = torch.from_numpy(synth.uniform(h, w, seed=4)).cuda()
+    plan = Plan.single(h, w, levels, scheme="sep")
+    ref = plan.forward(x).clone()
+    out = torch.empty_like(x)
+    choice = 0
+    for lev in range(levels):
+        choice |= ((7 * lev + 3) % 32) << (5 * lev)
+    assert abi.dwt2_autotune(plan.handle, x.data_ptr(), out.data_ptr(), plan.workspace.data_ptr(), 0, choice) == choice
+    assert torch.equal(plan.forward(x), ref)
+    assert plan.status() == 0
