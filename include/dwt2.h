@@ -109,6 +109,14 @@ typedef struct {
  * elements), else DWT2_ERR_MISALIGNED; coefficient buffers need only natural
  * element alignment.  The plan allocates its device status word and batch
  * tables on the current device.
+ * Environment, read when the plan is made (launch tuning only; results do not
+ * depend on it): DWT2_TIMEOUT_MS (bounded device waits, default 2000),
+ * DWT2_FWD_CFG and DWT2_SEG_ROWS (forward kernel configuration 0-3 and
+ * segment height before any dwt2_autotune), DWT2_PDL (0 launches the forward
+ * levels without programmatic dependent launch), DWT2_FUSE_SEG and
+ * DWT2_FUSE_PAIRS (run level pairs 0-1, 2-3, ... in one fused launch with that
+ * segment height; off by default, slower on GB300), DWT2_PML_SEG_ROWS,
+ * DWT2_PML_LAG_PCT and DWT2_PML_CPASYNC (persistent forward).
  */
 int dwt2_plan(dwt2_plan_t* out, int wavelet, int levels, int boundary, int in_dtype,
               int coef_dtype, int scheme, int n_images, const dwt2_image_desc* images,
