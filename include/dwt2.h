@@ -17,7 +17,19 @@
  *   DWT2_NONSEP_REDUCED  the Optimization Approach: the constant parts P0, U0
  *                        applied as separable lifting inside the quad right
  *                        after the non-separable parts P1, U1 (CDF 9/7 only);
- *   DWT2_SEP_LIFTING     the separable lifting T^H, T^V, S^H, S^V per pair.
+ *   DWT2_SEP_LIFTING     the separable lifting T^H, T^V, S^H, S^V per pair;
+ *   DWT2_POLYCONV        the polyconvolution N_{P,U} (Proposed Schemes): each
+ *                        pair applied as one step on pre-pair values, with
+ *                        V = 1 + PU as one 3-tap filter (CDF 9/7 only);
+ *   DWT2_CONV            the convolution scheme (Background, Proposed
+ *                        Schemes): the 9-tap / 7-tap filter bank per axis,
+ *                        multiplied out from the lifting constants, in one
+ *                        step (CDF 9/7 only).
+ * The kernels stream rows through registers and exchange horizontal
+ * neighbours by warp shuffles, so no scheme has barriers between its steps
+ * and the paper's separable and non-separable variants of the polyconvolution
+ * and of the convolution coincide; the schemes differ in arithmetic and in the
+ * number of neighbour exchanges (4, 4, 4, 2 and 1 per CDF 9/7 level).
  *
  * Conventions (readings where the paper is silent):
  *   - odd sample x[2n+1] is predicted from x[2n], x[2n+2]; even sample x[2n]
@@ -57,7 +69,13 @@ typedef struct dwt2_plan_s* dwt2_plan_t;
 
 enum dwt2_wavelet { DWT2_CDF97 = 0, DWT2_CDF53_INT = 1 };
 enum dwt2_dtype { DWT2_F32 = 0, DWT2_F16 = 1, DWT2_BF16 = 2, DWT2_I32 = 3 };
-enum dwt2_scheme { DWT2_NONSEP = 0, DWT2_NONSEP_REDUCED = 1, DWT2_SEP_LIFTING = 2 };
+enum dwt2_scheme {
+    DWT2_NONSEP = 0,
+    DWT2_NONSEP_REDUCED = 1,
+    DWT2_SEP_LIFTING = 2,
+    DWT2_POLYCONV = 3,
+    DWT2_CONV = 4
+};
 enum dwt2_boundary { DWT2_SYMMETRIC = 0 };
 
 #define DWT2_OK 0
@@ -95,8 +113,11 @@ typedef struct {
  *   coef_dtype coefficient element type: F32, F16 or BF16 for CDF 9/7 (the
  *              lifting always runs in FP32 and intermediate LL bands are kept
  *              in FP32), I32 for CDF 5/3.
- *   scheme     DWT2_NONSEP, DWT2_NONSEP_REDUCED (CDF 9/7 only) or
- *              DWT2_SEP_LIFTING.
+ *   scheme     DWT2_NONSEP, DWT2_NONSEP_REDUCED (CDF 9/7 only),
+ *              DWT2_SEP_LIFTING, DWT2_POLYCONV or DWT2_CONV (both CDF 9/7 only
+ *              and not with DWT2_FLAG_PERSISTENT: DWT2_ERR_UNSUPPORTED).  The
+ *              inverse and adjoint of a plan run the non-separable lifting
+ *              kernels for the last two (the same transform).
  *   n_images   number of images (>= 1); images is a host array of that many
  *              descriptors, copied into the plan.
  *   flags      0 or DWT2_FLAG_PERSISTENT: dwt2_forward then runs every level of every

@@ -135,6 +135,11 @@ int env_int(const char* name, int dflt) {
 
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
+// The inverse and the adjoint do not depend on how the forward was scheduled:
+// plans of the polyconvolution and convolution schemes run the non-separable
+// lifting inverse and adjoint kernels.
+int inv_scheme(int scheme) { return scheme > DWT2_SEP_LIFTING ? DWT2_NONSEP : scheme; }
+
 }  // namespace
 
 struct dwt2_plan_s {
@@ -371,10 +376,10 @@ int inverse_batch(dwt2_plan_t p, const void* coef, void* out, void* workspace, c
             e = launch_adj_batch_f32(b, grid, s);
         } else {
             switch (p->coef_dtype) {
-                case DWT2_F32: e = launch_inv_batch_f32(p->wavelet, p->scheme, b, grid, s); break;
-                case DWT2_F16: e = launch_inv_batch_f16(p->wavelet, p->scheme, b, grid, s); break;
-                case DWT2_BF16: e = launch_inv_batch_bf16(p->wavelet, p->scheme, b, grid, s); break;
-                default: e = launch_inv_batch_i32(p->wavelet, p->scheme, b, grid, s); break;
+                case DWT2_F32: e = launch_inv_batch_f32(p->wavelet, inv_scheme(p->scheme), b, grid, s); break;
+                case DWT2_F16: e = launch_inv_batch_f16(p->wavelet, inv_scheme(p->scheme), b, grid, s); break;
+                case DWT2_BF16: e = launch_inv_batch_bf16(p->wavelet, inv_scheme(p->scheme), b, grid, s); break;
+                default: e = launch_inv_batch_i32(p->wavelet, inv_scheme(p->scheme), b, grid, s); break;
             }
         }
         if (e != cudaSuccess) return DWT2_ERR_CUDA;
@@ -578,15 +583,18 @@ int dwt2_plan(dwt2_plan_t* out, int wavelet, int levels, int boundary, int in_dt
     if (!images || n_images < 1 || levels < 1 || levels > 30) return DWT2_ERR_INVALID_ARG;
     if (boundary != DWT2_SYMMETRIC) return DWT2_ERR_INVALID_ARG;
     if (wavelet != DWT2_CDF97 && wavelet != DWT2_CDF53_INT) return DWT2_ERR_INVALID_ARG;
-    if (scheme < DWT2_NONSEP || scheme > DWT2_SEP_LIFTING) return DWT2_ERR_INVALID_ARG;
+    if (scheme < DWT2_NONSEP || scheme > DWT2_CONV) return DWT2_ERR_INVALID_ARG;
     if (in_dtype < DWT2_F32 || in_dtype > DWT2_I32 || coef_dtype < DWT2_F32 || coef_dtype > DWT2_I32)
         return DWT2_ERR_INVALID_ARG;
     if (flags & ~(DWT2_FLAG_PERSISTENT | DWT2_FLAG_TEST_DROP_SIGNAL)) return DWT2_ERR_INVALID_ARG;
+    if ((flags & DWT2_FLAG_PERSISTENT) && scheme > DWT2_SEP_LIFTING) return DWT2_ERR_UNSUPPORTED;
     if (wavelet == DWT2_CDF97) {
         if (in_dtype != DWT2_F32 || coef_dtype == DWT2_I32) return DWT2_ERR_UNSUPPORTED;
     } else {
         if (in_dtype != DWT2_I32 || coef_dtype != DWT2_I32) return DWT2_ERR_UNSUPPORTED;
         if (scheme == DWT2_NONSEP_REDUCED) return DWT2_ERR_UNSUPPORTED;  // floor does not split
+        // floor rounding belongs to the lifting steps: no filter-bank form
+        if (scheme == DWT2_POLYCONV || scheme == DWT2_CONV) return DWT2_ERR_UNSUPPORTED;
     }
     std::vector<ImagePlan> imgs(n_images);
     size_t ws = 0;
@@ -636,7 +644,7 @@ int dwt2_plan(dwt2_plan_t* out, int wavelet, int levels, int boundary, int in_dt
     p->cfg_env = env_int("DWT2_FWD_CFG", 0);
     if (p->cfg_env < 0 || p->cfg_env >= N_FWD_CFGS) p->cfg_env = 0;
     for (int c = 0; c < N_FWD_CFGS; ++c) p->cfg_bps[c] = forward_blocks_per_sm(wavelet, scheme, coef_dtype, FWD_CFGS[c]);
-    p->inv_bps = inverse_blocks_per_sm(wavelet, scheme, coef_dtype, false);
+    p->inv_bps = inverse_blocks_per_sm(wavelet, inv_scheme(scheme), coef_dtype, false);
     if (cudaGetDevice(&p->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess ||
         cudaMalloc(&p->d_status, sizeof(unsigned)) != cudaSuccess ||
@@ -779,7 +787,7 @@ static int run_inverse_like(dwt2_plan_t p, const void* coef, void* out, void* wo
     if (!aligned(coef, csz) || !aligned(out, 4)) return DWT2_ERR_MISALIGNED;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (p->n_images > 1) return inverse_batch(p, coef, out, workspace, s, adj, l1, l1_scale);
-    const int inv_bps = adj ? inverse_blocks_per_sm(p->wavelet, p->scheme, p->coef_dtype, true) : p->inv_bps;
+    const int inv_bps = adj ? inverse_blocks_per_sm(p->wavelet, inv_scheme(p->scheme), p->coef_dtype, true) : p->inv_bps;
     for (int l = p->levels - 1; l >= 0; --l) {
         prof_mark(p, l, true, s);
         for (const ImagePlan& ip : p->imgs) {
@@ -828,10 +836,10 @@ static int run_inverse_like(dwt2_plan_t p, const void* coef, void* out, void* wo
                 e = launch_adjoint_f32(ipm, grid, s);
             } else {
                 switch (p->coef_dtype) {
-                    case DWT2_F32: e = launch_inverse_f32(p->wavelet, p->scheme, ipm, grid, s); break;
-                    case DWT2_F16: e = launch_inverse_f16(p->wavelet, p->scheme, ipm, grid, s); break;
-                    case DWT2_BF16: e = launch_inverse_bf16(p->wavelet, p->scheme, ipm, grid, s); break;
-                    default: e = launch_inverse_i32(p->wavelet, p->scheme, ipm, grid, s); break;
+                    case DWT2_F32: e = launch_inverse_f32(p->wavelet, inv_scheme(p->scheme), ipm, grid, s); break;
+                    case DWT2_F16: e = launch_inverse_f16(p->wavelet, inv_scheme(p->scheme), ipm, grid, s); break;
+                    case DWT2_BF16: e = launch_inverse_bf16(p->wavelet, inv_scheme(p->scheme), ipm, grid, s); break;
+                    default: e = launch_inverse_i32(p->wavelet, inv_scheme(p->scheme), ipm, grid, s); break;
                 }
             }
             if (e != cudaSuccess) return DWT2_ERR_CUDA;

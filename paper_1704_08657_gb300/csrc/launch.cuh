@@ -71,6 +71,8 @@ int occupancy_forward_t(int wav, int scheme, const FwdCfg& c) {
     } else {
         if (scheme == SCHEME_NONSEP) return occupancy_fwd_cfgs<Fwd97, SCHEME_NONSEP, OutT>(c);
         if (scheme == SCHEME_REDUCED) return occupancy_fwd_cfgs<Fwd97, SCHEME_REDUCED, OutT>(c);
+        if (scheme == SCHEME_POLYCONV) return occupancy_fwd_cfgs<Fwd97S, SCHEME_POLYCONV, OutT>(c);
+        if (scheme == SCHEME_CONV) return occupancy_fwd_cfgs<Fwd97S, SCHEME_CONV, OutT>(c);
         return occupancy_fwd_cfgs<Fwd97, SCHEME_SEP, OutT>(c);
     }
 }
@@ -122,6 +124,9 @@ int launch_forward_t(int wav, int scheme, const CUtensorMap& box, const CUtensor
         if (scheme == SCHEME_NONSEP) return launch_fwd_cfgs<Fwd97, SCHEME_NONSEP, OutT>(box, row, p, grid, c, s);
         if (scheme == SCHEME_REDUCED) return launch_fwd_cfgs<Fwd97, SCHEME_REDUCED, OutT>(box, row, p, grid, c, s);
         if (scheme == SCHEME_SEP) return launch_fwd_cfgs<Fwd97, SCHEME_SEP, OutT>(box, row, p, grid, c, s);
+        if (scheme == SCHEME_POLYCONV)
+            return launch_fwd_cfgs<Fwd97S, SCHEME_POLYCONV, OutT>(box, row, p, grid, c, s);
+        if (scheme == SCHEME_CONV) return launch_fwd_cfgs<Fwd97S, SCHEME_CONV, OutT>(box, row, p, grid, c, s);
         return cudaErrorInvalidValue;
     }
 }

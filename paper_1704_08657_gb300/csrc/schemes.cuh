@@ -359,6 +359,244 @@ struct Fwd97 {
     }
 };
 
+// --- polyconvolution (Proposed Schemes, N_{P,U}) -----------------------------
+// One lifting pair (P, U) as one step on pre-pair values: with V = 1 + PU the
+// pair's 4x4 matrix is the tensor product of the vertical [V* U*; P* 1] and
+// the horizontal [V U; P 1] 1-D pair matrices.  A row streams through the
+// horizontal part (h = [V U; P 1] on (c1, c2) and on (c3, c4), one exchange
+// of pre-pair neighbour values), and the vertical part combines the rows
+// above, here and below of h from registers.  V is applied as the 3-tap
+// filter 1 + ab(z^-1 + 2 + z) rather than as a predict followed by an update.
+// In this row-streaming design the separable and non-separable polyconvolution
+// schemes of the paper coincide: neither has a barrier between its
+// horizontal and vertical parts.
+template <int QL>
+__device__ __forceinline__ void pc_horiz(Row<float, QL>& X, float a, float b, float ab, float k0) {
+    float l1[QL], r1[QL], l2[QL], l3[QL], r3[QL], l4[QL];
+    left_of(X.c1, l1);
+    right_of(X.c1, r1);
+    left_of(X.c2, l2);
+    left_of(X.c3, l3);
+    right_of(X.c3, r3);
+    left_of(X.c4, l4);
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+        const float h1 = fmaf(ab, l1[q] + r1[q], fmaf(b, l2[q] + X.c2[q], k0 * X.c1[q]));  // V c1 + U c2
+        const float h2 = fmaf(a, X.c1[q] + r1[q], X.c2[q]);                                // P c1 + c2
+        const float h3 = fmaf(ab, l3[q] + r3[q], fmaf(b, l4[q] + X.c4[q], k0 * X.c3[q]));  // V c3 + U c4
+        const float h4 = fmaf(a, X.c3[q] + r3[q], X.c4[q]);                                // P c3 + c4
+        X.c1[q] = h1;
+        X.c2[q] = h2;
+        X.c3[q] = h3;
+        X.c4[q] = h4;
+    }
+}
+
+// O = [V* U*; P* 1] on the columns (h1, h3) and (h2, h4) of the rows above
+// (Up), here (H) and below (Dn).
+template <int QL>
+__device__ __forceinline__ void pc_vert(Row<float, QL>& O, const Row<float, QL>& Up, const Row<float, QL>& H,
+                                        const Row<float, QL>& Dn, float a, float b, float ab, float k0) {
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+        O.c1[q] = fmaf(ab, Up.c1[q] + Dn.c1[q], fmaf(b, Up.c3[q] + H.c3[q], k0 * H.c1[q]));  // V* h1 + U* h3
+        O.c3[q] = fmaf(a, H.c1[q] + Dn.c1[q], H.c3[q]);                                      // P* h1 + h3
+        O.c2[q] = fmaf(ab, Up.c2[q] + Dn.c2[q], fmaf(b, Up.c4[q] + H.c4[q], k0 * H.c2[q]));  // V* h2 + U* h4
+        O.c4[q] = fmaf(a, H.c2[q] + Dn.c2[q], H.c4[q]);                                      // P* h2 + h4
+    }
+}
+
+// CDF 9/7 by polyconvolution: pair (alpha, beta) on arrival n gives row n-1,
+// pair (gamma, delta) then gives row n-2; each pair keeps three rows of h.
+template <int QL>
+struct Fwd97PC {
+    static constexpr int LAG = 2;
+    using CT = float;
+    using R = Row<float, QL>;
+    static constexpr float AB = float(C97::Ad * C97::Bd), K1 = float(1.0 + 2.0 * C97::Ad * C97::Bd);
+    static constexpr float GD = float(C97::Gd * C97::Dd), K2 = float(1.0 + 2.0 * C97::Gd * C97::Dd);
+    R w1[3], w2[3], o;
+    __device__ __forceinline__ void init() {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            zero_row(w1[i]);
+            zero_row(w2[i]);
+        }
+    }
+    template <int PH>
+    __device__ __forceinline__ R& slot() {
+        return w1[PH % 3];
+    }
+    template <int PH>
+    __device__ __forceinline__ R& step(int /*row*/) {
+        R& x = w1[PH % 3];  // arrival n
+        pc_horiz(x, C97::A, C97::B, AB, K1);
+        R& y = w2[PH % 3];  // pair 1, row n-1
+        pc_vert(y, w1[(PH + 1) % 3], w1[(PH + 2) % 3], x, C97::A, C97::B, AB, K1);
+        pc_horiz(y, C97::G, C97::D, GD, K2);
+        pc_vert(o, w2[(PH + 1) % 3], w2[(PH + 2) % 3], y, C97::G, C97::D, GD, K2);  // row n-2
+        scale97(o);
+        return o;
+    }
+};
+
+// --- convolution --------------------------------------------------------------
+// The whole CDF 9/7 analysis as one 1-D filter bank per axis: the polyphase
+// matrix diag(zeta, 1/zeta) [V2 U2; P2 1] [V1 U1; P1 1] multiplied out at
+// compile time from the lifting constants,
+//   [s'; d'] = [A(z) B(z); C(z) D(z)] [s; d],
+// A: taps -2..2 (symmetric), B: -2..1 (B_k = B_{-1-k}), C: -1..2 (C_k = C_{1-k}),
+// D: -1..1 (symmetric), i.e. the 9-tap low-pass and 7-tap high-pass filters.
+// A row streams through the horizontal bank (one exchange of pre-transform
+// neighbours up to two quads away), and the vertical bank combines five rows
+// of its result held in a ring of six registers rows.  As with the
+// polyconvolution, the separable and non-separable convolution schemes of the
+// paper coincide here.
+struct LPoly9 {  // Laurent polynomial, coefficients of z^-4 .. z^4
+    double c[9];
+};
+constexpr LPoly9 lp_term(int k, double v) {
+    LPoly9 r{};
+    r.c[k + 4] = v;
+    return r;
+}
+constexpr LPoly9 lp_add(const LPoly9& x, const LPoly9& y) {
+    LPoly9 r{};
+    for (int i = 0; i < 9; ++i) r.c[i] = x.c[i] + y.c[i];
+    return r;
+}
+constexpr LPoly9 lp_mul(const LPoly9& x, const LPoly9& y) {
+    LPoly9 r{};
+    for (int i = 0; i < 9; ++i)
+        for (int j = 0; j < 9; ++j) {
+            const int k = i + j - 4;
+            if (k >= 0 && k < 9) r.c[k] += x.c[i] * y.c[j];
+        }
+    return r;
+}
+constexpr LPoly9 lp_scale(const LPoly9& x, double s) {
+    LPoly9 r{};
+    for (int i = 0; i < 9; ++i) r.c[i] = x.c[i] * s;
+    return r;
+}
+struct Conv97 {
+    static constexpr LPoly9 P1 = lp_add(lp_term(0, C97::Ad), lp_term(1, C97::Ad));   // a(1 + z)
+    static constexpr LPoly9 U1 = lp_add(lp_term(0, C97::Bd), lp_term(-1, C97::Bd));  // b(1 + z^-1)
+    static constexpr LPoly9 P2 = lp_add(lp_term(0, C97::Gd), lp_term(1, C97::Gd));
+    static constexpr LPoly9 U2 = lp_add(lp_term(0, C97::Dd), lp_term(-1, C97::Dd));
+    static constexpr LPoly9 V1 = lp_add(lp_term(0, 1.0), lp_mul(U1, P1));
+    static constexpr LPoly9 V2 = lp_add(lp_term(0, 1.0), lp_mul(U2, P2));
+    static constexpr LPoly9 A = lp_scale(lp_add(lp_mul(V2, V1), lp_mul(U2, P1)), C97::Zd);
+    static constexpr LPoly9 B = lp_scale(lp_add(lp_mul(V2, U1), U2), C97::Zd);
+    static constexpr LPoly9 C = lp_scale(lp_add(lp_mul(P2, V1), P1), 1.0 / C97::Zd);
+    static constexpr LPoly9 D = lp_scale(lp_add(lp_mul(P2, U1), lp_term(0, 1.0)), 1.0 / C97::Zd);
+    // distinct taps (index k + 4 is the coefficient of z^k)
+    static constexpr float A0 = float(A.c[4]), A1 = float(A.c[5]), A2 = float(A.c[6]);
+    static constexpr float B0 = float(B.c[4]), B1 = float(B.c[5]);  // B_0 = B_-1, B_1 = B_-2
+    static constexpr float C0 = float(C.c[4]), C2 = float(C.c[6]);  // C_0 = C_1, C_2 = C_-1
+    static constexpr float D0 = float(D.c[4]), D1 = float(D.c[5]);  // D_1 = D_-1
+};
+
+// values of the quads two to the left / right (QL >= 2)
+template <class CT, int QL>
+__device__ __forceinline__ void left2_of(const CT (&x)[QL], CT (&l)[QL]) {
+    static_assert(QL >= 2, "two-quad neighbours come from the adjacent lane");
+    const CT p0 = __shfl_up_sync(FULL, x[QL - 2], 1), p1 = __shfl_up_sync(FULL, x[QL - 1], 1);
+    l[0] = p0;
+    l[1] = p1;
+#pragma unroll
+    for (int q = 2; q < QL; ++q) l[q] = x[q - 2];
+}
+template <class CT, int QL>
+__device__ __forceinline__ void right2_of(const CT (&x)[QL], CT (&r)[QL]) {
+    static_assert(QL >= 2, "two-quad neighbours come from the adjacent lane");
+    const CT n0 = __shfl_down_sync(FULL, x[0], 1), n1 = __shfl_down_sync(FULL, x[1], 1);
+#pragma unroll
+    for (int q = 0; q + 2 < QL; ++q) r[q] = x[q + 2];
+    r[QL - 2] = n0;
+    r[QL - 1] = n1;
+}
+
+// the horizontal bank on the pixel row (s, d) of every quad, in place
+template <int QL>
+__device__ __forceinline__ void cv_bank(float (&s)[QL], float (&d)[QL]) {
+    using K = Conv97;
+    float sl[QL], sr[QL], sll[QL], srr[QL], dl[QL], dr[QL], dll[QL];
+    left_of(s, sl);
+    right_of(s, sr);
+    left2_of(s, sll);
+    right2_of(s, srr);
+    left_of(d, dl);
+    right_of(d, dr);
+    left2_of(d, dll);
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+        const float lo = fmaf(K::A2, sll[q] + srr[q], fmaf(K::A1, sl[q] + sr[q], K::A0 * s[q])) +
+                         fmaf(K::B1, dll[q] + dr[q], K::B0 * (dl[q] + d[q]));
+        const float hi = fmaf(K::C2, sl[q] + srr[q], K::C0 * (s[q] + sr[q])) +
+                         fmaf(K::D1, dl[q] + dr[q], K::D0 * d[q]);
+        s[q] = lo;
+        d[q] = hi;
+    }
+}
+
+template <int QL>
+struct Fwd97CV {
+    static constexpr int LAG = 2;
+    using CT = float;
+    using R = Row<float, QL>;
+    R hw[6], o;  // horizontal results of the last rows, ring indexed by phase
+    __device__ __forceinline__ void init() {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) zero_row(hw[i]);
+    }
+    template <int PH>
+    __device__ __forceinline__ R& slot() {
+        return hw[PH % 6];
+    }
+    template <int PH>
+    __device__ __forceinline__ R& step(int /*row*/) {
+        using K = Conv97;
+        R& x = hw[PH % 6];  // arrival n; output row r = n - 2
+        cv_bank(x.c1, x.c2);
+        cv_bank(x.c3, x.c4);
+        const R& m2 = hw[(PH + 2) % 6];  // row r-2
+        const R& m1 = hw[(PH + 3) % 6];  // row r-1
+        const R& z0 = hw[(PH + 4) % 6];  // row r
+        const R& p1 = hw[(PH + 5) % 6];  // row r+1
+        const R& p2 = x;                 // row r+2
+#pragma unroll
+        for (int q = 0; q < QL; ++q) {
+            // vertical bank on the columns (h1, h3) -> (c1, c3) and (h2, h4) -> (c2, c4)
+            o.c1[q] = fmaf(K::A2, m2.c1[q] + p2.c1[q], fmaf(K::A1, m1.c1[q] + p1.c1[q], K::A0 * z0.c1[q])) +
+                      fmaf(K::B1, m2.c3[q] + p1.c3[q], K::B0 * (m1.c3[q] + z0.c3[q]));
+            o.c3[q] = fmaf(K::C2, m1.c1[q] + p2.c1[q], K::C0 * (z0.c1[q] + p1.c1[q])) +
+                      fmaf(K::D1, m1.c3[q] + p1.c3[q], K::D0 * z0.c3[q]);
+            o.c2[q] = fmaf(K::A2, m2.c2[q] + p2.c2[q], fmaf(K::A1, m1.c2[q] + p1.c2[q], K::A0 * z0.c2[q])) +
+                      fmaf(K::B1, m2.c4[q] + p1.c4[q], K::B0 * (m1.c4[q] + z0.c4[q]));
+            o.c4[q] = fmaf(K::C2, m1.c2[q] + p2.c2[q], K::C0 * (z0.c2[q] + p1.c2[q])) +
+                      fmaf(K::D1, m1.c4[q] + p1.c4[q], K::D0 * z0.c4[q]);
+        }
+        return o;
+    }
+};
+
+// the CDF 9/7 forward pipeline of a scheme
+template <int SCHEME, int QL>
+struct Fwd97Sel {
+    using type = Fwd97<SCHEME, QL>;
+};
+template <int QL>
+struct Fwd97Sel<SCHEME_POLYCONV, QL> {
+    using type = Fwd97PC<QL>;
+};
+template <int QL>
+struct Fwd97Sel<SCHEME_CONV, QL> {
+    using type = Fwd97CV<QL>;
+};
+template <int SCHEME, int QL>
+using Fwd97S = typename Fwd97Sel<SCHEME, QL>::type;
+
 // inverse: unscale, then for each pair in reverse order S_{-U}, T_{-P}
 template <int SCHEME, int QL>
 struct Inv97 {

@@ -51,6 +51,11 @@ def test_strerror_names_every_code(lib):
     ((abi.DWT2_CDF53_INT, 1, 0, abi.DWT2_I32, abi.DWT2_I32, abi.DWT2_NONSEP_REDUCED, [(0, 16, 16, 16)]),
      abi.DWT2_ERR_UNSUPPORTED),
     ((abi.DWT2_CDF53_INT, 1, 0, abi.DWT2_F32, abi.DWT2_F32, 0, [(0, 16, 16, 16)]), abi.DWT2_ERR_UNSUPPORTED),
+    ((abi.DWT2_CDF97, 1, 0, 0, 0, 5, [(0, 16, 16, 16)]), abi.DWT2_ERR_INVALID_ARG),          # scheme past CONV
+    ((abi.DWT2_CDF53_INT, 1, 0, abi.DWT2_I32, abi.DWT2_I32, abi.DWT2_POLYCONV, [(0, 16, 16, 16)]),
+     abi.DWT2_ERR_UNSUPPORTED),                                                             # floor: lifting only
+    ((abi.DWT2_CDF53_INT, 1, 0, abi.DWT2_I32, abi.DWT2_I32, abi.DWT2_CONV, [(0, 16, 16, 16)]),
+     abi.DWT2_ERR_UNSUPPORTED),
 ])
 def test_plan_validation(lib, args, code):
     wav, lv, bd, idt, cdt, sch, imgs = args
@@ -61,6 +66,13 @@ def test_plan_validation(lib, args, code):
     with pytest.raises(abi.Dwt2Error) as e:
         abi.dwt2_plan(wav, lv, bd, idt, cdt, sch, imgs)
     assert e.value.code == code
+
+
+@pytest.mark.parametrize("scheme", [abi.DWT2_POLYCONV, abi.DWT2_CONV])
+def test_filter_bank_schemes_have_no_persistent_form(lib, scheme):
+    with pytest.raises(abi.Dwt2Error) as e:
+        abi.dwt2_plan(abi.DWT2_CDF97, 1, 0, 0, 0, scheme, [(0, 16, 16, 16)], abi.DWT2_FLAG_PERSISTENT)
+    assert e.value.code == abi.DWT2_ERR_UNSUPPORTED
 
 
 def test_null_arguments(lib):
