@@ -119,7 +119,9 @@ typedef struct {
  *              inverse and adjoint of a plan run the non-separable lifting
  *              kernels for the last two (the same transform).
  *   n_images   number of images (>= 1); images is a host array of that many
- *              descriptors, copied into the plan.
+ *              descriptors, copied into the plan.  With several images (and
+ *              a lifting scheme) dwt2_forward makes one launch per level for
+ *              all images, the inverse and adjoint likewise.
  *   flags      0 or DWT2_FLAG_PERSISTENT: dwt2_forward then runs every level of every
  *              image in one persistent launch whose units take work from a device
  *              queue and wait (bounded by DWT2_TIMEOUT_MS, default 2000) for the
@@ -132,7 +134,7 @@ typedef struct {
  * tables on the current device.
  * Environment, read when the plan is made (launch tuning only; results do not
  * depend on it): DWT2_TIMEOUT_MS (bounded device waits, default 2000),
- * DWT2_FWD_CFG and DWT2_SEG_ROWS (forward kernel configuration 0-3 and
+ * DWT2_FWD_CFG and DWT2_SEG_ROWS (forward kernel configuration 0-4 and
  * segment height before any dwt2_autotune), DWT2_PDL (0 launches the forward
  * levels without programmatic dependent launch), DWT2_FUSE_SEG and
  * DWT2_FUSE_PAIRS (run level pairs 0-1, 2-3, ... in one fused launch with that
@@ -187,9 +189,9 @@ int dwt2_adjoint_l1(dwt2_plan_t plan, const void* coef, void* in_grad, float sca
  * segment height; segment height for persistent plans), a few calls each on
  * the stream timed per level with the plan's profile events, keep the fastest
  * candidate of every level (of the whole launch for persistent plans) and
- * store the choice in *choice: 5 bits per level for the first six levels,
- * deeper levels sharing the sixth field (persistent plans: the candidate
- * index).  With *choice >= 0: apply that choice without timing (e.g. from a
+ * store the choice in *choice: 6 bits per level for the first five levels,
+ * deeper levels sharing the fifth field (persistent plans and plans of
+ * several images: the index of one segment height for every level).  With *choice >= 0: apply that choice without timing (e.g. from a
  * cache of an earlier run on the same GPU); DWT2_ERR_INVALID_ARG if it is not
  * a valid choice for this plan.  The coefficient buffer is overwritten and the
  * plan's profile ring is reset.  Synchronises the stream; not for use during

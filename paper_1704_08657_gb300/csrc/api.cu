@@ -163,6 +163,12 @@ struct dwt2_plan_s {
     bool persistent;
     int pml_bps, pml_seg, pml_force_cpasync, pml_lag_pct;
     std::vector<PmlDesc> h_descs;  // host copy (TMA maps are encoded per call from it)
+    // level-major batched forward (several images, not persistent): per
+    // (image, level) descriptors and the units of each level
+    int fb_seg;
+    PmlDesc* d_fb_descs;
+    PmlUnit* d_fb_units;
+    std::vector<int> fb_level_start;  // units of level l: [start[l], start[l+1])
     // batched inverse / adjoint (several images): descriptors, units by level
     InvDesc* d_inv_descs;
     InvUnit* d_inv_units;
@@ -297,6 +303,73 @@ int build_persistent(dwt2_plan_t p) {
     return DWT2_OK;
 }
 
+// Descriptor of one (image, level) of the batched forward kernels.
+PmlDesc pml_desc(dwt2_plan_t p, const ImagePlan& ip, int l, int seg) {
+    const LevelGeom& g = ip.lv[l];
+    const size_t csz = dtype_size(p->coef_dtype);
+    PmlDesc d;
+    memset(&d, 0, sizeof(d));
+    d.h = g.h, d.w = g.w, d.hq = g.hq, d.wq = g.wq, d.hh = g.hh, d.wh = g.wh;
+    const int outq = fwd_out_quads(FwdCfg{PML_QL, PML_QR, PML_NST, PML_NW, 0});
+    d.n_strips = (g.wq + outq - 1) / outq;
+    d.seg_rows = std::min(seg, g.hq);
+    d.src_is_ws = l > 0;
+    d.src_off = (l == 0) ? ip.d.offset_elems : int64_t(ip.ws_off[l - 1] / 4);
+    d.src_pitch = (l == 0) ? ip.d.pitch_elems : round4(ip.lv[l - 1].wq);
+    d.coef_off = ip.d.offset_elems;
+    d.coef_pitch = ip.d.pitch_elems;
+    const bool last = (l == p->levels - 1);
+    d.ll_is_ct = !last;
+    d.ll_off = last ? ip.d.offset_elems : int64_t(ip.ws_off[l] / 4);
+    d.ll_pitch = last ? ip.d.pitch_elems : round4(g.wq);
+    const bool cvec = (ip.d.pitch_elems % 2 == 0) && ((ip.d.offset_elems * csz) % (2 * csz) == 0);
+    d.vec_lo = cvec;
+    d.vec_hi = cvec && (g.wq % 2 == 0);
+    d.vec_ll = last ? cvec : 1;
+    d.dep_base = -1;
+    return d;
+}
+
+// Tables of the level-major batched forward: every level's units of every
+// image in (image, segment, strip) order, one launch per level.
+constexpr int FB_SEG_DEFAULT = 32;
+
+int build_forward_batch(dwt2_plan_t p) {
+    const int L = p->levels;
+    std::vector<PmlDesc> descs;
+    std::vector<std::vector<PmlUnit>> by_level(L);
+    for (size_t i = 0; i < p->imgs.size(); ++i) {
+        for (int l = 0; l < L; ++l) {
+            const PmlDesc d = pml_desc(p, p->imgs[i], l, p->fb_seg);
+            const int di = int(descs.size());
+            descs.push_back(d);
+            const int n_segs = (d.hq + d.seg_rows - 1) / d.seg_rows;
+            for (int g = 0; g < n_segs; ++g)
+                for (int st = 0; st < d.n_strips; ++st) by_level[l].push_back(PmlUnit{di, st, g, 0, -1});
+        }
+    }
+    std::vector<PmlUnit> units;
+    p->fb_level_start.assign(1, 0);
+    for (int l = 0; l < L; ++l) {
+        units.insert(units.end(), by_level[l].begin(), by_level[l].end());
+        p->fb_level_start.push_back(int(units.size()));
+    }
+    if (p->d_fb_descs) cudaFree(p->d_fb_descs);
+    if (p->d_fb_units) cudaFree(p->d_fb_units);
+    p->d_fb_descs = nullptr;
+    p->d_fb_units = nullptr;
+    if (cudaMalloc(&p->d_fb_descs, descs.size() * sizeof(PmlDesc)) != cudaSuccess ||
+        cudaMalloc(&p->d_fb_units, std::max<size_t>(1, units.size()) * sizeof(PmlUnit)) != cudaSuccess ||
+        cudaMemcpy(p->d_fb_descs, descs.data(), descs.size() * sizeof(PmlDesc), cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(p->d_fb_units, units.data(), units.size() * sizeof(PmlUnit), cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        return DWT2_ERR_CUDA;
+    }
+    return DWT2_OK;
+}
+
 // Tables of the batched inverse / adjoint: per (image, level) a descriptor,
 // per level the units of every image (segments of INV_BATCH_SEG quad rows).
 constexpr int INV_BATCH_SEG = 32;
@@ -384,6 +457,40 @@ int inverse_batch(dwt2_plan_t p, const void* coef, void* out, void* workspace, c
         }
         if (e != cudaSuccess) return DWT2_ERR_CUDA;
         prof_mark(p, l, false, s);
+    }
+    if (p->prof_on) ++p->prof_calls;
+    return DWT2_OK;
+}
+
+int forward_batch(dwt2_plan_t p, const void* in, void* coef, void* workspace, cudaStream_t s) {
+    const size_t csz = dtype_size(p->coef_dtype);
+    std::unique_ptr<PmlLaunch> lp(new (std::nothrow) PmlLaunch());
+    if (!lp) return DWT2_ERR_INVALID_ARG;
+    PmlParams& pp = lp->base;
+    memset(&pp, 0, sizeof(pp));
+    pp.in = in;
+    pp.coef = coef;
+    pp.ws = workspace;
+    pp.descs = p->d_fb_descs;
+    pp.coef_vec = aligned(coef, 2 * csz);
+    pp.status = p->d_status;
+    pp.timeout_ns = p->timeout_ns;
+    pp.level_major = 1;
+    lp->use_tma = 0;
+    for (int l = 0; l < p->levels; ++l) {
+        pp.units = p->d_fb_units + p->fb_level_start[l];
+        pp.n_units = p->fb_level_start[l + 1] - p->fb_level_start[l];
+        const int grid = std::max(1, std::min((pp.n_units + PML_NW - 1) / PML_NW, p->sm_count * p->pml_bps * 4));
+        prof_mark(p, l, true, s);
+        int e;
+        switch (p->coef_dtype) {
+            case DWT2_F32: e = launch_pml_f32(p->wavelet, p->scheme, *lp, grid, s); break;
+            case DWT2_F16: e = launch_pml_f16(p->wavelet, p->scheme, *lp, grid, s); break;
+            case DWT2_BF16: e = launch_pml_bf16(p->wavelet, p->scheme, *lp, grid, s); break;
+            default: e = launch_pml_i32(p->wavelet, p->scheme, *lp, grid, s); break;
+        }
+        prof_mark(p, l, false, s);
+        if (e != cudaSuccess) return DWT2_ERR_CUDA;
     }
     if (p->prof_on) ++p->prof_calls;
     return DWT2_OK;
@@ -491,7 +598,7 @@ int level_maps(dwt2_plan_t p, const ImagePlan& ip, int l, const void* in, void* 
 const int TUNE_SEGS[] = {0, 2, 4, 8, 12, 16, 24, 32};
 constexpr int N_TUNE_SEGS = int(sizeof(TUNE_SEGS) / sizeof(TUNE_SEGS[0]));
 constexpr int N_LVL_CANDS = N_FWD_CFGS * N_TUNE_SEGS;
-constexpr int TUNE_BITS = 5, TUNE_LEVELS = 6;  // a plan's choice: 5 bits per level, levels >= 5 share one
+constexpr int TUNE_BITS = 6, TUNE_LEVELS = 5;  // a plan's choice: 6 bits per level, levels >= 4 share one
 static_assert(N_LVL_CANDS <= (1 << TUNE_BITS), "candidates fit the choice field");
 
 int forward_level(dwt2_plan_t p, const ImagePlan& ip, int l, const void* in, void* coef, void* workspace,
@@ -666,6 +773,9 @@ int dwt2_plan(dwt2_plan_t* out, int wavelet, int levels, int boundary, int in_dt
     if (p->pml_seg < 4) p->pml_seg = PML_SEG_DEFAULT;
     p->d_inv_descs = nullptr;
     p->d_inv_units = nullptr;
+    p->fb_seg = FB_SEG_DEFAULT;
+    p->d_fb_descs = nullptr;
+    p->d_fb_units = nullptr;
     if (p->persistent) {
         const int rc = build_persistent(p);
         if (rc != DWT2_OK) {
@@ -674,7 +784,12 @@ int dwt2_plan(dwt2_plan_t* out, int wavelet, int levels, int boundary, int in_dt
         }
     }
     if (n_images > 1) {
-        const int rc = build_inverse_batch(p);
+        int rc = build_inverse_batch(p);
+        // several images, lifting schemes: one level-major launch per level
+        if (rc == DWT2_OK && !p->persistent && scheme <= DWT2_SEP_LIFTING) {
+            p->pml_bps = pml_blocks_per_sm(wavelet, scheme, coef_dtype);
+            rc = p->pml_bps > 0 ? build_forward_batch(p) : DWT2_ERR_CUDA;
+        }
         if (rc != DWT2_OK) {
             dwt2_destroy(p);
             return rc;
@@ -694,6 +809,8 @@ void dwt2_destroy(dwt2_plan_t p) {
     if (p->d_counters) cudaFree(p->d_counters);
     if (p->d_inv_descs) cudaFree(p->d_inv_descs);
     if (p->d_inv_units) cudaFree(p->d_inv_units);
+    if (p->d_fb_descs) cudaFree(p->d_fb_descs);
+    if (p->d_fb_units) cudaFree(p->d_fb_units);
     for (cudaEvent_t e : p->ev0) cudaEventDestroy(e);
     for (cudaEvent_t e : p->ev1) cudaEventDestroy(e);
     delete p;
@@ -754,6 +871,7 @@ int dwt2_forward(dwt2_plan_t p, const void* in, void* coef, void* workspace, voi
     if (!aligned(coef, csz)) return DWT2_ERR_MISALIGNED;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (p->persistent) return forward_persistent(p, in, coef, workspace, s);
+    if (p->d_fb_units) return forward_batch(p, in, coef, workspace, s);
     for (int l = 0; l < p->levels;) {
         bool fuse = p->fuse_seg > 0 && l / 2 < p->fuse_pairs && l % 2 == 0 && l + 1 < p->levels && p->fused_bps > 0;
         for (const ImagePlan& ip : p->imgs) fuse = fuse && fused_eligible(ip.lv[l]);
@@ -865,12 +983,19 @@ constexpr int N_TUNE_PML = int(sizeof(TUNE_PML_SEGS) / sizeof(TUNE_PML_SEGS[0]))
 
 static int tune_fields(dwt2_plan_t p) { return std::min(p->levels, TUNE_LEVELS); }
 
+// persistent and level-major batch plans tune one segment height for all levels
+static bool tune_seg_only(dwt2_plan_t p) { return p->persistent || p->d_fb_units != nullptr; }
+
 static int tune_apply(dwt2_plan_t p, int choice) {
     if (choice < 0) return DWT2_ERR_INVALID_ARG;
-    if (p->persistent) {
+    if (tune_seg_only(p)) {
         if (choice >= N_TUNE_PML) return DWT2_ERR_INVALID_ARG;
-        p->pml_seg = TUNE_PML_SEGS[choice];
-        return build_persistent(p);
+        if (p->persistent) {
+            p->pml_seg = TUNE_PML_SEGS[choice];
+            return build_persistent(p);
+        }
+        p->fb_seg = TUNE_PML_SEGS[choice];
+        return build_forward_batch(p);
     }
     const int nf = tune_fields(p);
     if (nf * TUNE_BITS < 31 && choice >= (1 << (nf * TUNE_BITS))) return DWT2_ERR_INVALID_ARG;
@@ -886,21 +1011,22 @@ int dwt2_autotune(dwt2_plan_t p, const void* in, void* coef, void* workspace, vo
     const bool prof = p->prof_on;
     int rc = DWT2_OK;
     const int L = p->levels;
-    const int n_cand = p->persistent ? N_TUNE_PML : N_LVL_CANDS;
+    const bool seg_only = tune_seg_only(p);
+    const int n_cand = seg_only ? N_TUNE_PML : N_LVL_CANDS;
     std::vector<float> ms(size_t(n_cand) * L, 0.f);
     for (int c = 0; c < n_cand && rc == DWT2_OK; ++c) {
-        if (p->persistent) {
+        if (seg_only) {
             rc = tune_apply(p, c);
         } else {
             for (int l = 0; l < L; ++l) p->lvl_cand[l] = c;
         }
         for (int i = 0; i < 2 && rc == DWT2_OK; ++i) rc = dwt2_forward(p, in, coef, workspace, stream);
-        // the smallest of three means of four calls, per level
+        // the smallest of three means of eight calls, per level
         float* mc = &ms[size_t(c) * L];
         for (int r = 0; r < 3 && rc == DWT2_OK; ++r) {
             std::vector<float> m(L, 0.f);
             rc = dwt2_profile(p, 1);
-            for (int i = 0; i < 4 && rc == DWT2_OK; ++i) rc = dwt2_forward(p, in, coef, workspace, stream);
+            for (int i = 0; i < 8 && rc == DWT2_OK; ++i) rc = dwt2_forward(p, in, coef, workspace, stream);
             if (rc == DWT2_OK) rc = dwt2_profile_read(p, m.data(), L);
             for (int l = 0; l < L && rc == DWT2_OK; ++l) mc[l] = (r == 0) ? m[l] : std::min(mc[l], m[l]);
         }
@@ -910,9 +1036,15 @@ int dwt2_autotune(dwt2_plan_t p, const void* in, void* coef, void* workspace, vo
     p->prof_calls = 0;
     if (rc != DWT2_OK) return rc;
     int best = 0;
-    if (p->persistent) {
+    if (seg_only) {
+        // the whole call: a persistent launch is timed as level 0, the others read 0
+        auto total = [&](int c) {
+            float t = 0.f;
+            for (int l = 0; l < L; ++l) t += ms[size_t(c) * L + l];
+            return t;
+        };
         for (int c = 1; c < n_cand; ++c)
-            if (ms[size_t(c) * L] < ms[size_t(best) * L]) best = c;
+            if (total(c) < total(best)) best = c;
     } else {
         const int nf = tune_fields(p);
         for (int f = 0; f < nf; ++f) {

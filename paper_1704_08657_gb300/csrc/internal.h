@@ -90,6 +90,10 @@ struct PmlParams {
     int test_drop_signal;  // test hook: queue entry 0 never signals completion
     unsigned* status;
     uint64_t timeout_ns;
+    // level-major batch: the units are one level's, taken in order by a static
+    // round-robin over the grid, with no queue, waits or counters (the previous
+    // level is complete: stream order)
+    int level_major;
 };
 
 // Batched inverse / adjoint: one launch per level for every image; offsets in

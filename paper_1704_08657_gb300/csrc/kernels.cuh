@@ -428,15 +428,20 @@ __global__ void __launch_bounds__(NW * 32) pml_kernel(const __grid_constant__ Pm
         fence_mbar_init();
     }
     __syncwarp();
+    griddep_wait();  // level-major launches are programmatic dependents of the previous level
+    griddep_launch_dependents();
     uint32_t gstage = 0;
-    for (;;) {
-        int u = 0;
-        if (lane == 0) u = int(atomicAdd(P.queue, 1u));
-        u = __shfl_sync(FULL, u, 0);
+    const int stride = gridDim.x * NW;
+    for (int it = blockIdx.x * NW + warp;; it += stride) {
+        int u = it;
+        if (!P.level_major) {
+            if (lane == 0) u = int(atomicAdd(P.queue, 1u));
+            u = __shfl_sync(FULL, u, 0);
+        }
         if (u >= P.n_units) break;
         const PmlUnit un = P.units[u];
         const PmlDesc& d = P.descs[un.desc];
-        if (d.dep_base >= 0) {
+        if (!P.level_major && d.dep_base >= 0) {
             bool waited_ok = true;
             if (lane == 0) {
                 for (int g = un.dep_lo; g <= un.dep_hi; ++g) {
@@ -483,6 +488,7 @@ __global__ void __launch_bounds__(NW * 32) pml_kernel(const __grid_constant__ Pm
             ok = fwd_unit<Pipe, OutT, QL, QR, NST>(v, ld, un.s, R0, R1, bufs, bars, gstage, lane);
         }
         if (!ok) return;
+        if (P.level_major) continue;
         // this unit's stores must be visible to the TMA reads of later units
         if (TMA) asm volatile("fence.proxy.async.global;" ::: "memory");
         __syncwarp();

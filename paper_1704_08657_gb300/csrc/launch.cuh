@@ -135,11 +135,24 @@ template <class Pipe, class OutT>
 int launch_pml_one(const PmlLaunch& p, int grid, cudaStream_t s) {
     constexpr size_t smem = fwd_smem_bytes<PML_QL, PML_QR, PML_NST, PML_NW>();
     static_assert(smem <= 48 * 1024, "persistent kernel stages fit the default shared-memory limit");
-    if (p.use_tma)
-        pml_kernel<Pipe, OutT, PML_QL, PML_QR, PML_NST, PML_NW, true><<<grid, PML_NW * 32, smem, s>>>(p);
-    else
-        pml_kernel<Pipe, OutT, PML_QL, PML_QR, PML_NST, PML_NW, false><<<grid, PML_NW * 32, smem, s>>>(p);
-    return cudaGetLastError();
+    auto k = p.use_tma ? pml_kernel<Pipe, OutT, PML_QL, PML_QR, PML_NST, PML_NW, true>
+                       : pml_kernel<Pipe, OutT, PML_QL, PML_QR, PML_NST, PML_NW, false>;
+    if (!p.base.level_major) {
+        k<<<grid, PML_NW * 32, smem, s>>>(p);
+        return cudaGetLastError();
+    }
+    // level-major batch levels: programmatic dependents of the previous level
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(grid);
+    lc.blockDim = dim3(PML_NW * 32);
+    lc.dynamicSmemBytes = smem;
+    lc.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    return cudaLaunchKernelEx(&lc, k, p);
 }
 
 template <class Pipe, class OutT>

@@ -38,9 +38,10 @@ def test_autotune_keeps_results(tmp_path, flags):
     assert torch.equal(p2.forward(x), before)
 
 
-@pytest.mark.parametrize("flags,bad", [(0, 1 << 10), (abi.DWT2_FLAG_PERSISTENT, 99)])
+@pytest.mark.parametrize("flags,bad", [(0, 1 << 12), (0, 63), (abi.DWT2_FLAG_PERSISTENT, 99)])
 def test_autotune_rejects_bad_choice(flags, bad):
-    # a two-level plan packs 5 bits per level: a choice of 2^10 or more is not one of its choices
+    # a two-level plan packs 6 bits per level (32 candidates): 2^12 or more, or a
+    # field of 32 or more, is not one of its choices
     plan = Plan.single(64, 64, 2, flags=flags)
     x = torch.zeros((64, 64), device="cuda")
     with pytest.raises(abi.Dwt2Error):
@@ -57,7 +58,7 @@ def test_autotune_choice_fields_per_level():
     out = torch.empty_like(x)
     choice = 0
     for lev in range(levels):
-        choice |= ((7 * lev + 3) % 32) << (5 * lev)
+        choice |= ((9 * lev + 3) % 32) << (6 * lev)
     assert abi.dwt2_autotune(plan.handle, x.data_ptr(), out.data_ptr(), plan.workspace.data_ptr(), 0, choice) == choice
     assert torch.equal(plan.forward(x), ref)
     assert plan.status() == 0

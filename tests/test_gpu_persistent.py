@@ -171,3 +171,48 @@ def test_batch_inverse_adjoint_and_l1():
     back = pi.inverse(ci)
     for x, r in zip(_unpack(bi, descs), _unpack(back.cpu().numpy(), descs)):
         assert np.array_equal(x, r)
+
+
+@pytest.mark.parametrize("scheme,coef_dtype", [("reduced", torch.float32), ("sep", torch.float16),
+                                               ("polyconv", torch.float32)])
+def test_level_major_batch_equals_single_image_plans(scheme, coef_dtype):
+    """A plan of several images makes one launch per level for all of them
+    (lifting schemes; the filter-bank schemes launch per image); every image
+    equals its own single-image plan bit for bit."""
+    shapes = synth.batch_shapes(40, seed=7)
+    buf, descs = _batch(shapes, seed=8)
+    xd = torch.from_numpy(buf).cuda()
+    plan = Plan(descs, 3, scheme=scheme, coef_dtype=coef_dtype)
+    for choice in (-1, 0, 3):  # the automatic default, then two tuned segment heights
+        if choice >= 0:
+            assert abi.dwt2_autotune(plan.handle, xd.data_ptr(), torch.empty_like(xd, dtype=coef_dtype).data_ptr(),
+                                     plan.workspace.data_ptr(), 0, choice) == choice
+        c = plan.forward(xd, torch.zeros_like(xd, dtype=coef_dtype))
+        torch.cuda.synchronize()
+        assert plan.status() == 0
+        got = _unpack(c.float().cpu().numpy(), descs)
+        for i, (o, h, w, p) in enumerate(descs):
+            if i % 5:
+                continue
+            xi = xd[o:o + h * p].view(h, p).contiguous()
+            single = Plan.single(h, w, 3, pitch=p, scheme=scheme, coef_dtype=coef_dtype).forward(xi)
+            assert np.array_equal(single[:, :w].float().cpu().numpy(), got[i]), f"image {i} {h}x{w} choice {choice}"
+    imgs = _unpack(buf, descs)
+    for i in (0, 17, 39):
+        ref = oracle.forward97(imgs[i].astype(np.float64), 3)
+        if coef_dtype == torch.float32:
+            assert_fp32_close(got[i], ref, 3, 255.0, f"image {i}")
+        else:
+            assert_lowp_close(got[i], ref, 3, 1e-3, f"image {i}")
+
+
+def test_level_major_batch_int53():
+    shapes = synth.batch_shapes(24, seed=12)
+    buf, descs = _batch(shapes)
+    bi = np.rint(buf).astype(np.int32)
+    plan = Plan(descs, 3, wavelet="cdf53", scheme="nonsep", coef_dtype=torch.int32)
+    c = plan.forward(torch.from_numpy(bi).cuda())
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    for g, x in zip(_unpack(c.cpu().numpy(), descs), _unpack(bi, descs)):
+        assert np.array_equal(g.astype(np.int64), oracle.forward53i(x.astype(np.int64), 3))
