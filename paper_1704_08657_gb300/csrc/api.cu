@@ -154,6 +154,9 @@ struct dwt2_plan_s {
     std::vector<int> lvl_cand;      // per level: tuning candidate, or -1 for cfg_env / seg_env
     int inv_bps;                    // resident blocks per SM of the inverse kernel
     int pdl;                        // per-level forward launches as programmatic dependents (DWT2_PDL)
+    int overlap;                    // single image: inter-level overlap by segment counters (DWT2_LEVEL_OVERLAP)
+    unsigned* d_lvl_ctr;            // the segment counters
+    size_t n_lvl_ctr;
     int balanced_env;
     // fused level pairs: segment height in level l+1 quad rows (0: off) and
     // how many pairs, from level 0 on, may run fused
@@ -601,33 +604,86 @@ constexpr int N_LVL_CANDS = N_FWD_CFGS * N_TUNE_SEGS;
 constexpr int TUNE_BITS = 6, TUNE_LEVELS = 5;  // a plan's choice: 6 bits per level, levels >= 4 share one
 static_assert(N_LVL_CANDS <= (1 << TUNE_BITS), "candidates fit the choice field");
 
-int forward_level(dwt2_plan_t p, const ImagePlan& ip, int l, const void* in, void* coef, void* workspace,
-                  cudaStream_t s) {
-    int ci = p->cfg_env, seg = p->seg_env;
+// The launch configuration of one forward level of one image.
+struct LevelLaunch {
+    int ci;  // index into FWD_CFGS
+    Decomp dc;
+    int grid, balanced;
+};
+
+LevelLaunch level_launch(dwt2_plan_t p, const ImagePlan& ip, int l) {
+    LevelLaunch ll;
+    ll.ci = p->cfg_env;
+    int seg = p->seg_env;
     const int cand = p->lvl_cand[l];
     if (cand >= 0) {
-        ci = cand / N_TUNE_SEGS;
+        ll.ci = cand / N_TUNE_SEGS;
         seg = TUNE_SEGS[cand % N_TUNE_SEGS];
     }
-    const FwdCfg& cfg = FWD_CFGS[ci];
+    const FwdCfg& cfg = FWD_CFGS[ll.ci];
+    ll.dc = decompose(ip.lv[l], fwd_out_quads(cfg), p->sm_count, p->cfg_bps[ll.ci], cfg.nw, seg, p->balanced_env,
+                      &ll.grid, &ll.balanced);
+    return ll;
+}
+
+// One forward level of one image.  dep_ctr / out_ctr: inter-level overlap
+// (FwdParams); null for a launch that waits for the previous grid.
+int forward_level(dwt2_plan_t p, const ImagePlan& ip, int l, const void* in, void* coef, void* workspace,
+                  cudaStream_t s, const LevelLaunch& ll, const unsigned* dep_ctr = nullptr, int dep_need = 0,
+                  int dep_seg = 1, unsigned* out_ctr = nullptr) {
+    const FwdCfg& cfg = FWD_CFGS[ll.ci];
     CUtensorMap box, row;
     const int rc = level_maps(p, ip, l, in, workspace, cfg.ql, cfg.qr, &box, &row);
     if (rc != DWT2_OK) return rc;
     FwdParams fp = level_outputs(p, ip, l, coef, workspace);
-    int grid = 0, balanced = 0;
-    const Decomp dc = decompose(ip.lv[l], fwd_out_quads(cfg), p->sm_count, p->cfg_bps[ci], cfg.nw, seg,
-                                p->balanced_env, &grid, &balanced);
+    const Decomp& dc = ll.dc;
     fp.n_strips = dc.n_strips, fp.seg_rows = dc.seg_rows, fp.n_segs = dc.n_segs, fp.n_units = dc.n_units;
-    fp.balanced = balanced;
+    fp.balanced = ll.balanced;
     fp.pdl = p->pdl;
+    FwdSync y;
+    y.dep_ctr = dep_ctr;
+    y.dep_need = dep_need;
+    y.dep_seg = dep_seg;
+    y.out_ctr = out_ctr;
+    y.test_drop = (p->flags & DWT2_FLAG_TEST_DROP_SIGNAL) != 0;
     int e;
     switch (p->coef_dtype) {
-        case DWT2_F32: e = launch_forward_f32(p->wavelet, p->scheme, box, row, fp, grid, cfg, s); break;
-        case DWT2_F16: e = launch_forward_f16(p->wavelet, p->scheme, box, row, fp, grid, cfg, s); break;
-        case DWT2_BF16: e = launch_forward_bf16(p->wavelet, p->scheme, box, row, fp, grid, cfg, s); break;
-        default: e = launch_forward_i32(p->wavelet, p->scheme, box, row, fp, grid, cfg, s); break;
+        case DWT2_F32: e = launch_forward_f32(p->wavelet, p->scheme, box, row, fp, ll.grid, cfg, s, y); break;
+        case DWT2_F16: e = launch_forward_f16(p->wavelet, p->scheme, box, row, fp, ll.grid, cfg, s, y); break;
+        case DWT2_BF16: e = launch_forward_bf16(p->wavelet, p->scheme, box, row, fp, ll.grid, cfg, s, y); break;
+        default: e = launch_forward_i32(p->wavelet, p->scheme, box, row, fp, ll.grid, cfg, s, y); break;
     }
     return e == cudaSuccess ? DWT2_OK : DWT2_ERR_CUDA;
+}
+
+// Single-image pyramid with inter-level overlap: the segment counters of
+// levels 0 .. L-2 are cleared, then every level after the first waits on
+// its predecessor's counters instead of its grid.
+int forward_overlapped(dwt2_plan_t p, const void* in, void* coef, void* workspace, cudaStream_t s) {
+    const ImagePlan& ip = p->imgs[0];
+    const int L = p->levels;
+    std::vector<LevelLaunch> lls(L);
+    std::vector<size_t> base(L, 0);
+    size_t n = 0;
+    for (int l = 0; l < L; ++l) {
+        lls[l] = level_launch(p, ip, l);
+        if (lls[l].balanced) return DWT2_ERR_INVALID_ARG;  // counters need whole segments
+        base[l] = n;
+        if (l + 1 < L) n += size_t(lls[l].dc.n_segs);
+    }
+    if (n > p->n_lvl_ctr) return DWT2_ERR_INVALID_ARG;
+    if (n && cudaMemsetAsync(p->d_lvl_ctr, 0, n * sizeof(unsigned), s) != cudaSuccess) return DWT2_ERR_CUDA;
+    for (int l = 0; l < L; ++l) {
+        prof_mark(p, l, true, s);
+        const unsigned* dep = l > 0 ? p->d_lvl_ctr + base[l - 1] : nullptr;
+        unsigned* out = l + 1 < L ? p->d_lvl_ctr + base[l] : nullptr;
+        const int rc = forward_level(p, ip, l, in, coef, workspace, s, lls[l], dep,
+                                     l > 0 ? lls[l - 1].dc.n_strips : 0, l > 0 ? lls[l - 1].dc.seg_rows : 1, out);
+        if (rc != DWT2_OK) return rc;
+        prof_mark(p, l, false, s);
+    }
+    if (p->prof_on) ++p->prof_calls;
+    return DWT2_OK;
 }
 
 // Levels l and l+1 in one launch need a level-l input of at least 64 x 64
@@ -743,6 +799,9 @@ int dwt2_plan(dwt2_plan_t* out, int wavelet, int levels, int boundary, int in_dt
     p->timeout_ns = uint64_t(env_int("DWT2_TIMEOUT_MS", 2000)) * 1000000ull;
     p->seg_env = env_int("DWT2_SEG_ROWS", 0);
     p->pdl = env_int("DWT2_PDL", 1) != 0;
+    p->overlap = env_int("DWT2_LEVEL_OVERLAP", 1) != 0;
+    p->d_lvl_ctr = nullptr;
+    p->n_lvl_ctr = 0;
     p->lvl_cand.assign(levels, -1);
     p->fuse_seg = std::max(0, env_int("DWT2_FUSE_SEG", 0));
     p->fuse_pairs = std::max(0, env_int("DWT2_FUSE_PAIRS", 1));
@@ -783,6 +842,17 @@ int dwt2_plan(dwt2_plan_t* out, int wavelet, int levels, int boundary, int in_dt
             return rc;
         }
     }
+    if (n_images == 1 && !p->persistent && levels > 1) {
+        // at most one segment per quad row and level
+        size_t n = 0;
+        for (int l = 0; l + 1 < levels; ++l) n += size_t(p->imgs[0].lv[l].hq);
+        if (cudaMalloc(&p->d_lvl_ctr, n * sizeof(unsigned)) != cudaSuccess) {
+            cudaGetLastError();
+            dwt2_destroy(p);
+            return DWT2_ERR_CUDA;
+        }
+        p->n_lvl_ctr = n;
+    }
     if (n_images > 1) {
         int rc = build_inverse_batch(p);
         // several images, lifting schemes: one level-major launch per level
@@ -811,6 +881,7 @@ void dwt2_destroy(dwt2_plan_t p) {
     if (p->d_inv_units) cudaFree(p->d_inv_units);
     if (p->d_fb_descs) cudaFree(p->d_fb_descs);
     if (p->d_fb_units) cudaFree(p->d_fb_units);
+    if (p->d_lvl_ctr) cudaFree(p->d_lvl_ctr);
     for (cudaEvent_t e : p->ev0) cudaEventDestroy(e);
     for (cudaEvent_t e : p->ev1) cudaEventDestroy(e);
     delete p;
@@ -872,13 +943,15 @@ int dwt2_forward(dwt2_plan_t p, const void* in, void* coef, void* workspace, voi
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (p->persistent) return forward_persistent(p, in, coef, workspace, s);
     if (p->d_fb_units) return forward_batch(p, in, coef, workspace, s);
+    if (p->d_lvl_ctr && p->overlap && p->fuse_seg == 0 && !p->balanced_env)
+        return forward_overlapped(p, in, coef, workspace, s);
     for (int l = 0; l < p->levels;) {
         bool fuse = p->fuse_seg > 0 && l / 2 < p->fuse_pairs && l % 2 == 0 && l + 1 < p->levels && p->fused_bps > 0;
         for (const ImagePlan& ip : p->imgs) fuse = fuse && fused_eligible(ip.lv[l]);
         prof_mark(p, l, true, s);
         for (const ImagePlan& ip : p->imgs) {
             const int rc = fuse ? forward_fused(p, ip, l, in, coef, workspace, s)
-                                : forward_level(p, ip, l, in, coef, workspace, s);
+                                : forward_level(p, ip, l, in, coef, workspace, s, level_launch(p, ip, l));
             if (rc != DWT2_OK) return rc;
         }
         prof_mark(p, l, false, s);
@@ -1005,6 +1078,32 @@ static int tune_apply(dwt2_plan_t p, int choice) {
     return DWT2_OK;
 }
 
+// Mean time of one whole forward call: the smallest of three means of eight
+// calls, timed with one event pair around each group (no per-level events).
+static int time_whole_call(dwt2_plan_t p, const void* in, void* coef, void* workspace, void* stream, float* ms) {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        cudaGetLastError();
+        return DWT2_ERR_CUDA;
+    }
+    int rc = DWT2_OK;
+    for (int i = 0; i < 2 && rc == DWT2_OK; ++i) rc = dwt2_forward(p, in, coef, workspace, stream);
+    for (int r = 0; r < 3 && rc == DWT2_OK; ++r) {
+        cudaEventRecord(e0, s);
+        for (int i = 0; i < 8 && rc == DWT2_OK; ++i) rc = dwt2_forward(p, in, coef, workspace, stream);
+        cudaEventRecord(e1, s);
+        float t = 0.f;
+        if (rc == DWT2_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess))
+            rc = DWT2_ERR_CUDA;
+        if (rc == DWT2_OK) *ms = (r == 0) ? t / 8 : std::min(*ms, t / 8);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
+}
+
 int dwt2_autotune(dwt2_plan_t p, const void* in, void* coef, void* workspace, void* stream, int* choice) {
     if (!p || !choice) return DWT2_ERR_INVALID_ARG;
     if (*choice >= 0) return tune_apply(p, *choice);
@@ -1012,6 +1111,10 @@ int dwt2_autotune(dwt2_plan_t p, const void* in, void* coef, void* workspace, vo
     int rc = DWT2_OK;
     const int L = p->levels;
     const bool seg_only = tune_seg_only(p);
+    // candidates are timed level by level with every level waiting for its
+    // predecessor's grid (per-level events would misattribute overlapped levels)
+    const int overlap = p->overlap;
+    p->overlap = 0;
     const int n_cand = seg_only ? N_TUNE_PML : N_LVL_CANDS;
     std::vector<float> ms(size_t(n_cand) * L, 0.f);
     for (int c = 0; c < n_cand && rc == DWT2_OK; ++c) {
@@ -1034,6 +1137,7 @@ int dwt2_autotune(dwt2_plan_t p, const void* in, void* coef, void* workspace, vo
     }
     p->prof_on = prof;
     p->prof_calls = 0;
+    p->overlap = overlap;
     if (rc != DWT2_OK) return rc;
     int best = 0;
     if (seg_only) {
@@ -1057,6 +1161,37 @@ int dwt2_autotune(dwt2_plan_t p, const void* in, void* coef, void* workspace, vo
                 if (c == 0 || t < bt) bc = c, bt = t;
             }
             best |= bc << (f * TUNE_BITS);
+        }
+        if (overlap && p->d_lvl_ctr) {
+            // With inter-level overlap the fastest pyramid need not be made of
+            // the fastest levels: time the per-level choice, the default, the
+            // per-level choice on the first levels only and the best uniform
+            // candidates end to end, overlap on.
+            std::vector<int> cands = {best, 0};
+            // the per-level choice for the first k fields, the default after them
+            for (int k = 1; k < nf; ++k) cands.push_back(best & ((1 << (k * TUNE_BITS)) - 1));
+            std::vector<std::pair<float, int>> tot;
+            for (int c = 0; c < n_cand; ++c) {
+                float t = 0.f;
+                for (int l = 0; l < L; ++l) t += ms[size_t(c) * L + l];
+                tot.push_back({t, c});
+            }
+            std::sort(tot.begin(), tot.end());
+            for (int k = 0; k < 3 && k < int(tot.size()); ++k) {
+                int u = 0;
+                for (int f = 0; f < nf; ++f) u |= tot[k].second << (f * TUNE_BITS);
+                cands.push_back(u);
+            }
+            float best_ms = 0.f;
+            int best_c = best;
+            for (size_t k = 0; k < cands.size() && rc == DWT2_OK; ++k) {
+                rc = tune_apply(p, cands[k]);
+                float t = 0.f;
+                if (rc == DWT2_OK) rc = time_whole_call(p, in, coef, workspace, stream, &t);
+                if (rc == DWT2_OK && (k == 0 || t < best_ms)) best_ms = t, best_c = cands[k];
+            }
+            if (rc != DWT2_OK) return rc;
+            best = best_c;
         }
     }
     *choice = best;

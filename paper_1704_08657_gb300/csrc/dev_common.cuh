@@ -101,6 +101,12 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, in
         : "memory");
 }
 
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
 // Programmatic dependent launch: wait until the grids this one depends on
 // have completed and their writes are visible (returns at once when the
 // launch had no programmatic dependency), and let the next grid in the stream

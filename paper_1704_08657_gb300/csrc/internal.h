@@ -35,6 +35,20 @@ struct FwdParams {
     int pdl;                   // host side: launch as a programmatic dependent of the previous kernel
 };
 
+// Overlap with the previous level (single-image plans): instead of waiting
+// for the previous grid, a unit waits (bounded) until the previous level's
+// segments covering its input rows are complete, and every unit bumps its own
+// segment's counter after its stores.  A kernel parameter of its own: growing
+// FwdParams from 120 to 152 bytes made forward launches lose or misplace the
+// stores of whole units on this toolchain (deterministic per build, gone when
+// debug prints were added; not explained), so FwdParams keeps its size.
+struct FwdSync {
+    const unsigned* dep_ctr;  // previous level's segment counters (null: wait for the previous grid)
+    int dep_need, dep_seg;    // strips of a previous-level segment; its height in input rows
+    unsigned* out_ctr;        // this level's segment counters (null: none)
+    int test_drop;            // test hook: unit (strip 0, segment 0) never bumps its counter
+};
+
 // One inverse or adjoint level: bands in, pixels (compute type) out.
 struct InvParams {
     int h, w;
@@ -170,13 +184,13 @@ inline int fwd_strip_px(const FwdCfg& c) { return 64 * c.ql; }
 // kernel launchers, one translation unit per coefficient type; they return a
 // cudaError_t value
 int launch_forward_f32(int wav, int scheme, const CUtensorMap& box, const CUtensorMap& row, const FwdParams& p,
-                       int grid, const FwdCfg& cfg, cudaStream_t s);
+                       int grid, const FwdCfg& cfg, cudaStream_t s, const FwdSync& y);
 int launch_forward_f16(int wav, int scheme, const CUtensorMap& box, const CUtensorMap& row, const FwdParams& p,
-                       int grid, const FwdCfg& cfg, cudaStream_t s);
+                       int grid, const FwdCfg& cfg, cudaStream_t s, const FwdSync& y);
 int launch_forward_bf16(int wav, int scheme, const CUtensorMap& box, const CUtensorMap& row, const FwdParams& p,
-                        int grid, const FwdCfg& cfg, cudaStream_t s);
+                        int grid, const FwdCfg& cfg, cudaStream_t s, const FwdSync& y);
 int launch_forward_i32(int wav, int scheme, const CUtensorMap& box, const CUtensorMap& row, const FwdParams& p,
-                       int grid, const FwdCfg& cfg, cudaStream_t s);
+                       int grid, const FwdCfg& cfg, cudaStream_t s, const FwdSync& y);
 
 int launch_inverse_f32(int wav, int scheme, const InvParams& p, int grid, cudaStream_t s);
 int launch_inverse_f16(int wav, int scheme, const InvParams& p, int grid, cudaStream_t s);

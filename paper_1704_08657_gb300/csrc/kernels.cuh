@@ -343,12 +343,51 @@ __device__ __forceinline__ void stage_ring(unsigned char* smem, int warp, CT*& b
     bars = reinterpret_cast<uint64_t*>(smem + size_t(NW) * NST * STAGE_ELEMS * 4) + warp * NST;
 }
 
+// Inter-level overlap.  A unit of quad rows [R0, R1) streams input rows
+// 2*R0-4 .. 2*(R1+LAG+QR-2)+1 (warm-up, pipeline lag, stage rounding), folded
+// into [0, h) by the symmetric extension; lane 0 waits (bounded) until every
+// previous-level segment holding such a row has all its strips complete, then
+// orders its later TMA reads after what it observed.
+template <int LAG, int QR>
+__device__ __forceinline__ bool fwd_wait_inputs(const FwdParams& p, const FwdSync& y, int R0, int R1, int lane) {
+    bool ok = true;
+    if (lane == 0) {
+        int lo = max(0, 2 * R0 - 4);
+        const int end = 2 * (R1 + LAG + QR - 2) + 2;  // one past the last streamed row
+        const int hi = min(p.h, end);
+        if (end > p.h) lo = max(0, min(lo, 2 * p.h - 1 - end));  // mirrored rows past the bottom
+        for (int g = lo / y.dep_seg; g <= (hi - 1) / y.dep_seg && ok; ++g) {
+            const unsigned* c = y.dep_ctr + g;
+            if (ld_acquire(c) >= unsigned(y.dep_need)) continue;
+            const uint64_t t0 = globaltimer_ns();
+            while (ld_acquire(c) < unsigned(y.dep_need)) {
+                if (globaltimer_ns() - t0 > p.timeout_ns) {
+                    ok = false;
+                    break;
+                }
+                __nanosleep(128);
+            }
+        }
+        if (!ok && p.status) atomicOr(p.status, DEV_TIMEOUT);
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+    }
+    return __shfl_sync(FULL, ok ? 1 : 0, 0) != 0;
+}
+
+// after a unit's stores: count the unit in its segment with a release
+// reduction (the warp barrier orders every lane's stores before lane 0's
+// release); the consumer acquires the count and fences its async proxy
+__device__ __forceinline__ void fwd_signal(unsigned* ctr, int lane) {
+    __syncwarp();
+    if (lane == 0) asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(ctr) : "memory");
+}
+
 // One pyramid level, TMA-fed: the warps take their units from Pieces.  SPEC
 // compiles the specialised row loops for interior strips as well.
 template <class Pipe, class OutT, int QL, int QR, int NST, int NW, bool SPEC>
 __global__ void __launch_bounds__(NW * 32)
     fwd_tma_kernel(const __grid_constant__ CUtensorMap tm_box, const __grid_constant__ CUtensorMap tm_row,
-                   const FwdParams p) {
+                   const FwdParams p, const FwdSync y) {
     using CT = typename Pipe::CT;
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -364,14 +403,16 @@ __global__ void __launch_bounds__(NW * 32)
     }
     __syncwarp();
     // the input (the previous level's low-low band) and the outputs are only
-    // touched after the previous grid in the stream has completed
-    griddep_wait();
+    // touched after the previous grid in the stream has completed, or, with
+    // inter-level overlap, after the segments a unit reads are complete
+    if (y.dep_ctr == nullptr) griddep_wait();
     griddep_launch_dependents();
     const TmaLoader ld{&tm_box, &tm_row};
     uint32_t gstage = 0;
     Pieces<FwdParams> pieces(p, blockIdx.x * NW + warp, gridDim.x * NW);
     int s, R0, R1;
     while (pieces.next(p, s, R0, R1)) {
+        if (y.dep_ctr != nullptr && !fwd_wait_inputs<Pipe::LAG, QR>(p, y, R0, R1, lane)) return;
         bool ok;
         if constexpr (SPEC) {
             if (fwd_interior(p, s * (2 * (32 * QL - 2 * HALO_Q)) - 2 * HALO_Q, QL))
@@ -383,6 +424,7 @@ __global__ void __launch_bounds__(NW * 32)
             ok = fwd_unit<Pipe, OutT, QL, QR, NST, 0>(p, ld, s, R0, R1, bufs, bars, gstage, lane);
         }
         if (!ok) return;
+        if (y.out_ctr != nullptr && !(y.test_drop && s == 0 && R0 == 0)) fwd_signal(y.out_ctr + R0 / p.seg_rows, lane);
     }
 }
 
@@ -394,11 +436,6 @@ __global__ void __launch_bounds__(NW * 32)
 // its own segment.  The queue order puts every unit about one GPU round behind
 // the segments it depends on, so waits are rare and the low-low band it reads
 // was written moments before (usually still in L2).
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
 
 // the geometry and outputs of one unit's level, with the field names fwd_unit uses
 struct PmlView {

@@ -16,6 +16,7 @@
 // without ordering) race on the array.
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <string.h>
 
 #include <algorithm>
 #include <mutex>
@@ -167,6 +168,7 @@ extern "C" int dwt2_forward_noalloc(int wavelet, int levels, int scheme, int coe
         if (rc == DWT2_OK) rc = noalloc_map(&row, src, W, H, src_pitch, fwd_strip_px(cfg), 1, is_int);
         if (rc != DWT2_OK) return rc;
         FwdParams fp;
+        memset(&fp, 0, sizeof(fp));
         fp.h = H, fp.w = W, fp.hq = (H + 1) / 2, fp.wq = (W + 1) / 2, fp.hh = H / 2, fp.wh = W / 2;
         // segments of the height dwt2_forward chooses (rounds x (rows + 4) minimal)
         fp.n_strips = (fp.wq + fwd_out_quads(cfg) - 1) / fwd_out_quads(cfg);
@@ -207,10 +209,10 @@ extern "C" int dwt2_forward_noalloc(int wavelet, int levels, int scheme, int coe
         fp.timeout_ns = 2000000000ull;
         int e;
         switch (coef_dtype) {
-            case DWT2_F32: e = launch_forward_f32(wavelet, scheme, box, row, fp, grid, cfg, s); break;
-            case DWT2_F16: e = launch_forward_f16(wavelet, scheme, box, row, fp, grid, cfg, s); break;
-            case DWT2_BF16: e = launch_forward_bf16(wavelet, scheme, box, row, fp, grid, cfg, s); break;
-            default: e = launch_forward_i32(wavelet, scheme, box, row, fp, grid, cfg, s); break;
+            case DWT2_F32: e = launch_forward_f32(wavelet, scheme, box, row, fp, grid, cfg, s, FwdSync{nullptr, 0, 1, nullptr, 0}); break;
+            case DWT2_F16: e = launch_forward_f16(wavelet, scheme, box, row, fp, grid, cfg, s, FwdSync{nullptr, 0, 1, nullptr, 0}); break;
+            case DWT2_BF16: e = launch_forward_bf16(wavelet, scheme, box, row, fp, grid, cfg, s, FwdSync{nullptr, 0, 1, nullptr, 0}); break;
+            default: e = launch_forward_i32(wavelet, scheme, box, row, fp, grid, cfg, s, FwdSync{nullptr, 0, 1, nullptr, 0}); break;
         }
         if (e != cudaSuccess) return DWT2_ERR_CUDA;
     }

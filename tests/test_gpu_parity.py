@@ -174,3 +174,21 @@ def test_plan_errors_on_gpu():
     rc = abi.raw_call("dwt2_forward", p.handle, x.data_ptr() + 4, torch.empty(64 * 64, device="cuda").data_ptr(),
                       p.workspace.data_ptr(), 0)
     assert rc == abi.DWT2_ERR_MISALIGNED
+
+
+@pytest.mark.parametrize("n,levels", [(128, 1), (256, 1), (384, 1), (512, 1), (2048, 4), (2048, 5)])
+@pytest.mark.parametrize("cfg", ["0", "1", "2", "3"])
+def test_unpadded_pitch_every_configuration(n, levels, cfg, monkeypatch):
+    """pitch == width, every compiled kernel configuration: every coefficient
+    is written (the output starts as NaN) and matches the oracle."""
+    monkeypatch.setenv("DWT2_FWD_CFG", cfg)
+    x = synth.gradient(n, n, seed=3)
+    xd = torch.from_numpy(x).cuda()
+    plan = Plan.single(n, n, levels, scheme="reduced")
+    out = torch.full_like(xd, float("nan"))
+    plan.forward(xd, out)
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    got = out.cpu().numpy()
+    assert not np.isnan(got).any(), f"{int(np.isnan(got).sum())} coefficients left unwritten"
+    assert_fp32_close(got, oracle.forward97(x.astype(np.float64), levels), levels, 255.0, f"{n} L{levels} cfg {cfg}")
