@@ -195,6 +195,31 @@ def gpu_selector(dev, local: int) -> str:
     return vis.split(",")[local] if vis else str(local)
 
 
+def max_over_ranks(v: float, pg, dev=None) -> float:
+    """The largest of every rank's v (the job ends with its slowest rank);
+    pg is torch.distributed (any backend) or None for one process."""
+    if pg is None:
+        return float(v)
+    import torch
+    t = torch.tensor([float(v)], dtype=torch.float64, device=dev)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(side: int, world: int, ms_step: float) -> float:
+    """Whole-job Gpixel/s: every rank transforms its own side x side image per
+    step, and a step lasts ms_step (the maximum over ranks)."""
+    return side * side * world / (ms_step * 1e-3) / 1e9
+
+
+def emit(line: dict, rank: int) -> bool:
+    """Rank 0 prints the job's one JSON line; the other ranks print nothing."""
+    if rank != 0:
+        return False
+    print(json.dumps(line), flush=True)
+    return True
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -365,13 +390,10 @@ def run_ours(a):
     clocks = sampler.summary(t_soak, time.time())
     assert plan.status() == 0, "device status word set during the bench"
 
-    if pg is not None:
-        t = torch.tensor([ms_total], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(ms_total, pg, dev)
     ms_step = ms_total / a.steps
     px = n * n * world
-    value = px / (ms_step * 1e-3) / 1e9
+    value = replica_value(n, world, ms_step)
 
     # roofline of the level-1 kernel: 4 B read + 4 B written per pixel
     peak, peak_kind = measured_peaks()
@@ -438,10 +460,7 @@ def run_ours(a):
         ee1.record(stream)
         barrier()
         e2e_ms = ee0.elapsed_time(ee1) / a.e2e_steps
-        if pg is not None:
-            t = torch.tensor([e2e_ms], device=dev)
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            e2e_ms = float(t.item())
+        e2e_ms = max_over_ranks(e2e_ms, pg, dev)
         ok = bool(torch.equal(hout[(a.e2e_steps - 1) % 2], coef.cpu()))
         line["e2e"] = {"value": px / (e2e_ms * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": 4 * n * n,
                        "d2h_bytes_per_step": 4 * n * n, "steps": a.e2e_steps, "ms_per_step": e2e_ms,
@@ -515,8 +534,7 @@ def run_ours(a):
         line["cpu_baseline"] = {"value": per_s / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
                                 "sample": f"oracle (C, FP64 separable lifting, OpenMP) on a 4096x4096 image "
                                           f"of the same recipe, {a.levels} levels, {runs} runs in {secs:.1f} s"}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    emit(line, rank)
     if pg is not None:
         pg.barrier()
         pg.destroy_process_group()
