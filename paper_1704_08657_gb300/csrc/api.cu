@@ -166,12 +166,19 @@ struct dwt2_plan_s {
     bool persistent;
     int pml_bps, pml_seg, pml_force_cpasync, pml_lag_pct;
     std::vector<PmlDesc> h_descs;  // host copy (TMA maps are encoded per call from it)
-    // level-major batched forward (several images, not persistent): per
-    // (image, level) descriptors and the units of each level
-    int fb_seg;
-    PmlDesc* d_fb_descs;
-    PmlUnit* d_fb_units;
-    std::vector<int> fb_level_start;  // units of level l: [start[l], start[l+1])
+    // grouped forward (several images, not persistent): the launch blocks of
+    // every level (up to GROUP_MAX images each), built for one set of buffers
+    // and one configuration and reused while those stay the same
+    struct GroupCache {
+        const void* in = nullptr;
+        void* coef = nullptr;
+        void* ws = nullptr;
+        std::vector<int> cand;
+        int cfg_env = -1, seg_env = -1, pdl = -1;
+        std::vector<std::unique_ptr<GroupLaunch>> blocks;
+        std::vector<int> level, grid, ci;  // per block
+    } gcache;
+    bool grouped;
     // batched inverse / adjoint (several images): descriptors, units by level
     InvDesc* d_inv_descs;
     InvUnit* d_inv_units;
@@ -306,73 +313,6 @@ int build_persistent(dwt2_plan_t p) {
     return DWT2_OK;
 }
 
-// Descriptor of one (image, level) of the batched forward kernels.
-PmlDesc pml_desc(dwt2_plan_t p, const ImagePlan& ip, int l, int seg) {
-    const LevelGeom& g = ip.lv[l];
-    const size_t csz = dtype_size(p->coef_dtype);
-    PmlDesc d;
-    memset(&d, 0, sizeof(d));
-    d.h = g.h, d.w = g.w, d.hq = g.hq, d.wq = g.wq, d.hh = g.hh, d.wh = g.wh;
-    const int outq = fwd_out_quads(FwdCfg{PML_QL, PML_QR, PML_NST, PML_NW, 0});
-    d.n_strips = (g.wq + outq - 1) / outq;
-    d.seg_rows = std::min(seg, g.hq);
-    d.src_is_ws = l > 0;
-    d.src_off = (l == 0) ? ip.d.offset_elems : int64_t(ip.ws_off[l - 1] / 4);
-    d.src_pitch = (l == 0) ? ip.d.pitch_elems : round4(ip.lv[l - 1].wq);
-    d.coef_off = ip.d.offset_elems;
-    d.coef_pitch = ip.d.pitch_elems;
-    const bool last = (l == p->levels - 1);
-    d.ll_is_ct = !last;
-    d.ll_off = last ? ip.d.offset_elems : int64_t(ip.ws_off[l] / 4);
-    d.ll_pitch = last ? ip.d.pitch_elems : round4(g.wq);
-    const bool cvec = (ip.d.pitch_elems % 2 == 0) && ((ip.d.offset_elems * csz) % (2 * csz) == 0);
-    d.vec_lo = cvec;
-    d.vec_hi = cvec && (g.wq % 2 == 0);
-    d.vec_ll = last ? cvec : 1;
-    d.dep_base = -1;
-    return d;
-}
-
-// Tables of the level-major batched forward: every level's units of every
-// image in (image, segment, strip) order, one launch per level.
-constexpr int FB_SEG_DEFAULT = 32;
-
-int build_forward_batch(dwt2_plan_t p) {
-    const int L = p->levels;
-    std::vector<PmlDesc> descs;
-    std::vector<std::vector<PmlUnit>> by_level(L);
-    for (size_t i = 0; i < p->imgs.size(); ++i) {
-        for (int l = 0; l < L; ++l) {
-            const PmlDesc d = pml_desc(p, p->imgs[i], l, p->fb_seg);
-            const int di = int(descs.size());
-            descs.push_back(d);
-            const int n_segs = (d.hq + d.seg_rows - 1) / d.seg_rows;
-            for (int g = 0; g < n_segs; ++g)
-                for (int st = 0; st < d.n_strips; ++st) by_level[l].push_back(PmlUnit{di, st, g, 0, -1});
-        }
-    }
-    std::vector<PmlUnit> units;
-    p->fb_level_start.assign(1, 0);
-    for (int l = 0; l < L; ++l) {
-        units.insert(units.end(), by_level[l].begin(), by_level[l].end());
-        p->fb_level_start.push_back(int(units.size()));
-    }
-    if (p->d_fb_descs) cudaFree(p->d_fb_descs);
-    if (p->d_fb_units) cudaFree(p->d_fb_units);
-    p->d_fb_descs = nullptr;
-    p->d_fb_units = nullptr;
-    if (cudaMalloc(&p->d_fb_descs, descs.size() * sizeof(PmlDesc)) != cudaSuccess ||
-        cudaMalloc(&p->d_fb_units, std::max<size_t>(1, units.size()) * sizeof(PmlUnit)) != cudaSuccess ||
-        cudaMemcpy(p->d_fb_descs, descs.data(), descs.size() * sizeof(PmlDesc), cudaMemcpyHostToDevice) !=
-            cudaSuccess ||
-        cudaMemcpy(p->d_fb_units, units.data(), units.size() * sizeof(PmlUnit), cudaMemcpyHostToDevice) !=
-            cudaSuccess) {
-        cudaGetLastError();
-        return DWT2_ERR_CUDA;
-    }
-    return DWT2_OK;
-}
-
 // Tables of the batched inverse / adjoint: per (image, level) a descriptor,
 // per level the units of every image (segments of INV_BATCH_SEG quad rows).
 constexpr int INV_BATCH_SEG = 32;
@@ -460,40 +400,6 @@ int inverse_batch(dwt2_plan_t p, const void* coef, void* out, void* workspace, c
         }
         if (e != cudaSuccess) return DWT2_ERR_CUDA;
         prof_mark(p, l, false, s);
-    }
-    if (p->prof_on) ++p->prof_calls;
-    return DWT2_OK;
-}
-
-int forward_batch(dwt2_plan_t p, const void* in, void* coef, void* workspace, cudaStream_t s) {
-    const size_t csz = dtype_size(p->coef_dtype);
-    std::unique_ptr<PmlLaunch> lp(new (std::nothrow) PmlLaunch());
-    if (!lp) return DWT2_ERR_INVALID_ARG;
-    PmlParams& pp = lp->base;
-    memset(&pp, 0, sizeof(pp));
-    pp.in = in;
-    pp.coef = coef;
-    pp.ws = workspace;
-    pp.descs = p->d_fb_descs;
-    pp.coef_vec = aligned(coef, 2 * csz);
-    pp.status = p->d_status;
-    pp.timeout_ns = p->timeout_ns;
-    pp.level_major = 1;
-    lp->use_tma = 0;
-    for (int l = 0; l < p->levels; ++l) {
-        pp.units = p->d_fb_units + p->fb_level_start[l];
-        pp.n_units = p->fb_level_start[l + 1] - p->fb_level_start[l];
-        const int grid = std::max(1, std::min((pp.n_units + PML_NW - 1) / PML_NW, p->sm_count * p->pml_bps * 4));
-        prof_mark(p, l, true, s);
-        int e;
-        switch (p->coef_dtype) {
-            case DWT2_F32: e = launch_pml_f32(p->wavelet, p->scheme, *lp, grid, s); break;
-            case DWT2_F16: e = launch_pml_f16(p->wavelet, p->scheme, *lp, grid, s); break;
-            case DWT2_BF16: e = launch_pml_bf16(p->wavelet, p->scheme, *lp, grid, s); break;
-            default: e = launch_pml_i32(p->wavelet, p->scheme, *lp, grid, s); break;
-        }
-        prof_mark(p, l, false, s);
-        if (e != cudaSuccess) return DWT2_ERR_CUDA;
     }
     if (p->prof_on) ++p->prof_calls;
     return DWT2_OK;
@@ -654,6 +560,102 @@ int forward_level(dwt2_plan_t p, const ImagePlan& ip, int l, const void* in, voi
         default: e = launch_forward_i32(p->wavelet, p->scheme, box, row, fp, ll.grid, cfg, s, y); break;
     }
     return e == cudaSuccess ? DWT2_OK : DWT2_ERR_CUDA;
+}
+
+// Segment height of a grouped level when the tuner left it automatic: the
+// units of many images fill the GPU, so no short segments are needed.
+constexpr int GROUP_SEG_DEFAULT = 24;
+
+// (Re)build the launch blocks of a grouped plan for these buffers.
+int group_build(dwt2_plan_t p, const void* in, void* coef, void* workspace) {
+    auto& gc = p->gcache;
+    gc.blocks.clear();
+    gc.level.clear();
+    gc.grid.clear();
+    gc.ci.clear();
+    const int n = int(p->imgs.size());
+    // groups are formed largest image first, so that the last launches of a
+    // level (whose tails nothing overlaps) hold the smallest units
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return int64_t(p->imgs[a].d.h) * p->imgs[a].d.w > int64_t(p->imgs[b].d.h) * p->imgs[b].d.w;
+    });
+    for (int l = 0; l < p->levels; ++l) {
+        int ci = p->cfg_env, seg = p->seg_env;
+        if (p->lvl_cand[l] >= 0) {
+            ci = p->lvl_cand[l] / N_TUNE_SEGS;
+            seg = TUNE_SEGS[p->lvl_cand[l] % N_TUNE_SEGS];
+        }
+        if (seg <= 0) seg = GROUP_SEG_DEFAULT;
+        const FwdCfg& cfg = FWD_CFGS[ci];
+        const int outq = fwd_out_quads(cfg);
+        for (int i0 = 0; i0 < n; i0 += GROUP_MAX) {
+            std::unique_ptr<GroupLaunch> g(new (std::nothrow) GroupLaunch());
+            if (!g) return DWT2_ERR_INVALID_ARG;
+            int units = 0;
+            for (int k = 0; k < GROUP_MAX && i0 + k < n; ++k) {
+                const ImagePlan& ip = p->imgs[order[i0 + k]];
+                const int rc = level_maps(p, ip, l, in, workspace, cfg.ql, cfg.qr, &g->maps[2 * k], &g->maps[2 * k + 1]);
+                if (rc != DWT2_OK) return rc;
+                FwdParams fp = level_outputs(p, ip, l, coef, workspace);
+                const LevelGeom& lg = ip.lv[l];
+                fp.n_strips = (lg.wq + outq - 1) / outq;
+                fp.seg_rows = std::min(seg, lg.hq);
+                fp.n_segs = (lg.hq + fp.seg_rows - 1) / fp.seg_rows;
+                fp.n_units = fp.n_segs * fp.n_strips;
+                fp.balanced = 0;
+                fp.pdl = p->pdl;
+                g->img[k].p = fp;
+                g->img[k].u_begin = units;
+                units += fp.n_units;
+                g->n_img = k + 1;
+            }
+            g->n_units = units;
+            g->wait_prev = (i0 == 0);
+            gc.grid.push_back((units + cfg.nw - 1) / cfg.nw);
+            gc.level.push_back(l);
+            gc.ci.push_back(ci);
+            gc.blocks.push_back(std::move(g));
+        }
+    }
+    gc.in = in, gc.coef = coef, gc.ws = workspace;
+    gc.cand = p->lvl_cand;
+    gc.cfg_env = p->cfg_env, gc.seg_env = p->seg_env, gc.pdl = p->pdl;
+    return DWT2_OK;
+}
+
+// Plans of several images: every level as launches of up to GROUP_MAX images
+// (programmatic dependents of one another), from the cached launch blocks.
+int forward_grouped(dwt2_plan_t p, const void* in, void* coef, void* workspace, cudaStream_t s) {
+    auto& gc = p->gcache;
+    if (gc.blocks.empty() || gc.in != in || gc.coef != coef || gc.ws != workspace || gc.cand != p->lvl_cand ||
+        gc.cfg_env != p->cfg_env || gc.seg_env != p->seg_env || gc.pdl != p->pdl) {
+        const int rc = group_build(p, in, coef, workspace);
+        if (rc != DWT2_OK) {
+            gc.blocks.clear();
+            return rc;
+        }
+    }
+    for (size_t b = 0; b < gc.blocks.size(); ++b) {
+        const int l = gc.level[b];
+        if (b == 0 || gc.level[b - 1] != l) prof_mark(p, l, true, s);
+        // the first launch of a level waits for every earlier launch (plain
+        // stream order); the others overlap the launch before them
+        const int pdl = gc.blocks[b]->wait_prev ? (l == 0 && p->pdl) : 1;
+        const FwdCfg& cfg = FWD_CFGS[gc.ci[b]];
+        int e;
+        switch (p->coef_dtype) {
+            case DWT2_F32: e = launch_group_f32(p->wavelet, p->scheme, *gc.blocks[b], gc.grid[b], cfg, pdl, s); break;
+            case DWT2_F16: e = launch_group_f16(p->wavelet, p->scheme, *gc.blocks[b], gc.grid[b], cfg, pdl, s); break;
+            case DWT2_BF16: e = launch_group_bf16(p->wavelet, p->scheme, *gc.blocks[b], gc.grid[b], cfg, pdl, s); break;
+            default: e = launch_group_i32(p->wavelet, p->scheme, *gc.blocks[b], gc.grid[b], cfg, pdl, s); break;
+        }
+        if (e != cudaSuccess) return DWT2_ERR_CUDA;
+        if (b + 1 == gc.blocks.size() || gc.level[b + 1] != l) prof_mark(p, l, false, s);
+    }
+    if (p->prof_on) ++p->prof_calls;
+    return DWT2_OK;
 }
 
 // Single-image pyramid with inter-level overlap: the segment counters of
@@ -832,9 +834,7 @@ int dwt2_plan(dwt2_plan_t* out, int wavelet, int levels, int boundary, int in_dt
     if (p->pml_seg < 4) p->pml_seg = PML_SEG_DEFAULT;
     p->d_inv_descs = nullptr;
     p->d_inv_units = nullptr;
-    p->fb_seg = FB_SEG_DEFAULT;
-    p->d_fb_descs = nullptr;
-    p->d_fb_units = nullptr;
+    p->grouped = false;
     if (p->persistent) {
         const int rc = build_persistent(p);
         if (rc != DWT2_OK) {
@@ -855,11 +855,8 @@ int dwt2_plan(dwt2_plan_t* out, int wavelet, int levels, int boundary, int in_dt
     }
     if (n_images > 1) {
         int rc = build_inverse_batch(p);
-        // several images, lifting schemes: one level-major launch per level
-        if (rc == DWT2_OK && !p->persistent && scheme <= DWT2_SEP_LIFTING) {
-            p->pml_bps = pml_blocks_per_sm(wavelet, scheme, coef_dtype);
-            rc = p->pml_bps > 0 ? build_forward_batch(p) : DWT2_ERR_CUDA;
-        }
+        // several images: grouped launches of the single-image row loop
+        p->grouped = !p->persistent;
         if (rc != DWT2_OK) {
             dwt2_destroy(p);
             return rc;
@@ -879,8 +876,6 @@ void dwt2_destroy(dwt2_plan_t p) {
     if (p->d_counters) cudaFree(p->d_counters);
     if (p->d_inv_descs) cudaFree(p->d_inv_descs);
     if (p->d_inv_units) cudaFree(p->d_inv_units);
-    if (p->d_fb_descs) cudaFree(p->d_fb_descs);
-    if (p->d_fb_units) cudaFree(p->d_fb_units);
     if (p->d_lvl_ctr) cudaFree(p->d_lvl_ctr);
     for (cudaEvent_t e : p->ev0) cudaEventDestroy(e);
     for (cudaEvent_t e : p->ev1) cudaEventDestroy(e);
@@ -942,7 +937,7 @@ int dwt2_forward(dwt2_plan_t p, const void* in, void* coef, void* workspace, voi
     if (!aligned(coef, csz)) return DWT2_ERR_MISALIGNED;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (p->persistent) return forward_persistent(p, in, coef, workspace, s);
-    if (p->d_fb_units) return forward_batch(p, in, coef, workspace, s);
+    if (p->grouped) return forward_grouped(p, in, coef, workspace, s);
     if (p->d_lvl_ctr && p->overlap && p->fuse_seg == 0 && !p->balanced_env)
         return forward_overlapped(p, in, coef, workspace, s);
     for (int l = 0; l < p->levels;) {
@@ -1056,19 +1051,15 @@ constexpr int N_TUNE_PML = int(sizeof(TUNE_PML_SEGS) / sizeof(TUNE_PML_SEGS[0]))
 
 static int tune_fields(dwt2_plan_t p) { return std::min(p->levels, TUNE_LEVELS); }
 
-// persistent and level-major batch plans tune one segment height for all levels
-static bool tune_seg_only(dwt2_plan_t p) { return p->persistent || p->d_fb_units != nullptr; }
+// persistent plans tune one segment height for all levels
+static bool tune_seg_only(dwt2_plan_t p) { return p->persistent; }
 
 static int tune_apply(dwt2_plan_t p, int choice) {
     if (choice < 0) return DWT2_ERR_INVALID_ARG;
     if (tune_seg_only(p)) {
         if (choice >= N_TUNE_PML) return DWT2_ERR_INVALID_ARG;
-        if (p->persistent) {
-            p->pml_seg = TUNE_PML_SEGS[choice];
-            return build_persistent(p);
-        }
-        p->fb_seg = TUNE_PML_SEGS[choice];
-        return build_forward_batch(p);
+        p->pml_seg = TUNE_PML_SEGS[choice];
+        return build_persistent(p);
     }
     const int nf = tune_fields(p);
     if (nf * TUNE_BITS < 31 && choice >= (1 << (nf * TUNE_BITS))) return DWT2_ERR_INVALID_ARG;

@@ -104,10 +104,6 @@ struct PmlParams {
     int test_drop_signal;  // test hook: queue entry 0 never signals completion
     unsigned* status;
     uint64_t timeout_ns;
-    // level-major batch: the units are one level's, taken in order by a static
-    // round-robin over the grid, with no queue, waits or counters (the previous
-    // level is complete: stream order)
-    int level_major;
 };
 
 // Batched inverse / adjoint: one launch per level for every image; offsets in
@@ -171,6 +167,23 @@ int launch_fused_i32(int wav, int scheme, const CUtensorMap& box, const CUtensor
                      int grid, cudaStream_t s);
 int fused_blocks_per_sm(int wav, int scheme, int coef_dtype);
 
+// Grouped forward (plans of several images): one launch runs one level of up
+// to GROUP_MAX images with the single-image kernel's row loop.  The images'
+// tensor maps and parameters are one __grid_constant__ kernel parameter (read
+// from the constant bank where used); unit u belongs to the image whose
+// [u_begin, u_begin + n_units) holds it.
+constexpr int GROUP_MAX = 80;
+struct GroupImg {
+    FwdParams p;
+    int u_begin;
+};
+struct GroupLaunch {
+    CUtensorMap maps[2 * GROUP_MAX];  // [2i] box, [2i+1] single row of image i
+    GroupImg img[GROUP_MAX];
+    int n_img, n_units;
+    int wait_prev;  // 1: the first launch of a level (its inputs come from earlier launches)
+};
+
 // forward launch configuration
 struct FwdCfg {
     int ql, qr, nst, nw;  // quads per lane, quad rows per stage, stages per warp, warps per block
@@ -191,6 +204,10 @@ int launch_forward_bf16(int wav, int scheme, const CUtensorMap& box, const CUten
                         int grid, const FwdCfg& cfg, cudaStream_t s, const FwdSync& y);
 int launch_forward_i32(int wav, int scheme, const CUtensorMap& box, const CUtensorMap& row, const FwdParams& p,
                        int grid, const FwdCfg& cfg, cudaStream_t s, const FwdSync& y);
+int launch_group_f32(int wav, int scheme, const GroupLaunch& g, int grid, const FwdCfg& cfg, int pdl, cudaStream_t s);
+int launch_group_f16(int wav, int scheme, const GroupLaunch& g, int grid, const FwdCfg& cfg, int pdl, cudaStream_t s);
+int launch_group_bf16(int wav, int scheme, const GroupLaunch& g, int grid, const FwdCfg& cfg, int pdl, cudaStream_t s);
+int launch_group_i32(int wav, int scheme, const GroupLaunch& g, int grid, const FwdCfg& cfg, int pdl, cudaStream_t s);
 
 int launch_inverse_f32(int wav, int scheme, const InvParams& p, int grid, cudaStream_t s);
 int launch_inverse_f16(int wav, int scheme, const InvParams& p, int grid, cudaStream_t s);

@@ -32,4 +32,8 @@ int occupancy_fused_f16(int wav, int scheme) {
     return launch_fused_t<__half>(wav, scheme, nullptr, nullptr, nullptr, 0, nullptr, true);
 }
 
+int launch_group_f16(int wav, int scheme, const GroupLaunch& g, int grid, const FwdCfg& cfg, int pdl, cudaStream_t s) {
+    return launch_group_t<__half>(wav, scheme, g, grid, cfg, pdl, s);
+}
+
 }  // namespace dwt2

@@ -32,6 +32,10 @@ int occupancy_fused_f32(int wav, int scheme) {
     return launch_fused_t<float>(wav, scheme, nullptr, nullptr, nullptr, 0, nullptr, true);
 }
 
+int launch_group_f32(int wav, int scheme, const GroupLaunch& g, int grid, const FwdCfg& cfg, int pdl, cudaStream_t s) {
+    return launch_group_t<float>(wav, scheme, g, grid, cfg, pdl, s);
+}
+
 }  // namespace dwt2
 
 namespace dwt2 {

@@ -32,4 +32,8 @@ int occupancy_fused_i32(int wav, int scheme) {
     return launch_fused_t<int>(wav, scheme, nullptr, nullptr, nullptr, 0, nullptr, true);
 }
 
+int launch_group_i32(int wav, int scheme, const GroupLaunch& g, int grid, const FwdCfg& cfg, int pdl, cudaStream_t s) {
+    return launch_group_t<int>(wav, scheme, g, grid, cfg, pdl, s);
+}
+
 }  // namespace dwt2

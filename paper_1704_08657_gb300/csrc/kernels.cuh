@@ -428,6 +428,61 @@ __global__ void __launch_bounds__(NW * 32)
     }
 }
 
+// One level of a group of images (GroupLaunch): the warps take units in order,
+// find their image by a binary search over the group's unit ranges, and run
+// the single-image row loop with that image's parameters and tensor maps.
+// Launches of one level touch disjoint images, so only the first launch of a
+// level waits for what came before it; the others start as soon as the
+// previous launch has placed all its blocks.
+template <class Pipe, class OutT, int QL, int QR, int NST, int NW, bool SPEC>
+__global__ void __launch_bounds__(NW * 32) fwd_group_kernel(const __grid_constant__ GroupLaunch L) {
+    using CT = typename Pipe::CT;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    CT* bufs;
+    uint64_t* bars;
+    stage_ring<CT, QL, QR, NST, NW>(smem, warp, bufs, bars);
+    if (lane == 0) {
+#pragma unroll
+        for (int i = 0; i < NST; ++i) mbar_init(&bars[i], TmaLoader::ARRIVALS);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    if (L.wait_prev) griddep_wait();
+    griddep_launch_dependents();
+    uint32_t gstage = 0;
+    const int stride = gridDim.x * NW;
+    for (int u = blockIdx.x * NW + warp; u < L.n_units; u += stride) {
+        int lo = 0, hi = L.n_img - 1;  // the last image whose u_begin <= u
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (L.img[mid].u_begin <= u) lo = mid;
+            else hi = mid - 1;
+        }
+        const FwdParams& p = L.img[lo].p;
+        const int lu = u - L.img[lo].u_begin;
+        const int s = lu % p.n_strips;
+        const int R0 = (lu / p.n_strips) * p.seg_rows;
+        const int R1 = min(R0 + p.seg_rows, p.hq);
+        const TmaLoader ld{&L.maps[2 * lo], &L.maps[2 * lo + 1]};
+        if (lane == 0) {
+            tma_prefetch_desc(ld.box);
+            tma_prefetch_desc(ld.row);
+        }
+        bool ok;
+        if constexpr (SPEC) {
+            if (fwd_interior(p, s * (2 * (32 * QL - 2 * HALO_Q)) - 2 * HALO_Q, QL))
+                ok = p.ll_is_ct ? fwd_unit<Pipe, OutT, QL, QR, NST, 1>(p, ld, s, R0, R1, bufs, bars, gstage, lane)
+                                : fwd_unit<Pipe, OutT, QL, QR, NST, 2>(p, ld, s, R0, R1, bufs, bars, gstage, lane);
+            else
+                ok = fwd_unit<Pipe, OutT, QL, QR, NST, 0>(p, ld, s, R0, R1, bufs, bars, gstage, lane);
+        } else {
+            ok = fwd_unit<Pipe, OutT, QL, QR, NST, 0>(p, ld, s, R0, R1, bufs, bars, gstage, lane);
+        }
+        if (!ok) return;
+    }
+}
+
 // ------------------------------------------------- persistent (batched) forward
 // All units of all images and levels of a plan in one launch.  Units are taken
 // from a device queue in the plan's order; a unit of level l first waits
@@ -465,20 +520,15 @@ __global__ void __launch_bounds__(NW * 32) pml_kernel(const __grid_constant__ Pm
         fence_mbar_init();
     }
     __syncwarp();
-    griddep_wait();  // level-major launches are programmatic dependents of the previous level
-    griddep_launch_dependents();
     uint32_t gstage = 0;
-    const int stride = gridDim.x * NW;
-    for (int it = blockIdx.x * NW + warp;; it += stride) {
-        int u = it;
-        if (!P.level_major) {
-            if (lane == 0) u = int(atomicAdd(P.queue, 1u));
-            u = __shfl_sync(FULL, u, 0);
-        }
+    for (;;) {
+        int u = 0;
+        if (lane == 0) u = int(atomicAdd(P.queue, 1u));
+        u = __shfl_sync(FULL, u, 0);
         if (u >= P.n_units) break;
         const PmlUnit un = P.units[u];
         const PmlDesc& d = P.descs[un.desc];
-        if (!P.level_major && d.dep_base >= 0) {
+        if (d.dep_base >= 0) {
             bool waited_ok = true;
             if (lane == 0) {
                 for (int g = un.dep_lo; g <= un.dep_hi; ++g) {
@@ -525,7 +575,6 @@ __global__ void __launch_bounds__(NW * 32) pml_kernel(const __grid_constant__ Pm
             ok = fwd_unit<Pipe, OutT, QL, QR, NST>(v, ld, un.s, R0, R1, bufs, bars, gstage, lane);
         }
         if (!ok) return;
-        if (P.level_major) continue;
         // this unit's stores must be visible to the TMA reads of later units
         if (TMA) asm volatile("fence.proxy.async.global;" ::: "memory");
         __syncwarp();

@@ -44,6 +44,59 @@ int launch_fwd_one(const CUtensorMap& box, const CUtensorMap& row, const FwdPara
 #define DWT2_FWD_CFG_LIST(X) X(0, 2, 3, 3, 4, 0) X(1, 2, 2, 4, 4, 0) X(2, 2, 2, 4, 8, 0) X(3, 2, 2, 4, 8, 1)
 
 template <class Pipe, class OutT, int QL, int QR, int NST, int NW, bool SPEC>
+int launch_group_one(const GroupLaunch& g, int grid, int pdl, cudaStream_t s) {
+    auto k = fwd_group_kernel<Pipe, OutT, QL, QR, NST, NW, SPEC>;
+    constexpr size_t smem = fwd_smem_bytes<QL, QR, NST, NW>();
+    if (smem > 48 * 1024) {
+        static bool done = false;
+        if (!done) {
+            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+            if (e != cudaSuccess) return e;
+            done = true;
+        }
+    }
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(grid);
+    lc.blockDim = dim3(NW * 32);
+    lc.dynamicSmemBytes = smem;
+    lc.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    lc.attrs = attr;
+    lc.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&lc, k, g);
+}
+
+template <template <int, int> class PipeT, int S, class OutT>
+int launch_group_cfgs(const GroupLaunch& g, int grid, const FwdCfg& c, int pdl, cudaStream_t s) {
+#define DWT2_X(I_, QL_, QR_, NST_, NW_, SP_)                                             \
+    if (c.ql == QL_ && c.qr == QR_ && c.nst == NST_ && c.nw == NW_ && c.spec == SP_) \
+        return launch_group_one<PipeT<S, QL_>, OutT, QL_, QR_, NST_, NW_, SP_ != 0>(g, grid, pdl, s);
+    DWT2_FWD_CFG_LIST(DWT2_X)
+#undef DWT2_X
+    return cudaErrorInvalidValue;
+}
+
+template <class OutT>
+int launch_group_t(int wav, int scheme, const GroupLaunch& g, int grid, const FwdCfg& c, int pdl, cudaStream_t s) {
+    if constexpr (std::is_same<OutT, int>::value) {
+        if (wav != WAV_CDF53I) return cudaErrorInvalidValue;
+        if (scheme == SCHEME_SEP) return launch_group_cfgs<Fwd53, SCHEME_SEP, int>(g, grid, c, pdl, s);
+        if (scheme == SCHEME_NONSEP) return launch_group_cfgs<Fwd53, SCHEME_NONSEP, int>(g, grid, c, pdl, s);
+        return cudaErrorInvalidValue;
+    } else {
+        if (wav != WAV_CDF97) return cudaErrorInvalidValue;
+        if (scheme == SCHEME_NONSEP) return launch_group_cfgs<Fwd97, SCHEME_NONSEP, OutT>(g, grid, c, pdl, s);
+        if (scheme == SCHEME_REDUCED) return launch_group_cfgs<Fwd97, SCHEME_REDUCED, OutT>(g, grid, c, pdl, s);
+        if (scheme == SCHEME_SEP) return launch_group_cfgs<Fwd97, SCHEME_SEP, OutT>(g, grid, c, pdl, s);
+        if (scheme == SCHEME_POLYCONV) return launch_group_cfgs<Fwd97S, SCHEME_POLYCONV, OutT>(g, grid, c, pdl, s);
+        if (scheme == SCHEME_CONV) return launch_group_cfgs<Fwd97S, SCHEME_CONV, OutT>(g, grid, c, pdl, s);
+        return cudaErrorInvalidValue;
+    }
+}
+
+template <class Pipe, class OutT, int QL, int QR, int NST, int NW, bool SPEC>
 int occupancy_fwd_one() {
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fwd_tma_kernel<Pipe, OutT, QL, QR, NST, NW, SPEC>, NW * 32,
@@ -136,24 +189,11 @@ template <class Pipe, class OutT>
 int launch_pml_one(const PmlLaunch& p, int grid, cudaStream_t s) {
     constexpr size_t smem = fwd_smem_bytes<PML_QL, PML_QR, PML_NST, PML_NW>();
     static_assert(smem <= 48 * 1024, "persistent kernel stages fit the default shared-memory limit");
-    auto k = p.use_tma ? pml_kernel<Pipe, OutT, PML_QL, PML_QR, PML_NST, PML_NW, true>
-                       : pml_kernel<Pipe, OutT, PML_QL, PML_QR, PML_NST, PML_NW, false>;
-    if (!p.base.level_major) {
-        k<<<grid, PML_NW * 32, smem, s>>>(p);
-        return cudaGetLastError();
-    }
-    // level-major batch levels: programmatic dependents of the previous level
-    cudaLaunchConfig_t lc = {};
-    lc.gridDim = dim3(grid);
-    lc.blockDim = dim3(PML_NW * 32);
-    lc.dynamicSmemBytes = smem;
-    lc.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    lc.attrs = attr;
-    lc.numAttrs = 1;
-    return cudaLaunchKernelEx(&lc, k, p);
+    if (p.use_tma)
+        pml_kernel<Pipe, OutT, PML_QL, PML_QR, PML_NST, PML_NW, true><<<grid, PML_NW * 32, smem, s>>>(p);
+    else
+        pml_kernel<Pipe, OutT, PML_QL, PML_QR, PML_NST, PML_NW, false><<<grid, PML_NW * 32, smem, s>>>(p);
+    return cudaGetLastError();
 }
 
 template <class Pipe, class OutT>

@@ -176,14 +176,14 @@ def test_batch_inverse_adjoint_and_l1():
 @pytest.mark.parametrize("scheme,coef_dtype", [("reduced", torch.float32), ("sep", torch.float16),
                                                ("polyconv", torch.float32)])
 def test_level_major_batch_equals_single_image_plans(scheme, coef_dtype):
-    """A plan of several images makes one launch per level for all of them
-    (lifting schemes; the filter-bank schemes launch per image); every image
-    equals its own single-image plan bit for bit."""
+    """A plan of several images runs each level as grouped launches (up to 80
+    images per launch, every scheme); every image equals its own single-image
+    plan bit for bit, for the default and for tuned configurations."""
     shapes = synth.batch_shapes(40, seed=7)
     buf, descs = _batch(shapes, seed=8)
     xd = torch.from_numpy(buf).cuda()
     plan = Plan(descs, 3, scheme=scheme, coef_dtype=coef_dtype)
-    for choice in (-1, 0, 3):  # the automatic default, then two tuned segment heights
+    for choice in (-1, 0, 3 | (30 << 6) | (17 << 12)):  # the default, then per-level tuned configurations
         if choice >= 0:
             assert abi.dwt2_autotune(plan.handle, xd.data_ptr(), torch.empty_like(xd, dtype=coef_dtype).data_ptr(),
                                      plan.workspace.data_ptr(), 0, choice) == choice
@@ -216,3 +216,34 @@ def test_level_major_batch_int53():
     assert plan.status() == 0
     for g, x in zip(_unpack(c.cpu().numpy(), descs), _unpack(bi, descs)):
         assert np.array_equal(g.astype(np.int64), oracle.forward53i(x.astype(np.int64), 3))
+
+
+def test_grouped_batch_over_several_launches_and_graph():
+    """More images than one launch holds (80): the level's launches overlap,
+    the next level waits for all of them; the same under CUDA-graph capture."""
+    shapes = synth.batch_shapes(200, seed=13)
+    buf, descs = _batch(shapes, seed=14)
+    xd = torch.from_numpy(buf).cuda()
+    plan = Plan(descs, 3, scheme="reduced")
+    ref = plan.forward(xd, torch.zeros_like(xd))
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    got = _unpack(ref.cpu().numpy(), descs)
+    imgs = _unpack(buf, descs)
+    for i in range(0, 200, 9):
+        assert_fp32_close(got[i], oracle.forward97(imgs[i].astype(np.float64), 3), 3, 255.0, f"image {i}")
+    out = torch.zeros_like(xd)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        plan.forward(xd, out, stream=s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    out.zero_()
+    with torch.cuda.graph(g, stream=s):
+        plan.forward(xd, out, stream=s)
+    for _ in range(3):
+        out.zero_()
+        g.replay()
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    assert torch.equal(out, ref)
