@@ -179,10 +179,16 @@ struct dwt2_plan_s {
         std::vector<int> level, grid, ci;  // per block
     } gcache;
     bool grouped;
-    // batched inverse / adjoint (several images): descriptors, units by level
-    InvDesc* d_inv_descs;
-    InvUnit* d_inv_units;
-    std::vector<int> inv_level_start;  // units of level l: [start[l], start[l+1])
+    // grouped inverse / adjoint launch blocks (plans of several images), built
+    // for one set of buffers and reused while those stay the same
+    struct InvGroupCache {
+        const void* coef = nullptr;
+        void* out = nullptr;
+        void* ws = nullptr;
+        int adj = -1;
+        std::vector<std::unique_ptr<InvGroupLaunch>> blocks;
+        std::vector<int> level, grid;  // per block
+    } icache;
     PmlDesc* d_descs;
     PmlUnit* d_units;
     unsigned* d_counters;  // n_counters segment counters followed by the queue word
@@ -313,93 +319,126 @@ int build_persistent(dwt2_plan_t p) {
     return DWT2_OK;
 }
 
-// Tables of the batched inverse / adjoint: per (image, level) a descriptor,
-// per level the units of every image (segments of INV_BATCH_SEG quad rows).
-constexpr int INV_BATCH_SEG = 32;
+// The parameters of one image's inverse (or adjoint) level, without the
+// decomposition into units.
+InvParams inv_level_params(dwt2_plan_t p, const ImagePlan& ip, int l, const void* coef, void* out, void* workspace,
+                           size_t csz, bool l1, float l1_scale) {
+    const char* coef_img = static_cast<const char*>(coef) + ip.d.offset_elems * csz;
+    char* out_img = static_cast<char*>(out) + ip.d.offset_elems * 4;
+    char* wsb = static_cast<char*>(workspace);
+    const LevelGeom& g = ip.lv[l];
+    InvParams ipm;
+    memset(&ipm, 0, sizeof(ipm));
+    ipm.h = g.h, ipm.w = g.w, ipm.hq = g.hq, ipm.wq = g.wq, ipm.hh = g.hh, ipm.wh = g.wh;
+    ipm.coef = coef_img;
+    ipm.coef_pitch = ip.d.pitch_elems;
+    const bool coarsest = (l == p->levels - 1);
+    if (coarsest) {
+        ipm.ll = coef_img;
+        ipm.ll_pitch = ip.d.pitch_elems;
+        ipm.ll_is_ct = 0;
+    } else {
+        ipm.ll = wsb + ip.ws_off[l];
+        ipm.ll_pitch = round4(g.wq);
+        ipm.ll_is_ct = 1;
+    }
+    if (l == 0) {
+        ipm.out = out_img;
+        ipm.out_pitch = ip.d.pitch_elems;
+    } else {
+        ipm.out = wsb + ip.ws_off[l - 1];
+        ipm.out_pitch = round4(g.w);  // = round4(wq of level l-1)
+    }
+    const bool cvec = (ip.d.pitch_elems % 2 == 0) && aligned(coef_img, 2 * csz);
+    ipm.vec_in_lo = cvec;
+    ipm.vec_in_hi = cvec && (g.wq % 2 == 0);
+    ipm.vec_ll = coarsest ? cvec : 1;
+    ipm.vec_out = (ipm.out_pitch % 4 == 0) && aligned(ipm.out, 16);
+    ipm.status = p->d_status;
+    ipm.l1 = l1;
+    ipm.l1_scale = l1_scale;
+    return ipm;
+}
 
-int build_inverse_batch(dwt2_plan_t p) {
-    const int L = p->levels;
-    std::vector<InvDesc> descs;
-    std::vector<std::vector<InvUnit>> by_level(L);
-    for (size_t i = 0; i < p->imgs.size(); ++i) {
-        const ImagePlan& ip = p->imgs[i];
-        const int64_t off = ip.d.offset_elems, pitch = ip.d.pitch_elems;
-        const bool cvec = (pitch % 2 == 0);  // offsets are multiples of 4 elements
-        for (int l = 0; l < L; ++l) {
-            const LevelGeom& g = ip.lv[l];
-            InvDesc d;
-            d.h = g.h, d.w = g.w, d.hq = g.hq, d.wq = g.wq, d.hh = g.hh, d.wh = g.wh;
-            d.n_strips = (g.wq + INV_OUT_Q - 1) / INV_OUT_Q;
-            d.seg_rows = std::min(INV_BATCH_SEG, g.hq);
-            d.coef_off = off;
-            d.coef_pitch = pitch;
-            const bool coarsest = (l == L - 1);
-            d.ll_is_ct = !coarsest;
-            d.ll_off = coarsest ? off : int64_t(ip.ws_off[l] / 4);
-            d.ll_pitch = coarsest ? pitch : round4(g.wq);
-            d.out_is_ws = l > 0;
-            d.out_off = (l == 0) ? off : int64_t(ip.ws_off[l - 1] / 4);
-            d.out_pitch = (l == 0) ? pitch : round4(g.w);
-            d.vec_in_lo = cvec;
-            d.vec_in_hi = cvec && (g.wq % 2 == 0);
-            d.vec_ll = coarsest ? cvec : 1;
-            d.vec_out = (d.out_pitch % 4 == 0);
-            const int di = int(descs.size());
-            descs.push_back(d);
-            const int n_segs = (g.hq + d.seg_rows - 1) / d.seg_rows;
-            for (int gseg = 0; gseg < n_segs; ++gseg)
-                for (int s = 0; s < d.n_strips; ++s) by_level[l].push_back(InvUnit{di, s, gseg});
+// Plans of several images: every level, coarsest first, as launches of up to
+// INV_GROUP_MAX images in segments of INV_GROUP_SEG quad rows.
+constexpr int INV_GROUP_SEG = 32;
+
+int inv_group_build(dwt2_plan_t p, const void* coef, void* out, void* workspace, bool adj) {
+    auto& ic = p->icache;
+    ic.blocks.clear();
+    ic.level.clear();
+    ic.grid.clear();
+    const int n = int(p->imgs.size());
+    const size_t csz = adj ? 4 : dtype_size(p->coef_dtype);
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return int64_t(p->imgs[a].d.h) * p->imgs[a].d.w > int64_t(p->imgs[b].d.h) * p->imgs[b].d.w;
+    });
+    for (int l = p->levels - 1; l >= 0; --l) {
+        for (int i0 = 0; i0 < n; i0 += INV_GROUP_MAX) {
+            std::unique_ptr<InvGroupLaunch> g(new (std::nothrow) InvGroupLaunch());
+            if (!g) return DWT2_ERR_INVALID_ARG;
+            int units = 0;
+            for (int k = 0; k < INV_GROUP_MAX && i0 + k < n; ++k) {
+                const ImagePlan& ip = p->imgs[order[i0 + k]];
+                InvParams ipm = inv_level_params(p, ip, l, coef, out, workspace, csz, false, 0.f);
+                ipm.n_strips = (ipm.wq + INV_OUT_Q - 1) / INV_OUT_Q;
+                ipm.seg_rows = std::min(INV_GROUP_SEG, ipm.hq);
+                ipm.n_segs = (ipm.hq + ipm.seg_rows - 1) / ipm.seg_rows;
+                ipm.n_units = ipm.n_segs * ipm.n_strips;
+                g->img[k].p = ipm;
+                g->img[k].u_begin = units;
+                units += ipm.n_units;
+                g->n_img = k + 1;
+            }
+            g->n_units = units;
+            g->wait_prev = (i0 == 0);
+            ic.grid.push_back((units + INV_NW - 1) / INV_NW);
+            ic.level.push_back(l);
+            ic.blocks.push_back(std::move(g));
         }
     }
-    std::vector<InvUnit> units;
-    p->inv_level_start.assign(1, 0);
-    for (int l = 0; l < L; ++l) {
-        units.insert(units.end(), by_level[l].begin(), by_level[l].end());
-        p->inv_level_start.push_back(int(units.size()));
-    }
-    if (cudaMalloc(&p->d_inv_descs, descs.size() * sizeof(InvDesc)) != cudaSuccess ||
-        cudaMalloc(&p->d_inv_units, std::max<size_t>(1, units.size()) * sizeof(InvUnit)) != cudaSuccess ||
-        cudaMemcpy(p->d_inv_descs, descs.data(), descs.size() * sizeof(InvDesc), cudaMemcpyHostToDevice) !=
-            cudaSuccess ||
-        cudaMemcpy(p->d_inv_units, units.data(), units.size() * sizeof(InvUnit), cudaMemcpyHostToDevice) !=
-            cudaSuccess) {
-        cudaGetLastError();
-        return DWT2_ERR_CUDA;
-    }
+    ic.coef = coef, ic.out = out, ic.ws = workspace, ic.adj = adj;
     return DWT2_OK;
 }
 
-int inverse_batch(dwt2_plan_t p, const void* coef, void* out, void* workspace, cudaStream_t s, bool adj, bool l1,
-                  float l1_scale) {
-    const size_t csz = adj ? 4 : dtype_size(p->coef_dtype);
-    InvBatchParams b;
-    b.coef = coef;
-    b.out = out;
-    b.ws = workspace;
-    b.descs = p->d_inv_descs;
-    b.coef_vec = aligned(coef, 2 * csz);
-    b.out_vec = aligned(out, 16);
-    b.l1 = l1;
-    b.l1_scale = l1_scale;
-    b.status = p->d_status;
-    for (int l = p->levels - 1; l >= 0; --l) {
-        prof_mark(p, l, true, s);
-        b.units = p->d_inv_units + p->inv_level_start[l];
-        b.n_units = p->inv_level_start[l + 1] - p->inv_level_start[l];
-        const int grid = (b.n_units + INV_NW - 1) / INV_NW;
+int inverse_grouped(dwt2_plan_t p, const void* coef, void* out, void* workspace, cudaStream_t s, bool adj, bool l1,
+                    float l1_scale) {
+    auto& ic = p->icache;
+    if (ic.blocks.empty() || ic.coef != coef || ic.out != out || ic.ws != workspace || ic.adj != int(adj)) {
+        const int rc = inv_group_build(p, coef, out, workspace, adj);
+        if (rc != DWT2_OK) {
+            ic.blocks.clear();
+            return rc;
+        }
+    }
+    for (size_t b = 0; b < ic.blocks.size(); ++b) {
+        InvGroupLaunch& g = *ic.blocks[b];
+        for (int k = 0; k < g.n_img; ++k) {
+            g.img[k].p.l1 = l1;
+            g.img[k].p.l1_scale = l1_scale;
+        }
+        const int l = ic.level[b];
+        if (b == 0 || ic.level[b - 1] != l) prof_mark(p, l, true, s);
+        // the first launch of a level waits for every earlier launch (plain
+        // stream order); the others overlap the launch before them
+        const int pdl = g.wait_prev ? 0 : 1;
         int e;
         if (adj) {
-            e = launch_adj_batch_f32(b, grid, s);
+            e = launch_adj_group_f32(g, ic.grid[b], pdl, s);
         } else {
+            const int sc = inv_scheme(p->scheme);
             switch (p->coef_dtype) {
-                case DWT2_F32: e = launch_inv_batch_f32(p->wavelet, inv_scheme(p->scheme), b, grid, s); break;
-                case DWT2_F16: e = launch_inv_batch_f16(p->wavelet, inv_scheme(p->scheme), b, grid, s); break;
-                case DWT2_BF16: e = launch_inv_batch_bf16(p->wavelet, inv_scheme(p->scheme), b, grid, s); break;
-                default: e = launch_inv_batch_i32(p->wavelet, inv_scheme(p->scheme), b, grid, s); break;
+                case DWT2_F32: e = launch_inv_group_f32(p->wavelet, sc, g, ic.grid[b], pdl, s); break;
+                case DWT2_F16: e = launch_inv_group_f16(p->wavelet, sc, g, ic.grid[b], pdl, s); break;
+                case DWT2_BF16: e = launch_inv_group_bf16(p->wavelet, sc, g, ic.grid[b], pdl, s); break;
+                default: e = launch_inv_group_i32(p->wavelet, sc, g, ic.grid[b], pdl, s); break;
             }
         }
         if (e != cudaSuccess) return DWT2_ERR_CUDA;
-        prof_mark(p, l, false, s);
+        if (b + 1 == ic.blocks.size() || ic.level[b + 1] != l) prof_mark(p, l, false, s);
     }
     if (p->prof_on) ++p->prof_calls;
     return DWT2_OK;
@@ -832,8 +871,6 @@ int dwt2_plan(dwt2_plan_t* out, int wavelet, int levels, int boundary, int in_dt
     p->pml_force_cpasync = env_int("DWT2_PML_CPASYNC", 0);
     p->pml_lag_pct = env_int("DWT2_PML_LAG_PCT", 300);
     if (p->pml_seg < 4) p->pml_seg = PML_SEG_DEFAULT;
-    p->d_inv_descs = nullptr;
-    p->d_inv_units = nullptr;
     p->grouped = false;
     if (p->persistent) {
         const int rc = build_persistent(p);
@@ -853,15 +890,8 @@ int dwt2_plan(dwt2_plan_t* out, int wavelet, int levels, int boundary, int in_dt
         }
         p->n_lvl_ctr = n;
     }
-    if (n_images > 1) {
-        int rc = build_inverse_batch(p);
-        // several images: grouped launches of the single-image row loop
-        p->grouped = !p->persistent;
-        if (rc != DWT2_OK) {
-            dwt2_destroy(p);
-            return rc;
-        }
-    }
+    // several images: grouped launches of the single-image row loop
+    if (n_images > 1) p->grouped = !p->persistent;
     *out = p;
     return DWT2_OK;
 }
@@ -874,8 +904,6 @@ void dwt2_destroy(dwt2_plan_t p) {
     if (p->d_descs) cudaFree(p->d_descs);
     if (p->d_units) cudaFree(p->d_units);
     if (p->d_counters) cudaFree(p->d_counters);
-    if (p->d_inv_descs) cudaFree(p->d_inv_descs);
-    if (p->d_inv_units) cudaFree(p->d_inv_units);
     if (p->d_lvl_ctr) cudaFree(p->d_lvl_ctr);
     for (cudaEvent_t e : p->ev0) cudaEventDestroy(e);
     for (cudaEvent_t e : p->ev1) cudaEventDestroy(e);
@@ -972,51 +1000,17 @@ static int run_inverse_like(dwt2_plan_t p, const void* coef, void* out, void* wo
     const size_t csz = adj ? 4 : dtype_size(p->coef_dtype);
     if (!aligned(coef, csz) || !aligned(out, 4)) return DWT2_ERR_MISALIGNED;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (p->n_images > 1) return inverse_batch(p, coef, out, workspace, s, adj, l1, l1_scale);
+    if (p->n_images > 1) return inverse_grouped(p, coef, out, workspace, s, adj, l1, l1_scale);
     const int inv_bps = adj ? inverse_blocks_per_sm(p->wavelet, inv_scheme(p->scheme), p->coef_dtype, true) : p->inv_bps;
     for (int l = p->levels - 1; l >= 0; --l) {
         prof_mark(p, l, true, s);
         for (const ImagePlan& ip : p->imgs) {
-            const char* coef_img = static_cast<const char*>(coef) + ip.d.offset_elems * csz;
-            char* out_img = static_cast<char*>(out) + ip.d.offset_elems * 4;
-            char* wsb = static_cast<char*>(workspace);
-            const LevelGeom& g = ip.lv[l];
-            InvParams ipm;
-            ipm.h = g.h, ipm.w = g.w, ipm.hq = g.hq, ipm.wq = g.wq, ipm.hh = g.hh, ipm.wh = g.wh;
+            InvParams ipm = inv_level_params(p, ip, l, coef, out, workspace, csz, l1, l1_scale);
             int grid = 0, balanced = 0;
-            const Decomp dc =
-                decompose(g, INV_OUT_Q, p->sm_count, inv_bps, INV_NW, p->seg_env, p->balanced_env, &grid,
-                          &balanced);
+            const Decomp dc = decompose(ip.lv[l], INV_OUT_Q, p->sm_count, inv_bps, INV_NW, p->seg_env,
+                                        p->balanced_env, &grid, &balanced);
             ipm.n_strips = dc.n_strips, ipm.seg_rows = dc.seg_rows, ipm.n_segs = dc.n_segs, ipm.n_units = dc.n_units;
             ipm.balanced = balanced;
-            ipm.coef = coef_img;
-            ipm.coef_pitch = ip.d.pitch_elems;
-            const bool coarsest = (l == p->levels - 1);
-            if (coarsest) {
-                ipm.ll = coef_img;
-                ipm.ll_pitch = ip.d.pitch_elems;
-                ipm.ll_is_ct = 0;
-            } else {
-                ipm.ll = wsb + ip.ws_off[l];
-                ipm.ll_pitch = round4(g.wq);
-                ipm.ll_is_ct = 1;
-            }
-            if (l == 0) {
-                ipm.out = out_img;
-                ipm.out_pitch = ip.d.pitch_elems;
-            } else {
-                ipm.out = wsb + ip.ws_off[l - 1];
-                ipm.out_pitch = round4(g.w);  // = round4(wq of level l-1)
-            }
-            const size_t pair = 2 * csz;
-            const bool cvec = (ip.d.pitch_elems % 2 == 0) && aligned(coef_img, pair);
-            ipm.vec_in_lo = cvec;
-            ipm.vec_in_hi = cvec && (g.wq % 2 == 0);
-            ipm.vec_ll = coarsest ? cvec : 1;
-            ipm.vec_out = (ipm.out_pitch % 4 == 0) && aligned(ipm.out, 16);
-            ipm.status = p->d_status;
-            ipm.l1 = l1;
-            ipm.l1_scale = l1_scale;
             int e;
             if (adj) {
                 e = launch_adjoint_f32(ipm, grid, s);

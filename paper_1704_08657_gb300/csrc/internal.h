@@ -106,41 +106,25 @@ struct PmlParams {
     uint64_t timeout_ns;
 };
 
-// Batched inverse / adjoint: one launch per level for every image; offsets in
-// elements from the base pointers of InvBatchParams.
-struct InvDesc {
-    int h, w, hq, wq, hh, wh;
-    int n_strips, seg_rows;
-    int64_t coef_off, coef_pitch;  // coefficient elements (image origin)
-    int ll_is_ct;                  // LL from the workspace (compute type) or the coefficients
-    int64_t ll_off, ll_pitch;
-    int out_is_ws;                 // output to the workspace (a finer level's LL) or the images
-    int64_t out_off, out_pitch;    // compute-type elements
-    int vec_in_lo, vec_in_hi, vec_ll, vec_out;  // alignment for aligned base pointers
+// Grouped inverse / adjoint (plans of several images): one launch runs one
+// level of up to INV_GROUP_MAX images, their parameters in one
+// __grid_constant__ kernel parameter, as for the grouped forward.
+constexpr int INV_GROUP_MAX = 200;
+struct InvGroupImg {
+    InvParams p;
+    int u_begin;
+};
+struct InvGroupLaunch {
+    InvGroupImg img[INV_GROUP_MAX];
+    int n_img, n_units;
+    int wait_prev;  // 1: the first launch of a level
 };
 
-struct InvUnit {
-    int desc, s, g;
-};
-
-struct InvBatchParams {
-    const void* coef;
-    void* out;
-    void* ws;
-    const InvDesc* descs;
-    const InvUnit* units;  // this level's units
-    int n_units;
-    int coef_vec, out_vec;
-    int l1;
-    float l1_scale;
-    unsigned* status;
-};
-
-int launch_inv_batch_f32(int wav, int scheme, const InvBatchParams& p, int grid, cudaStream_t s);
-int launch_inv_batch_f16(int wav, int scheme, const InvBatchParams& p, int grid, cudaStream_t s);
-int launch_inv_batch_bf16(int wav, int scheme, const InvBatchParams& p, int grid, cudaStream_t s);
-int launch_inv_batch_i32(int wav, int scheme, const InvBatchParams& p, int grid, cudaStream_t s);
-int launch_adj_batch_f32(const InvBatchParams& p, int grid, cudaStream_t s);
+int launch_inv_group_f32(int wav, int scheme, const InvGroupLaunch& g, int grid, int pdl, cudaStream_t s);
+int launch_inv_group_f16(int wav, int scheme, const InvGroupLaunch& g, int grid, int pdl, cudaStream_t s);
+int launch_inv_group_bf16(int wav, int scheme, const InvGroupLaunch& g, int grid, int pdl, cudaStream_t s);
+int launch_inv_group_i32(int wav, int scheme, const InvGroupLaunch& g, int grid, int pdl, cudaStream_t s);
+int launch_adj_group_f32(const InvGroupLaunch& g, int grid, int pdl, cudaStream_t s);
 
 // Two forward levels in one launch (fused.cuh): level l comes through the
 // tensor maps, level l+1 reads the level-l low-low band from a ring of rows in

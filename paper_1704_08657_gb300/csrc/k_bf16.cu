@@ -12,8 +12,8 @@ int launch_inverse_bf16(int wav, int scheme, const InvParams& p, int grid, cudaS
     return launch_inverse_t<__nv_bfloat16>(wav, scheme, p, grid, s);
 }
 
-int launch_inv_batch_bf16(int wav, int scheme, const InvBatchParams& p, int grid, cudaStream_t s) {
-    return launch_inv_batch_t<__nv_bfloat16>(wav, scheme, p, grid, s);
+int launch_inv_group_bf16(int wav, int scheme, const InvGroupLaunch& g, int grid, int pdl, cudaStream_t s) {
+    return launch_inv_group_t<__nv_bfloat16>(wav, scheme, g, grid, pdl, s);
 }
 
 int occupancy_forward_bf16(int wav, int scheme, const FwdCfg& cfg) { return occupancy_forward_t<__nv_bfloat16>(wav, scheme, cfg); }

@@ -12,8 +12,8 @@ int launch_inverse_f16(int wav, int scheme, const InvParams& p, int grid, cudaSt
     return launch_inverse_t<__half>(wav, scheme, p, grid, s);
 }
 
-int launch_inv_batch_f16(int wav, int scheme, const InvBatchParams& p, int grid, cudaStream_t s) {
-    return launch_inv_batch_t<__half>(wav, scheme, p, grid, s);
+int launch_inv_group_f16(int wav, int scheme, const InvGroupLaunch& g, int grid, int pdl, cudaStream_t s) {
+    return launch_inv_group_t<__half>(wav, scheme, g, grid, pdl, s);
 }
 
 int occupancy_forward_f16(int wav, int scheme, const FwdCfg& cfg) { return occupancy_forward_t<__half>(wav, scheme, cfg); }

@@ -12,8 +12,8 @@ int launch_inverse_f32(int wav, int scheme, const InvParams& p, int grid, cudaSt
     return launch_inverse_t<float>(wav, scheme, p, grid, s);
 }
 
-int launch_inv_batch_f32(int wav, int scheme, const InvBatchParams& p, int grid, cudaStream_t s) {
-    return launch_inv_batch_t<float>(wav, scheme, p, grid, s);
+int launch_inv_group_f32(int wav, int scheme, const InvGroupLaunch& g, int grid, int pdl, cudaStream_t s) {
+    return launch_inv_group_t<float>(wav, scheme, g, grid, pdl, s);
 }
 
 int occupancy_forward_f32(int wav, int scheme, const FwdCfg& cfg) { return occupancy_forward_t<float>(wav, scheme, cfg); }
@@ -60,8 +60,8 @@ int forward_blocks_per_sm(int wav, int scheme, int coef_dtype, const FwdCfg& cfg
     }
 }
 
-int launch_adj_batch_f32(const InvBatchParams& p, int grid, cudaStream_t s) {
-    return launch_inv_batch_one<Adj97<INV_QL>, float, true>(p, grid, s);
+int launch_adj_group_f32(const InvGroupLaunch& g, int grid, int pdl, cudaStream_t s) {
+    return launch_inv_group_one<Adj97<INV_QL>, float, true>(g, grid, pdl, s);
 }
 
 int occupancy_pml_f16(int wav, int scheme);

@@ -12,8 +12,8 @@ int launch_inverse_i32(int wav, int scheme, const InvParams& p, int grid, cudaSt
     return launch_inverse_t<int>(wav, scheme, p, grid, s);
 }
 
-int launch_inv_batch_i32(int wav, int scheme, const InvBatchParams& p, int grid, cudaStream_t s) {
-    return launch_inv_batch_t<int>(wav, scheme, p, grid, s);
+int launch_inv_group_i32(int wav, int scheme, const InvGroupLaunch& g, int grid, int pdl, cudaStream_t s) {
+    return launch_inv_group_t<int>(wav, scheme, g, grid, pdl, s);
 }
 
 int occupancy_forward_i32(int wav, int scheme, const FwdCfg& cfg) { return occupancy_forward_t<int>(wav, scheme, cfg); }

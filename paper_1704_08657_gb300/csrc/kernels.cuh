@@ -999,41 +999,31 @@ __global__ void __launch_bounds__(NW * 32) inv_kernel(const InvParams p) {
         if (!inv_unit_any<Pipe, BT, ADJ, INV_QR, INV_NST>(p, s, R0, R1, lane, ring, bars, gstage)) return;
 }
 
-// One level of every image of a batch in one launch: units from the plan's
-// table, dealt round-robin; geometry and offsets from per-image descriptors.
+// One level of a group of images (InvGroupLaunch): units in order, the image
+// found by binary search over the group's unit ranges; only the first launch
+// of a level waits for earlier work.
 template <class Pipe, class BT, bool ADJ, int QL, int NW>
-__global__ void __launch_bounds__(NW * 32, 4) inv_batch_kernel(const InvBatchParams B) {
-    using CT = typename Pipe::CT;
+__global__ void __launch_bounds__(NW * 32) inv_group_kernel(const __grid_constant__ InvGroupLaunch L) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char* ring;
     uint64_t* bars;
     inv_ring<INV_QR, INV_NST, NW>(smem, warp, lane, ring, bars);
+    if (L.wait_prev) griddep_wait();
+    griddep_launch_dependents();
     uint32_t gstage = 0;
-    for (int u = blockIdx.x * NW + warp; u < B.n_units; u += gridDim.x * NW) {
-        const InvUnit un = B.units[u];
-        const InvDesc& d = B.descs[un.desc];
-        InvParams p;
-        p.h = d.h, p.w = d.w, p.hq = d.hq, p.wq = d.wq, p.hh = d.hh, p.wh = d.wh;
-        p.n_strips = d.n_strips, p.seg_rows = d.seg_rows, p.n_segs = 0, p.n_units = 0, p.balanced = 0;
-        p.coef = static_cast<const BT*>(B.coef) + d.coef_off;
-        p.coef_pitch = d.coef_pitch;
-        p.ll = d.ll_is_ct ? static_cast<const void*>(static_cast<const CT*>(B.ws) + d.ll_off)
-                          : static_cast<const void*>(static_cast<const BT*>(B.coef) + d.ll_off);
-        p.ll_pitch = d.ll_pitch;
-        p.ll_is_ct = d.ll_is_ct;
-        p.out = d.out_is_ws ? static_cast<void*>(static_cast<CT*>(B.ws) + d.out_off)
-                            : static_cast<void*>(static_cast<CT*>(B.out) + d.out_off);
-        p.out_pitch = d.out_pitch;
-        p.vec_in_lo = d.vec_in_lo && B.coef_vec;
-        p.vec_in_hi = d.vec_in_hi && B.coef_vec;
-        p.vec_ll = d.ll_is_ct ? 1 : (d.vec_ll && B.coef_vec);
-        p.vec_out = d.out_is_ws ? 1 : (d.vec_out && B.out_vec);
-        p.status = B.status;
-        p.l1 = B.l1;
-        p.l1_scale = B.l1_scale;
-        const int R0 = un.g * d.seg_rows;
-        if (!inv_unit_any<Pipe, BT, ADJ, INV_QR, INV_NST>(p, un.s, R0, min(R0 + d.seg_rows, d.hq), lane, ring, bars,
+    for (int u = blockIdx.x * NW + warp; u < L.n_units; u += gridDim.x * NW) {
+        int lo = 0, hi = L.n_img - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (L.img[mid].u_begin <= u) lo = mid;
+            else hi = mid - 1;
+        }
+        const InvParams& p = L.img[lo].p;
+        const int lu = u - L.img[lo].u_begin;
+        const int s = lu % p.n_strips;
+        const int R0 = (lu / p.n_strips) * p.seg_rows;
+        if (!inv_unit_any<Pipe, BT, ADJ, INV_QR, INV_NST>(p, s, R0, min(R0 + p.seg_rows, p.hq), lane, ring, bars,
                                                           gstage))
             return;
     }

@@ -240,24 +240,33 @@ int launch_inv_one(const InvParams& p, int grid, cudaStream_t s) {
 }
 
 template <class Pipe, class BT, bool ADJ>
-int launch_inv_batch_one(const InvBatchParams& p, int grid, cudaStream_t s) {
-    inv_batch_kernel<Pipe, BT, ADJ, INV_QL, INV_NW>
-        <<<grid, INV_NW * 32, inv_smem_bytes<INV_QR, INV_NST, INV_NW>(), s>>>(p);
-    return cudaGetLastError();
+int launch_inv_group_one(const InvGroupLaunch& g, int grid, int pdl, cudaStream_t s) {
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(grid);
+    lc.blockDim = dim3(INV_NW * 32);
+    lc.dynamicSmemBytes = inv_smem_bytes<INV_QR, INV_NST, INV_NW>();
+    lc.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    lc.attrs = attr;
+    lc.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&lc, inv_group_kernel<Pipe, BT, ADJ, INV_QL, INV_NW>, g);
 }
 
 template <class BT>
-int launch_inv_batch_t(int wav, int scheme, const InvBatchParams& p, int grid, cudaStream_t s) {
+int launch_inv_group_t(int wav, int scheme, const InvGroupLaunch& g, int grid, int pdl, cudaStream_t s) {
     if constexpr (std::is_same<BT, int>::value) {
         if (wav != WAV_CDF53I) return cudaErrorInvalidValue;
-        if (scheme == SCHEME_SEP) return launch_inv_batch_one<Inv53<SCHEME_SEP, INV_QL>, int, false>(p, grid, s);
-        return launch_inv_batch_one<Inv53<SCHEME_NONSEP, INV_QL>, int, false>(p, grid, s);
+        if (scheme == SCHEME_SEP) return launch_inv_group_one<Inv53<SCHEME_SEP, INV_QL>, int, false>(g, grid, pdl, s);
+        return launch_inv_group_one<Inv53<SCHEME_NONSEP, INV_QL>, int, false>(g, grid, pdl, s);
     } else {
         if (wav != WAV_CDF97) return cudaErrorInvalidValue;
-        if (scheme == SCHEME_NONSEP) return launch_inv_batch_one<Inv97<SCHEME_NONSEP, INV_QL>, BT, false>(p, grid, s);
+        if (scheme == SCHEME_NONSEP)
+            return launch_inv_group_one<Inv97<SCHEME_NONSEP, INV_QL>, BT, false>(g, grid, pdl, s);
         if (scheme == SCHEME_REDUCED)
-            return launch_inv_batch_one<Inv97<SCHEME_REDUCED, INV_QL>, BT, false>(p, grid, s);
-        return launch_inv_batch_one<Inv97<SCHEME_SEP, INV_QL>, BT, false>(p, grid, s);
+            return launch_inv_group_one<Inv97<SCHEME_REDUCED, INV_QL>, BT, false>(g, grid, pdl, s);
+        return launch_inv_group_one<Inv97<SCHEME_SEP, INV_QL>, BT, false>(g, grid, pdl, s);
     }
 }
 
