@@ -385,7 +385,7 @@ int inv_group_build(dwt2_plan_t p, const void* coef, void* out, void* workspace,
                 const ImagePlan& ip = p->imgs[order[i0 + k]];
                 InvParams ipm = inv_level_params(p, ip, l, coef, out, workspace, csz, false, 0.f);
                 ipm.n_strips = (ipm.wq + INV_OUT_Q - 1) / INV_OUT_Q;
-                ipm.seg_rows = std::min(INV_GROUP_SEG, ipm.hq);
+                ipm.seg_rows = std::min(p->seg_env > 0 ? p->seg_env : INV_GROUP_SEG, ipm.hq);
                 ipm.n_segs = (ipm.hq + ipm.seg_rows - 1) / ipm.seg_rows;
                 ipm.n_units = ipm.n_segs * ipm.n_strips;
                 g->img[k].p = ipm;

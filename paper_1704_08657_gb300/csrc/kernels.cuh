@@ -819,11 +819,13 @@ constexpr size_t inv_smem_bytes() {
     return size_t(NW) * NST * QR * 4 * 256 + size_t(NW) * NST * 8;
 }
 
-// One unit of an interior strip whose band rows take paired copies: the bands
-// stream through a ring of NST stages of QR quad rows filled by cp.async
-// (mirrored rows for the inverse, zero rows for the adjoint at the top and
-// bottom).  Returns false when a stage wait timed out.
-template <class Pipe, class BT, bool ADJ, int QR, int NST>
+// One unit of a strip: the bands stream through a ring of NST stages of QR
+// quad rows filled by cp.async (mirrored rows for the inverse, zero rows for
+// the adjoint at the top and bottom).  Interior strips copy each lane's quad
+// pair at once; EDGE strips (the first and last of a row, 4-byte types) copy
+// element by element from the mirrored (inverse) or zero-filled (adjoint)
+// columns.  Returns false when a stage wait timed out.
+template <class Pipe, class BT, bool ADJ, int QR, int NST, bool EDGE>
 __device__ __forceinline__ bool inv_unit_staged(const InvParams& p, int s, int R0, int R1, int lane,
                                                 unsigned char* ring, uint64_t* bars, uint32_t& gstage) {
     using CT = typename Pipe::CT;
@@ -840,6 +842,27 @@ __device__ __forceinline__ bool inv_unit_staged(const InvParams& p, int s, int R
     const int jb = x0 / 2 + QL * lane;
     const bool mine = (lane >= 1) && (lane <= 30);
     const BT* coef = reinterpret_cast<const BT*>(p.coef);
+
+    // EDGE: every lane copies its band elements one by one (4-byte types), at
+    // the mirrored (inverse) or zero-filled (adjoint) columns
+    int ce[2], co[2];
+    bool cev[2], cov[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int j = jb + q;
+        if (ADJ) {
+            cev[q] = (j >= 0) && (j < p.wq);
+            cov[q] = (j >= 0) && (j < p.wh);
+            ce[q] = cev[q] ? j : 0;
+            co[q] = cov[q] ? j : 0;
+        } else {
+            ce[q] = fold_ws(2 * j, p.w) >> 1;
+            co[q] = fold_ws(2 * j + 1, p.w) >> 1;
+            cev[q] = cov[q] = true;
+        }
+        ce[q] = min(max(ce[q], 0), p.wq - 1);
+        co[q] = min(max(co[q], 0), max(p.wh - 1, 0));
+    }
 
     auto issue = [&](int t, int slot) {
         unsigned char* st = ring + slot * STAGEB;
@@ -860,14 +883,31 @@ __device__ __forceinline__ bool inv_unit_staged(const InvParams& p, int s, int R
                 rev = rov = true;
             }
             unsigned char* d = st + r * ROWB;
-            if (p.ll_is_ct)
-                cp_async_small<8>(d + lane * 8, reinterpret_cast<const CT*>(p.ll) + int64_t(re) * p.ll_pitch + jb, rev);
-            else
-                cp_async_small<PB>(d + lane * PB, reinterpret_cast<const BT*>(p.ll) + int64_t(re) * p.ll_pitch + jb,
-                                   rev);
-            cp_async_small<PB>(d + BAND + lane * PB, coef + int64_t(re) * p.coef_pitch + p.wq + jb, rev);
-            cp_async_small<PB>(d + 2 * BAND + lane * PB, coef + int64_t(p.hq + ro) * p.coef_pitch + jb, rov);
-            cp_async_small<PB>(d + 3 * BAND + lane * PB, coef + int64_t(p.hq + ro) * p.coef_pitch + p.wq + jb, rov);
+            if constexpr (EDGE) {
+                static_assert(sizeof(BT) == 4 && sizeof(CT) == 4, "element copies of 4-byte types");
+                const CT* llr = reinterpret_cast<const CT*>(p.ll) + int64_t(re) * p.ll_pitch;
+                const BT* hlr = coef + int64_t(re) * p.coef_pitch + p.wq;
+                const BT* lhr = coef + int64_t(p.hq + ro) * p.coef_pitch;
+                const BT* hhr = lhr + p.wq;
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    cp_async_small<4>(d + lane * 8 + q * 4, llr + ce[q], rev && cev[q]);
+                    cp_async_small<4>(d + BAND + lane * 8 + q * 4, hlr + co[q], rev && cov[q]);
+                    cp_async_small<4>(d + 2 * BAND + lane * 8 + q * 4, lhr + ce[q], rov && cev[q]);
+                    cp_async_small<4>(d + 3 * BAND + lane * 8 + q * 4, hhr + co[q], rov && cov[q]);
+                }
+            } else {
+                if (p.ll_is_ct)
+                    cp_async_small<8>(d + lane * 8, reinterpret_cast<const CT*>(p.ll) + int64_t(re) * p.ll_pitch + jb,
+                                      rev);
+                else
+                    cp_async_small<PB>(d + lane * PB,
+                                       reinterpret_cast<const BT*>(p.ll) + int64_t(re) * p.ll_pitch + jb, rev);
+                cp_async_small<PB>(d + BAND + lane * PB, coef + int64_t(re) * p.coef_pitch + p.wq + jb, rev);
+                cp_async_small<PB>(d + 2 * BAND + lane * PB, coef + int64_t(p.hq + ro) * p.coef_pitch + jb, rov);
+                cp_async_small<PB>(d + 3 * BAND + lane * PB, coef + int64_t(p.hq + ro) * p.coef_pitch + p.wq + jb,
+                                   rov);
+            }
         }
         asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&bars[slot]))
                      : "memory");
@@ -950,23 +990,29 @@ __device__ __forceinline__ bool inv_unit_staged(const InvParams& p, int s, int R
     return ok;
 }
 
-// inverse / adjoint unit: staged when the strip is interior and every band
-// row takes paired copies, else direct loads.  Adjoint units away from the
-// boundary (every quad of the strip and every row the steps weight in
-// [1, half - 2]) run the unweighted pipeline.
+// inverse / adjoint unit: staged when every band row takes paired copies,
+// else direct loads.  Adjoint units away from the boundary (every quad of
+// the strip and every row the steps weight in [1, half - 2]) run the
+// unweighted pipeline.
 template <class Pipe, class BT, bool ADJ, int QR, int NST>
 __device__ __forceinline__ bool inv_unit_any(const InvParams& p, int s, int R0, int R1, int lane,
                                              unsigned char* ring, uint64_t* bars, uint32_t& gstage) {
     constexpr int OUTQ = 32 * 2 - 2 * HALO_Q;
     const int x0 = s * (2 * OUTQ) - 2 * HALO_Q;
-    const bool staged = (x0 >= 0) && (x0 / 2 + 64 <= p.wh) && p.vec_in_lo && p.vec_in_hi && p.vec_ll;
+    const bool staged = p.vec_in_lo && p.vec_in_hi && p.vec_ll;
+    const bool interior = (x0 >= 0) && (x0 / 2 + 64 <= p.wh);
     if constexpr (ADJ) {
         // the steps weight rows R0-4 .. R1+1 (see Adj97::step) and quads x0/2 .. x0/2+63
-        const bool inner = staged && (x0 / 2 >= 1) && (x0 / 2 + 63 <= p.wh - 2) && (R0 - 4 >= 1) &&
+        const bool inner = staged && interior && (x0 / 2 >= 1) && (x0 / 2 + 63 <= p.wh - 2) && (R0 - 4 >= 1) &&
                            (R1 + 1 <= p.hh - 2);
-        if (inner) return inv_unit_staged<AdjInner97<2>, BT, true, QR, NST>(p, s, R0, R1, lane, ring, bars, gstage);
+        if (inner)
+            return inv_unit_staged<AdjInner97<2>, BT, true, QR, NST, false>(p, s, R0, R1, lane, ring, bars, gstage);
     }
-    if (staged) return inv_unit_staged<Pipe, BT, ADJ, QR, NST>(p, s, R0, R1, lane, ring, bars, gstage);
+    if (staged && interior)
+        return inv_unit_staged<Pipe, BT, ADJ, QR, NST, false>(p, s, R0, R1, lane, ring, bars, gstage);
+    if constexpr (sizeof(BT) == 4) {
+        if (staged) return inv_unit_staged<Pipe, BT, ADJ, QR, NST, true>(p, s, R0, R1, lane, ring, bars, gstage);
+    }
     inv_unit<Pipe, BT, ADJ, 2>(p, s, R0, R1, lane);
     return true;
 }
