@@ -132,6 +132,29 @@ __device__ __forceinline__ void load_quad_row(const CT* s0, Row<CT, QL>& r, int 
     }
 }
 
+// Edge strips of the forward: once a stage has landed, every pixel of the
+// lane outside [0, w) takes the value of its whole-sample mirror in place
+// (zero where the mirror lies outside the strip, beyond the filter support of
+// any stored output).  Sources are pixels inside the image, which no lane
+// rewrites, so the lanes need no barrier between them; the proxy fence orders
+// these generic writes before the next asynchronous fill of the stage.  Not
+// inlined: the row loop of interior strips stays as small as it was.
+template <class CT, int QL>
+__device__ __noinline__ void fwd_fix_edges(CT* stage, int rows, int x0, int w, int lane) {
+    constexpr int SPX = 64 * QL;
+    for (int k = 0; k < 2 * QL; ++k) {
+        const int px = x0 + 2 * QL * lane + k;
+        if (px >= 0 && px < w) continue;
+        const int src = fold_ws(px, w) - x0;
+        const bool in = (src >= 0) && (src < SPX);
+        for (int r = 0; r < rows; ++r) {
+            CT* row = stage + r * SPX;
+            row[2 * QL * lane + k] = in ? row[src] : CT(0);
+        }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 // ------------------------------------------------------------------ loaders
 // A loader fills one shared-memory stage (2*QR pixel rows of 64*QL pixels,
 // starting at pixel column x0 and pixel row y0 of the level's input) and
@@ -198,15 +221,19 @@ struct CpAsyncLoader {
 // warp's stage ring, gstage the warp's running stage count (slot and mbarrier
 // phase).  Returns false when a stage wait timed out.
 //
-// MODE 0 handles every strip.  MODE 1 and 2 are compiled for interior strips
-// (fwd_interior: no mirrored columns, every band row takes paired stores),
-// with the low-low band in the compute type (1) or the coefficient type (2):
-// their row loop has no edge or store-alignment branches, which keeps the hot
-// loop small in the instruction cache.
+// MODE 0 handles every strip.  MODE 1 and 2 are compiled for strips whose
+// band rows all take paired stores (fwd_pairs_ok), with the low-low band in
+// the compute type (1) or the coefficient type (2): their row loop has no
+// store-alignment branches, which keeps the hot loop small in the instruction
+// cache.  Edge strips run the same row loop as interior ones: their mirrored
+// columns are filled in the stage (fwd_fix_edges) and per-lane masks drop the
+// quads outside the bands.
 template <class P>
-__device__ __forceinline__ bool fwd_interior(const P& p, int x0, int QL) {
-    return x0 >= 0 && x0 + 64 * QL <= p.w && p.vec_lo && p.vec_hi && (p.ll_is_ct || p.vec_ll) &&
-           (x0 / 2 + 32 * QL - HALO_Q <= p.wh);
+__device__ __forceinline__ bool fwd_pairs_ok(const P& p, int x0, int QL) {
+    // every pair starts at an even quad: with both band widths even no pair
+    // straddles a band's last column; otherwise the strip must end inside both
+    return p.vec_lo && p.vec_hi && (p.ll_is_ct || p.vec_ll) &&
+           ((p.wq % 2 == 0 && p.wh % 2 == 0) || (x0 / 2 + 32 * QL - HALO_Q <= p.wh));
 }
 
 template <class Pipe, class OutT, int QL, int QR, int NST, int MODE = 0, class P, class Loader>
@@ -228,7 +255,7 @@ __device__ __forceinline__ bool fwd_unit(const P& p, const Loader& ld, int s, in
     const int x0 = s * (2 * OUTQ) - 2 * HALO_Q;       // first pixel (multiple of 4)
     const int jb = x0 / 2 + QL * lane;                // first quad column of the lane
     constexpr bool SPEC = MODE != 0;
-    const bool edge = SPEC ? false : ((x0 < 0) || (x0 + SPX > p.w));
+    const bool edge = (x0 < 0) || (x0 + SPX > p.w);
     const bool llct = MODE == 1 ? true : (MODE == 2 ? false : bool(p.ll_is_ct));
 
     // which of the lane's quads this strip outputs, per band parity
@@ -240,10 +267,16 @@ __device__ __forceinline__ bool fwd_unit(const P& p, const Loader& ld, int s, in
         ev[q] = mp[q] && (jb + q < p.wq);
         dv[q] = mp[q] && (jb + q < p.wh);
     }
-    // warp-uniform: every output quad of the strip exists in all four bands
-    // and every band row takes paired stores
-    const bool fast =
-        SPEC ? true : (p.vec_lo && p.vec_hi && (p.ll_is_ct || p.vec_ll) && (x0 / 2 + 32 * QL - HALO_Q <= p.wh));
+    // paired stores: both quads of the pair output by this strip and inside
+    // the even-column (LL, LH) or odd-column (HL, HH) bands
+    bool pe[QL / 2], po[QL / 2];
+#pragma unroll
+    for (int q = 0; q < QL; q += 2) {
+        pe[q / 2] = mp[q] && mp[q + 1] && (jb + q + 1 < p.wq);
+        po[q / 2] = mp[q] && mp[q + 1] && (jb + q + 1 < p.wh);
+    }
+    // warp-uniform: every band row takes paired stores
+    const bool fast = SPEC ? true : fwd_pairs_ok(p, x0, QL);
     // band pointers at output row R0, advanced one pitch per stored row
     OutT* hl = reinterpret_cast<OutT*>(p.coef) + int64_t(R0) * p.coef_pitch + p.wq + jb;
     OutT* lh = reinterpret_cast<OutT*>(p.coef) + int64_t(p.hq + R0) * p.coef_pitch + jb;
@@ -281,9 +314,10 @@ __device__ __forceinline__ bool fwd_unit(const P& p, const Loader& ld, int s, in
                     return;
                 }
                 stage = bufs + slot * STAGE_ELEMS;
+                if (edge) fwd_fix_edges<CT, QL>(const_cast<CT*>(stage), ROWS, x0, p.w, lane);
             }
             const int vi = A0 + gi * PHASES + PH;  // quad row streamed now
-            load_quad_row<CT, QL>(stage + (2 * QI) * SPX, pipe.template slot<PH>(), lane, edge, x0, p.w);
+            load_quad_row<CT, QL>(stage + (2 * QI) * SPX, pipe.template slot<PH>(), lane, false, x0, p.w);
             const R& out = pipe.template step<PH>(vi);
             const int oi = vi - Pipe::LAG;
             const bool row_on = (oi >= R0) & (oi < R1);
@@ -291,16 +325,16 @@ __device__ __forceinline__ bool fwd_unit(const P& p, const Loader& ld, int s, in
             if (fast) {
 #pragma unroll
                 for (int q = 0; q < QL; q += 2) {
-                    const bool on = row_on & mp[q] & mp[q + 1];
-                    const bool oo = orow & mp[q] & mp[q + 1];
+                    const bool on_e = row_on & pe[q / 2], on_o = row_on & po[q / 2];
+                    const bool oo_e = orow & pe[q / 2], oo_o = orow & po[q / 2];
                     if (llct) {
-                        if (on) st_pair<CT>(llc + q, out.c1[q], out.c1[q + 1]);
+                        if (on_e) st_pair<CT>(llc + q, out.c1[q], out.c1[q + 1]);
                     } else {
-                        if (on) st_pair<OutT>(llo + q, Cvt<OutT>::to(out.c1[q]), Cvt<OutT>::to(out.c1[q + 1]));
+                        if (on_e) st_pair<OutT>(llo + q, Cvt<OutT>::to(out.c1[q]), Cvt<OutT>::to(out.c1[q + 1]));
                     }
-                    if (on) st_pair<OutT>(hl + q, Cvt<OutT>::to(out.c2[q]), Cvt<OutT>::to(out.c2[q + 1]));
-                    if (oo) st_pair<OutT>(lh + q, Cvt<OutT>::to(out.c3[q]), Cvt<OutT>::to(out.c3[q + 1]));
-                    if (oo) st_pair<OutT>(hh + q, Cvt<OutT>::to(out.c4[q]), Cvt<OutT>::to(out.c4[q + 1]));
+                    if (on_o) st_pair<OutT>(hl + q, Cvt<OutT>::to(out.c2[q]), Cvt<OutT>::to(out.c2[q + 1]));
+                    if (oo_e) st_pair<OutT>(lh + q, Cvt<OutT>::to(out.c3[q]), Cvt<OutT>::to(out.c3[q + 1]));
+                    if (oo_o) st_pair<OutT>(hh + q, Cvt<OutT>::to(out.c4[q]), Cvt<OutT>::to(out.c4[q + 1]));
                 }
             } else if (row_on) {
 #pragma unroll
@@ -415,7 +449,7 @@ __global__ void __launch_bounds__(NW * 32)
         if (y.dep_ctr != nullptr && !fwd_wait_inputs<Pipe::LAG, QR>(p, y, R0, R1, lane)) return;
         bool ok;
         if constexpr (SPEC) {
-            if (fwd_interior(p, s * (2 * (32 * QL - 2 * HALO_Q)) - 2 * HALO_Q, QL))
+            if (fwd_pairs_ok(p, s * (2 * (32 * QL - 2 * HALO_Q)) - 2 * HALO_Q, QL))
                 ok = p.ll_is_ct ? fwd_unit<Pipe, OutT, QL, QR, NST, 1>(p, ld, s, R0, R1, bufs, bars, gstage, lane)
                                 : fwd_unit<Pipe, OutT, QL, QR, NST, 2>(p, ld, s, R0, R1, bufs, bars, gstage, lane);
             else
@@ -471,7 +505,7 @@ __global__ void __launch_bounds__(NW * 32) fwd_group_kernel(const __grid_constan
         }
         bool ok;
         if constexpr (SPEC) {
-            if (fwd_interior(p, s * (2 * (32 * QL - 2 * HALO_Q)) - 2 * HALO_Q, QL))
+            if (fwd_pairs_ok(p, s * (2 * (32 * QL - 2 * HALO_Q)) - 2 * HALO_Q, QL))
                 ok = p.ll_is_ct ? fwd_unit<Pipe, OutT, QL, QR, NST, 1>(p, ld, s, R0, R1, bufs, bars, gstage, lane)
                                 : fwd_unit<Pipe, OutT, QL, QR, NST, 2>(p, ld, s, R0, R1, bufs, bars, gstage, lane);
             else

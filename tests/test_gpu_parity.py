@@ -96,8 +96,11 @@ def test_forward97_fp32(h, w, scheme):
         assert_fp32_close(got, ref, levels, 255.0, f"{scheme} {h}x{w} L{levels}")
 
 
+# (100, 1028) and (66, 3000): widths a multiple of 4, whose first and last
+# strips of each row stream through the staged row loop with mirrored columns
 @pytest.mark.parametrize("scheme", SCHEMES97)
-@pytest.mark.parametrize("h,w", [(512, 512), (33, 65), (7, 5), (2, 2), (130, 250), (257, 129)])
+@pytest.mark.parametrize("h,w", [(512, 512), (33, 65), (7, 5), (2, 2), (130, 250), (257, 129), (100, 1028),
+                                 (66, 3000)])
 def test_inverse97_fp32(h, w, scheme):
     levels = _levels_max(h, w, 4)
     x = synth.uniform(h, w, seed=11)
@@ -123,7 +126,7 @@ def test_int53_bit_exact(h, w, scheme):
 
 
 @pytest.mark.parametrize("dtype,rel", [(torch.float16, 1e-3), (torch.bfloat16, 8e-3)])
-@pytest.mark.parametrize("h,w", [(512, 512), (130, 250)])
+@pytest.mark.parametrize("h,w", [(512, 512), (130, 250), (96, 1028)])
 def test_lowp_storage(h, w, dtype, rel):
     levels = _levels_max(h, w, 5)
     x = synth.noisy(h, w, seed=3)
@@ -138,7 +141,8 @@ def test_lowp_storage(h, w, dtype, rel):
     assert np.abs(got - ref_i).max() <= 2e-3 * np.abs(ref_i).max() / 255.0 * 2
 
 
-@pytest.mark.parametrize("h,w", [(512, 512), (33, 65), (7, 5), (2, 2), (3, 3), (130, 250), (257, 129)])
+@pytest.mark.parametrize("h,w", [(512, 512), (33, 65), (7, 5), (2, 2), (3, 3), (130, 250), (257, 129), (100, 1028),
+                                 (70, 1000)])
 def test_adjoint_matches_oracle(h, w):
     levels = _levels_max(h, w, 4)
     rng = np.random.default_rng(h * 1000 + w)
