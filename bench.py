@@ -44,7 +44,7 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--size", type=int, default=16384)
     ap.add_argument("--levels", type=int, default=5)
-    ap.add_argument("--scheme", default="reduced", choices=["nonsep", "reduced", "sep", "polyconv", "conv"])
+    ap.add_argument("--scheme", default="reduced", choices=["nonsep", "reduced", "sep", "polyconv", "conv", "nsconv"])
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
@@ -473,9 +473,10 @@ def run_ours(a):
         comp = {}
         ksteps = max(3, min(a.steps, 100))
         variants = [("nonsep", torch.float32), ("reduced", torch.float32), ("sep", torch.float32),
-                    ("polyconv", torch.float32), ("conv", torch.float32),
+                    ("polyconv", torch.float32), ("conv", torch.float32), ("nsconv", torch.float32),
                     ("reduced", torch.float16), ("reduced", torch.bfloat16), ("nonsep", torch.float16),
-                    ("sep", torch.float16), ("polyconv", torch.float16), ("conv", torch.float16)]
+                    ("sep", torch.float16), ("polyconv", torch.float16), ("conv", torch.float16),
+                    ("nsconv", torch.float16)]
         names = {torch.float32: "f32", torch.float16: "f16", torch.bfloat16: "bf16"}
         for scheme, cdt in variants:
             for levels in (1, a.levels):

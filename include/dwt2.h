@@ -21,15 +21,18 @@
  *   DWT2_POLYCONV        the polyconvolution N_{P,U} (Proposed Schemes): each
  *                        pair applied as one step on pre-pair values, with
  *                        V = 1 + PU as one 3-tap filter (CDF 9/7 only);
- *   DWT2_CONV            the convolution scheme (Background, Proposed
- *                        Schemes): the 9-tap / 7-tap filter bank per axis,
- *                        multiplied out from the lifting constants, in one
- *                        step (CDF 9/7 only).
+ *   DWT2_CONV            the separable convolution N^V | N^H (Background):
+ *                        the 9-tap / 7-tap filter bank, multiplied out from
+ *                        the lifting constants, on each row and then on each
+ *                        column of the row results (CDF 9/7 only);
+ *   DWT2_NONSEP_CONV     the non-separable convolution N = N^V N^H (Proposed
+ *                        Schemes): one step of 2-D filters of 9x9, 9x7, 7x9
+ *                        and 7x7 pixels, the products of the vertical and
+ *                        horizontal taps applied directly (CDF 9/7 only).
  * The kernels stream rows through registers and exchange horizontal
- * neighbours by warp shuffles, so no scheme has barriers between its steps
- * and the paper's separable and non-separable variants of the polyconvolution
- * and of the convolution coincide; the schemes differ in arithmetic and in the
- * number of neighbour exchanges (4, 4, 4, 2 and 1 per CDF 9/7 level).
+ * neighbours by warp shuffles, so no scheme has barriers between its steps;
+ * the schemes differ in arithmetic and in the number of neighbour exchanges
+ * (4, 4, 4, 2, 1 and 1 per CDF 9/7 level).
  *
  * Conventions (readings where the paper is silent):
  *   - odd sample x[2n+1] is predicted from x[2n], x[2n+2]; even sample x[2n]
@@ -74,7 +77,8 @@ enum dwt2_scheme {
     DWT2_NONSEP_REDUCED = 1,
     DWT2_SEP_LIFTING = 2,
     DWT2_POLYCONV = 3,
-    DWT2_CONV = 4
+    DWT2_CONV = 4,
+    DWT2_NONSEP_CONV = 5
 };
 enum dwt2_boundary { DWT2_SYMMETRIC = 0 };
 
@@ -114,10 +118,11 @@ typedef struct {
  *              lifting always runs in FP32 and intermediate LL bands are kept
  *              in FP32), I32 for CDF 5/3.
  *   scheme     DWT2_NONSEP, DWT2_NONSEP_REDUCED (CDF 9/7 only),
- *              DWT2_SEP_LIFTING, DWT2_POLYCONV or DWT2_CONV (both CDF 9/7 only
- *              and not with DWT2_FLAG_PERSISTENT: DWT2_ERR_UNSUPPORTED).  The
- *              inverse and adjoint of a plan run the non-separable lifting
- *              kernels for the last two (the same transform).
+ *              DWT2_SEP_LIFTING, DWT2_POLYCONV, DWT2_CONV or DWT2_NONSEP_CONV
+ *              (the last three CDF 9/7 only and not with
+ *              DWT2_FLAG_PERSISTENT: DWT2_ERR_UNSUPPORTED).  The inverse and
+ *              adjoint of a plan run the non-separable lifting kernels for
+ *              the last three (the same transform).
  *   n_images   number of images (>= 1); images is a host array of that many
  *              descriptors, copied into the plan.  With several images (and
  *              a lifting scheme) dwt2_forward makes one launch per level for

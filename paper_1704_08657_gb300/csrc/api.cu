@@ -787,7 +787,7 @@ int dwt2_plan(dwt2_plan_t* out, int wavelet, int levels, int boundary, int in_dt
     if (!images || n_images < 1 || levels < 1 || levels > 30) return DWT2_ERR_INVALID_ARG;
     if (boundary != DWT2_SYMMETRIC) return DWT2_ERR_INVALID_ARG;
     if (wavelet != DWT2_CDF97 && wavelet != DWT2_CDF53_INT) return DWT2_ERR_INVALID_ARG;
-    if (scheme < DWT2_NONSEP || scheme > DWT2_CONV) return DWT2_ERR_INVALID_ARG;
+    if (scheme < DWT2_NONSEP || scheme > DWT2_NONSEP_CONV) return DWT2_ERR_INVALID_ARG;
     if (in_dtype < DWT2_F32 || in_dtype > DWT2_I32 || coef_dtype < DWT2_F32 || coef_dtype > DWT2_I32)
         return DWT2_ERR_INVALID_ARG;
     if (flags & ~(DWT2_FLAG_PERSISTENT | DWT2_FLAG_TEST_DROP_SIGNAL)) return DWT2_ERR_INVALID_ARG;
@@ -798,7 +798,7 @@ int dwt2_plan(dwt2_plan_t* out, int wavelet, int levels, int boundary, int in_dt
         if (in_dtype != DWT2_I32 || coef_dtype != DWT2_I32) return DWT2_ERR_UNSUPPORTED;
         if (scheme == DWT2_NONSEP_REDUCED) return DWT2_ERR_UNSUPPORTED;  // floor does not split
         // floor rounding belongs to the lifting steps: no filter-bank form
-        if (scheme == DWT2_POLYCONV || scheme == DWT2_CONV) return DWT2_ERR_UNSUPPORTED;
+        if (scheme == DWT2_POLYCONV || scheme == DWT2_CONV || scheme == DWT2_NONSEP_CONV) return DWT2_ERR_UNSUPPORTED;
     }
     std::vector<ImagePlan> imgs(n_images);
     size_t ws = 0;

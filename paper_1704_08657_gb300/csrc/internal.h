@@ -11,7 +11,7 @@ namespace dwt2 {
 // device status word bits
 enum : unsigned { DEV_TIMEOUT = 1u, DEV_CHECK = 2u };
 
-enum { SCHEME_NONSEP = 0, SCHEME_REDUCED = 1, SCHEME_SEP = 2, SCHEME_POLYCONV = 3, SCHEME_CONV = 4 };
+enum { SCHEME_NONSEP = 0, SCHEME_REDUCED = 1, SCHEME_SEP = 2, SCHEME_POLYCONV = 3, SCHEME_CONV = 4, SCHEME_NSCONV = 5 };
 enum { WAV_CDF97 = 0, WAV_CDF53I = 1 };
 enum { DT_F32 = 0, DT_F16 = 1, DT_BF16 = 2, DT_I32 = 3 };
 

@@ -92,6 +92,7 @@ int launch_group_t(int wav, int scheme, const GroupLaunch& g, int grid, const Fw
         if (scheme == SCHEME_SEP) return launch_group_cfgs<Fwd97, SCHEME_SEP, OutT>(g, grid, c, pdl, s);
         if (scheme == SCHEME_POLYCONV) return launch_group_cfgs<Fwd97S, SCHEME_POLYCONV, OutT>(g, grid, c, pdl, s);
         if (scheme == SCHEME_CONV) return launch_group_cfgs<Fwd97S, SCHEME_CONV, OutT>(g, grid, c, pdl, s);
+        if (scheme == SCHEME_NSCONV) return launch_group_cfgs<Fwd97S, SCHEME_NSCONV, OutT>(g, grid, c, pdl, s);
         return cudaErrorInvalidValue;
     }
 }
@@ -127,6 +128,7 @@ int occupancy_forward_t(int wav, int scheme, const FwdCfg& c) {
         if (scheme == SCHEME_REDUCED) return occupancy_fwd_cfgs<Fwd97, SCHEME_REDUCED, OutT>(c);
         if (scheme == SCHEME_POLYCONV) return occupancy_fwd_cfgs<Fwd97S, SCHEME_POLYCONV, OutT>(c);
         if (scheme == SCHEME_CONV) return occupancy_fwd_cfgs<Fwd97S, SCHEME_CONV, OutT>(c);
+        if (scheme == SCHEME_NSCONV) return occupancy_fwd_cfgs<Fwd97S, SCHEME_NSCONV, OutT>(c);
         return occupancy_fwd_cfgs<Fwd97, SCHEME_SEP, OutT>(c);
     }
 }
@@ -181,6 +183,8 @@ int launch_forward_t(int wav, int scheme, const CUtensorMap& box, const CUtensor
         if (scheme == SCHEME_POLYCONV)
             return launch_fwd_cfgs<Fwd97S, SCHEME_POLYCONV, OutT>(box, row, p, grid, c, s, y);
         if (scheme == SCHEME_CONV) return launch_fwd_cfgs<Fwd97S, SCHEME_CONV, OutT>(box, row, p, grid, c, s, y);
+        if (scheme == SCHEME_NSCONV)
+            return launch_fwd_cfgs<Fwd97S, SCHEME_NSCONV, OutT>(box, row, p, grid, c, s, y);
         return cudaErrorInvalidValue;
     }
 }

@@ -581,6 +581,127 @@ struct Fwd97CV {
     }
 };
 
+// --- non-separable convolution ------------------------------------------------
+// The whole CDF 9/7 analysis as one step of 2-D filters, N = N^V N^H (Proposed
+// Schemes): each output band is the sum of the 2-D convolutions of the four
+// polyphase inputs with products of one vertical and one horizontal tap of
+// the 1-D bank above (filters of 9x9, 9x7, 7x9 and 7x7 pixels), applied
+// directly, with no intermediate result of either direction.  An arriving
+// quad row is multiplied into the five output rows it reaches (a ring of six
+// accumulator rows); its horizontal neighbours are fetched once and the
+// pairs of equal horizontal taps added first.  144 FMA and 14 additions per
+// quad, against about 70 operations of the separable bank.
+
+// 1-D taps by offset k = input - output (quads): low-pass on the even (A) and
+// odd (B) phase, high-pass on the even (C) and odd (D) phase
+constexpr double nc_tap(int f, int k) {
+    return f == 0 ? (k == 0 ? Conv97::A.c[4] : (k == 1 || k == -1) ? Conv97::A.c[5]
+                                                   : (k == 2 || k == -2) ? Conv97::A.c[6] : 0.0)
+         : f == 1 ? ((k == 0 || k == -1) ? Conv97::B.c[4] : (k == 1 || k == -2) ? Conv97::B.c[5] : 0.0)
+         : f == 2 ? ((k == 0 || k == 1) ? Conv97::C.c[4] : (k == 2 || k == -1) ? Conv97::C.c[6] : 0.0)
+                  : (k == 0 ? Conv97::D.c[4] : (k == 1 || k == -1) ? Conv97::D.c[5] : 0.0);
+}
+template <int F, int K>
+struct NcV {
+    static constexpr double v = nc_tap(F, K);
+};
+
+// one pixel row's horizontal terms, symmetric pairs added: a0..a2 for the
+// low-pass taps on the even columns, b0, b1 on the odd ones; c0, c2 and d0,
+// d1 likewise for the high-pass
+template <int QL>
+struct NcH {
+    float a0[QL], a1[QL], a2[QL], b0[QL], b1[QL], c0[QL], c2[QL], d0[QL], d1[QL];
+};
+template <int QL>
+__device__ __forceinline__ void nc_terms(const float (&s)[QL], const float (&d)[QL], NcH<QL>& t) {
+    float sl[QL], sr[QL], sll[QL], srr[QL], dl[QL], dr[QL], dll[QL];
+    left_of(s, sl);
+    right_of(s, sr);
+    left2_of(s, sll);
+    right2_of(s, srr);
+    left_of(d, dl);
+    right_of(d, dr);
+    left2_of(d, dll);
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+        t.a0[q] = s[q];
+        t.a1[q] = sl[q] + sr[q];
+        t.a2[q] = sll[q] + srr[q];
+        t.b0[q] = dl[q] + d[q];
+        t.b1[q] = dll[q] + dr[q];
+        t.c0[q] = s[q] + sr[q];
+        t.c2[q] = sl[q] + srr[q];
+        t.d0[q] = d[q];
+        t.d1[q] = dl[q] + dr[q];
+    }
+}
+// acc += V * (horizontal low-pass of t), every product a compile-time constant
+template <class V, int QL>
+__device__ __forceinline__ void nc_low(float (&acc)[QL], const NcH<QL>& t) {
+    if constexpr (V::v != 0.0) {
+        constexpr float k0 = float(V::v * Conv97::A.c[4]), k1 = float(V::v * Conv97::A.c[5]),
+                        k2 = float(V::v * Conv97::A.c[6]), k3 = float(V::v * Conv97::B.c[4]),
+                        k4 = float(V::v * Conv97::B.c[5]);
+#pragma unroll
+        for (int q = 0; q < QL; ++q)
+            acc[q] = fmaf(k4, t.b1[q], fmaf(k3, t.b0[q], fmaf(k2, t.a2[q], fmaf(k1, t.a1[q], fmaf(k0, t.a0[q], acc[q])))));
+    }
+}
+template <class V, int QL>
+__device__ __forceinline__ void nc_high(float (&acc)[QL], const NcH<QL>& t) {
+    if constexpr (V::v != 0.0) {
+        constexpr float k0 = float(V::v * Conv97::C.c[4]), k2 = float(V::v * Conv97::C.c[6]),
+                        k3 = float(V::v * Conv97::D.c[4]), k4 = float(V::v * Conv97::D.c[5]);
+#pragma unroll
+        for (int q = 0; q < QL; ++q)
+            acc[q] = fmaf(k4, t.d1[q], fmaf(k3, t.d0[q], fmaf(k2, t.c2[q], fmaf(k0, t.c0[q], acc[q]))));
+    }
+}
+// the contribution of an arriving row (even pixel row e, odd pixel row o) to
+// the output row K quad rows above it
+template <int K, int QL>
+__device__ __forceinline__ void nc_add(Row<float, QL>& r, const NcH<QL>& e, const NcH<QL>& o) {
+    nc_low<NcV<0, K>>(r.c1, e);  // LL: vertical low-pass, even / odd row
+    nc_low<NcV<1, K>>(r.c1, o);
+    nc_high<NcV<0, K>>(r.c2, e);  // HL
+    nc_high<NcV<1, K>>(r.c2, o);
+    nc_low<NcV<2, K>>(r.c3, e);  // LH: vertical high-pass
+    nc_low<NcV<3, K>>(r.c3, o);
+    nc_high<NcV<2, K>>(r.c4, e);  // HH
+    nc_high<NcV<3, K>>(r.c4, o);
+}
+
+template <int QL>
+struct Fwd97NC {
+    static constexpr int LAG = 2;
+    using CT = float;
+    using R = Row<float, QL>;
+    R x, acc[6];  // the arriving row; output rows n-2 .. n+3 by phase
+    __device__ __forceinline__ void init() {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) zero_row(acc[i]);
+    }
+    template <int PH>
+    __device__ __forceinline__ R& slot() {
+        return x;
+    }
+    template <int PH>
+    __device__ __forceinline__ R& step(int /*row*/) {
+        // arrival n reaches output rows n+2 (first) .. n-2 (last, complete now)
+        zero_row(acc[(PH + 2) % 6]);
+        NcH<QL> e, o;
+        nc_terms(x.c1, x.c2, e);
+        nc_terms(x.c3, x.c4, o);
+        nc_add<-2>(acc[(PH + 2) % 6], e, o);
+        nc_add<-1>(acc[(PH + 1) % 6], e, o);
+        nc_add<0>(acc[PH % 6], e, o);
+        nc_add<1>(acc[(PH + 5) % 6], e, o);
+        nc_add<2>(acc[(PH + 4) % 6], e, o);
+        return acc[(PH + 4) % 6];
+    }
+};
+
 // the CDF 9/7 forward pipeline of a scheme
 template <int SCHEME, int QL>
 struct Fwd97Sel {
@@ -593,6 +714,10 @@ struct Fwd97Sel<SCHEME_POLYCONV, QL> {
 template <int QL>
 struct Fwd97Sel<SCHEME_CONV, QL> {
     using type = Fwd97CV<QL>;
+};
+template <int QL>
+struct Fwd97Sel<SCHEME_NSCONV, QL> {
+    using type = Fwd97NC<QL>;
 };
 template <int SCHEME, int QL>
 using Fwd97S = typename Fwd97Sel<SCHEME, QL>::type;

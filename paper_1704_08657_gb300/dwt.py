@@ -18,7 +18,8 @@ from . import abi
 
 WAVELETS = {"cdf97": abi.DWT2_CDF97, "cdf53": abi.DWT2_CDF53_INT}
 SCHEMES = {"nonsep": abi.DWT2_NONSEP, "reduced": abi.DWT2_NONSEP_REDUCED, "sep": abi.DWT2_SEP_LIFTING,
-           "polyconv": abi.DWT2_POLYCONV, "conv": abi.DWT2_CONV}
+           "polyconv": abi.DWT2_POLYCONV, "conv": abi.DWT2_CONV,
+           "nsconv": abi.DWT2_NONSEP_CONV}
 DTYPES = {torch.float32: abi.DWT2_F32, torch.float16: abi.DWT2_F16, torch.bfloat16: abi.DWT2_BF16,
           torch.int32: abi.DWT2_I32}
 

@@ -51,10 +51,12 @@ def test_strerror_names_every_code(lib):
     ((abi.DWT2_CDF53_INT, 1, 0, abi.DWT2_I32, abi.DWT2_I32, abi.DWT2_NONSEP_REDUCED, [(0, 16, 16, 16)]),
      abi.DWT2_ERR_UNSUPPORTED),
     ((abi.DWT2_CDF53_INT, 1, 0, abi.DWT2_F32, abi.DWT2_F32, 0, [(0, 16, 16, 16)]), abi.DWT2_ERR_UNSUPPORTED),
-    ((abi.DWT2_CDF97, 1, 0, 0, 0, 5, [(0, 16, 16, 16)]), abi.DWT2_ERR_INVALID_ARG),          # scheme past CONV
+    ((abi.DWT2_CDF97, 1, 0, 0, 0, 6, [(0, 16, 16, 16)]), abi.DWT2_ERR_INVALID_ARG),          # past NONSEP_CONV
     ((abi.DWT2_CDF53_INT, 1, 0, abi.DWT2_I32, abi.DWT2_I32, abi.DWT2_POLYCONV, [(0, 16, 16, 16)]),
      abi.DWT2_ERR_UNSUPPORTED),                                                             # floor: lifting only
     ((abi.DWT2_CDF53_INT, 1, 0, abi.DWT2_I32, abi.DWT2_I32, abi.DWT2_CONV, [(0, 16, 16, 16)]),
+     abi.DWT2_ERR_UNSUPPORTED),
+    ((abi.DWT2_CDF53_INT, 1, 0, abi.DWT2_I32, abi.DWT2_I32, abi.DWT2_NONSEP_CONV, [(0, 16, 16, 16)]),
      abi.DWT2_ERR_UNSUPPORTED),
 ])
 def test_plan_validation(lib, args, code):
@@ -68,7 +70,7 @@ def test_plan_validation(lib, args, code):
     assert e.value.code == code
 
 
-@pytest.mark.parametrize("scheme", [abi.DWT2_POLYCONV, abi.DWT2_CONV])
+@pytest.mark.parametrize("scheme", [abi.DWT2_POLYCONV, abi.DWT2_CONV, abi.DWT2_NONSEP_CONV])
 def test_filter_bank_schemes_have_no_persistent_form(lib, scheme):
     with pytest.raises(abi.Dwt2Error) as e:
         abi.dwt2_plan(abi.DWT2_CDF97, 1, 0, 0, 0, scheme, [(0, 16, 16, 16)], abi.DWT2_FLAG_PERSISTENT)

@@ -25,7 +25,7 @@ def image():
     return x, oracle.forward97(x.astype(np.float64), LEVELS)
 
 
-@pytest.mark.parametrize("scheme", ["reduced", "sep", "nonsep", "polyconv", "conv"])
+@pytest.mark.parametrize("scheme", ["reduced", "sep", "nonsep", "polyconv", "conv", "nsconv"])
 def test_bench_workload_matches_oracle(image, scheme):
     x, ref = image
     xd = torch.from_numpy(x).cuda()

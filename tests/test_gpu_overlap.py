@@ -38,7 +38,7 @@ def _run(x, levels, scheme, coef_dtype, overlap, monkeypatch, choice=None, wavel
 
 @pytest.mark.parametrize("h,w,levels", [(2048, 2048, 5), (1031, 2050, 6), (300, 4100, 4), (4099, 130, 5),
                                         (66, 66, 3), (5000, 3000, 5)])
-@pytest.mark.parametrize("scheme", ["reduced", "sep", "conv"])
+@pytest.mark.parametrize("scheme", ["reduced", "sep", "conv", "nsconv"])
 def test_overlap_equals_grid_waits(h, w, levels, scheme, monkeypatch):
     x = synth.gradient(h, w, seed=h ^ w)
     a = _run(x, levels, scheme, torch.float32, True, monkeypatch)

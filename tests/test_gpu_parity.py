@@ -16,7 +16,7 @@ from tests.util import assert_fp32_close, assert_lowp_close
 pytestmark = pytest.mark.gpu
 
 SENT = -12345.0
-SCHEMES97 = ["nonsep", "reduced", "sep", "polyconv", "conv"]
+SCHEMES97 = ["nonsep", "reduced", "sep", "polyconv", "conv", "nsconv"]
 
 
 def _levels_max(h, w, cap):
