@@ -462,10 +462,25 @@ def run_ours(a):
         e2e_ms = ee0.elapsed_time(ee1) / a.e2e_steps
         e2e_ms = max_over_ranks(e2e_ms, pg, dev)
         ok = bool(torch.equal(hout[(a.e2e_steps - 1) % 2], coef.cpu()))
+
+        # the host link of this machine on the same buffers (one direction at a time), for context: the
+        # end-to-end figure is bounded by it and it differs between boxes
+        def link_gbs(dst, src):
+            with torch.cuda.stream(s_in):
+                dst.copy_(src, non_blocking=True)
+                l0 = torch.cuda.Event(enable_timing=True)
+                l1 = torch.cuda.Event(enable_timing=True)
+                l0.record(s_in)
+                for _ in range(3):
+                    dst.copy_(src, non_blocking=True)
+                l1.record(s_in)
+            l1.synchronize()
+            return 3 * 4 * n * n / (l0.elapsed_time(l1) * 1e-3) / 1e9
+        link = {"h2d_gbs": link_gbs(xd[0], hin), "d2h_gbs": link_gbs(hout[0], cd[0])}
         line["e2e"] = {"value": px / (e2e_ms * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": 4 * n * n,
                        "d2h_bytes_per_step": 4 * n * n, "steps": a.e2e_steps, "ms_per_step": e2e_ms,
                        "path": "pinned host -> dwt2_forward -> pinned host, pipelined over 2 buffer sets "
-                               "and 3 streams", "result_matches_device_run": ok}
+                               "and 3 streams", "result_matches_device_run": ok, "host_link": link}
         del hin, hout, xd, cd
 
     # schemes and precisions on the same image (level-1 kernel and whole pyramid)
@@ -527,6 +542,27 @@ def run_ours(a):
             comp[f"cdf53i/{scheme}/i32/L{a.levels}"] = {"gpx_s": n * n / (ms * 1e-3) / 1e9, "ms": ms}
             p.close()
             del out, xi
+        # inverse and adjoint of the same image (FP32 coefficients of the reduced scheme)
+        for levels in (1, a.levels):
+            p = make("reduced", torch.float32, levels)
+            coef = p.forward(x, None, stream)
+            back = torch.empty_like(x)
+            for name, fn in (("inverse", lambda: p.inverse(coef, back, stream)),
+                             ("adjoint", lambda: p.adjoint(coef, back, stream))):
+                ms = _time(fn, ksteps, stream, barrier)
+                abi.dwt2_profile(p.handle, True)
+                for _ in range(min(ksteps, 50)):
+                    fn()
+                barrier()
+                l1m = abi.dwt2_profile_read(p.handle, 1)[0]
+                abi.dwt2_profile(p.handle, False)
+                comp[f"{name}/reduced/f32/L{levels}"] = {
+                    "gpx_s": n * n / (ms * 1e-3) / 1e9, "ms": ms,
+                    "level1_gbs": 8 * n * n / (l1m * 1e-3) / 1e9,
+                    "level1_frac": 8 * n * n / (l1m * 1e-3) / 1e9 / peak}
+            assert p.status() == 0
+            p.close()
+            del coef, back
         comp.update(batch_and_grad(dev, stream, barrier))
         line["compare"] = comp
 

@@ -124,9 +124,10 @@ typedef struct {
  *              adjoint of a plan run the non-separable lifting kernels for
  *              the last three (the same transform).
  *   n_images   number of images (>= 1); images is a host array of that many
- *              descriptors, copied into the plan.  With several images (and
- *              a lifting scheme) dwt2_forward makes one launch per level for
- *              all images, the inverse and adjoint likewise.
+ *              descriptors, copied into the plan.  With several images
+ *              dwt2_forward runs each level as launches of up to 80 images
+ *              (the inverse and adjoint up to 200), whose parameter blocks are
+ *              built at the first call for a set of buffers and reused.
  *   flags      0 or DWT2_FLAG_PERSISTENT: dwt2_forward then runs every level of every
  *              image in one persistent launch whose units take work from a device
  *              queue and wait (bounded by DWT2_TIMEOUT_MS, default 2000) for the

@@ -418,8 +418,25 @@ __device__ __forceinline__ void fwd_signal(unsigned* ctr, int lane) {
 
 // One pyramid level, TMA-fed: the warps take their units from Pieces.  SPEC
 // compiles the specialised row loops for interior strips as well.
+// Register budget of the forward kernels: the lifting pipelines in 4-warp
+// blocks are held to five resident blocks per SM (at most 102 registers; the
+// 5-level 16384^2 pyramid measured ~1 % faster than with four), the other
+// pipelines and block sizes are left to the compiler.
+template <class Pipe, int NW>
+struct FwdMinBlocks {
+    static constexpr int value = 1;
+};
+template <int S, int QL>
+struct FwdMinBlocks<Fwd97<S, QL>, 4> {
+    static constexpr int value = 5;
+};
+template <int S, int QL>
+struct FwdMinBlocks<Fwd53<S, QL>, 4> {
+    static constexpr int value = 5;
+};
+
 template <class Pipe, class OutT, int QL, int QR, int NST, int NW, bool SPEC>
-__global__ void __launch_bounds__(NW * 32)
+__global__ void __launch_bounds__(NW * 32, FwdMinBlocks<Pipe, NW>::value)
     fwd_tma_kernel(const __grid_constant__ CUtensorMap tm_box, const __grid_constant__ CUtensorMap tm_row,
                    const FwdParams p, const FwdSync y) {
     using CT = typename Pipe::CT;
@@ -469,7 +486,8 @@ __global__ void __launch_bounds__(NW * 32)
 // level waits for what came before it; the others start as soon as the
 // previous launch has placed all its blocks.
 template <class Pipe, class OutT, int QL, int QR, int NST, int NW, bool SPEC>
-__global__ void __launch_bounds__(NW * 32) fwd_group_kernel(const __grid_constant__ GroupLaunch L) {
+__global__ void __launch_bounds__(NW * 32, FwdMinBlocks<Pipe, NW>::value)
+    fwd_group_kernel(const __grid_constant__ GroupLaunch L) {
     using CT = typename Pipe::CT;
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

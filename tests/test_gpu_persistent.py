@@ -135,8 +135,8 @@ def test_dropped_signal_times_out_without_hanging(monkeypatch):
 
 
 def test_batch_inverse_adjoint_and_l1():
-    """Multi-image plans run the inverse and adjoint as one launch per level
-    for all images (plan-time descriptor tables)."""
+    """Multi-image plans run the inverse and adjoint as grouped launches per
+    level (up to 200 images a launch)."""
     shapes = synth.batch_shapes(30, seed=11)
     buf, descs = _batch(shapes)
     xd = torch.from_numpy(buf).cuda()
@@ -175,7 +175,7 @@ def test_batch_inverse_adjoint_and_l1():
 
 @pytest.mark.parametrize("scheme,coef_dtype", [("reduced", torch.float32), ("sep", torch.float16),
                                                ("polyconv", torch.float32)])
-def test_level_major_batch_equals_single_image_plans(scheme, coef_dtype):
+def test_grouped_batch_equals_single_image_plans(scheme, coef_dtype):
     """A plan of several images runs each level as grouped launches (up to 80
     images per launch, every scheme); every image equals its own single-image
     plan bit for bit, for the default and for tuned configurations."""
@@ -206,7 +206,7 @@ def test_level_major_batch_equals_single_image_plans(scheme, coef_dtype):
             assert_lowp_close(got[i], ref, 3, 1e-3, f"image {i}")
 
 
-def test_level_major_batch_int53():
+def test_grouped_batch_int53():
     shapes = synth.batch_shapes(24, seed=12)
     buf, descs = _batch(shapes)
     bi = np.rint(buf).astype(np.int32)
