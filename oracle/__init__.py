@@ -6,8 +6,9 @@ not import it and shares no code with it.
 
 ``dwt2ref.c`` computes the separable lifting scheme of Barina et al.
 (arXiv:1704.08657, Background section: Eq. 2 and the separable lifting scheme
-"S_U^V | S_U^H | T_P^V | T_P^H") for CDF 9/7 in FP64 and the reversible integer
-CDF 5/3 in int64, multi-level, Mallat layout, whole-sample symmetric boundary.
+"S_U^V | S_U^H | T_P^V | T_P^H") for CDF 9/7 and DD 13/7 in FP64 and the
+reversible integer CDF 5/3 in int64, multi-level, Mallat layout, whole-sample
+symmetric boundary.
 ``polyphase.py`` holds the paper's 4x4 polyphase matrices over Laurent
 polynomials (Background, Proposed Schemes, Optimization Approach, Table 1).
 """
@@ -57,7 +58,8 @@ def _load():
             L = ctypes.c_long
             for name, p in (("dwt2ref_forward_f64", dp), ("dwt2ref_inverse_f64", dp),
                             ("dwt2ref_adjoint_f64", dp), ("dwt2ref_forward_i64", ip),
-                            ("dwt2ref_inverse_i64", ip)):
+                            ("dwt2ref_inverse_i64", ip), ("dwt2ref_forward_dd137_f64", dp),
+                            ("dwt2ref_inverse_dd137_f64", dp)):
                 f = getattr(lib, name)
                 f.argtypes = [p, p, L, L, ctypes.c_int]
                 f.restype = ctypes.c_int
@@ -95,6 +97,16 @@ def inverse97(c: np.ndarray, levels: int = 1) -> np.ndarray:
 def adjoint97(g: np.ndarray, levels: int = 1) -> np.ndarray:
     """Transpose of :func:`forward97` applied to a coefficient-domain array."""
     return _call("dwt2ref_adjoint_f64", g, levels, np.float64)
+
+
+def forward137(x: np.ndarray, levels: int = 1) -> np.ndarray:
+    """DD 13/7 forward pyramid in FP64, Mallat layout (no scaling step)."""
+    return _call("dwt2ref_forward_dd137_f64", x, levels, np.float64)
+
+
+def inverse137(c: np.ndarray, levels: int = 1) -> np.ndarray:
+    """Inverse of :func:`forward137`."""
+    return _call("dwt2ref_inverse_dd137_f64", c, levels, np.float64)
 
 
 def forward53i(x: np.ndarray, levels: int = 1) -> np.ndarray:

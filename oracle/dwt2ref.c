@@ -34,6 +34,15 @@
  *     j + b*ceil(w/2) of the level's h x w region; the next level works on the
  *     top-left ceil(h/2) x ceil(w/2) low-low region.
  *   - Every level's input must have both sides >= 2.
+ *   - DD 13/7 (Deslauriers-Dubuc interpolating wavelet, the paper's third
+ *     wavelet in Table 1; its constants are not printed there): one lifting
+ *     pair with the 4-tap cubic-interpolation predict
+ *     d[n] = x[2n+1] - (9 (x[2n] + x[2n+2]) - (x[2n-2] + x[2n+4])) / 16 and the
+ *     4-tap update s[n] = x[2n] + (9 (d[n-1] + d[n]) - (d[n-2] + d[n+1])) / 32,
+ *     which multiply out to the 13-tap low-pass and 7-tap high-pass filters;
+ *     no scaling step (low-pass DC gain 1).  Reflections may reach up to three
+ *     samples outside a row, so these steps fold indices with the periodic
+ *     whole-sample rule.
  *
  * The adjoint (not in the paper) is the product of the transposed steps in
  * reverse order; each transposed step is written as the scatter that mirrors
@@ -258,6 +267,65 @@ static int level97_adjoint(double* x, long h, long w, long ld) {
     return REF_OK;
 }
 
+/* ------------------------------------------------------------ DD 13/7 ---- */
+/* Four-tap lifting steps: a near pair at distance 1 and a far pair at distance
+ * 3 (in samples) around the updated sample, weights (near, far). */
+static const double kdd_pred[2] = {-9.0 / 16.0, 1.0 / 16.0};
+static const double kdd_upd[2] = {9.0 / 32.0, -1.0 / 32.0};
+
+/* whole-sample symmetric reflection of any index into [0, n) (n >= 2) */
+static long fold(long k, long n) {
+    const long per = 2 * (n - 1);
+    long m = k % per;
+    if (m < 0) m += per;
+    return m < n ? m : per - m;
+}
+
+/* x[c] += a0 (x[c-1] + x[c+1]) + a1 (x[c-3] + x[c+3]) for c = first, first+2, ...
+ * along rows */
+static void lift4_rows(double* x, long h, long w, long ld, long first, const double* a) {
+#pragma omp parallel for schedule(static)
+    for (long r = 0; r < h; ++r) {
+        double* row = x + r * ld;
+        for (long c = first; c < w; c += 2)
+            row[c] += a[0] * (row[fold(c - 1, w)] + row[fold(c + 1, w)]) +
+                      a[1] * (row[fold(c - 3, w)] + row[fold(c + 3, w)]);
+    }
+}
+
+/* the same along columns, rows r = first, first+2, ... */
+static void lift4_cols(double* x, long h, long w, long ld, long first, const double* a) {
+#pragma omp parallel for schedule(static)
+    for (long r = first; r < h; r += 2) {
+        double* row = x + r * ld;
+        const double* u1 = x + fold(r - 1, h) * ld;
+        const double* d1 = x + fold(r + 1, h) * ld;
+        const double* u3 = x + fold(r - 3, h) * ld;
+        const double* d3 = x + fold(r + 3, h) * ld;
+        for (long c = 0; c < w; ++c) row[c] += a[0] * (u1[c] + d1[c]) + a[1] * (u3[c] + d3[c]);
+    }
+}
+
+/* One level of DD 13/7 separable lifting: T_P^H, T_P^V, S_U^H, S_U^V. */
+static int level137_forward(double* x, long h, long w, long ld) {
+    lift4_rows(x, h, w, ld, 1, kdd_pred);
+    lift4_cols(x, h, w, ld, 1, kdd_pred);
+    lift4_rows(x, h, w, ld, 0, kdd_upd);
+    lift4_cols(x, h, w, ld, 0, kdd_upd);
+    return pack_f64(x, h, w, ld);
+}
+
+static int level137_inverse(double* x, long h, long w, long ld) {
+    int rc = unpack_f64(x, h, w, ld);
+    if (rc) return rc;
+    const double nu[2] = {-kdd_upd[0], -kdd_upd[1]}, np[2] = {-kdd_pred[0], -kdd_pred[1]};
+    lift4_cols(x, h, w, ld, 0, nu);
+    lift4_rows(x, h, w, ld, 0, nu);
+    lift4_cols(x, h, w, ld, 1, np);
+    lift4_rows(x, h, w, ld, 1, np);
+    return REF_OK;
+}
+
 /* level sizes: sizes[l] = input side of level l (l = 0 .. levels-1) */
 static void level_sides(long n, int levels, long* sides) {
     for (int l = 0; l < levels; ++l) {
@@ -309,6 +377,38 @@ int dwt2ref_adjoint_f64(const double* gcoef, double* gin, long h, long w, int le
     level_sides(w, levels, wsz);
     for (int l = levels - 1; l >= 0; --l) {
         rc = level97_adjoint(gin, hs[l], wsz[l], w);
+        if (rc) return rc;
+    }
+    return REF_OK;
+}
+
+int dwt2ref_forward_dd137_f64(const double* in, double* out, long h, long w, int levels) {
+    int rc = check_levels(h, w, levels);
+    if (rc) return rc;
+    if (!in || !out) return REF_ERR_ARG;
+    if (out != in) memcpy(out, in, sizeof(double) * (size_t)h * (size_t)w);
+    long hs[64], wsz[64];
+    if (levels > 64) return REF_ERR_LEVELS;
+    level_sides(h, levels, hs);
+    level_sides(w, levels, wsz);
+    for (int l = 0; l < levels; ++l) {
+        rc = level137_forward(out, hs[l], wsz[l], w);
+        if (rc) return rc;
+    }
+    return REF_OK;
+}
+
+int dwt2ref_inverse_dd137_f64(const double* coef, double* out, long h, long w, int levels) {
+    int rc = check_levels(h, w, levels);
+    if (rc) return rc;
+    if (!coef || !out) return REF_ERR_ARG;
+    if (out != coef) memcpy(out, coef, sizeof(double) * (size_t)h * (size_t)w);
+    long hs[64], wsz[64];
+    if (levels > 64) return REF_ERR_LEVELS;
+    level_sides(h, levels, hs);
+    level_sides(w, levels, wsz);
+    for (int l = levels - 1; l >= 0; --l) {
+        rc = level137_inverse(out, hs[l], wsz[l], w);
         if (rc) return rc;
     }
     return REF_OK;

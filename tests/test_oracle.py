@@ -57,25 +57,27 @@ def _fold(k, n):
     return k if k < n else p - k
 
 
-def _conv_matrix_1d(n, l9=L9, h7=H7):
-    """n x n analysis matrix: rows 0..ceil(n/2)-1 low-pass, then high-pass."""
+def _conv_matrix_1d(n, lo=L9, hi=H7):
+    """n x n analysis matrix: rows 0..ceil(n/2)-1 low-pass, then high-pass
+    (odd-length symmetric filters, centred on the even / odd sample)."""
     nl = (n + 1) // 2
+    cl, ch = len(lo) // 2, len(hi) // 2
     A = np.zeros((n, n))
     for i in range(nl):
-        for k in range(-4, 5):
-            A[i, _fold(2 * i + k, n)] += l9[k + 4]
+        for k in range(-cl, cl + 1):
+            A[i, _fold(2 * i + k, n)] += lo[k + cl]
     for i in range(n // 2):
-        for k in range(-3, 4):
-            A[nl + i, _fold(2 * i + 1 + k, n)] += h7[k + 3]
+        for k in range(-ch, ch + 1):
+            A[nl + i, _fold(2 * i + 1 + k, n)] += hi[k + ch]
     return A
 
 
-def _conv_dwt2(x, levels):
+def _conv_dwt2(x, levels, lo=L9, hi=H7):
     """Direct-convolution 2-D pyramid (rows, then columns), Mallat layout."""
     y = np.array(x, dtype=np.float64)
     h, w = y.shape
     for _ in range(levels):
-        Ah, Av = _conv_matrix_1d(w), _conv_matrix_1d(h)
+        Ah, Av = _conv_matrix_1d(w, lo, hi), _conv_matrix_1d(h, lo, hi)
         y[:h, :w] = Av @ y[:h, :w] @ Ah.T
         h, w = (h + 1) // 2, (w + 1) // 2
     return y
@@ -277,3 +279,64 @@ def test_oracle_adjoint_is_the_gradient_fp64():
 
     x = torch.from_numpy(RNG.standard_normal((32, 32))).requires_grad_(True)
     assert torch.autograd.gradcheck(F.apply, (x,), eps=1e-6, atol=1e-8, rtol=1e-6, fast_mode=True)
+
+
+# ------------------------------------------------------------------ DD 13/7
+# The interpolating Deslauriers-Dubuc 13/7 filter bank as published (13-tap
+# analysis low-pass / 512 and 7-tap high-pass / 16): an independent statement
+# of what the oracle's two 4-tap lifting steps must multiply out to.
+L13 = np.array([-1, 0, 18, -16, -63, 144, 348, 144, -63, -16, 18, 0, -1], dtype=np.float64) / 512.0
+H7DD = np.array([1, 0, -9, 16, -9, 0, 1], dtype=np.float64) / 16.0
+
+
+def test_dd137_closed_form_taps_sane():
+    # symmetric, low-pass DC gain 1, high-pass kills cubics (4 vanishing moments)
+    assert np.array_equal(L13, L13[::-1]) and np.array_equal(H7DD, H7DD[::-1])
+    assert L13.sum() == 1.0
+    k = np.arange(-3, 4)
+    for p in range(4):
+        assert (H7DD * k ** p).sum() == 0.0
+
+
+@pytest.mark.parametrize("h,w", [(16, 16), (17, 23), (8, 9), (2, 2), (3, 5), (2, 7), (5, 2), (33, 64), (4, 6)])
+def test_forward137_equals_closed_form_convolution(h, w):
+    x = RNG.uniform(0, 255, size=(h, w))
+    ref = _conv_dwt2(x, 1, L13, H7DD)
+    got = oracle.forward137(x, 1)
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(x).max()
+
+
+@pytest.mark.parametrize("h,w,levels", [(64, 64, 5), (40, 27, 3), (9, 13, 2), (8, 8, 3)])
+def test_forward137_pyramid_equals_closed_form(h, w, levels):
+    x = RNG.uniform(0, 255, size=(h, w))
+    ref = _conv_dwt2(x, levels, L13, H7DD)
+    assert np.abs(oracle.forward137(x, levels) - ref).max() <= 1e-11 * np.abs(x).max()
+
+
+def test_dd137_dense_operator_is_kron_of_1d_filter_banks():
+    for (h, w) in [(8, 8), (7, 9)]:
+        M = _dense(lambda e: oracle.forward137(e, 1), h, w)
+        K = np.kron(_conv_matrix_1d(h, L13, H7DD), _conv_matrix_1d(w, L13, H7DD))
+        assert np.abs(M - K).max() < 1e-13
+
+
+@pytest.mark.parametrize("h,w,levels", [(32, 32, 1), (45, 38, 4), (2, 3, 1), (128, 96, 5)])
+def test_perfect_reconstruction137(h, w, levels):
+    x = RNG.uniform(-100, 300, size=(h, w))
+    y = oracle.inverse137(oracle.forward137(x, levels), levels)
+    assert np.abs(y - x).max() <= 1e-11 * np.abs(x).max()
+
+
+def test_dd137_constant_and_cubic():
+    # a constant keeps every detail exactly 0 and the low-low value (DC gain 1)
+    y = oracle.forward137(np.full((21, 30), 117.0), 3)
+    for lev, name, rs, cs in oracle.band_slices(21, 30, 3):
+        assert np.all(y[rs, cs] == (117.0 if name == "LL" else 0.0))
+    # a cubic along the rows has no horizontal detail away from the mirror kinks
+    h, w = 24, 64
+    j = np.arange(w, dtype=np.float64)
+    x = np.tile(0.002 * j ** 3 - 0.1 * j ** 2 + 3.0 * j + 7.0, (h, 1))
+    y = oracle.forward137(x, 1)
+    hl = y[:(h + 1) // 2, (w + 1) // 2:]
+    m = 3
+    assert np.abs(hl[:, m:hl.shape[1] - m]).max() <= 1e-12 * np.abs(x).max()
