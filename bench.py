@@ -523,6 +523,24 @@ def run_ours(a):
                     "level1_frac": bpp * n * n / (l1m * 1e-3) / 1e9 / peak}
                 p.close()
                 del out
+        for scheme in ("nonsep", "sep"):  # the DD 13/7 wavelet (one 4-tap pair, no scaling)
+            for levels in (1, a.levels):
+                p = make(scheme, torch.float32, levels, "dd137")
+                out = torch.empty_like(x)
+                p.autotune(x, out, stream)
+                ms = _time(lambda: p.forward(x, out, stream), ksteps, stream, barrier)
+                abi.dwt2_profile(p.handle, True)
+                for _ in range(min(ksteps, 50)):
+                    p.forward(x, out, stream)
+                barrier()
+                l1m = abi.dwt2_profile_read(p.handle, 1)[0]
+                abi.dwt2_profile(p.handle, False)
+                assert p.status() == 0
+                comp[f"dd137/{scheme}/f32/L{levels}"] = {
+                    "gpx_s": n * n / (ms * 1e-3) / 1e9, "ms": ms,
+                    "level1_frac": 8 * n * n / (l1m * 1e-3) / 1e9 / peak}
+                p.close()
+                del out
         for scheme in ("nonsep", "sep"):
             xi = torch.from_numpy(synth.to_int(x_host)).to(dev)
             p = make(scheme, torch.int32, a.levels, "cdf53")

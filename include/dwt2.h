@@ -10,7 +10,11 @@
  * Eq. 2, the spatial predict T_P then the spatial update S_U (the
  * non-separable lifting "S_U | T_P"), then scaling.  CDF 9/7 has two pairs
  * (alpha, beta), (gamma, delta) with P = a(1 + z), U = b(1 + z^-1) and scaling
- * zeta; the integer-reversible CDF 5/3 has one pair with floor rounding.
+ * zeta; the integer-reversible CDF 5/3 has one pair with floor rounding; the
+ * interpolating Deslauriers-Dubuc DD 13/7 (Table 1's third wavelet, its
+ * constants from the published filter bank) has one pair with the 4-tap
+ * P = -(9/16)(1 + z) + (1/16)(z^-1 + z^2), U = (9/32)(1 + z^-1) -
+ * (1/32)(z + z^-2) and no scaling step.
  * All schemes compute the same values (Proposed Schemes); the scheme only
  * selects the kernel:
  *   DWT2_NONSEP          spatial predict / update, all terms in one step;
@@ -70,7 +74,7 @@ extern "C" {
 
 typedef struct dwt2_plan_s* dwt2_plan_t;
 
-enum dwt2_wavelet { DWT2_CDF97 = 0, DWT2_CDF53_INT = 1 };
+enum dwt2_wavelet { DWT2_CDF97 = 0, DWT2_CDF53_INT = 1, DWT2_DD137 = 2 };
 enum dwt2_dtype { DWT2_F32 = 0, DWT2_F16 = 1, DWT2_BF16 = 2, DWT2_I32 = 3 };
 enum dwt2_scheme {
     DWT2_NONSEP = 0,
@@ -110,14 +114,16 @@ typedef struct {
 /*
  * dwt2_plan -- validate a transform and prepare its launches.
  *   out        receives the plan (set to NULL on error).
- *   wavelet    DWT2_CDF97 or DWT2_CDF53_INT.
+ *   wavelet    DWT2_CDF97, DWT2_CDF53_INT or DWT2_DD137.
  *   levels     number of pyramid levels, >= 1.
  *   boundary   DWT2_SYMMETRIC.
- *   in_dtype   image element type: DWT2_F32 for CDF 9/7, DWT2_I32 for 5/3.
- *   coef_dtype coefficient element type: F32, F16 or BF16 for CDF 9/7 (the
- *              lifting always runs in FP32 and intermediate LL bands are kept
- *              in FP32), I32 for CDF 5/3.
- *   scheme     DWT2_NONSEP, DWT2_NONSEP_REDUCED (CDF 9/7 only),
+ *   in_dtype   image element type: DWT2_F32 for CDF 9/7 and DD 13/7,
+ *              DWT2_I32 for 5/3.
+ *   coef_dtype coefficient element type: F32, F16 or BF16 for CDF 9/7 and
+ *              DD 13/7 (the lifting always runs in FP32 and intermediate LL
+ *              bands are kept in FP32), I32 for CDF 5/3.
+ *   scheme     DWT2_NONSEP, DWT2_NONSEP_REDUCED (CDF 9/7 only; DD 13/7 takes
+ *              DWT2_NONSEP and DWT2_SEP_LIFTING, not DWT2_FLAG_PERSISTENT),
  *              DWT2_SEP_LIFTING, DWT2_POLYCONV, DWT2_CONV or DWT2_NONSEP_CONV
  *              (the last three CDF 9/7 only and not with
  *              DWT2_FLAG_PERSISTENT: DWT2_ERR_UNSUPPORTED).  The inverse and
@@ -228,8 +234,9 @@ int dwt2_profile_read(dwt2_plan_t plan, float* ms, int n);
  * that cannot allocate when they transform, e.g. code running during a CUDA
  * graph capture that forbids cudaMalloc, real-time pipelines that allow no
  * allocation after start-up, or plug-ins whose host owns all device memory).
- *   wavelet, levels, scheme, coef_dtype  as for dwt2_plan (in_dtype follows
- *              the wavelet: F32 for CDF 9/7, I32 for CDF 5/3).
+ *   wavelet, levels, scheme, coef_dtype  as for dwt2_plan, CDF 9/7 or CDF 5/3
+ *              only (in_dtype follows the wavelet: F32 for CDF 9/7, I32 for
+ *              CDF 5/3).
  *   h, w, pitch_elems  the image; pitch a multiple of 4 elements.
  *   in         device pointer to the image, 16-byte aligned, read only.
  *   coef       device pointer to the coefficients (Mallat layout, same pitch).

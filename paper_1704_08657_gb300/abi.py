@@ -12,7 +12,7 @@ import os
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libdwt2.so")
 
-DWT2_CDF97, DWT2_CDF53_INT = 0, 1
+DWT2_CDF97, DWT2_CDF53_INT, DWT2_DD137 = 0, 1, 2
 DWT2_F32, DWT2_F16, DWT2_BF16, DWT2_I32 = 0, 1, 2, 3
 DWT2_NONSEP, DWT2_NONSEP_REDUCED, DWT2_SEP_LIFTING, DWT2_POLYCONV, DWT2_CONV, DWT2_NONSEP_CONV = 0, 1, 2, 3, 4, 5
 DWT2_SYMMETRIC = 0

@@ -236,8 +236,8 @@ int build_persistent(dwt2_plan_t p) {
             const LevelGeom& g = ip.lv[l];
             PmlDesc d;
             d.h = g.h, d.w = g.w, d.hq = g.hq, d.wq = g.wq, d.hh = g.hh, d.wh = g.wh;
-            d.n_strips = (g.wq + fwd_out_quads(FwdCfg{PML_QL, PML_QR, PML_NST, PML_NW, 0}) - 1) /
-                         fwd_out_quads(FwdCfg{PML_QL, PML_QR, PML_NST, PML_NW, 0});
+            d.n_strips = (g.wq + fwd_out_quads(FwdCfg{PML_QL, PML_QR, PML_NST, PML_NW, 0}, p->wavelet) - 1) /
+                         fwd_out_quads(FwdCfg{PML_QL, PML_QR, PML_NST, PML_NW, 0}, p->wavelet);
             d.seg_rows = std::min(p->pml_seg, g.hq);
             const int n_segs = (g.hq + d.seg_rows - 1) / d.seg_rows;
             d.src_is_ws = l > 0;
@@ -384,7 +384,7 @@ int inv_group_build(dwt2_plan_t p, const void* coef, void* out, void* workspace,
             for (int k = 0; k < INV_GROUP_MAX && i0 + k < n; ++k) {
                 const ImagePlan& ip = p->imgs[order[i0 + k]];
                 InvParams ipm = inv_level_params(p, ip, l, coef, out, workspace, csz, false, 0.f);
-                ipm.n_strips = (ipm.wq + INV_OUT_Q - 1) / INV_OUT_Q;
+                ipm.n_strips = (ipm.wq + inv_out_quads(p->wavelet) - 1) / inv_out_quads(p->wavelet);
                 ipm.seg_rows = std::min(p->seg_env > 0 ? p->seg_env : INV_GROUP_SEG, ipm.hq);
                 ipm.n_segs = (ipm.hq + ipm.seg_rows - 1) / ipm.seg_rows;
                 ipm.n_units = ipm.n_segs * ipm.n_strips;
@@ -566,7 +566,7 @@ LevelLaunch level_launch(dwt2_plan_t p, const ImagePlan& ip, int l) {
         seg = TUNE_SEGS[cand % N_TUNE_SEGS];
     }
     const FwdCfg& cfg = FWD_CFGS[ll.ci];
-    ll.dc = decompose(ip.lv[l], fwd_out_quads(cfg), p->sm_count, p->cfg_bps[ll.ci], cfg.nw, seg, p->balanced_env,
+    ll.dc = decompose(ip.lv[l], fwd_out_quads(cfg, p->wavelet), p->sm_count, p->cfg_bps[ll.ci], cfg.nw, seg, p->balanced_env,
                       &ll.grid, &ll.balanced);
     return ll;
 }
@@ -628,7 +628,7 @@ int group_build(dwt2_plan_t p, const void* in, void* coef, void* workspace) {
         }
         if (seg <= 0) seg = GROUP_SEG_DEFAULT;
         const FwdCfg& cfg = FWD_CFGS[ci];
-        const int outq = fwd_out_quads(cfg);
+        const int outq = fwd_out_quads(cfg, p->wavelet);
         for (int i0 = 0; i0 < n; i0 += GROUP_MAX) {
             std::unique_ptr<GroupLaunch> g(new (std::nothrow) GroupLaunch());
             if (!g) return DWT2_ERR_INVALID_ARG;
@@ -786,7 +786,7 @@ int dwt2_plan(dwt2_plan_t* out, int wavelet, int levels, int boundary, int in_dt
     *out = nullptr;
     if (!images || n_images < 1 || levels < 1 || levels > 30) return DWT2_ERR_INVALID_ARG;
     if (boundary != DWT2_SYMMETRIC) return DWT2_ERR_INVALID_ARG;
-    if (wavelet != DWT2_CDF97 && wavelet != DWT2_CDF53_INT) return DWT2_ERR_INVALID_ARG;
+    if (wavelet != DWT2_CDF97 && wavelet != DWT2_CDF53_INT && wavelet != DWT2_DD137) return DWT2_ERR_INVALID_ARG;
     if (scheme < DWT2_NONSEP || scheme > DWT2_NONSEP_CONV) return DWT2_ERR_INVALID_ARG;
     if (in_dtype < DWT2_F32 || in_dtype > DWT2_I32 || coef_dtype < DWT2_F32 || coef_dtype > DWT2_I32)
         return DWT2_ERR_INVALID_ARG;
@@ -794,6 +794,11 @@ int dwt2_plan(dwt2_plan_t* out, int wavelet, int levels, int boundary, int in_dt
     if ((flags & DWT2_FLAG_PERSISTENT) && scheme > DWT2_SEP_LIFTING) return DWT2_ERR_UNSUPPORTED;
     if (wavelet == DWT2_CDF97) {
         if (in_dtype != DWT2_F32 || coef_dtype == DWT2_I32) return DWT2_ERR_UNSUPPORTED;
+    } else if (wavelet == DWT2_DD137) {
+        if (in_dtype != DWT2_F32 || coef_dtype == DWT2_I32) return DWT2_ERR_UNSUPPORTED;
+        // the lifting schemes (no reduced split, no filter-bank form) and no persistent launch
+        if (scheme != DWT2_NONSEP && scheme != DWT2_SEP_LIFTING) return DWT2_ERR_UNSUPPORTED;
+        if (flags & DWT2_FLAG_PERSISTENT) return DWT2_ERR_UNSUPPORTED;
     } else {
         if (in_dtype != DWT2_I32 || coef_dtype != DWT2_I32) return DWT2_ERR_UNSUPPORTED;
         if (scheme == DWT2_NONSEP_REDUCED) return DWT2_ERR_UNSUPPORTED;  // floor does not split
@@ -1007,7 +1012,7 @@ static int run_inverse_like(dwt2_plan_t p, const void* coef, void* out, void* wo
         for (const ImagePlan& ip : p->imgs) {
             InvParams ipm = inv_level_params(p, ip, l, coef, out, workspace, csz, l1, l1_scale);
             int grid = 0, balanced = 0;
-            const Decomp dc = decompose(ip.lv[l], INV_OUT_Q, p->sm_count, inv_bps, INV_NW, p->seg_env,
+            const Decomp dc = decompose(ip.lv[l], inv_out_quads(p->wavelet), p->sm_count, inv_bps, INV_NW, p->seg_env,
                                         p->balanced_env, &grid, &balanced);
             ipm.n_strips = dc.n_strips, ipm.seg_rows = dc.seg_rows, ipm.n_segs = dc.n_segs, ipm.n_units = dc.n_units;
             ipm.balanced = balanced;

@@ -12,7 +12,7 @@ namespace dwt2 {
 enum : unsigned { DEV_TIMEOUT = 1u, DEV_CHECK = 2u };
 
 enum { SCHEME_NONSEP = 0, SCHEME_REDUCED = 1, SCHEME_SEP = 2, SCHEME_POLYCONV = 3, SCHEME_CONV = 4, SCHEME_NSCONV = 5 };
-enum { WAV_CDF97 = 0, WAV_CDF53I = 1 };
+enum { WAV_CDF97 = 0, WAV_CDF53I = 1, WAV_DD137 = 2 };
 enum { DT_F32 = 0, DT_F16 = 1, DT_BF16 = 2, DT_I32 = 3 };
 
 // One forward level.  Input pixels come through the two tensor maps; the
@@ -175,7 +175,10 @@ struct FwdCfg {
 };
 
 // geometry of a strip: 64*ql pixels loaded, 32*ql - 4 quads output
-inline int fwd_out_quads(const FwdCfg& c) { return 32 * c.ql - 4; }
+// halo quads on each side of a strip per wavelet (2; 4 for DD 13/7) and the
+// quads a forward strip outputs
+inline int wav_halo(int wav) { return wav == WAV_DD137 ? 4 : 2; }
+inline int fwd_out_quads(const FwdCfg& c, int wav) { return 32 * c.ql - 2 * wav_halo(wav); }
 inline int fwd_strip_px(const FwdCfg& c) { return 64 * c.ql; }
 
 // kernel launchers, one translation unit per coefficient type; they return a
@@ -229,5 +232,6 @@ constexpr int INV_NW = 4;
 constexpr int INV_QL = 2;
 constexpr int INV_QR = 3, INV_NST = 3;  // staged inverse / adjoint ring
 constexpr int INV_OUT_Q = 32 * INV_QL - 4;
+inline int inv_out_quads(int wav) { return 32 * INV_QL - 2 * wav_halo(wav); }
 
 }  // namespace dwt2

@@ -17,7 +17,7 @@ int launch_inv_group_bf16(int wav, int scheme, const InvGroupLaunch& g, int grid
 }
 
 int occupancy_forward_bf16(int wav, int scheme, const FwdCfg& cfg) { return occupancy_forward_t<__nv_bfloat16>(wav, scheme, cfg); }
-int occupancy_inverse_bf16(int scheme) { return occupancy_inverse_t<__nv_bfloat16>(scheme); }
+int occupancy_inverse_bf16(int wav, int scheme) { return occupancy_inverse_t<__nv_bfloat16>(wav, scheme); }
 
 int launch_pml_bf16(int wav, int scheme, const PmlLaunch& p, int grid, cudaStream_t s) {
     return launch_pml_t<__nv_bfloat16>(wav, scheme, &p, grid, s, false);

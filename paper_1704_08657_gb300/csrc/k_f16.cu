@@ -17,7 +17,7 @@ int launch_inv_group_f16(int wav, int scheme, const InvGroupLaunch& g, int grid,
 }
 
 int occupancy_forward_f16(int wav, int scheme, const FwdCfg& cfg) { return occupancy_forward_t<__half>(wav, scheme, cfg); }
-int occupancy_inverse_f16(int scheme) { return occupancy_inverse_t<__half>(scheme); }
+int occupancy_inverse_f16(int wav, int scheme) { return occupancy_inverse_t<__half>(wav, scheme); }
 
 int launch_pml_f16(int wav, int scheme, const PmlLaunch& p, int grid, cudaStream_t s) {
     return launch_pml_t<__half>(wav, scheme, &p, grid, s, false);

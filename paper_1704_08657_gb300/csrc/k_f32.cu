@@ -17,7 +17,7 @@ int launch_inv_group_f32(int wav, int scheme, const InvGroupLaunch& g, int grid,
 }
 
 int occupancy_forward_f32(int wav, int scheme, const FwdCfg& cfg) { return occupancy_forward_t<float>(wav, scheme, cfg); }
-int occupancy_inverse_f32(int scheme) { return occupancy_inverse_t<float>(scheme); }
+int occupancy_inverse_f32(int wav, int scheme) { return occupancy_inverse_t<float>(wav, scheme); }
 
 int launch_pml_f32(int wav, int scheme, const PmlLaunch& p, int grid, cudaStream_t s) {
     return launch_pml_t<float>(wav, scheme, &p, grid, s, false);
@@ -47,9 +47,9 @@ int launch_adjoint_f32(const InvParams& p, int grid, cudaStream_t s) {
 int occupancy_forward_f16(int wav, int scheme, const FwdCfg& cfg);
 int occupancy_forward_bf16(int wav, int scheme, const FwdCfg& cfg);
 int occupancy_forward_i32(int wav, int scheme, const FwdCfg& cfg);
-int occupancy_inverse_f16(int scheme);
-int occupancy_inverse_bf16(int scheme);
-int occupancy_inverse_i32(int scheme);
+int occupancy_inverse_f16(int wav, int scheme);
+int occupancy_inverse_bf16(int wav, int scheme);
+int occupancy_inverse_i32(int wav, int scheme);
 
 int forward_blocks_per_sm(int wav, int scheme, int coef_dtype, const FwdCfg& cfg) {
     switch (coef_dtype) {
@@ -91,13 +91,12 @@ int fused_blocks_per_sm(int wav, int scheme, int coef_dtype) {
 }
 
 int inverse_blocks_per_sm(int wav, int scheme, int coef_dtype, bool adjoint) {
-    (void)wav;
     if (adjoint) return occupancy_inv_one<Adj97<INV_QL>, float, true>();
     switch (coef_dtype) {
-        case DT_F32: return occupancy_inverse_f32(scheme);
-        case DT_F16: return occupancy_inverse_f16(scheme);
-        case DT_BF16: return occupancy_inverse_bf16(scheme);
-        default: return occupancy_inverse_i32(scheme);
+        case DT_F32: return occupancy_inverse_f32(wav, scheme);
+        case DT_F16: return occupancy_inverse_f16(wav, scheme);
+        case DT_BF16: return occupancy_inverse_bf16(wav, scheme);
+        default: return occupancy_inverse_i32(wav, scheme);
     }
 }
 

@@ -17,7 +17,7 @@ int launch_inv_group_i32(int wav, int scheme, const InvGroupLaunch& g, int grid,
 }
 
 int occupancy_forward_i32(int wav, int scheme, const FwdCfg& cfg) { return occupancy_forward_t<int>(wav, scheme, cfg); }
-int occupancy_inverse_i32(int scheme) { return occupancy_inverse_t<int>(scheme); }
+int occupancy_inverse_i32(int wav, int scheme) { return occupancy_inverse_t<int>(wav, scheme); }
 
 int launch_pml_i32(int wav, int scheme, const PmlLaunch& p, int grid, cudaStream_t s) {
     return launch_pml_t<int>(wav, scheme, &p, grid, s, false);

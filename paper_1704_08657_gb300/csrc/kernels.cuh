@@ -229,11 +229,11 @@ struct CpAsyncLoader {
 // columns are filled in the stage (fwd_fix_edges) and per-lane masks drop the
 // quads outside the bands.
 template <class P>
-__device__ __forceinline__ bool fwd_pairs_ok(const P& p, int x0, int QL) {
+__device__ __forceinline__ bool fwd_pairs_ok(const P& p, int x0, int QL, int halo) {
     // every pair starts at an even quad: with both band widths even no pair
     // straddles a band's last column; otherwise the strip must end inside both
     return p.vec_lo && p.vec_hi && (p.ll_is_ct || p.vec_ll) &&
-           ((p.wq % 2 == 0 && p.wh % 2 == 0) || (x0 / 2 + 32 * QL - HALO_Q <= p.wh));
+           ((p.wq % 2 == 0 && p.wh % 2 == 0) || (x0 / 2 + 32 * QL - halo <= p.wh));
 }
 
 template <class Pipe, class OutT, int QL, int QR, int NST, int MODE = 0, class P, class Loader>
@@ -242,17 +242,18 @@ __device__ __forceinline__ bool fwd_unit(const P& p, const Loader& ld, int s, in
     using CT = typename Pipe::CT;
     using R = Row<CT, QL>;
     constexpr int SPX = 64 * QL;
-    constexpr int OUTQ = 32 * QL - 2 * HALO_Q;
+    constexpr int HQ = PipeGeom<Pipe>::HALO, WARM = PipeGeom<Pipe>::WARM;
+    constexpr int OUTQ = 32 * QL - 2 * HQ;
     constexpr int ROWS = 2 * QR;
     constexpr int STAGE_ELEMS = ROWS * SPX;
     static_assert(PHASES % QR == 0, "a group of arrivals must cover whole stages");
     static_assert(QL % 2 == 0, "band stores go in pairs");
 
-    const int A0 = R0 - 2;                            // first quad row streamed
-    const int n_arr = (R1 - R0) + 2 + Pipe::LAG;      // quad rows streamed
+    const int A0 = R0 - WARM;                         // first quad row streamed
+    const int n_arr = (R1 - R0) + WARM + Pipe::LAG;   // quad rows streamed
     const int n_grp = (n_arr + PHASES - 1) / PHASES;  // groups of arrivals (the last may stop early)
     const int NT = (n_arr + QR - 1) / QR;             // stages
-    const int x0 = s * (2 * OUTQ) - 2 * HALO_Q;       // first pixel (multiple of 4)
+    const int x0 = s * (2 * OUTQ) - 2 * HQ;           // first pixel (multiple of 4)
     const int jb = x0 / 2 + QL * lane;                // first quad column of the lane
     constexpr bool SPEC = MODE != 0;
     const bool edge = (x0 < 0) || (x0 + SPX > p.w);
@@ -263,7 +264,7 @@ __device__ __forceinline__ bool fwd_unit(const P& p, const Loader& ld, int s, in
 #pragma unroll
     for (int q = 0; q < QL; ++q) {
         const int lq = QL * lane + q;
-        mp[q] = (lq >= HALO_Q) && (lq < 32 * QL - HALO_Q);
+        mp[q] = (lq >= HQ) && (lq < 32 * QL - HQ);
         ev[q] = mp[q] && (jb + q < p.wq);
         dv[q] = mp[q] && (jb + q < p.wh);
     }
@@ -276,7 +277,7 @@ __device__ __forceinline__ bool fwd_unit(const P& p, const Loader& ld, int s, in
         po[q / 2] = mp[q] && mp[q + 1] && (jb + q + 1 < p.wh);
     }
     // warp-uniform: every band row takes paired stores
-    const bool fast = SPEC ? true : fwd_pairs_ok(p, x0, QL);
+    const bool fast = SPEC ? true : fwd_pairs_ok(p, x0, QL, HQ);
     // band pointers at output row R0, advanced one pitch per stored row
     OutT* hl = reinterpret_cast<OutT*>(p.coef) + int64_t(R0) * p.coef_pitch + p.wq + jb;
     OutT* lh = reinterpret_cast<OutT*>(p.coef) + int64_t(p.hq + R0) * p.coef_pitch + jb;
@@ -382,11 +383,11 @@ __device__ __forceinline__ void stage_ring(unsigned char* smem, int warp, CT*& b
 // into [0, h) by the symmetric extension; lane 0 waits (bounded) until every
 // previous-level segment holding such a row has all its strips complete, then
 // orders its later TMA reads after what it observed.
-template <int LAG, int QR>
+template <int LAG, int QR, int WARM>
 __device__ __forceinline__ bool fwd_wait_inputs(const FwdParams& p, const FwdSync& y, int R0, int R1, int lane) {
     bool ok = true;
     if (lane == 0) {
-        int lo = max(0, 2 * R0 - 4);
+        int lo = max(0, 2 * (R0 - WARM));
         const int end = 2 * (R1 + LAG + QR - 2) + 2;  // one past the last streamed row
         const int hi = min(p.h, end);
         if (end > p.h) lo = max(0, min(lo, 2 * p.h - 1 - end));  // mirrored rows past the bottom
@@ -440,6 +441,7 @@ __global__ void __launch_bounds__(NW * 32, FwdMinBlocks<Pipe, NW>::value)
     fwd_tma_kernel(const __grid_constant__ CUtensorMap tm_box, const __grid_constant__ CUtensorMap tm_row,
                    const FwdParams p, const FwdSync y) {
     using CT = typename Pipe::CT;
+    constexpr int HQ = PipeGeom<Pipe>::HALO;
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     CT* bufs;
@@ -463,10 +465,10 @@ __global__ void __launch_bounds__(NW * 32, FwdMinBlocks<Pipe, NW>::value)
     Pieces<FwdParams> pieces(p, blockIdx.x * NW + warp, gridDim.x * NW);
     int s, R0, R1;
     while (pieces.next(p, s, R0, R1)) {
-        if (y.dep_ctr != nullptr && !fwd_wait_inputs<Pipe::LAG, QR>(p, y, R0, R1, lane)) return;
+        if (y.dep_ctr != nullptr && !fwd_wait_inputs<Pipe::LAG, QR, PipeGeom<Pipe>::WARM>(p, y, R0, R1, lane)) return;
         bool ok;
         if constexpr (SPEC) {
-            if (fwd_pairs_ok(p, s * (2 * (32 * QL - 2 * HALO_Q)) - 2 * HALO_Q, QL))
+            if (fwd_pairs_ok(p, s * (2 * (32 * QL - 2 * HQ)) - 2 * HQ, QL, HQ))
                 ok = p.ll_is_ct ? fwd_unit<Pipe, OutT, QL, QR, NST, 1>(p, ld, s, R0, R1, bufs, bars, gstage, lane)
                                 : fwd_unit<Pipe, OutT, QL, QR, NST, 2>(p, ld, s, R0, R1, bufs, bars, gstage, lane);
             else
@@ -489,6 +491,7 @@ template <class Pipe, class OutT, int QL, int QR, int NST, int NW, bool SPEC>
 __global__ void __launch_bounds__(NW * 32, FwdMinBlocks<Pipe, NW>::value)
     fwd_group_kernel(const __grid_constant__ GroupLaunch L) {
     using CT = typename Pipe::CT;
+    constexpr int HQ = PipeGeom<Pipe>::HALO;
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     CT* bufs;
@@ -523,7 +526,7 @@ __global__ void __launch_bounds__(NW * 32, FwdMinBlocks<Pipe, NW>::value)
         }
         bool ok;
         if constexpr (SPEC) {
-            if (fwd_pairs_ok(p, s * (2 * (32 * QL - 2 * HALO_Q)) - 2 * HALO_Q, QL))
+            if (fwd_pairs_ok(p, s * (2 * (32 * QL - 2 * HQ)) - 2 * HQ, QL, HQ))
                 ok = p.ll_is_ct ? fwd_unit<Pipe, OutT, QL, QR, NST, 1>(p, ld, s, R0, R1, bufs, bars, gstage, lane)
                                 : fwd_unit<Pipe, OutT, QL, QR, NST, 2>(p, ld, s, R0, R1, bufs, bars, gstage, lane);
             else
@@ -764,11 +767,12 @@ __device__ __forceinline__ void inv_unit(const InvParams& p, int s, int R0, int 
     using CT = typename Pipe::CT;
     using R = Row<CT, QL>;
     constexpr bool MIRROR = !ADJ;
-    constexpr int OUTQ = 32 * QL - 2 * HALO_Q;
-    const int A0 = R0 - 2;
-    const int n_arr = (R1 - R0) + 2 + Pipe::LAG;
+    constexpr int HQ = PipeGeom<Pipe>::HALO, WARM = PipeGeom<Pipe>::WARM;
+    constexpr int OUTQ = 32 * QL - 2 * HQ;
+    const int A0 = R0 - WARM;
+    const int n_arr = (R1 - R0) + WARM + Pipe::LAG;
     const int n_grp = (n_arr + PHASES - 1) / PHASES;
-    const int x0 = s * (2 * OUTQ) - 2 * HALO_Q;
+    const int x0 = s * (2 * OUTQ) - 2 * HQ;
     const int jb = x0 / 2 + QL * lane;
     // the whole strip reads only existing band columns
     const bool fast_cols = (x0 >= 0) && (x0 / 2 + 32 * QL <= p.wh);
@@ -776,7 +780,7 @@ __device__ __forceinline__ void inv_unit(const InvParams& p, int s, int R0, int 
 #pragma unroll
     for (int q = 0; q < QL; ++q) {
         const int lq = QL * lane + q;
-        mine[q] = (lq >= HALO_Q) && (lq < 32 * QL - HALO_Q);
+        mine[q] = (lq >= HQ) && (lq < 32 * QL - HQ);
     }
 
     Pipe pipe;
@@ -882,17 +886,19 @@ __device__ __forceinline__ bool inv_unit_staged(const InvParams& p, int s, int R
                                                 unsigned char* ring, uint64_t* bars, uint32_t& gstage) {
     using CT = typename Pipe::CT;
     using R = Row<CT, 2>;
-    constexpr int QL = 2, OUTQ = 32 * QL - 2 * HALO_Q;
+    constexpr int HQ = PipeGeom<Pipe>::HALO, WARM = PipeGeom<Pipe>::WARM;
+    constexpr int QL = 2, OUTQ = 32 * QL - 2 * HQ;
     constexpr int BAND = 256, ROWB = 4 * BAND, STAGEB = QR * ROWB;
     constexpr int PB = 2 * int(sizeof(BT));  // bytes of a coefficient pair
     static_assert(PHASES % QR == 0, "a group of arrivals must cover whole stages");
-    const int A0 = R0 - 2;
-    const int n_arr = (R1 - R0) + 2 + Pipe::LAG;
+    static_assert(HQ % 2 == 0, "a lane's two quads are both output or both halo");
+    const int A0 = R0 - WARM;
+    const int n_arr = (R1 - R0) + WARM + Pipe::LAG;
     const int n_grp = (n_arr + PHASES - 1) / PHASES;
     const int NT = (n_arr + QR - 1) / QR;
-    const int x0 = s * (2 * OUTQ) - 2 * HALO_Q;
+    const int x0 = s * (2 * OUTQ) - 2 * HQ;
     const int jb = x0 / 2 + QL * lane;
-    const bool mine = (lane >= 1) && (lane <= 30);
+    const bool mine = (lane >= HQ / 2) && (lane < 32 - HQ / 2);
     const BT* coef = reinterpret_cast<const BT*>(p.coef);
 
     // EDGE: every lane copies its band elements one by one (4-byte types), at
@@ -1049,8 +1055,9 @@ __device__ __forceinline__ bool inv_unit_staged(const InvParams& p, int s, int R
 template <class Pipe, class BT, bool ADJ, int QR, int NST>
 __device__ __forceinline__ bool inv_unit_any(const InvParams& p, int s, int R0, int R1, int lane,
                                              unsigned char* ring, uint64_t* bars, uint32_t& gstage) {
-    constexpr int OUTQ = 32 * 2 - 2 * HALO_Q;
-    const int x0 = s * (2 * OUTQ) - 2 * HALO_Q;
+    constexpr int HQ = PipeGeom<Pipe>::HALO;
+    constexpr int OUTQ = 32 * 2 - 2 * HQ;
+    const int x0 = s * (2 * OUTQ) - 2 * HQ;
     const bool staged = p.vec_in_lo && p.vec_in_hi && p.vec_ll;
     const bool interior = (x0 >= 0) && (x0 / 2 + 64 <= p.wh);
     if constexpr (ADJ) {

@@ -86,6 +86,11 @@ int launch_group_t(int wav, int scheme, const GroupLaunch& g, int grid, const Fw
         if (scheme == SCHEME_NONSEP) return launch_group_cfgs<Fwd53, SCHEME_NONSEP, int>(g, grid, c, pdl, s);
         return cudaErrorInvalidValue;
     } else {
+        if (wav == WAV_DD137) {
+            if (scheme == SCHEME_NONSEP) return launch_group_cfgs<Fwd137, SCHEME_NONSEP, OutT>(g, grid, c, pdl, s);
+            if (scheme == SCHEME_SEP) return launch_group_cfgs<Fwd137, SCHEME_SEP, OutT>(g, grid, c, pdl, s);
+            return cudaErrorInvalidValue;
+        }
         if (wav != WAV_CDF97) return cudaErrorInvalidValue;
         if (scheme == SCHEME_NONSEP) return launch_group_cfgs<Fwd97, SCHEME_NONSEP, OutT>(g, grid, c, pdl, s);
         if (scheme == SCHEME_REDUCED) return launch_group_cfgs<Fwd97, SCHEME_REDUCED, OutT>(g, grid, c, pdl, s);
@@ -124,6 +129,10 @@ int occupancy_forward_t(int wav, int scheme, const FwdCfg& c) {
         if (scheme == SCHEME_SEP) return occupancy_fwd_cfgs<Fwd53, SCHEME_SEP, int>(c);
         return occupancy_fwd_cfgs<Fwd53, SCHEME_NONSEP, int>(c);
     } else {
+        if (wav == WAV_DD137) {
+            if (scheme == SCHEME_SEP) return occupancy_fwd_cfgs<Fwd137, SCHEME_SEP, OutT>(c);
+            return occupancy_fwd_cfgs<Fwd137, SCHEME_NONSEP, OutT>(c);
+        }
         if (scheme == SCHEME_NONSEP) return occupancy_fwd_cfgs<Fwd97, SCHEME_NONSEP, OutT>(c);
         if (scheme == SCHEME_REDUCED) return occupancy_fwd_cfgs<Fwd97, SCHEME_REDUCED, OutT>(c);
         if (scheme == SCHEME_POLYCONV) return occupancy_fwd_cfgs<Fwd97S, SCHEME_POLYCONV, OutT>(c);
@@ -145,11 +154,15 @@ int occupancy_inv_one() {
 }
 
 template <class BT>
-int occupancy_inverse_t(int scheme) {
+int occupancy_inverse_t(int wav, int scheme) {
     if constexpr (std::is_same<BT, int>::value) {
         if (scheme == SCHEME_SEP) return occupancy_inv_one<Inv53<SCHEME_SEP, INV_QL>, int, false>();
         return occupancy_inv_one<Inv53<SCHEME_NONSEP, INV_QL>, int, false>();
     } else {
+        if (wav == WAV_DD137) {
+            if (scheme == SCHEME_SEP) return occupancy_inv_one<Inv137<SCHEME_SEP, INV_QL>, BT, false>();
+            return occupancy_inv_one<Inv137<SCHEME_NONSEP, INV_QL>, BT, false>();
+        }
         if (scheme == SCHEME_NONSEP) return occupancy_inv_one<Inv97<SCHEME_NONSEP, INV_QL>, BT, false>();
         if (scheme == SCHEME_REDUCED) return occupancy_inv_one<Inv97<SCHEME_REDUCED, INV_QL>, BT, false>();
         return occupancy_inv_one<Inv97<SCHEME_SEP, INV_QL>, BT, false>();
@@ -176,6 +189,12 @@ int launch_forward_t(int wav, int scheme, const CUtensorMap& box, const CUtensor
         if (scheme == SCHEME_NONSEP) return launch_fwd_cfgs<Fwd53, SCHEME_NONSEP, int>(box, row, p, grid, c, s, y);
         return cudaErrorInvalidValue;
     } else {
+        if (wav == WAV_DD137) {
+            if (scheme == SCHEME_NONSEP)
+                return launch_fwd_cfgs<Fwd137, SCHEME_NONSEP, OutT>(box, row, p, grid, c, s, y);
+            if (scheme == SCHEME_SEP) return launch_fwd_cfgs<Fwd137, SCHEME_SEP, OutT>(box, row, p, grid, c, s, y);
+            return cudaErrorInvalidValue;
+        }
         if (wav != WAV_CDF97) return cudaErrorInvalidValue;
         if (scheme == SCHEME_NONSEP) return launch_fwd_cfgs<Fwd97, SCHEME_NONSEP, OutT>(box, row, p, grid, c, s, y);
         if (scheme == SCHEME_REDUCED) return launch_fwd_cfgs<Fwd97, SCHEME_REDUCED, OutT>(box, row, p, grid, c, s, y);
@@ -265,6 +284,11 @@ int launch_inv_group_t(int wav, int scheme, const InvGroupLaunch& g, int grid, i
         if (scheme == SCHEME_SEP) return launch_inv_group_one<Inv53<SCHEME_SEP, INV_QL>, int, false>(g, grid, pdl, s);
         return launch_inv_group_one<Inv53<SCHEME_NONSEP, INV_QL>, int, false>(g, grid, pdl, s);
     } else {
+        if (wav == WAV_DD137) {
+            if (scheme == SCHEME_SEP)
+                return launch_inv_group_one<Inv137<SCHEME_SEP, INV_QL>, BT, false>(g, grid, pdl, s);
+            return launch_inv_group_one<Inv137<SCHEME_NONSEP, INV_QL>, BT, false>(g, grid, pdl, s);
+        }
         if (wav != WAV_CDF97) return cudaErrorInvalidValue;
         if (scheme == SCHEME_NONSEP)
             return launch_inv_group_one<Inv97<SCHEME_NONSEP, INV_QL>, BT, false>(g, grid, pdl, s);
@@ -282,6 +306,10 @@ int launch_inverse_t(int wav, int scheme, const InvParams& p, int grid, cudaStre
         if (scheme == SCHEME_NONSEP) return launch_inv_one<Inv53<SCHEME_NONSEP, INV_QL>, int, false>(p, grid, s);
         return cudaErrorInvalidValue;
     } else {
+        if (wav == WAV_DD137) {
+            if (scheme == SCHEME_SEP) return launch_inv_one<Inv137<SCHEME_SEP, INV_QL>, BT, false>(p, grid, s);
+            return launch_inv_one<Inv137<SCHEME_NONSEP, INV_QL>, BT, false>(p, grid, s);
+        }
         if (wav != WAV_CDF97) return cudaErrorInvalidValue;
         if (scheme == SCHEME_NONSEP) return launch_inv_one<Inv97<SCHEME_NONSEP, INV_QL>, BT, false>(p, grid, s);
         if (scheme == SCHEME_REDUCED) return launch_inv_one<Inv97<SCHEME_REDUCED, INV_QL>, BT, false>(p, grid, s);

@@ -171,7 +171,7 @@ extern "C" int dwt2_forward_noalloc(int wavelet, int levels, int scheme, int coe
         memset(&fp, 0, sizeof(fp));
         fp.h = H, fp.w = W, fp.hq = (H + 1) / 2, fp.wq = (W + 1) / 2, fp.hh = H / 2, fp.wh = W / 2;
         // segments of the height dwt2_forward chooses (rounds x (rows + 4) minimal)
-        fp.n_strips = (fp.wq + fwd_out_quads(cfg) - 1) / fwd_out_quads(cfg);
+        fp.n_strips = (fp.wq + fwd_out_quads(cfg, wavelet) - 1) / fwd_out_quads(cfg, wavelet);
         {
             const int64_t max_warps =
                 int64_t(st->sm_count) * std::max(st->fwd_bps[coef_dtype][scheme], 1) * cfg.nw;

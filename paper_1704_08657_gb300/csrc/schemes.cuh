@@ -23,6 +23,8 @@
 // two slots, so that a group of 6 unrolled arrivals needs no register copies.
 #pragma once
 
+#include <type_traits>
+
 #include "dev_common.cuh"
 
 namespace dwt2 {
@@ -41,6 +43,20 @@ constexpr int PHASES = 6;  // arrivals per unrolled group
 template <class CT, int QL>
 struct Row {
     CT c1[QL], c2[QL], c3[QL], c4[QL];
+};
+
+// Strip and segment geometry of a pipeline: halo quads on each side of a
+// strip (a finished quad depends on input quads up to that far minus one; an
+// even count keeps a strip's first pixel a multiple of four) and warm-up quad
+// rows streamed above a segment.  Pipelines that declare neither use two and
+// two.
+template <class Pipe, class = void>
+struct PipeGeom {
+    static constexpr int HALO = 2, WARM = 2;
+};
+template <class Pipe>
+struct PipeGeom<Pipe, std::void_t<decltype(Pipe::HALO)>> {
+    static constexpr int HALO = Pipe::HALO, WARM = Pipe::WARM;
 };
 
 template <class CT, int QL>
@@ -1115,6 +1131,217 @@ struct Inv53 {
             int_ns_predict_inv(r1, r0);
         }
         return r1;
+    }
+};
+
+// ============================================================ DD 13/7 float
+// The interpolating Deslauriers-Dubuc 13/7 wavelet: one lifting pair with the
+// 4-tap predict P (cubic interpolation at the odd samples: weights 9/16 on
+// the two nearest even samples, -1/16 on the next two, sign folded in) and
+// the 4-tap update U (9/32, -1/32), no scaling step.  In quad terms P reads
+// quads -1 .. +2 (near 0, +1; far -1, +2) and U reads quads -2 .. +1 (near
+// -1, 0; far -2, +1); P* and U* are the same along columns.  A finished
+// quad depends on input quads up to three away, so these pipelines declare a
+// halo of four quads (which keeps a strip's first pixel a multiple of four)
+// and three warm-up rows; a row leaves LAG = 3 rows after it arrived.
+struct CDD {
+    static constexpr float PN = -9.0f / 16.0f, PF = 1.0f / 16.0f;  // predict near / far
+    static constexpr float UN = 9.0f / 32.0f, UF = -1.0f / 32.0f;  // update near / far
+};
+
+// P x along the row: near (x[q] + x[q+1]), far (x[q-1] + x[q+2])
+template <int QL>
+__device__ __forceinline__ void dd_ph(const float (&x)[QL], float (&o)[QL], float pn, float pf) {
+    float l[QL], r[QL], rr[QL];
+    left_of(x, l);
+    right_of(x, r);
+    right2_of(x, rr);
+#pragma unroll
+    for (int q = 0; q < QL; ++q) o[q] = fmaf(pf, l[q] + rr[q], pn * (x[q] + r[q]));
+}
+// U x along the row: near (x[q-1] + x[q]), far (x[q-2] + x[q+1])
+template <int QL>
+__device__ __forceinline__ void dd_uh(const float (&x)[QL], float (&o)[QL], float un, float uf) {
+    float l[QL], ll[QL], r[QL];
+    left_of(x, l);
+    left2_of(x, ll);
+    right_of(x, r);
+#pragma unroll
+    for (int q = 0; q < QL; ++q) o[q] = fmaf(uf, ll[q] + r[q], un * (l[q] + x[q]));
+}
+// the same along the column, from the rows a0 .. a3 (top to bottom) of the
+// window: P* for the row a1 (a0 far, a1 a2 near, a3 far), U* for the row a2
+__device__ __forceinline__ float dd_v(float a0, float a1, float a2, float a3, float near, float far) {
+    return fmaf(far, a0 + a3, near * (a1 + a2));
+}
+
+// Spatial predict T_P of row m from the pre-step rows m-1 .. m+2 (w0 .. w3):
+// the new (c1, c2, c3, c4) of row m.
+template <int QL>
+__device__ __forceinline__ void dd_ns_predict(const Row<float, QL>& w0, const Row<float, QL>& w1,
+                                              const Row<float, QL>& w2, const Row<float, QL>& w3, Row<float, QL>& o,
+                                              float pn, float pf) {
+    float v1[QL], v2[QL], h1[QL], h3[QL], hv1[QL];
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+        v1[q] = dd_v(w0.c1[q], w1.c1[q], w2.c1[q], w3.c1[q], pn, pf);  // P* c1
+        v2[q] = dd_v(w0.c2[q], w1.c2[q], w2.c2[q], w3.c2[q], pn, pf);  // P* c2
+    }
+    dd_ph(w1.c1, h1, pn, pf);  // P c1
+    dd_ph(w1.c3, h3, pn, pf);  // P c3
+    dd_ph(v1, hv1, pn, pf);    // P P* c1
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+        o.c1[q] = w1.c1[q];
+        o.c2[q] = w1.c2[q] + h1[q];
+        o.c3[q] = w1.c3[q] + v1[q];
+        o.c4[q] = w1.c4[q] + (hv1[q] + v2[q] + h3[q]);
+    }
+}
+// Spatial update S_U of row k from the pre-step rows k-2 .. k+1 (w0 .. w3).
+template <int QL>
+__device__ __forceinline__ void dd_ns_update(const Row<float, QL>& w0, const Row<float, QL>& w1,
+                                             const Row<float, QL>& w2, const Row<float, QL>& w3, Row<float, QL>& o,
+                                             float un, float uf) {
+    float v3[QL], v4[QL], h2[QL], h4[QL], hv4[QL];
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+        v3[q] = dd_v(w0.c3[q], w1.c3[q], w2.c3[q], w3.c3[q], un, uf);  // U* c3
+        v4[q] = dd_v(w0.c4[q], w1.c4[q], w2.c4[q], w3.c4[q], un, uf);  // U* c4
+    }
+    dd_uh(w2.c2, h2, un, uf);  // U c2
+    dd_uh(w2.c4, h4, un, uf);  // U c4
+    dd_uh(v4, hv4, un, uf);    // U U* c4
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+        o.c1[q] = w2.c1[q] + (h2[q] + v3[q] + hv4[q]);
+        o.c2[q] = w2.c2[q] + v4[q];
+        o.c3[q] = w2.c3[q] + h4[q];
+        o.c4[q] = w2.c4[q];
+    }
+}
+
+// Separable steps.  Row-local: T_P^H (c2 += P c1, c4 += P c3) and S_U^H
+// (c1 += U c2, c3 += U c4), in place.
+template <int QL>
+__device__ __forceinline__ void dd_sp_th(Row<float, QL>& x, float pn, float pf) {
+    float h1[QL], h3[QL];
+    dd_ph(x.c1, h1, pn, pf);
+    dd_ph(x.c3, h3, pn, pf);
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+        x.c2[q] += h1[q];
+        x.c4[q] += h3[q];
+    }
+}
+template <int QL>
+__device__ __forceinline__ void dd_sp_sh(Row<float, QL>& x, float un, float uf) {
+    float h2[QL], h4[QL];
+    dd_uh(x.c2, h2, un, uf);
+    dd_uh(x.c4, h4, un, uf);
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+        x.c1[q] += h2[q];
+        x.c3[q] += h4[q];
+    }
+}
+// Column steps into o: T_P^V of row m from rows m-1 .. m+2 (c3 += P* c1,
+// c4 += P* c2) and S_U^V of row k from rows k-2 .. k+1 (c1 += U* c3,
+// c2 += U* c4).
+template <int QL>
+__device__ __forceinline__ void dd_sp_tv(const Row<float, QL>& w0, const Row<float, QL>& w1, const Row<float, QL>& w2,
+                                         const Row<float, QL>& w3, Row<float, QL>& o, float pn, float pf) {
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+        o.c1[q] = w1.c1[q];
+        o.c2[q] = w1.c2[q];
+        o.c3[q] = w1.c3[q] + dd_v(w0.c1[q], w1.c1[q], w2.c1[q], w3.c1[q], pn, pf);
+        o.c4[q] = w1.c4[q] + dd_v(w0.c2[q], w1.c2[q], w2.c2[q], w3.c2[q], pn, pf);
+    }
+}
+template <int QL>
+__device__ __forceinline__ void dd_sp_sv(const Row<float, QL>& w0, const Row<float, QL>& w1, const Row<float, QL>& w2,
+                                         const Row<float, QL>& w3, Row<float, QL>& o, float un, float uf) {
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+        o.c1[q] = w2.c1[q] + dd_v(w0.c3[q], w1.c3[q], w2.c3[q], w3.c3[q], un, uf);
+        o.c2[q] = w2.c2[q] + dd_v(w0.c4[q], w1.c4[q], w2.c4[q], w3.c4[q], un, uf);
+        o.c3[q] = w2.c3[q];
+        o.c4[q] = w2.c4[q];
+    }
+}
+
+// Forward.  Arrival n (phase PH) lands in a[PH]; the first step runs on row
+// n-2 from the arrived rows n-3 .. n into b[(PH+4) % 6], the second on row
+// n-3 from b's rows n-5 .. n-2 into the output.  Rings of six rows, indexed by
+// the phase, so that no row is copied.
+template <int SCHEME, int QL>
+struct Fwd137 {
+    static constexpr int LAG = 3, HALO = 4, WARM = 3;
+    using CT = float;
+    using R = Row<float, QL>;
+    R a[6], b[6], o;
+    __device__ __forceinline__ void init() {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            zero_row(a[i]);
+            zero_row(b[i]);
+        }
+    }
+    template <int PH>
+    __device__ __forceinline__ R& slot() {
+        return a[PH];
+    }
+    template <int PH>
+    __device__ __forceinline__ R& step(int /*row*/) {
+        constexpr int M3 = (PH + 3) % 6, M2 = (PH + 4) % 6, M1 = (PH + 5) % 6, M5 = (PH + 1) % 6;
+        if constexpr (SCHEME == SCHEME_SEP) {
+            dd_sp_th(a[PH], CDD::PN, CDD::PF);  // rows enter after their T_P^H
+            dd_sp_tv(a[M3], a[M2], a[M1], a[PH], b[M2], CDD::PN, CDD::PF);
+            dd_sp_sh(b[M2], CDD::UN, CDD::UF);
+            dd_sp_sv(b[M5], b[(PH + 2) % 6], b[M3], b[M2], o, CDD::UN, CDD::UF);
+        } else {
+            dd_ns_predict(a[M3], a[M2], a[M1], a[PH], b[M2], CDD::PN, CDD::PF);
+            dd_ns_update(b[M5], b[(PH + 2) % 6], b[M3], b[M2], o, CDD::UN, CDD::UF);
+        }
+        return o;
+    }
+};
+
+// Inverse: arrival n (coefficients) lands in a[PH]; S_U undone on row n-1
+// from the rows n-3 .. n into b[(PH+5) % 6], then T_P undone on row n-3 from
+// b's rows n-4 .. n-1 into the output.
+template <int SCHEME, int QL>
+struct Inv137 {
+    static constexpr int LAG = 3, HALO = 4, WARM = 3;
+    using CT = float;
+    using R = Row<float, QL>;
+    R a[6], b[6], o;
+    __device__ __forceinline__ void init() {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            zero_row(a[i]);
+            zero_row(b[i]);
+        }
+    }
+    template <int PH>
+    __device__ __forceinline__ R& slot() {
+        return a[PH];
+    }
+    template <int PH>
+    __device__ __forceinline__ R& step(int /*row*/) {
+        constexpr int M1 = (PH + 5) % 6, M2 = (PH + 4) % 6, M3 = (PH + 3) % 6, M4 = (PH + 2) % 6;
+        if constexpr (SCHEME == SCHEME_SEP) {
+            // S_U^V then S_U^H undone on row n-1, T_P^V then T_P^H on row n-3
+            dd_sp_sv(a[M3], a[M2], a[M1], a[PH], b[M1], -CDD::UN, -CDD::UF);
+            dd_sp_sh(b[M1], -CDD::UN, -CDD::UF);
+            dd_sp_tv(b[M4], b[M3], b[M2], b[M1], o, -CDD::PN, -CDD::PF);
+            dd_sp_th(o, -CDD::PN, -CDD::PF);
+        } else {
+            dd_ns_update(a[M3], a[M2], a[M1], a[PH], b[M1], -CDD::UN, -CDD::UF);
+            dd_ns_predict(b[M4], b[M3], b[M2], b[M1], o, -CDD::PN, -CDD::PF);
+        }
+        return o;
     }
 };
 

@@ -16,7 +16,7 @@ import torch
 
 from . import abi
 
-WAVELETS = {"cdf97": abi.DWT2_CDF97, "cdf53": abi.DWT2_CDF53_INT}
+WAVELETS = {"cdf97": abi.DWT2_CDF97, "cdf53": abi.DWT2_CDF53_INT, "dd137": abi.DWT2_DD137}
 SCHEMES = {"nonsep": abi.DWT2_NONSEP, "reduced": abi.DWT2_NONSEP_REDUCED, "sep": abi.DWT2_SEP_LIFTING,
            "polyconv": abi.DWT2_POLYCONV, "conv": abi.DWT2_CONV,
            "nsconv": abi.DWT2_NONSEP_CONV}
@@ -48,7 +48,7 @@ class Plan:
         self.levels = int(levels)
         self.wavelet = wavelet
         self.scheme = scheme
-        self.in_dtype = torch.float32 if wavelet == "cdf97" else torch.int32
+        self.in_dtype = torch.int32 if wavelet == "cdf53" else torch.float32
         self.coef_dtype = coef_dtype
         self.flags = int(flags)
         self.tuned: Optional[int] = None

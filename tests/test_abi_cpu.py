@@ -58,6 +58,10 @@ def test_strerror_names_every_code(lib):
      abi.DWT2_ERR_UNSUPPORTED),
     ((abi.DWT2_CDF53_INT, 1, 0, abi.DWT2_I32, abi.DWT2_I32, abi.DWT2_NONSEP_CONV, [(0, 16, 16, 16)]),
      abi.DWT2_ERR_UNSUPPORTED),
+    ((abi.DWT2_DD137, 1, 0, 0, 0, abi.DWT2_NONSEP_REDUCED, [(0, 16, 16, 16)]), abi.DWT2_ERR_UNSUPPORTED),
+    ((abi.DWT2_DD137, 1, 0, 0, 0, abi.DWT2_CONV, [(0, 16, 16, 16)]), abi.DWT2_ERR_UNSUPPORTED),
+    ((abi.DWT2_DD137, 1, 0, abi.DWT2_I32, abi.DWT2_I32, 0, [(0, 16, 16, 16)]), abi.DWT2_ERR_UNSUPPORTED),
+    ((3, 1, 0, 0, 0, 0, [(0, 16, 16, 16)]), abi.DWT2_ERR_INVALID_ARG),                       # no such wavelet
 ])
 def test_plan_validation(lib, args, code):
     wav, lv, bd, idt, cdt, sch, imgs = args
@@ -68,6 +72,12 @@ def test_plan_validation(lib, args, code):
     with pytest.raises(abi.Dwt2Error) as e:
         abi.dwt2_plan(wav, lv, bd, idt, cdt, sch, imgs)
     assert e.value.code == code
+
+
+def test_dd137_has_no_persistent_form(lib):
+    with pytest.raises(abi.Dwt2Error) as e:
+        abi.dwt2_plan(abi.DWT2_DD137, 1, 0, 0, 0, abi.DWT2_NONSEP, [(0, 16, 16, 16)], abi.DWT2_FLAG_PERSISTENT)
+    assert e.value.code == abi.DWT2_ERR_UNSUPPORTED
 
 
 @pytest.mark.parametrize("scheme", [abi.DWT2_POLYCONV, abi.DWT2_CONV, abi.DWT2_NONSEP_CONV])

@@ -12,7 +12,7 @@ import torch
 import oracle
 from paper_1704_08657_gb300 import synth
 from paper_1704_08657_gb300.dwt import Plan
-from tests.util import assert_fp32_close, assert_lowp_close
+from tests.util import assert_dd_close, assert_fp32_close, assert_lowp_close
 
 pytestmark = pytest.mark.gpu
 
@@ -71,4 +71,24 @@ def test_int53_full_size_bit_exact(scheme):
     back = plan.inverse(c)
     torch.cuda.synchronize()
     assert np.array_equal(back.cpu().numpy(), x)
+    plan.close()
+
+
+def test_dd137_full_size():
+    x = synth.gradient(N, N, seed=2)
+    ref = oracle.forward137(x.astype(np.float64), LEVELS)
+    xd = torch.from_numpy(x).cuda()
+    plan = Plan.single(N, N, LEVELS, wavelet="dd137", scheme="nonsep")
+    out = torch.empty_like(xd)
+    plan.autotune(xd, out)
+    out.fill_(float("nan"))
+    plan.forward(xd, out)
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    got = out.cpu().numpy()
+    assert np.isfinite(got).all()
+    assert_dd_close(got, ref, LEVELS, 255.0, "16384^2 dd137")
+    back = plan.inverse(out)
+    torch.cuda.synchronize()
+    assert float((back - xd).abs().max()) <= 2e-3
     plan.close()

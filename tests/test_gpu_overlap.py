@@ -15,7 +15,7 @@ import oracle
 from paper_1704_08657_gb300 import abi, synth
 from paper_1704_08657_gb300.dwt import Plan
 from tests.test_gpu_parity import _padded
-from tests.util import assert_fp32_close
+from tests.util import assert_dd_close, assert_fp32_close
 
 pytestmark = pytest.mark.gpu
 
@@ -24,7 +24,7 @@ def _run(x, levels, scheme, coef_dtype, overlap, monkeypatch, choice=None, wavel
     """x: host array; odd widths get a padded pitch (a multiple of 4)."""
     monkeypatch.setenv("DWT2_LEVEL_OVERLAP", "1" if overlap else "0")
     h, w = x.shape
-    xin, pitch = _padded(x, torch.float32 if wavelet == "cdf97" else torch.int32, guard_rows=0)
+    xin, pitch = _padded(x, torch.int32 if wavelet == "cdf53" else torch.float32, guard_rows=0)
     plan = Plan.single(h, w, levels, pitch=pitch, scheme=scheme, coef_dtype=coef_dtype, wavelet=wavelet)
     out = torch.full_like(xin, float("nan") if coef_dtype != torch.int32 else 0, dtype=coef_dtype)
     if choice is not None:
@@ -78,3 +78,15 @@ def test_dropped_segment_signal_times_out(monkeypatch):
     c = ok.forward(x)
     assert ok.status() == 0
     assert_fp32_close(c.cpu().numpy(), oracle.forward97(x.cpu().numpy().astype(np.float64), 3), 3, 255.0)
+
+
+@pytest.mark.parametrize("h,w,levels", [(2048, 2048, 5), (1031, 2052, 6), (300, 4100, 4), (66, 66, 3)])
+@pytest.mark.parametrize("scheme", ["nonsep", "sep"])
+def test_overlap_dd137(h, w, levels, scheme, monkeypatch):
+    # three warm-up rows: a unit waits for one more row of the previous level
+    x = synth.gradient(h, w, seed=h + w)
+    a = _run(x, levels, scheme, torch.float32, True, monkeypatch, wavelet="dd137")
+    b = _run(x, levels, scheme, torch.float32, False, monkeypatch, wavelet="dd137")
+    assert not torch.isnan(a).any(), "coefficients left unwritten"
+    assert torch.equal(a, b)
+    assert_dd_close(a.numpy(), oracle.forward137(x.astype(np.float64), levels), levels, 255.0)

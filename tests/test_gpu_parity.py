@@ -11,7 +11,7 @@ import torch
 import oracle
 from paper_1704_08657_gb300 import synth
 from paper_1704_08657_gb300.dwt import Plan, round_up
-from tests.util import assert_fp32_close, assert_lowp_close
+from tests.util import assert_dd_close, assert_fp32_close, assert_lowp_close
 
 pytestmark = pytest.mark.gpu
 
@@ -44,7 +44,7 @@ def _guard_ok(buf: torch.Tensor, h, w):
 
 def gpu_forward(x, levels, scheme="nonsep", coef_dtype=torch.float32, wavelet="cdf97"):
     h, w = x.shape
-    in_dt = torch.float32 if wavelet == "cdf97" else torch.int32
+    in_dt = torch.int32 if wavelet == "cdf53" else torch.float32
     xin, pitch = _padded(x, in_dt)
     out = torch.full_like(xin, SENT, dtype=coef_dtype)
     plan = Plan.single(h, w, levels, pitch=pitch, wavelet=wavelet, scheme=scheme, coef_dtype=coef_dtype)
@@ -57,7 +57,7 @@ def gpu_forward(x, levels, scheme="nonsep", coef_dtype=torch.float32, wavelet="c
 
 def gpu_inverse(c, levels, scheme="nonsep", coef_dtype=torch.float32, wavelet="cdf97"):
     h, w = c.shape
-    out_dt = torch.float32 if wavelet == "cdf97" else torch.int32
+    out_dt = torch.int32 if wavelet == "cdf53" else torch.float32
     cin, pitch = _padded(c, coef_dtype)
     out = torch.full_like(cin, SENT, dtype=out_dt)
     plan = Plan.single(h, w, levels, pitch=pitch, wavelet=wavelet, scheme=scheme, coef_dtype=coef_dtype)
@@ -196,3 +196,60 @@ def test_unpadded_pitch_every_configuration(n, levels, cfg, monkeypatch):
     got = out.cpu().numpy()
     assert not np.isnan(got).any(), f"{int(np.isnan(got).sum())} coefficients left unwritten"
     assert_fp32_close(got, oracle.forward97(x.astype(np.float64), levels), levels, 255.0, f"{n} L{levels} cfg {cfg}")
+
+
+# ------------------------------------------------------------------ DD 13/7
+# one lifting pair with 4-tap steps: strips with a 4-quad halo, 3 warm-up rows
+DD_SCHEMES = ["nonsep", "sep"]
+
+
+@pytest.mark.parametrize("scheme", DD_SCHEMES)
+@pytest.mark.parametrize("h,w", SHAPES + [(100, 1028), (66, 3000), (5, 7)])
+def test_forward137_fp32(h, w, scheme):
+    x = synth.uniform(h, w, seed=3 + h * 5 + w)
+    for levels in sorted({1, _levels_max(h, w, 5)}):
+        if levels == 0:
+            continue
+        ref = oracle.forward137(x.astype(np.float64), levels)
+        got = gpu_forward(x, levels, scheme, wavelet="dd137")
+        assert_dd_close(got, ref, levels, 255.0, f"dd137 {scheme} {h}x{w} L{levels}")
+
+
+@pytest.mark.parametrize("scheme", DD_SCHEMES)
+@pytest.mark.parametrize("h,w", [(512, 512), (33, 65), (7, 5), (2, 2), (130, 250), (257, 129), (100, 1028),
+                                 (66, 3000)])
+def test_inverse137_fp32(h, w, scheme):
+    levels = _levels_max(h, w, 4)
+    x = synth.uniform(h, w, seed=11)
+    c = oracle.forward137(x.astype(np.float64), levels)
+    got = gpu_inverse(c.astype(np.float32), levels, scheme, wavelet="dd137")
+    ref = oracle.inverse137(c.astype(np.float32).astype(np.float64), levels)
+    assert np.abs(got - ref).max() <= 1e-3, f"max err {np.abs(got - ref).max()}"
+    rec = gpu_inverse(gpu_forward(x, levels, scheme, wavelet="dd137"), levels, scheme, wavelet="dd137")
+    assert np.abs(rec - x).max() <= 2e-3
+
+
+@pytest.mark.parametrize("dtype,rel", [(torch.float16, 1e-3), (torch.bfloat16, 8e-3)])
+@pytest.mark.parametrize("h,w", [(512, 512), (130, 250), (96, 1028)])
+def test_dd137_lowp_storage(h, w, dtype, rel):
+    levels = _levels_max(h, w, 5)
+    x = synth.noisy(h, w, seed=3)
+    ref = oracle.forward137(x.astype(np.float64), levels)
+    for scheme in DD_SCHEMES:
+        got = gpu_forward(x, levels, scheme, dtype, "dd137")
+        assert_lowp_close(got, ref, levels, rel, f"dd137 {dtype} {scheme}")
+    c = ref.astype(np.float32)
+    got = gpu_inverse(torch.from_numpy(c).to(dtype).float().numpy(), levels, "nonsep", dtype, "dd137")
+    ref_i = oracle.inverse137(torch.from_numpy(c).to(dtype).double().numpy(), levels)
+    assert np.abs(got - ref_i).max() <= 2e-3 * np.abs(ref_i).max() / 255.0 * 2
+
+
+def test_dd137_has_no_adjoint_or_reduced_form():
+    from paper_1704_08657_gb300 import abi
+    with pytest.raises(abi.Dwt2Error) as e:
+        Plan.single(64, 64, 2, wavelet="dd137", scheme="reduced")
+    assert e.value.code == abi.DWT2_ERR_UNSUPPORTED
+    p = Plan.single(64, 64, 2, wavelet="dd137")
+    g = torch.zeros(64, 64, device="cuda")
+    rc = abi.raw_call("dwt2_adjoint", p.handle, g.data_ptr(), torch.empty_like(g).data_ptr(), p.workspace.data_ptr(), 0)
+    assert rc == abi.DWT2_ERR_UNSUPPORTED

@@ -34,3 +34,12 @@ def assert_lowp_close(got: np.ndarray, ref: np.ndarray, levels: int, rel: float,
     """FP16 / BF16 storage: per band max |q - ref| / max |ref band| <= rel."""
     for lev, name, err, bmax in band_errors(got, ref, levels):
         assert err <= rel * max(bmax, 1e-30), f"{what} level {lev} {name}: rel err {err / max(bmax, 1e-30):.3e} > {rel}"
+
+
+def assert_dd_close(got: np.ndarray, ref: np.ndarray, levels: int, x_max: float, what: str = ""):
+    """FP32 DD 13/7 lifting vs the FP64 oracle.  The transform has no scaling
+    step (low-pass DC gain 1), so every band stays on the input's scale: each
+    band within 1e-3 * x_max / 255 of the oracle."""
+    for lev, name, err, bmax in band_errors(got, ref, levels):
+        tol = 1e-3 * max(x_max, 1e-30) / 255.0
+        assert err <= tol, f"{what} level {lev} {name}: max abs err {err:.3e} > {tol:.3e} (band max {bmax:.3e})"
