@@ -39,8 +39,9 @@
  * (4, 4, 4, 2, 1 and 1 per CDF 9/7 level).
  *
  * Conventions (readings where the paper is silent):
- *   - odd sample x[2n+1] is predicted from x[2n], x[2n+2]; even sample x[2n]
- *     is updated from x[2n-1], x[2n+1];
+ *   - odd sample x[2n+1] is predicted from x[2n], x[2n+2] (DD 13/7: also
+ *     x[2n-2], x[2n+4]); even sample x[2n] is updated from x[2n-1], x[2n+1]
+ *     (DD 13/7: also x[2n-3], x[2n+3]);
  *   - boundary: whole-sample symmetric extension (x[-1] = x[1],
  *     x[n] = x[n-2]) in every step;
  *   - CDF 9/7 scaling: low-pass times zeta and high-pass divided by zeta per
@@ -55,9 +56,12 @@
  *     sides >= 2.
  *
  * Memory and ownership.  The caller owns every device buffer and the stream.
- * A plan owns its device status word and its batch tables; calls are
- * asynchronous on the given stream and allocate nothing after the plan is
- * made.  A plan must not be used on two streams at the same time.
+ * A plan owns its device status word, segment counters and persistent-launch
+ * tables (device memory allocated when the plan is made) and the launch
+ * blocks of several-image plans (host memory, built at the first call for a
+ * set of buffers); calls are asynchronous on the given stream and allocate no
+ * device memory after the plan is made.  A plan must not be used on two
+ * streams at the same time.
  *
  * Errors.  Every function returns DWT2_OK (0) or a negative DWT2_ERR_* code;
  * nothing aborts or traps.  dwt2_strerror() names a code.
