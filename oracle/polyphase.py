@@ -213,11 +213,14 @@ def pairs_cdf53() -> List[Tuple[LPoly, LPoly]]:
 
 
 def pairs_dd137() -> List[Tuple[LPoly, LPoly]]:
-    """Deslauriers-Dubuc 13/7 shape: four-tap predict and update (the paper
-    prints no coefficients; only the tap structure matters for Table 1)."""
-    a, b = Fraction(-1, 16), Fraction(9, 16)
-    c, d = Fraction(1, 32), Fraction(-9, 32)
-    return [(LPoly.h({-1: a, 0: b, 1: b, 2: a}), LPoly.h({-2: -c, -1: -d, 0: -d, 1: -c}))]
+    """Deslauriers-Dubuc 13/7: four-tap predict (odd += P even, the negated
+    cubic interpolation -(9/16)(1 + z) + (1/16)(z^-1 + z^2)) and four-tap
+    update (even += U odd, (9/32)(1 + z^-1) - (1/32)(z + z^-2)).  The paper
+    prints no coefficients (Table 1 only counts its terms); these are the
+    published filter bank's, as in dwt2ref.c."""
+    pn, pf = Fraction(-9, 16), Fraction(1, 16)
+    un, uf = Fraction(9, 32), Fraction(-1, 32)
+    return [(LPoly.h({-1: pf, 0: pn, 1: pn, 2: pf}), LPoly.h({-2: uf, -1: un, 0: un, 1: uf}))]
 
 
 # ---- schemes as step sequences (lists of barrier-separated steps) -----------

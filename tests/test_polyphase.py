@@ -118,6 +118,39 @@ def test_lifting_product_is_the_closed_form_filter_bank():
     assert np.abs(high - H7).max() < 1e-8
 
 
+def test_dd137_lifting_product_is_the_published_filter_bank():
+    """The DD 13/7 pair multiplied out (Eq. 2, no scaling) is the published
+    13-tap / 7-tap analysis bank."""
+    from tests.test_oracle import L13, H7DD
+    (P, U), = pp.pairs_dd137()
+    # even output n: s = e + U(odd after predict); odd output: d = o + P e
+    low = np.zeros(13)
+    high = np.zeros(7)
+    for (k, _), p in P.t.items():          # d[n] = x[2n+1] + sum_k p_k x[2(n+k)]
+        high[2 * k - 1 + 3] += float(p)
+    high[3] += 1.0
+    low[6] += 1.0                            # s[n] = x[2n] + sum_j u_j d[n+j]
+    for (j, _), u in U.t.items():
+        low[2 * j + 1 + 6] += float(u)
+        for (k, _), p in P.t.items():
+            low[2 * (j + k) + 6] += float(u * p)
+    assert np.array_equal(low, L13)
+    assert np.array_equal(high, H7DD)
+
+
+def test_dd137_schemes_compute_the_same_values_as_the_oracle():
+    hq, wq = 16, 20
+    x = RNG.uniform(0, 255, size=(2 * hq, 2 * wq))
+    pairs = pp.pairs_dd137()
+    q = pp.to_quads(x)
+    outs = [pp.apply_steps(s(pairs), q) for s in (pp.scheme_separable, pp.scheme_nonsep)]
+    assert np.abs(outs[0] - outs[1]).max() < 1e-10
+    ref = oracle.forward137(x, 1)
+    bands = np.stack([ref[:hq, :wq], ref[:hq, wq:], ref[hq:, :wq], ref[hq:, wq:]])
+    m = 4  # the periodic and the symmetric extension differ only near the edges
+    assert np.abs(outs[1][:, m:-m, m:-m] - bands[:, m:-m, m:-m]).max() < 1e-9
+
+
 @pytest.mark.parametrize("hq,wq", [(16, 16), (12, 20)])
 def test_schemes_compute_the_same_values_as_the_oracle(hq, wq):
     h, w = 2 * hq, 2 * wq
