@@ -102,9 +102,14 @@ enum dwt2_boundary { DWT2_SYMMETRIC = 0 };
 
 /* plan flags */
 #define DWT2_FLAG_PERSISTENT 0x1u /* forward: one persistent launch for all images and levels */
-#define DWT2_FLAG_TEST_DROP_SIGNAL 0x100u /* test hook (persistent forward): the first queued
-                                             unit never reports completion, so its dependants
-                                             time out and dwt2_status returns DWT2_ERR_TIMEOUT */
+
+/* TEST ONLY -- failure injection on the host side, never for production use:
+ * a plan made with this flag has one unit of its forward (the first queued
+ * unit of a persistent launch; strip 0 of segment 0 of each level with
+ * inter-level overlap) never report completion, so the units that depend on
+ * it time out after DWT2_TIMEOUT_MS and dwt2_status returns DWT2_ERR_TIMEOUT
+ * while the CUDA context stays usable; the coefficients are then incomplete. */
+#define DWT2_TESTONLY_DROP_SIGNAL 0x100u
 
 /* One image of a batch: element offset of its first pixel from the base
  * pointer, its size, and its row pitch in elements (pitch >= w).  The same
@@ -135,7 +140,7 @@ typedef struct {
  *              the last three (the same transform).
  *   n_images   number of images (>= 1); images is a host array of that many
  *              descriptors, copied into the plan.  With several images
- *              dwt2_forward runs each level as launches of up to 80 images
+ *              dwt2_forward runs each level as launches of up to 76 images
  *              (the inverse and adjoint up to 200), whose parameter blocks are
  *              built at the first call for a set of buffers and reused.
  *   flags      0 or DWT2_FLAG_PERSISTENT: dwt2_forward then runs every level of every
@@ -199,6 +204,15 @@ int dwt2_adjoint(dwt2_plan_t plan, const void* coef_grad, void* in_grad, void* w
 int dwt2_adjoint_l1(dwt2_plan_t plan, const void* coef, void* in_grad, float scale, void* workspace,
                     void* stream);
 
+/* dwt2_adjoint_l1_dev -- dwt2_adjoint_l1 with the scale scale * *scale_dev,
+ * where scale_dev is a device pointer to one float read by the kernels when
+ * they run: the gradient of a loss whose upstream gradient lives on the
+ * device (autograd) is formed without a host synchronisation, so the call is
+ * asynchronous and can be captured in a CUDA graph.  scale_dev must not be
+ * NULL and stays valid until the call has completed on the stream. */
+int dwt2_adjoint_l1_dev(dwt2_plan_t plan, const void* coef, void* in_grad, const float* scale_dev,
+                        float scale, void* workspace, void* stream);
+
 /* dwt2_autotune -- choose the plan's launch configuration (not in the paper).
  * With *choice < 0: run the forward on the given buffers (same arguments as
  * dwt2_forward) for each candidate configuration (kernel tile shape and
@@ -240,21 +254,87 @@ int dwt2_profile_read(dwt2_plan_t plan, float* ms, int n);
  * allocation after start-up, or plug-ins whose host owns all device memory).
  *   wavelet, levels, scheme, coef_dtype  as for dwt2_plan, CDF 9/7 or CDF 5/3
  *              only (in_dtype follows the wavelet: F32 for CDF 9/7, I32 for
- *              CDF 5/3).
+ *              CDF 5/3); schemes DWT2_NONSEP, DWT2_NONSEP_REDUCED (CDF 9/7)
+ *              and DWT2_SEP_LIFTING.
  *   h, w, pitch_elems  the image; pitch a multiple of 4 elements.
  *   in         device pointer to the image, 16-byte aligned, read only.
  *   coef       device pointer to the coefficients (Mallat layout, same pitch).
  *   stream     a cudaStream_t (NULL for the legacy default stream).
  * The intermediate low-low bands live in a static 32 MiB device array inside
- * the library (held by every GPU that loads it until exit): enough for a
- * 4096 x 4096 image; larger requests return DWT2_ERR_TOO_LARGE.  The first
- * call on a device looks up that array's device address; make it before any
- * stream capture.  All calls share the array, so calls that overlap on the
- * GPU race; order them on one stream.  There is no status word: a device-side
- * timeout is not reported by this entry point.  Same results as dwt2_forward.
+ * the library (held by every GPU that loads it until exit), in two
+ * alternating buffers: levels 1, 3, 5, ... write their low-low band (FP32 or
+ * int32, ceil(h_l / 2) rows of round4(ceil(w_l / 2)) elements for a level
+ * input of h_l x w_l) to the first, levels 2, 4, ... to the second, and the
+ * request fits when the largest band of each kind, each rounded up to 256
+ * bytes, add up to at most 32 MiB; else DWT2_ERR_TOO_LARGE before any GPU
+ * work.  A one-level transform uses no scratch; a square n x n image fits
+ * for n <= 5176 at any depth (4096 x 4096 takes 20 MiB).  The first call on a
+ * device looks up the array's device address; make it before any stream
+ * capture.  All calls share the array, so calls that overlap on the GPU race;
+ * order them on one stream.  Same results as dwt2_forward.
  */
 int dwt2_forward_noalloc(int wavelet, int levels, int scheme, int coef_dtype, int h, int w,
                          int64_t pitch_elems, const void* in, void* coef, void* stream);
+
+/* dwt2_noalloc_status -- synchronise the stream, then return and clear the
+ * status word that dwt2_forward_noalloc calls on the current device share
+ * (another static word of the library, zero when it is loaded): DWT2_OK, or
+ * DWT2_ERR_TIMEOUT when a bounded device wait (DWT2_TIMEOUT_MS, default 2000,
+ * read at the first call on the device) ran out in some call since the last
+ * read, in which case that call's coefficients are incomplete.  Allocates
+ * nothing. */
+int dwt2_noalloc_status(void* stream);
+
+/*
+ * Row bands of one image (not in the paper, whose Evaluation scales one GPU
+ * over image resolution): an image too large for one GPU, or a pyramid to be
+ * spread over several GPUs, is cut into n_bands bands of whole rows that
+ * transform independently -- no data moves between bands -- and whose owned
+ * rows are then copied into the image's Mallat layout.
+ *
+ * Band b owns input rows [own0, own1): the cuts are the multiples of
+ * 2^levels nearest to b*h/n_bands (the last band ends at h), so the band's
+ * 2x2 quads are the image's quads at every level.  It transforms rows
+ * [in0, in1) = [own0 - H, own1 + H) clipped to [0, h), where H is
+ * a*(2^levels - 1) rounded up to a multiple of 2^levels and a is the reach of
+ * one level in rows of its input (4 for CDF 9/7, 2 for CDF 5/3, 6 for DD
+ * 13/7: the half length of the longer analysis filter).  Every coefficient
+ * the band owns then depends on image rows only (the symmetric extension at
+ * the band's cut edges reaches only rows other bands own), so a band
+ * transform computes exactly the coefficients of the whole-image transform
+ * for its owned rows.  The halo rows are transformed twice (by two bands):
+ * with n bands, 2*(n-1)*H extra rows in all.
+ */
+
+/* dwt2_band_rows -- rows[0..3] = own0, own1, in0, in1 of band `band`
+ * (0 <= band < n_bands) of an image of h rows and `levels` levels of
+ * `wavelet`.  DWT2_ERR_INVALID_ARG when a band would own fewer than
+ * 2^levels rows.  Host only (no CUDA call). */
+int dwt2_band_rows(int wavelet, int levels, int h, int n_bands, int band, int32_t rows[4]);
+
+/* dwt2_band_rects -- the copy that dwt2_band_stitch performs, as rectangles
+ * of five int32 each: source row (in the band's own coefficients, rows
+ * counted from in0), destination row (in the image's coefficients), number
+ * of rows, first column and number of columns (the same columns in both).
+ * With rects == NULL and max_rects == 0 returns the count; else writes up to
+ * max_rects rectangles and returns their count (DWT2_ERR_INVALID_ARG when
+ * more are needed).  Host only. */
+int dwt2_band_rects(int wavelet, int levels, int h, int w, int n_bands, int band, int32_t* rects,
+                    int max_rects);
+
+/* dwt2_band_stitch -- copy the coefficients band `band` owns from its own
+ * forward transform into the image's coefficient buffer (one kernel launch,
+ * asynchronous on the stream).
+ *   band_coef   device pointer: the band's coefficients, (in1 - in0) rows of
+ *               w elements in Mallat layout (what dwt2_forward of a plan of
+ *               the (in1 - in0) x w image starting at input row in0 writes),
+ *               row pitch band_pitch elements.
+ *   coef        device pointer: the image's coefficients (h rows, pitch
+ *               `pitch`), written only in the band's owned rectangles.
+ * Both of coef_dtype, naturally aligned; levels and wavelet as for the band
+ * transform, levels <= 24. */
+int dwt2_band_stitch(int wavelet, int levels, int coef_dtype, int h, int w, int n_bands, int band,
+                     const void* band_coef, int64_t band_pitch, void* coef, int64_t pitch, void* stream);
 
 /* dwt2_destroy -- free the plan (NULL is accepted). */
 void dwt2_destroy(dwt2_plan_t plan);

@@ -32,12 +32,18 @@ ERRORS = {0: "ok", -1: "invalid argument", -3: "levels too deep", -8: "out of me
 
 
 def build(force: bool = False) -> str:
-    """Compile dwt2ref.c into libdwt2ref.so with gcc (OpenMP when available)."""
+    """Compile dwt2ref.c into libdwt2ref.so with gcc (OpenMP when available).
+
+    -O3 without -ffast-math: ISO C11 mode keeps every floating-point operation
+    as written (no contraction into fused multiply-adds, no reassociation), so
+    the optimisation level changes the speed of the oracle, not its values.
+    The build is portable (no -march=native): the same source runs on the
+    host of the GPU machine, an Arm machine."""
     if (not force and os.path.exists(_LIB)
             and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
         return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
-    base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", _SRC, "-o", tmp]
+    base = ["gcc", "-O3", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", _SRC, "-o", tmp]
     try:
         subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True,
                        capture_output=True)

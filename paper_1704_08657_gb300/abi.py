@@ -26,12 +26,12 @@ DWT2_ERR_TIMEOUT = -6
 DWT2_ERR_DEVICE_CHECK = -7
 DWT2_ERR_TOO_LARGE = -8
 DWT2_FLAG_PERSISTENT = 0x1
-DWT2_FLAG_TEST_DROP_SIGNAL = 0x100
+DWT2_TESTONLY_DROP_SIGNAL = 0x100  # test-only failure injection
 
 # the functions the header declares (checked by the CPU test suite)
-EXPORTS = ("dwt2_plan", "dwt2_workspace_bytes", "dwt2_forward", "dwt2_inverse", "dwt2_adjoint", "dwt2_adjoint_l1",
+EXPORTS = ("dwt2_plan", "dwt2_workspace_bytes", "dwt2_forward", "dwt2_inverse", "dwt2_adjoint", "dwt2_adjoint_l1", "dwt2_adjoint_l1_dev",
            "dwt2_autotune", "dwt2_status", "dwt2_profile", "dwt2_profile_read", "dwt2_forward_noalloc",
-           "dwt2_destroy", "dwt2_strerror")
+           "dwt2_noalloc_status", "dwt2_band_rows", "dwt2_band_rects", "dwt2_band_stitch", "dwt2_destroy", "dwt2_strerror")
 
 
 class dwt2_image_desc(ctypes.Structure):
@@ -69,6 +69,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         f.restype = ctypes.c_int
     lib.dwt2_adjoint_l1.argtypes = [vp, vp, vp, ctypes.c_float, vp, vp]
     lib.dwt2_adjoint_l1.restype = ctypes.c_int
+    lib.dwt2_adjoint_l1_dev.argtypes = [vp, vp, vp, vp, ctypes.c_float, vp, vp]
+    lib.dwt2_adjoint_l1_dev.restype = ctypes.c_int
     lib.dwt2_autotune.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int)]
     lib.dwt2_autotune.restype = ctypes.c_int
     lib.dwt2_status.argtypes = [vp, vp]
@@ -80,6 +82,15 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.dwt2_forward_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_int, ctypes.c_int64, vp, vp, vp]
     lib.dwt2_forward_noalloc.restype = ctypes.c_int
+    lib.dwt2_noalloc_status.argtypes = [vp]
+    lib.dwt2_noalloc_status.restype = ctypes.c_int
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    lib.dwt2_band_rows.argtypes = [ctypes.c_int] * 5 + [i32p]
+    lib.dwt2_band_rows.restype = ctypes.c_int
+    lib.dwt2_band_rects.argtypes = [ctypes.c_int] * 6 + [i32p, ctypes.c_int]
+    lib.dwt2_band_rects.restype = ctypes.c_int
+    lib.dwt2_band_stitch.argtypes = [ctypes.c_int] * 7 + [vp, ctypes.c_int64, vp, ctypes.c_int64, vp]
+    lib.dwt2_band_stitch.restype = ctypes.c_int
     lib.dwt2_destroy.argtypes = [vp]
     lib.dwt2_destroy.restype = None
     lib.dwt2_strerror.argtypes = [ctypes.c_int]
@@ -137,6 +148,15 @@ def dwt2_adjoint_l1(plan: int, coef_ptr: int, gin_ptr: int, scale: float, ws_ptr
         raise Dwt2Error(rc, "dwt2_adjoint_l1")
 
 
+def dwt2_adjoint_l1_dev(plan: int, coef_ptr: int, gin_ptr: int, scale_dev_ptr: int, scale: float, ws_ptr: int = 0,
+                        stream: int = 0) -> None:
+    rc = load().dwt2_adjoint_l1_dev(ctypes.c_void_p(plan), ctypes.c_void_p(coef_ptr), ctypes.c_void_p(gin_ptr),
+                                    ctypes.c_void_p(scale_dev_ptr), ctypes.c_float(scale), ctypes.c_void_p(ws_ptr),
+                                    ctypes.c_void_p(stream))
+    if rc != DWT2_OK:
+        raise Dwt2Error(rc, "dwt2_adjoint_l1_dev")
+
+
 def dwt2_autotune(plan: int, in_ptr: int, coef_ptr: int, ws_ptr: int = 0, stream: int = 0,
                   choice: int = -1) -> int:
     """Time the candidate configurations (choice < 0) or apply one; returns the choice."""
@@ -174,6 +194,42 @@ def dwt2_forward_noalloc(wavelet: int, levels: int, scheme: int, coef_dtype: int
     return int(load().dwt2_forward_noalloc(int(wavelet), int(levels), int(scheme), int(coef_dtype), int(h),
                                            int(w), int(pitch_elems), ctypes.c_void_p(in_ptr),
                                            ctypes.c_void_p(coef_ptr), ctypes.c_void_p(stream)))
+
+
+def dwt2_noalloc_status(stream: int = 0) -> int:
+    """Synchronise the stream, return and clear dwt2_forward_noalloc's status word."""
+    return int(load().dwt2_noalloc_status(ctypes.c_void_p(stream)))
+
+
+def dwt2_band_rows(wavelet: int, levels: int, h: int, n_bands: int, band: int):
+    """(own0, own1, in0, in1): the input rows band `band` of `n_bands` owns and
+    the rows it transforms (host only)."""
+    r = (ctypes.c_int32 * 4)()
+    rc = load().dwt2_band_rows(int(wavelet), int(levels), int(h), int(n_bands), int(band), r)
+    if rc != DWT2_OK:
+        raise Dwt2Error(rc, "dwt2_band_rows")
+    return tuple(int(v) for v in r)
+
+
+def dwt2_band_rects(wavelet: int, levels: int, h: int, w: int, n_bands: int, band: int):
+    """The band's copy rectangles (src_row, dst_row, rows, col0, cols) (host only)."""
+    n = load().dwt2_band_rects(int(wavelet), int(levels), int(h), int(w), int(n_bands), int(band), None, 0)
+    if n < 0:
+        raise Dwt2Error(n, "dwt2_band_rects")
+    buf = (ctypes.c_int32 * (5 * max(n, 1)))()
+    n = load().dwt2_band_rects(int(wavelet), int(levels), int(h), int(w), int(n_bands), int(band), buf, n)
+    if n < 0:
+        raise Dwt2Error(n, "dwt2_band_rects")
+    return [tuple(int(buf[5 * i + k]) for k in range(5)) for i in range(n)]
+
+
+def dwt2_band_stitch(wavelet: int, levels: int, coef_dtype: int, h: int, w: int, n_bands: int, band: int,
+                     band_coef_ptr: int, band_pitch: int, coef_ptr: int, pitch: int, stream: int = 0) -> None:
+    rc = load().dwt2_band_stitch(int(wavelet), int(levels), int(coef_dtype), int(h), int(w), int(n_bands),
+                                 int(band), ctypes.c_void_p(band_coef_ptr), int(band_pitch),
+                                 ctypes.c_void_p(coef_ptr), int(pitch), ctypes.c_void_p(stream))
+    if rc != DWT2_OK:
+        raise Dwt2Error(rc, "dwt2_band_stitch")
 
 
 def dwt2_destroy(plan: int) -> None:

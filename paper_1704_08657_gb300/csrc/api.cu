@@ -322,7 +322,7 @@ int build_persistent(dwt2_plan_t p) {
 // The parameters of one image's inverse (or adjoint) level, without the
 // decomposition into units.
 InvParams inv_level_params(dwt2_plan_t p, const ImagePlan& ip, int l, const void* coef, void* out, void* workspace,
-                           size_t csz, bool l1, float l1_scale) {
+                           size_t csz, bool l1, float l1_scale, const float* l1_scale_dev = nullptr) {
     const char* coef_img = static_cast<const char*>(coef) + ip.d.offset_elems * csz;
     char* out_img = static_cast<char*>(out) + ip.d.offset_elems * 4;
     char* wsb = static_cast<char*>(workspace);
@@ -355,8 +355,10 @@ InvParams inv_level_params(dwt2_plan_t p, const ImagePlan& ip, int l, const void
     ipm.vec_ll = coarsest ? cvec : 1;
     ipm.vec_out = (ipm.out_pitch % 4 == 0) && aligned(ipm.out, 16);
     ipm.status = p->d_status;
+    ipm.timeout_ns = p->timeout_ns;
     ipm.l1 = l1;
     ipm.l1_scale = l1_scale;
+    ipm.l1_scale_dev = l1_scale_dev;
     return ipm;
 }
 
@@ -405,7 +407,7 @@ int inv_group_build(dwt2_plan_t p, const void* coef, void* out, void* workspace,
 }
 
 int inverse_grouped(dwt2_plan_t p, const void* coef, void* out, void* workspace, cudaStream_t s, bool adj, bool l1,
-                    float l1_scale) {
+                    float l1_scale, const float* l1_scale_dev) {
     auto& ic = p->icache;
     if (ic.blocks.empty() || ic.coef != coef || ic.out != out || ic.ws != workspace || ic.adj != int(adj)) {
         const int rc = inv_group_build(p, coef, out, workspace, adj);
@@ -419,6 +421,7 @@ int inverse_grouped(dwt2_plan_t p, const void* coef, void* out, void* workspace,
         for (int k = 0; k < g.n_img; ++k) {
             g.img[k].p.l1 = l1;
             g.img[k].p.l1_scale = l1_scale;
+            g.img[k].p.l1_scale_dev = l1_scale_dev;
         }
         const int l = ic.level[b];
         if (b == 0 || ic.level[b - 1] != l) prof_mark(p, l, true, s);
@@ -461,7 +464,7 @@ int forward_persistent(dwt2_plan_t p, const void* in, void* coef, void* workspac
     pp.counters = p->d_counters;
     pp.queue = p->d_counters + p->n_counters;
     pp.coef_vec = aligned(coef, 2 * csz);
-    pp.test_drop_signal = (p->flags & DWT2_FLAG_TEST_DROP_SIGNAL) != 0;
+    pp.test_drop_signal = (p->flags & DWT2_TESTONLY_DROP_SIGNAL) != 0;
     pp.status = p->d_status;
     pp.timeout_ns = p->timeout_ns;
     lp->use_tma = int(p->h_descs.size()) <= PML_TMA_MAX_DESCS && !p->pml_force_cpasync;
@@ -503,8 +506,7 @@ FwdParams level_outputs(dwt2_plan_t p, const ImagePlan& ip, int l, void* coef, v
     char* coef_img = static_cast<char*>(coef) + ip.d.offset_elems * csz;
     char* wsb = static_cast<char*>(workspace);
     const LevelGeom& g = ip.lv[l];
-    FwdParams fp;
-    memset(&fp, 0, sizeof(fp));
+    FwdParams fp{};  // every field not set below (overlap, test hook) is zero
     fp.h = g.h, fp.w = g.w, fp.hq = g.hq, fp.wq = g.wq, fp.hh = g.hh, fp.wh = g.wh;
     fp.coef = coef_img;
     fp.coef_pitch = ip.d.pitch_elems;
@@ -572,7 +574,8 @@ LevelLaunch level_launch(dwt2_plan_t p, const ImagePlan& ip, int l) {
 }
 
 // One forward level of one image.  dep_ctr / out_ctr: inter-level overlap
-// (FwdParams); null for a launch that waits for the previous grid.
+// (the FwdParams fields of those names); null for a launch that waits for the
+// previous grid.
 int forward_level(dwt2_plan_t p, const ImagePlan& ip, int l, const void* in, void* coef, void* workspace,
                   cudaStream_t s, const LevelLaunch& ll, const unsigned* dep_ctr = nullptr, int dep_need = 0,
                   int dep_seg = 1, unsigned* out_ctr = nullptr) {
@@ -585,18 +588,17 @@ int forward_level(dwt2_plan_t p, const ImagePlan& ip, int l, const void* in, voi
     fp.n_strips = dc.n_strips, fp.seg_rows = dc.seg_rows, fp.n_segs = dc.n_segs, fp.n_units = dc.n_units;
     fp.balanced = ll.balanced;
     fp.pdl = p->pdl;
-    FwdSync y;
-    y.dep_ctr = dep_ctr;
-    y.dep_need = dep_need;
-    y.dep_seg = dep_seg;
-    y.out_ctr = out_ctr;
-    y.test_drop = (p->flags & DWT2_FLAG_TEST_DROP_SIGNAL) != 0;
+    fp.dep_ctr = dep_ctr;
+    fp.dep_need = dep_need;
+    fp.dep_seg = dep_seg;
+    fp.out_ctr = out_ctr;
+    fp.test_drop = (p->flags & DWT2_TESTONLY_DROP_SIGNAL) != 0;
     int e;
     switch (p->coef_dtype) {
-        case DWT2_F32: e = launch_forward_f32(p->wavelet, p->scheme, box, row, fp, ll.grid, cfg, s, y); break;
-        case DWT2_F16: e = launch_forward_f16(p->wavelet, p->scheme, box, row, fp, ll.grid, cfg, s, y); break;
-        case DWT2_BF16: e = launch_forward_bf16(p->wavelet, p->scheme, box, row, fp, ll.grid, cfg, s, y); break;
-        default: e = launch_forward_i32(p->wavelet, p->scheme, box, row, fp, ll.grid, cfg, s, y); break;
+        case DWT2_F32: e = launch_forward_f32(p->wavelet, p->scheme, box, row, fp, ll.grid, cfg, s); break;
+        case DWT2_F16: e = launch_forward_f16(p->wavelet, p->scheme, box, row, fp, ll.grid, cfg, s); break;
+        case DWT2_BF16: e = launch_forward_bf16(p->wavelet, p->scheme, box, row, fp, ll.grid, cfg, s); break;
+        default: e = launch_forward_i32(p->wavelet, p->scheme, box, row, fp, ll.grid, cfg, s); break;
     }
     return e == cudaSuccess ? DWT2_OK : DWT2_ERR_CUDA;
 }
@@ -790,7 +792,7 @@ int dwt2_plan(dwt2_plan_t* out, int wavelet, int levels, int boundary, int in_dt
     if (scheme < DWT2_NONSEP || scheme > DWT2_NONSEP_CONV) return DWT2_ERR_INVALID_ARG;
     if (in_dtype < DWT2_F32 || in_dtype > DWT2_I32 || coef_dtype < DWT2_F32 || coef_dtype > DWT2_I32)
         return DWT2_ERR_INVALID_ARG;
-    if (flags & ~(DWT2_FLAG_PERSISTENT | DWT2_FLAG_TEST_DROP_SIGNAL)) return DWT2_ERR_INVALID_ARG;
+    if (flags & ~(DWT2_FLAG_PERSISTENT | DWT2_TESTONLY_DROP_SIGNAL)) return DWT2_ERR_INVALID_ARG;
     if ((flags & DWT2_FLAG_PERSISTENT) && scheme > DWT2_SEP_LIFTING) return DWT2_ERR_UNSUPPORTED;
     if (wavelet == DWT2_CDF97) {
         if (in_dtype != DWT2_F32 || coef_dtype == DWT2_I32) return DWT2_ERR_UNSUPPORTED;
@@ -996,7 +998,7 @@ int dwt2_forward(dwt2_plan_t p, const void* in, void* coef, void* workspace, voi
 // shared by the inverse and the adjoint: levels from the coarsest down.
 // l1: adjoint of l1_scale * sum |detail coefficients| (coef holds coefficients).
 static int run_inverse_like(dwt2_plan_t p, const void* coef, void* out, void* workspace, void* stream, bool adj,
-                            bool l1 = false, float l1_scale = 0.f) {
+                            bool l1 = false, float l1_scale = 0.f, const float* l1_scale_dev = nullptr) {
     if (!p || !coef || !out) return DWT2_ERR_INVALID_ARG;
     if (p->ws_bytes && !workspace) return DWT2_ERR_INVALID_ARG;
     if (workspace && !aligned(workspace, 256)) return DWT2_ERR_MISALIGNED;
@@ -1005,12 +1007,13 @@ static int run_inverse_like(dwt2_plan_t p, const void* coef, void* out, void* wo
     const size_t csz = adj ? 4 : dtype_size(p->coef_dtype);
     if (!aligned(coef, csz) || !aligned(out, 4)) return DWT2_ERR_MISALIGNED;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (p->n_images > 1) return inverse_grouped(p, coef, out, workspace, s, adj, l1, l1_scale);
+    if (l1_scale_dev && !aligned(l1_scale_dev, 4)) return DWT2_ERR_MISALIGNED;
+    if (p->n_images > 1) return inverse_grouped(p, coef, out, workspace, s, adj, l1, l1_scale, l1_scale_dev);
     const int inv_bps = adj ? inverse_blocks_per_sm(p->wavelet, inv_scheme(p->scheme), p->coef_dtype, true) : p->inv_bps;
     for (int l = p->levels - 1; l >= 0; --l) {
         prof_mark(p, l, true, s);
         for (const ImagePlan& ip : p->imgs) {
-            InvParams ipm = inv_level_params(p, ip, l, coef, out, workspace, csz, l1, l1_scale);
+            InvParams ipm = inv_level_params(p, ip, l, coef, out, workspace, csz, l1, l1_scale, l1_scale_dev);
             int grid = 0, balanced = 0;
             const Decomp dc = decompose(ip.lv[l], inv_out_quads(p->wavelet), p->sm_count, inv_bps, INV_NW, p->seg_env,
                                         p->balanced_env, &grid, &balanced);
@@ -1198,6 +1201,12 @@ int dwt2_adjoint(dwt2_plan_t p, const void* coef_grad, void* in_grad, void* work
 
 int dwt2_adjoint_l1(dwt2_plan_t p, const void* coef, void* in_grad, float scale, void* workspace, void* stream) {
     return run_inverse_like(p, coef, in_grad, workspace, stream, true, true, scale);
+}
+
+int dwt2_adjoint_l1_dev(dwt2_plan_t p, const void* coef, void* in_grad, const float* scale_dev, float scale,
+                        void* workspace, void* stream) {
+    if (!scale_dev) return DWT2_ERR_INVALID_ARG;
+    return run_inverse_like(p, coef, in_grad, workspace, stream, true, true, scale, scale_dev);
 }
 
 }  // extern "C"

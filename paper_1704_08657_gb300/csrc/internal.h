@@ -33,20 +33,14 @@ struct FwdParams {
     unsigned* status;          // device status word (may be null)
     uint64_t timeout_ns;       // bounded-wait limit
     int pdl;                   // host side: launch as a programmatic dependent of the previous kernel
-};
-
-// Overlap with the previous level (single-image plans): instead of waiting
-// for the previous grid, a unit waits (bounded) until the previous level's
-// segments covering its input rows are complete, and every unit bumps its own
-// segment's counter after its stores.  A kernel parameter of its own: growing
-// FwdParams from 120 to 152 bytes made forward launches lose or misplace the
-// stores of whole units on this toolchain (deterministic per build, gone when
-// debug prints were added; not explained), so FwdParams keeps its size.
-struct FwdSync {
-    const unsigned* dep_ctr;  // previous level's segment counters (null: wait for the previous grid)
-    int dep_need, dep_seg;    // strips of a previous-level segment; its height in input rows
-    unsigned* out_ctr;        // this level's segment counters (null: none)
-    int test_drop;            // test hook: unit (strip 0, segment 0) never bumps its counter
+    // Overlap with the previous level (single-image plans): instead of
+    // waiting for the previous grid, a unit waits (bounded) until the previous
+    // level's segments covering its input rows are complete, and every unit
+    // bumps its own segment's counter after its stores.
+    int dep_need, dep_seg;     // strips of a previous-level segment; its height in input rows
+    const unsigned* dep_ctr;   // previous level's segment counters (null: wait for the previous grid)
+    unsigned* out_ctr;         // this level's segment counters (null: none)
+    int test_drop;             // test-only hook: unit (strip 0, segment 0) never bumps its counter
 };
 
 // One inverse or adjoint level: bands in, pixels (compute type) out.
@@ -64,10 +58,13 @@ struct InvParams {
     int64_t out_pitch;
     int vec_in_lo, vec_in_hi, vec_ll, vec_out;
     unsigned* status;
+    uint64_t timeout_ns;       // bounded-wait limit
     // adjoint of an L1 loss on the detail bands: band values v read from the
-    // coefficients become l1_scale * sign(v) (detail bands) or 0 (coarsest LL)
+    // coefficients become l1_scale * sign(v) (detail bands) or 0 (coarsest LL);
+    // with l1_scale_dev the scale is l1_scale * *l1_scale_dev, read on the device
     int l1;
     float l1_scale;
+    const float* l1_scale_dev;
 };
 
 // Persistent forward: one descriptor per (image, level), one entry per unit
@@ -110,6 +107,7 @@ struct PmlParams {
 // level of up to INV_GROUP_MAX images, their parameters in one
 // __grid_constant__ kernel parameter, as for the grouped forward.
 constexpr int INV_GROUP_MAX = 200;
+static_assert(sizeof(InvParams) <= 152, "INV_GROUP_MAX images of parameters fit the 32 KB parameter space");
 struct InvGroupImg {
     InvParams p;
     int u_begin;
@@ -156,7 +154,7 @@ int fused_blocks_per_sm(int wav, int scheme, int coef_dtype);
 // tensor maps and parameters are one __grid_constant__ kernel parameter (read
 // from the constant bank where used); unit u belongs to the image whose
 // [u_begin, u_begin + n_units) holds it.
-constexpr int GROUP_MAX = 80;
+constexpr int GROUP_MAX = 76;
 struct GroupImg {
     FwdParams p;
     int u_begin;
@@ -167,6 +165,7 @@ struct GroupLaunch {
     int n_img, n_units;
     int wait_prev;  // 1: the first launch of a level (its inputs come from earlier launches)
 };
+static_assert(sizeof(GroupLaunch) <= 32764, "a grouped launch block fits the kernel parameter space");
 
 // forward launch configuration
 struct FwdCfg {
@@ -184,13 +183,13 @@ inline int fwd_strip_px(const FwdCfg& c) { return 64 * c.ql; }
 // kernel launchers, one translation unit per coefficient type; they return a
 // cudaError_t value
 int launch_forward_f32(int wav, int scheme, const CUtensorMap& box, const CUtensorMap& row, const FwdParams& p,
-                       int grid, const FwdCfg& cfg, cudaStream_t s, const FwdSync& y);
+                       int grid, const FwdCfg& cfg, cudaStream_t s);
 int launch_forward_f16(int wav, int scheme, const CUtensorMap& box, const CUtensorMap& row, const FwdParams& p,
-                       int grid, const FwdCfg& cfg, cudaStream_t s, const FwdSync& y);
+                       int grid, const FwdCfg& cfg, cudaStream_t s);
 int launch_forward_bf16(int wav, int scheme, const CUtensorMap& box, const CUtensorMap& row, const FwdParams& p,
-                        int grid, const FwdCfg& cfg, cudaStream_t s, const FwdSync& y);
+                        int grid, const FwdCfg& cfg, cudaStream_t s);
 int launch_forward_i32(int wav, int scheme, const CUtensorMap& box, const CUtensorMap& row, const FwdParams& p,
-                       int grid, const FwdCfg& cfg, cudaStream_t s, const FwdSync& y);
+                       int grid, const FwdCfg& cfg, cudaStream_t s);
 int launch_group_f32(int wav, int scheme, const GroupLaunch& g, int grid, const FwdCfg& cfg, int pdl, cudaStream_t s);
 int launch_group_f16(int wav, int scheme, const GroupLaunch& g, int grid, const FwdCfg& cfg, int pdl, cudaStream_t s);
 int launch_group_bf16(int wav, int scheme, const GroupLaunch& g, int grid, const FwdCfg& cfg, int pdl, cudaStream_t s);

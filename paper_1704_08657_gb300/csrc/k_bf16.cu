@@ -4,8 +4,8 @@
 namespace dwt2 {
 
 int launch_forward_bf16(int wav, int scheme, const CUtensorMap& box, const CUtensorMap& row, const FwdParams& p,
-                   int grid, const FwdCfg& cfg, cudaStream_t s, const FwdSync& y) {
-    return launch_forward_t<__nv_bfloat16>(wav, scheme, box, row, p, grid, cfg, s, y);
+                   int grid, const FwdCfg& cfg, cudaStream_t s) {
+    return launch_forward_t<__nv_bfloat16>(wav, scheme, box, row, p, grid, cfg, s);
 }
 
 int launch_inverse_bf16(int wav, int scheme, const InvParams& p, int grid, cudaStream_t s) {

@@ -384,18 +384,18 @@ __device__ __forceinline__ void stage_ring(unsigned char* smem, int warp, CT*& b
 // previous-level segment holding such a row has all its strips complete, then
 // orders its later TMA reads after what it observed.
 template <int LAG, int QR, int WARM>
-__device__ __forceinline__ bool fwd_wait_inputs(const FwdParams& p, const FwdSync& y, int R0, int R1, int lane) {
+__device__ __forceinline__ bool fwd_wait_inputs(const FwdParams& p, int R0, int R1, int lane) {
     bool ok = true;
     if (lane == 0) {
         int lo = max(0, 2 * (R0 - WARM));
         const int end = 2 * (R1 + LAG + QR - 2) + 2;  // one past the last streamed row
         const int hi = min(p.h, end);
         if (end > p.h) lo = max(0, min(lo, 2 * p.h - 1 - end));  // mirrored rows past the bottom
-        for (int g = lo / y.dep_seg; g <= (hi - 1) / y.dep_seg && ok; ++g) {
-            const unsigned* c = y.dep_ctr + g;
-            if (ld_acquire(c) >= unsigned(y.dep_need)) continue;
+        for (int g = lo / p.dep_seg; g <= (hi - 1) / p.dep_seg && ok; ++g) {
+            const unsigned* c = p.dep_ctr + g;
+            if (ld_acquire(c) >= unsigned(p.dep_need)) continue;
             const uint64_t t0 = globaltimer_ns();
-            while (ld_acquire(c) < unsigned(y.dep_need)) {
+            while (ld_acquire(c) < unsigned(p.dep_need)) {
                 if (globaltimer_ns() - t0 > p.timeout_ns) {
                     ok = false;
                     break;
@@ -439,7 +439,7 @@ struct FwdMinBlocks<Fwd53<S, QL>, 4> {
 template <class Pipe, class OutT, int QL, int QR, int NST, int NW, bool SPEC>
 __global__ void __launch_bounds__(NW * 32, FwdMinBlocks<Pipe, NW>::value)
     fwd_tma_kernel(const __grid_constant__ CUtensorMap tm_box, const __grid_constant__ CUtensorMap tm_row,
-                   const FwdParams p, const FwdSync y) {
+                   const FwdParams p) {
     using CT = typename Pipe::CT;
     constexpr int HQ = PipeGeom<Pipe>::HALO;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -458,14 +458,14 @@ __global__ void __launch_bounds__(NW * 32, FwdMinBlocks<Pipe, NW>::value)
     // the input (the previous level's low-low band) and the outputs are only
     // touched after the previous grid in the stream has completed, or, with
     // inter-level overlap, after the segments a unit reads are complete
-    if (y.dep_ctr == nullptr) griddep_wait();
+    if (p.dep_ctr == nullptr) griddep_wait();
     griddep_launch_dependents();
     const TmaLoader ld{&tm_box, &tm_row};
     uint32_t gstage = 0;
     Pieces<FwdParams> pieces(p, blockIdx.x * NW + warp, gridDim.x * NW);
     int s, R0, R1;
     while (pieces.next(p, s, R0, R1)) {
-        if (y.dep_ctr != nullptr && !fwd_wait_inputs<Pipe::LAG, QR, PipeGeom<Pipe>::WARM>(p, y, R0, R1, lane)) return;
+        if (p.dep_ctr != nullptr && !fwd_wait_inputs<Pipe::LAG, QR, PipeGeom<Pipe>::WARM>(p, R0, R1, lane)) return;
         bool ok;
         if constexpr (SPEC) {
             if (fwd_pairs_ok(p, s * (2 * (32 * QL - 2 * HQ)) - 2 * HQ, QL, HQ))
@@ -477,7 +477,7 @@ __global__ void __launch_bounds__(NW * 32, FwdMinBlocks<Pipe, NW>::value)
             ok = fwd_unit<Pipe, OutT, QL, QR, NST, 0>(p, ld, s, R0, R1, bufs, bars, gstage, lane);
         }
         if (!ok) return;
-        if (y.out_ctr != nullptr && !(y.test_drop && s == 0 && R0 == 0)) fwd_signal(y.out_ctr + R0 / p.seg_rows, lane);
+        if (p.out_ctr != nullptr && !(p.test_drop && s == 0 && R0 == 0)) fwd_signal(p.out_ctr + R0 / p.seg_rows, lane);
     }
 }
 
@@ -749,7 +749,7 @@ __device__ __forceinline__ void load_bands(const InvParams& p, int vi, int jb, b
 // L1 adjoint: the gradient of l1_scale * sum |detail| w.r.t. the coefficients
 template <class CT, int QL>
 __device__ __forceinline__ void l1_transform(const InvParams& p, Row<CT, QL>& r) {
-    const float s = p.l1_scale;
+    const float s = p.l1_scale_dev ? p.l1_scale * *p.l1_scale_dev : p.l1_scale;
 #pragma unroll
     for (int q = 0; q < QL; ++q) {
         if (!p.ll_is_ct) r.c1[q] = CT(0);  // the coarsest LL is not in the loss
@@ -993,10 +993,10 @@ __device__ __forceinline__ bool inv_unit_staged(const InvParams& p, int s, int R
                 if (!ok) return;
                 const uint32_t gs = gstage + t;
                 slot = gs % NST;
-                if (!mbar_wait_bounded(&bars[slot], (gs / NST) & 1u, p.status, 2000000000ull)) {
+                if (!mbar_wait_bounded(&bars[slot], (gs / NST) & 1u, p.status, p.timeout_ns)) {
                     for (int u = t + 1; u < NT && u < t + NST; ++u) {
                         const uint32_t gu = gstage + u;
-                        mbar_wait_bounded(&bars[gu % NST], (gu / NST) & 1u, nullptr, 2000000000ull);
+                        mbar_wait_bounded(&bars[gu % NST], (gu / NST) & 1u, nullptr, p.timeout_ns);
                     }
                     ok = false;
                     return;

@@ -10,8 +10,7 @@
 namespace dwt2 {
 
 template <class Pipe, class OutT, int QL, int QR, int NST, int NW, bool SPEC>
-int launch_fwd_one(const CUtensorMap& box, const CUtensorMap& row, const FwdParams& p, int grid, cudaStream_t s,
-                   const FwdSync& y) {
+int launch_fwd_one(const CUtensorMap& box, const CUtensorMap& row, const FwdParams& p, int grid, cudaStream_t s) {
     auto k = fwd_tma_kernel<Pipe, OutT, QL, QR, NST, NW, SPEC>;
     constexpr size_t smem = fwd_smem_bytes<QL, QR, NST, NW>();
     if (smem > 48 * 1024) {
@@ -23,7 +22,7 @@ int launch_fwd_one(const CUtensorMap& box, const CUtensorMap& row, const FwdPara
         }
     }
     if (!p.pdl) {
-        k<<<grid, NW * 32, smem, s>>>(box, row, p, y);
+        k<<<grid, NW * 32, smem, s>>>(box, row, p);
         return cudaGetLastError();
     }
     cudaLaunchConfig_t lc = {};
@@ -36,7 +35,7 @@ int launch_fwd_one(const CUtensorMap& box, const CUtensorMap& row, const FwdPara
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     lc.attrs = attr;
     lc.numAttrs = 1;
-    return cudaLaunchKernelEx(&lc, k, box, row, p, y);
+    return cudaLaunchKernelEx(&lc, k, box, row, p);
 }
 
 // the compiled forward configurations (quads per lane, quad rows per stage,
@@ -171,10 +170,10 @@ int occupancy_inverse_t(int wav, int scheme) {
 
 template <template <int, int> class PipeT, int S, class OutT>
 int launch_fwd_cfgs(const CUtensorMap& box, const CUtensorMap& row, const FwdParams& p, int grid,
-                    const FwdCfg& c, cudaStream_t s, const FwdSync& y) {
+                    const FwdCfg& c, cudaStream_t s) {
 #define DWT2_X(I_, QL_, QR_, NST_, NW_, SP_)                                             \
     if (c.ql == QL_ && c.qr == QR_ && c.nst == NST_ && c.nw == NW_ && c.spec == SP_) \
-        return launch_fwd_one<PipeT<S, QL_>, OutT, QL_, QR_, NST_, NW_, SP_ != 0>(box, row, p, grid, s, y);
+        return launch_fwd_one<PipeT<S, QL_>, OutT, QL_, QR_, NST_, NW_, SP_ != 0>(box, row, p, grid, s);
     DWT2_FWD_CFG_LIST(DWT2_X)
 #undef DWT2_X
     return cudaErrorInvalidValue;
@@ -182,28 +181,28 @@ int launch_fwd_cfgs(const CUtensorMap& box, const CUtensorMap& row, const FwdPar
 
 template <class OutT>
 int launch_forward_t(int wav, int scheme, const CUtensorMap& box, const CUtensorMap& row, const FwdParams& p,
-                     int grid, const FwdCfg& c, cudaStream_t s, const FwdSync& y) {
+                     int grid, const FwdCfg& c, cudaStream_t s) {
     if constexpr (std::is_same<OutT, int>::value) {
         if (wav != WAV_CDF53I) return cudaErrorInvalidValue;
-        if (scheme == SCHEME_SEP) return launch_fwd_cfgs<Fwd53, SCHEME_SEP, int>(box, row, p, grid, c, s, y);
-        if (scheme == SCHEME_NONSEP) return launch_fwd_cfgs<Fwd53, SCHEME_NONSEP, int>(box, row, p, grid, c, s, y);
+        if (scheme == SCHEME_SEP) return launch_fwd_cfgs<Fwd53, SCHEME_SEP, int>(box, row, p, grid, c, s);
+        if (scheme == SCHEME_NONSEP) return launch_fwd_cfgs<Fwd53, SCHEME_NONSEP, int>(box, row, p, grid, c, s);
         return cudaErrorInvalidValue;
     } else {
         if (wav == WAV_DD137) {
             if (scheme == SCHEME_NONSEP)
-                return launch_fwd_cfgs<Fwd137, SCHEME_NONSEP, OutT>(box, row, p, grid, c, s, y);
-            if (scheme == SCHEME_SEP) return launch_fwd_cfgs<Fwd137, SCHEME_SEP, OutT>(box, row, p, grid, c, s, y);
+                return launch_fwd_cfgs<Fwd137, SCHEME_NONSEP, OutT>(box, row, p, grid, c, s);
+            if (scheme == SCHEME_SEP) return launch_fwd_cfgs<Fwd137, SCHEME_SEP, OutT>(box, row, p, grid, c, s);
             return cudaErrorInvalidValue;
         }
         if (wav != WAV_CDF97) return cudaErrorInvalidValue;
-        if (scheme == SCHEME_NONSEP) return launch_fwd_cfgs<Fwd97, SCHEME_NONSEP, OutT>(box, row, p, grid, c, s, y);
-        if (scheme == SCHEME_REDUCED) return launch_fwd_cfgs<Fwd97, SCHEME_REDUCED, OutT>(box, row, p, grid, c, s, y);
-        if (scheme == SCHEME_SEP) return launch_fwd_cfgs<Fwd97, SCHEME_SEP, OutT>(box, row, p, grid, c, s, y);
+        if (scheme == SCHEME_NONSEP) return launch_fwd_cfgs<Fwd97, SCHEME_NONSEP, OutT>(box, row, p, grid, c, s);
+        if (scheme == SCHEME_REDUCED) return launch_fwd_cfgs<Fwd97, SCHEME_REDUCED, OutT>(box, row, p, grid, c, s);
+        if (scheme == SCHEME_SEP) return launch_fwd_cfgs<Fwd97, SCHEME_SEP, OutT>(box, row, p, grid, c, s);
         if (scheme == SCHEME_POLYCONV)
-            return launch_fwd_cfgs<Fwd97S, SCHEME_POLYCONV, OutT>(box, row, p, grid, c, s, y);
-        if (scheme == SCHEME_CONV) return launch_fwd_cfgs<Fwd97S, SCHEME_CONV, OutT>(box, row, p, grid, c, s, y);
+            return launch_fwd_cfgs<Fwd97S, SCHEME_POLYCONV, OutT>(box, row, p, grid, c, s);
+        if (scheme == SCHEME_CONV) return launch_fwd_cfgs<Fwd97S, SCHEME_CONV, OutT>(box, row, p, grid, c, s);
         if (scheme == SCHEME_NSCONV)
-            return launch_fwd_cfgs<Fwd97S, SCHEME_NSCONV, OutT>(box, row, p, grid, c, s, y);
+            return launch_fwd_cfgs<Fwd97S, SCHEME_NSCONV, OutT>(box, row, p, grid, c, s);
         return cudaErrorInvalidValue;
     }
 }

@@ -13,9 +13,13 @@
 // it keeps the last call's contents; nothing in it has to start at zero
 // (each call writes every element before reading it).  Calls whose work
 // overlaps on the GPU (two streams, or two host threads on one stream
-// without ordering) race on the array.
+// without ordering) race on the array.  A second file-scope word is the
+// status word of these calls: a bounded device wait that runs out sets it,
+// and dwt2_noalloc_status reads and clears it (it starts at zero when the
+// library is loaded).
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -32,10 +36,13 @@ constexpr int NOALLOC_MAX_DEVICES = 64;
 // The scratch.  In host code this name is only a host-side stand-in for the
 // device array; kernels get the device address from cudaGetSymbolAddress.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+static __device__ unsigned g_noalloc_status;
 
 struct NoallocDevice {
     bool ready;
-    void* scratch;  // device address of g_noalloc_scratch on this device
+    void* scratch;     // device address of g_noalloc_scratch on this device
+    unsigned* status;  // device address of g_noalloc_status on this device
+    uint64_t timeout_ns;
     int sm_count;
     int fwd_bps[4][3];  // resident forward blocks per SM by coefficient type and scheme
 };
@@ -43,15 +50,18 @@ struct NoallocDevice {
 std::mutex g_noalloc_mu;
 NoallocDevice g_noalloc_dev[NOALLOC_MAX_DEVICES];
 
-// Set-up, once per device, with that device current: the device address of
-// the scratch array and the SM count.
+// Set-up, once per device, with that device current: the device addresses
+// of the scratch array and the status word, the SM count and the bounded-wait
+// limit (DWT2_TIMEOUT_MS, as for plans; read once).
 int noalloc_setup(int dev, NoallocDevice** out) {
     if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return DWT2_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
     NoallocDevice& d = g_noalloc_dev[dev];
     if (!d.ready) {
         void* ptr = nullptr;
-        if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || ptr == nullptr) {
+        void* sptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || ptr == nullptr ||
+            cudaGetSymbolAddress(&sptr, g_noalloc_status) != cudaSuccess || sptr == nullptr) {
             cudaGetLastError();
             return DWT2_ERR_CUDA;
         }
@@ -61,6 +71,10 @@ int noalloc_setup(int dev, NoallocDevice** out) {
             return DWT2_ERR_CUDA;
         }
         d.scratch = ptr;
+        d.status = static_cast<unsigned*>(sptr);
+        const char* tm = getenv("DWT2_TIMEOUT_MS");
+        const int ms = (tm && *tm) ? atoi(tm) : 2000;
+        d.timeout_ns = uint64_t(ms > 0 ? ms : 2000) * 1000000ull;
         d.sm_count = sms;
         for (int dt = 0; dt < 4; ++dt)
             for (int sc = 0; sc < 3; ++sc)
@@ -167,8 +181,7 @@ extern "C" int dwt2_forward_noalloc(int wavelet, int levels, int scheme, int coe
         rc = noalloc_map(&box, src, W, H, src_pitch, fwd_strip_px(cfg), 2 * cfg.qr, is_int);
         if (rc == DWT2_OK) rc = noalloc_map(&row, src, W, H, src_pitch, fwd_strip_px(cfg), 1, is_int);
         if (rc != DWT2_OK) return rc;
-        FwdParams fp;
-        memset(&fp, 0, sizeof(fp));
+        FwdParams fp{};  // no inter-level overlap: every level waits for the previous grid
         fp.h = H, fp.w = W, fp.hq = (H + 1) / 2, fp.wq = (W + 1) / 2, fp.hh = H / 2, fp.wh = W / 2;
         // segments of the height dwt2_forward chooses (rounds x (rows + 4) minimal)
         fp.n_strips = (fp.wq + fwd_out_quads(cfg, wavelet) - 1) / fwd_out_quads(cfg, wavelet);
@@ -205,16 +218,41 @@ extern "C" int dwt2_forward_noalloc(int wavelet, int levels, int scheme, int coe
         fp.vec_lo = coef_vec;
         fp.vec_hi = coef_vec && (fp.wq % 2 == 0);
         fp.vec_ll = last ? coef_vec : 1;
-        fp.status = nullptr;  // no status word: device-side timeouts are not reported here
-        fp.timeout_ns = 2000000000ull;
+        fp.status = st->status;
+        fp.timeout_ns = st->timeout_ns;
         int e;
         switch (coef_dtype) {
-            case DWT2_F32: e = launch_forward_f32(wavelet, scheme, box, row, fp, grid, cfg, s, FwdSync{nullptr, 0, 1, nullptr, 0}); break;
-            case DWT2_F16: e = launch_forward_f16(wavelet, scheme, box, row, fp, grid, cfg, s, FwdSync{nullptr, 0, 1, nullptr, 0}); break;
-            case DWT2_BF16: e = launch_forward_bf16(wavelet, scheme, box, row, fp, grid, cfg, s, FwdSync{nullptr, 0, 1, nullptr, 0}); break;
-            default: e = launch_forward_i32(wavelet, scheme, box, row, fp, grid, cfg, s, FwdSync{nullptr, 0, 1, nullptr, 0}); break;
+            case DWT2_F32: e = launch_forward_f32(wavelet, scheme, box, row, fp, grid, cfg, s); break;
+            case DWT2_F16: e = launch_forward_f16(wavelet, scheme, box, row, fp, grid, cfg, s); break;
+            case DWT2_BF16: e = launch_forward_bf16(wavelet, scheme, box, row, fp, grid, cfg, s); break;
+            default: e = launch_forward_i32(wavelet, scheme, box, row, fp, grid, cfg, s); break;
         }
         if (e != cudaSuccess) return DWT2_ERR_CUDA;
     }
+    return DWT2_OK;
+}
+
+// The status word of dwt2_forward_noalloc on the current device: wait for the
+// stream, read the word and clear it.  Copies through no caller or library
+// allocation (a four-byte read into a local variable, a four-byte clear).
+extern "C" int dwt2_noalloc_status(void* stream) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return DWT2_ERR_CUDA;
+    }
+    NoallocDevice* st = nullptr;
+    const int rc = noalloc_setup(dev, &st);
+    if (rc != DWT2_OK) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned h = 0;
+    if (cudaMemcpyAsync(&h, st->status, sizeof(unsigned), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess || cudaMemsetAsync(st->status, 0, sizeof(unsigned), s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return DWT2_ERR_CUDA;
+    }
+    if (h & dwt2::DEV_TIMEOUT) return DWT2_ERR_TIMEOUT;
+    if (h & dwt2::DEV_CHECK) return DWT2_ERR_DEVICE_CHECK;
     return DWT2_OK;
 }

@@ -223,11 +223,67 @@ class L1DetailLoss(torch.autograd.Function):
     def backward(ctx, gout: torch.Tensor):
         (c,) = ctx.saved_tensors
         plan = ctx.plan
-        return plan.adjoint_l1(c, float(gout) / plan.n_detail()), None
+        # the upstream gradient stays on the device: the kernels read it, so
+        # the backward neither synchronises nor leaves CUDA-graph capture
+        g = gout.detach().to(device=c.device, dtype=torch.float32).reshape(1).contiguous()
+        out = torch.empty_like(c)
+        plan._check(out, torch.float32, "out")
+        abi.dwt2_adjoint_l1_dev(plan.handle, c.data_ptr(), out.data_ptr(), g.data_ptr(), 1.0 / plan.n_detail(),
+                                plan.workspace.data_ptr(), _stream_handle(None))
+        ctx.keep = g  # alive until the kernels that read it have been queued after it
+        return out, None
 
 
 def l1_detail_loss(x: torch.Tensor, plan: Plan) -> torch.Tensor:
     return L1DetailLoss.apply(x, plan)
+
+
+def band_rows(h: int, levels: int, n_bands: int, wavelet: str = "cdf97") -> List[Tuple[int, int, int, int]]:
+    """(own0, own1, in0, in1) of every row band of an image of h rows
+    (dwt2_band_rows)."""
+    return [abi.dwt2_band_rows(WAVELETS[wavelet], levels, h, n_bands, b) for b in range(n_bands)]
+
+
+class BandPlan:
+    """Forward transform of one row band of an h x w image (dwt2_band_rows):
+    a single-image plan over the band's rows [in0, in1) and the copy of the
+    coefficients it owns into the image's Mallat layout (dwt2_band_stitch).
+    Bands exchange no data: each can run on its own GPU from its own rows of
+    the image."""
+
+    def __init__(self, h: int, w: int, levels: int, n_bands: int, band: int, pitch: Optional[int] = None,
+                 wavelet: str = "cdf97", scheme: str = "nonsep", coef_dtype: torch.dtype = torch.float32,
+                 device: Optional[torch.device] = None):
+        self.h, self.w, self.levels = h, w, levels
+        self.n_bands, self.band = n_bands, band
+        self.pitch = pitch if pitch is not None else w
+        self.wavelet, self.coef_dtype = wavelet, coef_dtype
+        self.own0, self.own1, self.in0, self.in1 = abi.dwt2_band_rows(WAVELETS[wavelet], levels, h, n_bands, band)
+        self.plan = Plan.single(self.in1 - self.in0, w, levels, pitch=self.pitch, wavelet=wavelet, scheme=scheme,
+                                coef_dtype=coef_dtype, device=device)
+        self.band_coef = torch.empty((self.in1 - self.in0) * self.pitch, dtype=coef_dtype, device=self.plan.device)
+
+    def forward_rows(self, x_rows: torch.Tensor, coef: torch.Tensor,
+                     stream: Optional[torch.cuda.Stream] = None) -> torch.Tensor:
+        """x_rows: the image rows [in0, in1) (pitch elements each); coef: the
+        whole image's coefficient buffer, of which the owned rectangles are
+        written."""
+        self.plan._check(x_rows, self.plan.in_dtype, "x_rows")
+        st = _stream_handle(stream)
+        abi.dwt2_forward(self.plan.handle, x_rows.data_ptr(), self.band_coef.data_ptr(),
+                         self.plan.workspace.data_ptr(), st)
+        abi.dwt2_band_stitch(WAVELETS[self.wavelet], self.levels, DTYPES[self.coef_dtype], self.h, self.w,
+                             self.n_bands, self.band, self.band_coef.data_ptr(), self.pitch, coef.data_ptr(),
+                             self.pitch, st)
+        return coef
+
+    def forward(self, x: torch.Tensor, coef: torch.Tensor, stream: Optional[torch.cuda.Stream] = None):
+        """x: the whole image (h rows of pitch elements)."""
+        rows = x.reshape(-1)[self.in0 * self.pitch:self.in1 * self.pitch]
+        return self.forward_rows(rows, coef, stream)
+
+    def close(self):
+        self.plan.close()
 
 
 def band_slices(h: int, w: int, levels: int) -> List[Tuple[int, str, slice, slice]]:

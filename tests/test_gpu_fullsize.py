@@ -12,7 +12,7 @@ import torch
 import oracle
 from paper_1704_08657_gb300 import synth
 from paper_1704_08657_gb300.dwt import Plan
-from tests.util import assert_dd_close, assert_fp32_close, assert_lowp_close
+from tests.util import assert_dd_close, assert_fp32_close, assert_lowp_close, report_band_errors
 
 pytestmark = pytest.mark.gpu
 
@@ -38,6 +38,7 @@ def test_bench_workload_matches_oracle(image, scheme):
     assert plan.status() == 0
     got = out.cpu().numpy()
     assert np.isfinite(got).all()
+    report_band_errors(got, ref, LEVELS, 255.0, f"16384^2 {scheme} FP32")
     assert_fp32_close(got, ref, LEVELS, 255.0, f"16384^2 {scheme}")
     plan.close()
 
@@ -51,6 +52,7 @@ def test_bench_workload_fp16_storage(image):
     c = plan.forward(xd, out)
     torch.cuda.synchronize()
     assert plan.status() == 0
+    report_band_errors(c.float().cpu().numpy(), ref, LEVELS, 255.0, "16384^2 reduced FP16 storage")
     assert_lowp_close(c.float().cpu().numpy(), ref, LEVELS, 1e-3, "16384^2 fp16")
     plan.close()
 

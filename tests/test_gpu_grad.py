@@ -98,3 +98,38 @@ def test_l1_finite_differences_full_size():
         bound = float(((cp.abs() + cm.abs()).double() * flip).sum()) / (2 * hstep * n)
         assert abs(fd - ad) <= bound + 1e-3 * abs(ad) + 1e-9, (k, fd, ad, bound, int(flip.sum()))
         del cp, cm, v, flip
+
+
+def test_l1_backward_reads_its_scale_on_the_device():
+    """dwt2_adjoint_l1_dev: the upstream gradient stays on the device (no host
+    synchronisation in L1DetailLoss.backward), so the call also replays from a
+    CUDA graph with a scale written after the capture."""
+    from paper_1704_08657_gb300 import abi
+    h, w, levels = 300, 260, 3
+    plan = Plan.single(h, w, levels)
+    x = torch.from_numpy(synth.uniform(h, w, seed=2)).cuda()
+    c = plan.forward(x)
+    inv_n = 1.0 / plan.n_detail()
+    ref = plan.adjoint_l1(c, 2.5 * inv_n)
+    sd = torch.tensor([2.5], device="cuda")
+    out = torch.full_like(c, float("nan"))
+    abi.dwt2_adjoint_l1_dev(plan.handle, c.data_ptr(), out.data_ptr(), sd.data_ptr(), inv_n,
+                            plan.workspace.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert torch.allclose(out, ref, rtol=1e-6, atol=0)
+    graph = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.graph(graph, stream=s):
+        abi.dwt2_adjoint_l1_dev(plan.handle, c.data_ptr(), out.data_ptr(), sd.data_ptr(), inv_n,
+                                plan.workspace.data_ptr(), s.cuda_stream)
+    sd.fill_(-5.0)
+    out.fill_(float("nan"))
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.allclose(out, -2.0 * ref, rtol=1e-6, atol=0)
+    assert plan.status() == 0
+    # and autograd's backward goes through it
+    xg = x.clone().requires_grad_(True)
+    (3.0 * l1_detail_loss(xg, plan)).backward()
+    assert torch.allclose(xg.grad, plan.adjoint_l1(c, 3.0 * inv_n), rtol=1e-6, atol=0)

@@ -70,7 +70,7 @@ def test_dropped_segment_signal_times_out(monkeypatch):
     monkeypatch.setenv("DWT2_LEVEL_OVERLAP", "1")
     h = w = 1024
     x = torch.from_numpy(synth.uniform(h, w, seed=1)).cuda()
-    plan = Plan.single(h, w, 3, flags=abi.DWT2_FLAG_TEST_DROP_SIGNAL)
+    plan = Plan.single(h, w, 3, flags=abi.DWT2_TESTONLY_DROP_SIGNAL)
     plan.forward(x)
     assert plan.status() == abi.DWT2_ERR_TIMEOUT
     assert plan.status() == 0

@@ -122,7 +122,7 @@ def test_dropped_signal_times_out_without_hanging(monkeypatch):
     monkeypatch.setenv("DWT2_TIMEOUT_MS", "30")
     h = w = 512
     x = torch.from_numpy(synth.uniform(h, w, seed=1)).cuda()
-    plan = Plan.single(h, w, 3, flags=abi.DWT2_FLAG_PERSISTENT | abi.DWT2_FLAG_TEST_DROP_SIGNAL)
+    plan = Plan.single(h, w, 3, flags=abi.DWT2_FLAG_PERSISTENT | abi.DWT2_TESTONLY_DROP_SIGNAL)
     plan.forward(x)
     assert plan.status() == abi.DWT2_ERR_TIMEOUT
     assert plan.status() == 0  # the status word was cleared
@@ -176,7 +176,7 @@ def test_batch_inverse_adjoint_and_l1():
 @pytest.mark.parametrize("scheme,coef_dtype", [("reduced", torch.float32), ("sep", torch.float16),
                                                ("polyconv", torch.float32)])
 def test_grouped_batch_equals_single_image_plans(scheme, coef_dtype):
-    """A plan of several images runs each level as grouped launches (up to 80
+    """A plan of several images runs each level as grouped launches (up to 76
     images per launch, every scheme); every image equals its own single-image
     plan bit for bit, for the default and for tuned configurations."""
     shapes = synth.batch_shapes(40, seed=7)
@@ -219,7 +219,7 @@ def test_grouped_batch_int53():
 
 
 def test_grouped_batch_over_several_launches_and_graph():
-    """More images than one launch holds (80): the level's launches overlap,
+    """More images than one launch holds (76): the level's launches overlap,
     the next level waits for all of them; the same under CUDA-graph capture."""
     shapes = synth.batch_shapes(200, seed=13)
     buf, descs = _batch(shapes, seed=14)
