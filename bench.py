@@ -483,116 +483,56 @@ def run_ours(a):
                                "and 3 streams", "result_matches_device_run": ok, "host_link": link}
         del hin, hout, xd, cd
 
-    # schemes and precisions on the same image (level-1 kernel and whole pyramid)
-    if not a.no_compare:
+    # every workload of the benchmark's configurations, each with its own
+    # roofline fraction (C1 small image, C2 size sweep, C3 precision, C4
+    # batching, C5 differentiation)
+    if not a.no_compare and world == 1:
         comp = {}
-        ksteps = max(3, min(a.steps, 100))
-        variants = [("nonsep", torch.float32), ("reduced", torch.float32), ("sep", torch.float32),
-                    ("polyconv", torch.float32), ("conv", torch.float32), ("nsconv", torch.float32),
-                    ("reduced", torch.float16), ("reduced", torch.bfloat16), ("nonsep", torch.float16),
-                    ("sep", torch.float16), ("polyconv", torch.float16), ("conv", torch.float16),
-                    ("nsconv", torch.float16)]
-        names = {torch.float32: "f32", torch.float16: "f16", torch.bfloat16: "bf16"}
-        for scheme, cdt in variants:
-            for levels in (1, a.levels):
-                p = make(scheme, cdt, levels)
-                out = torch.empty_like(x, dtype=cdt)
-                p.autotune(x, out, stream)
-                for _ in range(3):
-                    p.forward(x, out, stream)
-                barrier()
-                c0 = torch.cuda.Event(enable_timing=True)
-                c1 = torch.cuda.Event(enable_timing=True)
-                c0.record(stream)
-                for _ in range(ksteps):
-                    p.forward(x, out, stream)
-                c1.record(stream)
-                barrier()
-                ms = c0.elapsed_time(c1) / ksteps
-                # the level-1 kernel from the plan's event pairs, in a pass of its own
-                abi.dwt2_profile(p.handle, True)
-                for _ in range(min(ksteps, 50)):
-                    p.forward(x, out, stream)
-                barrier()
-                bpp = 4 + (4 if cdt == torch.float32 else 2)
-                l1m = abi.dwt2_profile_read(p.handle, 1)[0]
-                abi.dwt2_profile(p.handle, False)
-                comp[f"{scheme}/{names[cdt]}/L{levels}"] = {
-                    "gpx_s": n * n / (ms * 1e-3) / 1e9, "ms": ms,
-                    "level1_gbs": bpp * n * n / (l1m * 1e-3) / 1e9,
-                    "level1_frac": bpp * n * n / (l1m * 1e-3) / 1e9 / peak}
-                p.close()
-                del out
-        for scheme in ("nonsep", "sep"):  # the DD 13/7 wavelet (one 4-tap pair, no scaling)
-            for levels in (1, a.levels):
-                p = make(scheme, torch.float32, levels, "dd137")
-                out = torch.empty_like(x)
-                p.autotune(x, out, stream)
-                ms = _time(lambda: p.forward(x, out, stream), ksteps, stream, barrier)
-                abi.dwt2_profile(p.handle, True)
-                for _ in range(min(ksteps, 50)):
-                    p.forward(x, out, stream)
-                barrier()
-                l1m = abi.dwt2_profile_read(p.handle, 1)[0]
-                abi.dwt2_profile(p.handle, False)
-                assert p.status() == 0
-                comp[f"dd137/{scheme}/f32/L{levels}"] = {
-                    "gpx_s": n * n / (ms * 1e-3) / 1e9, "ms": ms,
-                    "level1_frac": 8 * n * n / (l1m * 1e-3) / 1e9 / peak}
-                p.close()
-                del out
-        for scheme in ("nonsep", "sep"):
-            xi = torch.from_numpy(synth.to_int(x_host)).to(dev)
-            p = make(scheme, torch.int32, a.levels, "cdf53")
-            out = torch.empty_like(xi)
-            p.autotune(xi, out, stream)
-            for _ in range(3):
-                p.forward(xi, out, stream)
-            barrier()
-            c0 = torch.cuda.Event(enable_timing=True)
-            c1 = torch.cuda.Event(enable_timing=True)
-            c0.record(stream)
-            for _ in range(ksteps):
-                p.forward(xi, out, stream)
-            c1.record(stream)
-            barrier()
-            ms = c0.elapsed_time(c1) / ksteps
-            comp[f"cdf53i/{scheme}/i32/L{a.levels}"] = {"gpx_s": n * n / (ms * 1e-3) / 1e9, "ms": ms}
-            p.close()
-            del out, xi
-        # inverse and adjoint of the same image (FP32 coefficients of the reduced scheme)
-        for levels in (1, a.levels):
-            p = make("reduced", torch.float32, levels)
-            coef = p.forward(x, None, stream)
-            back = torch.empty_like(x)
-            for name, fn in (("inverse", lambda: p.inverse(coef, back, stream)),
-                             ("adjoint", lambda: p.adjoint(coef, back, stream))):
-                ms = _time(fn, ksteps, stream, barrier)
-                abi.dwt2_profile(p.handle, True)
-                for _ in range(min(ksteps, 50)):
-                    fn()
-                barrier()
-                l1m = abi.dwt2_profile_read(p.handle, 1)[0]
-                abi.dwt2_profile(p.handle, False)
-                comp[f"{name}/reduced/f32/L{levels}"] = {
-                    "gpx_s": n * n / (ms * 1e-3) / 1e9, "ms": ms,
-                    "level1_gbs": 8 * n * n / (l1m * 1e-3) / 1e9,
-                    "level1_frac": 8 * n * n / (l1m * 1e-3) / 1e9 / peak}
-            assert p.status() == 0
-            p.close()
-            del coef, back
-        comp.update(batch_and_grad(dev, stream, barrier))
+        ctx = Ctx(dev, stream, barrier, peak)
+        comp.update(c1_small(ctx))
+        comp.update(c2_sweep(ctx, x_host if n == 16384 else None))
+        comp.update(c3_precision(ctx))
+        comp.update(c4_batch(ctx))
+        comp.update(c5_grad(ctx))
         line["compare"] = comp
 
     if rank == 0 and world == 1 and not a.no_cpu:
-        per_s, runs, secs, threads = time_oracle(4096, a.levels, budget_s=10.0)
-        line["cpu_baseline"] = {"value": per_s / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
-                                "sample": f"oracle (C, FP64 separable lifting, OpenMP) on a 4096x4096 image "
-                                          f"of the same recipe, {a.levels} levels, {runs} runs in {secs:.1f} s"}
+        line["cpu_baseline"] = oracle_baseline(a.levels)
     emit(line, rank)
     if pg is not None:
         pg.barrier()
         pg.destroy_process_group()
+
+
+# ------------------------------------------------------------ the configurations
+
+class Ctx:
+    """Device, stream, barrier and the roofline denominator shared by the
+    configuration runners."""
+
+    def __init__(self, dev, stream, barrier, peak):
+        import torch
+        self.dev, self.stream, self.barrier, self.peak = dev, stream, barrier, peak
+        # a buffer of twice the L2 size: writing it evicts earlier data from L2
+        self.flush_buf = torch.empty(2 * 129 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
+
+    def flush(self):
+        self.flush_buf.zero_()
+
+
+def alg_bytes(h: int, w: int, levels: int, coef_bytes: int = 4, in_bytes: int = 4) -> int:
+    """Algorithmic bytes of a pyramid of per-level launches: every level reads
+    its input once (the image, then the FP32/int32 low-low band of the level
+    before) and writes its four bands once (intermediate low-low bands in the
+    compute type, everything else in the coefficient type)."""
+    tot = 0
+    for k in range(levels):
+        hq, wq = (h + 1) // 2, (w + 1) // 2
+        last = k == levels - 1
+        tot += h * w * (in_bytes if k == 0 else 4)
+        tot += (h * w - hq * wq) * coef_bytes + hq * wq * (coef_bytes if last else 4)
+        h, w = hq, wq
+    return tot
 
 
 def _time(fn, steps, stream, barrier):
@@ -610,85 +550,312 @@ def _time(fn, steps, stream, barrier):
     return e0.elapsed_time(e1) / steps
 
 
-def batch_and_grad(dev, stream, barrier):
-    """The batching and differentiation forms on their own workloads."""
+def _time_flushed(fn, reps, ctx):
+    """Median of single calls, each after writing a buffer of twice the L2
+    size (the flush is outside the events)."""
+    import torch
+    for _ in range(3):
+        fn()
+    ctx.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for e0, e1 in ev:
+        ctx.flush()
+        e0.record(ctx.stream)
+        fn()
+        e1.record(ctx.stream)
+    ctx.barrier()
+    return statistics.median(e0.elapsed_time(e1) for e0, e1 in ev)
+
+
+def level_ms(plan, fn, ctx, n):
+    """Mean milliseconds of the first n levels of a plan's calls, from the
+    plan's own event pairs (a pass of its own, after the timed loop)."""
+    from paper_1704_08657_gb300 import abi
+    abi.dwt2_profile(plan.handle, True)
+    for _ in range(20):
+        fn()
+    ctx.barrier()
+    ms = abi.dwt2_profile_read(plan.handle, n)
+    abi.dwt2_profile(plan.handle, False)
+    return ms
+
+
+def _entry(ctx, px, ms, nbytes, **kw):
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    return {"gpx_s": px / (ms * 1e-3) / 1e9, "ms": ms, "alg_bytes": nbytes, "alg_gbs": gbs,
+            "frac": gbs / ctx.peak, **kw}
+
+
+def c1_small(ctx):
+    """512 x 512 uniform FP32 image (seed 1), one level of CDF 9/7, plain
+    non-separable lifting: forward, inverse and the pair in microseconds
+    (L2-resident, launch-bound), beside the oracle's seconds for the same pair."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_1704_08657_gb300 import synth
+    from paper_1704_08657_gb300.dwt import Plan
+    n = 512
+    xh = synth.uniform(n, n, seed=1)
+    x = torch.from_numpy(xh).to(ctx.dev)
+    p = Plan.single(n, n, 1, scheme="nonsep", device=ctx.dev)
+    c = torch.empty_like(x)
+    r = torch.empty_like(x)
+    ms_f = _time(lambda: p.forward(x, c, ctx.stream), 200, ctx.stream, ctx.barrier)
+    ms_i = _time(lambda: p.inverse(c, r, ctx.stream), 200, ctx.stream, ctx.barrier)
+
+    def pair():
+        p.forward(x, c, ctx.stream)
+        p.inverse(c, r, ctx.stream)
+    ms_p = _time(pair, 200, ctx.stream, ctx.barrier)
+    ms_pf = _time_flushed(pair, 50, ctx)
+    assert p.status() == 0
+    err = float((r - x).abs().max())
+    p.close()
+    oracle.build()
+    x64 = xh.astype(np.float64)
+    res = {"oracle_cores": oracle.threads()}
+    cores = oracle.threads()
+    for thr, key in ((1, "oracle_s_1thread"), (cores, "oracle_s_all_cores")):
+        oracle.set_threads(thr)
+        runs, t = 0, 0.0
+        while runs < 5 or t < 1.0:
+            t0 = time.perf_counter()
+            oracle.inverse97(oracle.forward97(x64, 1), 1)
+            t += time.perf_counter() - t0
+            runs += 1
+        res[key] = t / runs
+    oracle.set_threads(cores)
+    return {"C1/512x512/L1/nonsep/f32/forward+inverse": {
+        "us_forward": ms_f * 1e3, "us_inverse": ms_i * 1e3, "us_pair": ms_p * 1e3, "us_pair_l2_flushed": ms_pf * 1e3,
+        "gpx_s_pair": n * n / (ms_p * 1e-3) / 1e9, "alg_bytes_pair": 2 * alg_bytes(n, n, 1),
+        "frac_pair": 2 * alg_bytes(n, n, 1) / (ms_p * 1e-3) / 1e9 / ctx.peak,
+        "reconstruction_max_err": err, **res,
+        "note": "1 MiB image: L2-resident and launch-bound, frac is against HBM only for scale"}}
+
+
+def c2_sweep(ctx, x16384=None):
+    """One FP32 gradient image (seed 2) at 2048^2, 8192^2 and 16384^2, 1 and 5
+    levels, non-separable, reduced and separable lifting (FP32, and FP16
+    coefficients at 16384^2), plus integer 5/3 on round(x) by non-separable
+    and separable lifting; each plan autotuned.  2048^2 (16 MiB) fits in L2:
+    it is reported L2-flushed (a 2 x L2 write before every call) and warm."""
+    import torch
+
+    from paper_1704_08657_gb300 import synth
+    from paper_1704_08657_gb300.dwt import Plan
+    out = {}
+    for n in (2048, 8192, 16384):
+        xh = x16384 if (n == 16384 and x16384 is not None) else synth.gradient(n, n, seed=2)
+        x = torch.from_numpy(xh).to(ctx.dev)
+        xi = torch.from_numpy(synth.to_int(xh)).to(ctx.dev)
+        steps = 400 if n == 2048 else (100 if n == 8192 else 40)
+        variants = [("cdf97", s, torch.float32) for s in ("nonsep", "reduced", "sep")]
+        if n == 16384:
+            variants += [("cdf97", "reduced", torch.float16), ("cdf97", "sep", torch.float16)]
+        variants += [("cdf53", s, torch.int32) for s in ("nonsep", "sep")]
+        for wav, scheme, cdt in variants:
+            for levels in (1, 5):
+                src = xi if wav == "cdf53" else x
+                p = Plan.single(n, n, levels, wavelet=wav, scheme=scheme, coef_dtype=cdt, device=ctx.dev)
+                c = torch.empty_like(src, dtype=cdt)
+                tuned = p.autotune(src, c, ctx.stream)
+                cb = 2 if cdt in (torch.float16, torch.bfloat16) else 4
+                nb = alg_bytes(n, n, levels, cb)
+                key = f"C2/{n}x{n}/L{levels}/{'cdf53i' if wav == 'cdf53' else 'cdf97'}/{scheme}/" \
+                      f"{ {torch.float32: 'f32', torch.float16: 'f16', torch.int32: 'i32'}[cdt]}"
+                if n == 2048:
+                    ms_w = _time(lambda: p.forward(src, c, ctx.stream), steps, ctx.stream, ctx.barrier)
+                    ms_f = _time_flushed(lambda: p.forward(src, c, ctx.stream), 100, ctx)
+                    out[key] = _entry(ctx, n * n, ms_f, nb, l2="flushed before every call", autotuned_choice=tuned,
+                                      warm=_entry(ctx, n * n, ms_w, nb, l2="warm, back to back"))
+                else:
+                    ms = _time(lambda: p.forward(src, c, ctx.stream), steps, ctx.stream, ctx.barrier)
+                    l1 = level_ms(p, lambda: p.forward(src, c, ctx.stream), ctx, 1)[0]
+                    out[key] = _entry(ctx, n * n, ms, nb, l2="inputs larger than L2, back to back",
+                                      level1_ms=l1, level1_frac=alg_bytes(n, n, 1, cb) / (l1 * 1e-3) / 1e9 / ctx.peak,
+                                      autotuned_choice=tuned,
+                                      per_level_config=[dict(zip(("ql", "qr", "nst", "nw", "interior_loop", "seg_rows"),
+                                                                 c_)) for c_ in tuned_levels(tuned, levels, False)])
+                assert p.status() == 0
+                p.close()
+                del c
+        del x, xi
+    return out
+
+
+def c3_precision(ctx):
+    """8192^2 image u + N(0, 10^2) (seed 3, unclipped), 5-level CDF 9/7 with
+    FP16 and BF16 coefficient storage and FP32 lifting: throughput and, per
+    subband, the max abs error and the max relative error (max |q - ref| /
+    max |ref band|) against the FP64 oracle; the integer 5/3 path on
+    round(clip(x, 0, 255)) compared bit for bit."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_1704_08657_gb300 import synth
+    from paper_1704_08657_gb300.dwt import Plan, band_slices
+    n, levels = 8192, 5
+    xh = synth.noisy(n, n, seed=3)
+    ref = oracle.forward97(xh.astype(np.float64), levels)
+    x = torch.from_numpy(xh).to(ctx.dev)
+    out = {}
+    for scheme in ("reduced", "sep"):
+        for cdt, name in ((torch.float16, "f16"), (torch.bfloat16, "bf16"), (torch.float32, "f32")):
+            p = Plan.single(n, n, levels, scheme=scheme, coef_dtype=cdt, device=ctx.dev)
+            c = torch.empty_like(x, dtype=cdt)
+            p.autotune(x, c, ctx.stream)
+            ms = _time(lambda: p.forward(x, c, ctx.stream), 100, ctx.stream, ctx.barrier)
+            p.forward(x, c, ctx.stream)
+            assert p.status() == 0
+            got = c.float().cpu().numpy()
+            bands = []
+            for lev, bn, rs, cs in band_slices(n, n, levels):
+                g, r = got[rs, cs].astype(np.float64), ref[rs, cs]
+                e = float(np.abs(g - r).max())
+                m = float(np.abs(r).max())
+                bands.append({"level": lev, "band": bn, "max_abs": e, "max_rel": e / max(m, 1e-30), "band_max": m})
+            worst = max(b["max_rel"] for b in bands)
+            bound = {"f16": 1e-3, "bf16": 8e-3}.get(name)
+            out[f"C3/8192x8192/L5/cdf97/{scheme}/{name}"] = _entry(
+                ctx, n * n, ms, alg_bytes(n, n, levels, 2 if name != "f32" else 4), bands=bands,
+                worst_rel=worst, rel_bound=bound, within_bound=(worst <= bound) if bound else None)
+            p.close()
+            del c
+    xi = synth.to_int(xh, clip=True)
+    refi = oracle.forward53i(xi.astype(np.int64), levels)
+    xid = torch.from_numpy(xi).to(ctx.dev)
+    for scheme in ("nonsep", "sep"):
+        p = Plan.single(n, n, levels, wavelet="cdf53", scheme=scheme, coef_dtype=torch.int32, device=ctx.dev)
+        c = torch.empty_like(xid)
+        p.autotune(xid, c, ctx.stream)
+        ms = _time(lambda: p.forward(xid, c, ctx.stream), 100, ctx.stream, ctx.barrier)
+        p.forward(xid, c, ctx.stream)
+        assert p.status() == 0
+        same = bool(np.array_equal(c.cpu().numpy().astype(np.int64), refi))
+        out[f"C3/8192x8192/L5/cdf53i/{scheme}/i32"] = _entry(ctx, n * n, ms, alg_bytes(n, n, levels), bit_exact=same)
+        p.close()
+    return out
+
+
+def c4_batch(ctx):
+    """512 images, sides log-uniform in [64, 2048] rounded to even (seed 4),
+    uniform pixels (seed 5), 3-level CDF 9/7 forward: one persistent launch in
+    a CUDA graph, grouped launches (eager and in a graph), and one launch per
+    image and level (eager and in a graph)."""
     import torch
 
     from paper_1704_08657_gb300 import abi, synth
     from paper_1704_08657_gb300.dwt import Plan
     out = {}
-    # 512 uneven images, sides log-uniform in [64, 2048], three levels
     shapes = synth.batch_shapes(512, seed=4)
     buf, descs = synth.batch_pack(shapes, seed=5)
     px = sum(h * w for h, w in shapes)
-    xb = torch.from_numpy(buf).to(dev)
+    nb = sum(alg_bytes(h, w, 3) for h, w in shapes)
+    xb = torch.from_numpy(buf).to(ctx.dev)
     cb = torch.empty_like(xb)
-    per = Plan(descs, 3, device=dev)  # grouped launches: up to 80 images per launch and level
-    choice_lm = per.autotune(xb, cb, stream)
-    ms_per = _time(lambda: per.forward(xb, cb, stream), 20, stream, barrier)
-    per.forward(xb, cb, stream)  # launch blocks built for these buffers (outside the capture)
-    barrier()
-    gg = torch.cuda.CUDAGraph()
-    s3 = torch.cuda.Stream(dev)
-    s3.wait_stream(stream)
-    with torch.cuda.graph(gg, stream=s3):
-        per.forward(xb, cb, s3)
-    ms_per_graph = _time(lambda: gg.replay(), 50, stream, barrier)
+
+    def graph_of(fn):
+        fn()  # launch blocks built for these buffers outside the capture
+        ctx.barrier()
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream(ctx.dev)
+        s.wait_stream(ctx.stream)
+        with torch.cuda.graph(g, stream=s):
+            fn(s)
+        return g
+
+    grp = Plan(descs, 3, device=ctx.dev)
+    choice_g = grp.autotune(xb, cb, ctx.stream)
+    ms = _time(lambda: grp.forward(xb, cb, ctx.stream), 20, ctx.stream, ctx.barrier)
+    out["C4/batch512/L3/grouped"] = _entry(ctx, px, ms, nb, pixels=px, autotuned_choice=choice_g,
+                                           launches=3 * ((len(shapes) + 75) // 76))
+    g = graph_of(lambda s=None: grp.forward(xb, cb, s or ctx.stream))
+    ms = _time(lambda: g.replay(), 50, ctx.stream, ctx.barrier)
+    out["C4/batch512/L3/grouped_graph"] = _entry(ctx, px, ms, nb)
+    assert grp.status() == 0
+    del g
+    grp.close()
+    per = Plan(descs, 3, flags=abi.DWT2_FLAG_PERSISTENT, device=ctx.dev)
+    choice_p = per.autotune(xb, cb, ctx.stream)
+    g = graph_of(lambda s=None: per.forward(xb, cb, s or ctx.stream))
+    ms = _time(lambda: g.replay(), 50, ctx.stream, ctx.barrier)
+    out["C4/batch512/L3/persistent_graph"] = _entry(ctx, px, ms, nb, autotuned_choice=choice_p, launches=1)
     assert per.status() == 0
-    del gg
+    del g
     per.close()
-    pp = Plan(descs, 3, flags=abi.DWT2_FLAG_PERSISTENT, device=dev)
-    choice = pp.autotune(xb, cb, stream)
-    pp.forward(xb, cb, stream)
-    barrier()
-    g = torch.cuda.CUDAGraph()
-    s2 = torch.cuda.Stream(dev)
-    s2.wait_stream(stream)
-    with torch.cuda.graph(g, stream=s2):
-        pp.forward(xb, cb, s2)
-    ms_graph = _time(lambda: g.replay(), 50, stream, barrier)
-    assert pp.status() == 0
-    out["batch512/L3/persistent_graph"] = {"gpx_s": px / (ms_graph * 1e-3) / 1e9, "ms": ms_graph, "pixels": px,
-                                           "autotuned_choice": choice, "launches": 1}
-    out["batch512/L3/grouped"] = {"gpx_s": px / (ms_per * 1e-3) / 1e9, "ms": ms_per,
-                                  "autotuned_choice": choice_lm, "launches": 3 * ((len(shapes) + 79) // 80)}
-    out["batch512/L3/grouped_graph"] = {"gpx_s": px / (ms_per_graph * 1e-3) / 1e9, "ms": ms_per_graph,
-                                        "autotuned_choice": choice_lm}
+    # one plan per image: one launch per image and level
+    plans = [Plan([(0, h, w, p)], 3, device=ctx.dev) for (o, h, w, p) in descs]
+    xp = xb.data_ptr()
+    cp = cb.data_ptr()
+
+    def each(s=None):
+        st = (s or ctx.stream).cuda_stream
+        for pl, (o, h, w, p) in zip(plans, descs):
+            abi.dwt2_forward(pl.handle, xp + 4 * o, cp + 4 * o, pl.workspace.data_ptr(), st)
+    ms = _time(each, 5, ctx.stream, ctx.barrier)
+    out["C4/batch512/L3/one_launch_per_image"] = _entry(ctx, px, ms, nb, launches=3 * len(shapes))
+    g = graph_of(each)
+    ms = _time(lambda: g.replay(), 20, ctx.stream, ctx.barrier)
+    out["C4/batch512/L3/one_launch_per_image_graph"] = _entry(ctx, px, ms, nb, launches=3 * len(shapes))
+    for pl in plans:
+        assert pl.status() == 0
+        pl.close()
     del g, xb, cb
-    pp.close()
-    # 16 x 4096^2, four levels: forward + adjoint of the L1 detail loss
+    return out
+
+
+def c5_grad(ctx):
+    """16 x 4096^2 uniform FP32 images (seed 6), 4-level CDF 9/7 forward and
+    the hand-written adjoint of the mean-L1 loss over the detail bands."""
+    import torch
+
+    from paper_1704_08657_gb300 import abi
+    from paper_1704_08657_gb300.dwt import Plan
+    out = {}
     side, nimg, levels = 4096, 16, 4
     descs = [(i * side * side, side, side, side) for i in range(nimg)]
-    pg = Plan(descs, levels, scheme="reduced", flags=abi.DWT2_FLAG_PERSISTENT, device=dev)
-    x = torch.randint(0, 256, (nimg * side * side,), device=dev, generator=torch.Generator(dev).manual_seed(6)).float()
+    x = torch.randint(0, 256, (nimg * side * side,), device=ctx.dev,
+                      generator=torch.Generator(ctx.dev).manual_seed(6)).float()
     cbuf = torch.empty_like(x)
     gin = torch.empty_like(x)
-    scale = 1.0 / pg.n_detail()
-
-    def fwd_bwd():
-        pg.forward(x, cbuf, stream)
-        pg.adjoint_l1(cbuf, scale, gin, stream)
-    ms = _time(fwd_bwd, 20, stream, barrier)
-    ms_f = _time(lambda: pg.forward(x, cbuf, stream), 20, stream, barrier)
     npx = nimg * side * side
-    out["grad16x4096/L4/forward+adjoint_l1"] = {"gpx_s": npx / (ms * 1e-3) / 1e9, "ms": ms, "forward_ms": ms_f,
-                                                 "adjoint_ms": ms - ms_f,
-                                                 "launches": "forward: 1 persistent; adjoint: 1 per level"}
-    pg.close()
-    # the same with the grouped per-level forward (autotuned)
-    pl = Plan(descs, levels, scheme="reduced", device=dev)
-    pl.autotune(x, cbuf, stream)
+    nb_f = nimg * alg_bytes(side, side, levels)
+    for name, flags in (("grouped_forward", 0), ("persistent_forward", abi.DWT2_FLAG_PERSISTENT)):
+        pl = Plan(descs, levels, scheme="reduced", flags=flags, device=ctx.dev)
+        pl.autotune(x, cbuf, ctx.stream)
+        scale = 1.0 / pl.n_detail()
 
-    def fwd_bwd_pl():
-        pl.forward(x, cbuf, stream)
-        pl.adjoint_l1(cbuf, scale, gin, stream)
-    ms = _time(fwd_bwd_pl, 20, stream, barrier)
-    ms_f = _time(lambda: pl.forward(x, cbuf, stream), 20, stream, barrier)
-    out["grad16x4096/L4/forward+adjoint_l1/grouped_forward"] = {
-        "gpx_s": npx / (ms * 1e-3) / 1e9, "ms": ms, "forward_ms": ms_f, "adjoint_ms": ms - ms_f,
-        "launches": "forward: 1 per level (16 images each); adjoint: 1 per level"}
-    pl.close()
+        def fwd_bwd():
+            pl.forward(x, cbuf, ctx.stream)
+            pl.adjoint_l1(cbuf, scale, gin, ctx.stream)
+        ms = _time(fwd_bwd, 20, ctx.stream, ctx.barrier)
+        ms_f = _time(lambda: pl.forward(x, cbuf, ctx.stream), 20, ctx.stream, ctx.barrier)
+        ms_a = _time(lambda: pl.adjoint_l1(cbuf, scale, gin, ctx.stream), 20, ctx.stream, ctx.barrier)
+        assert pl.status() == 0
+        out[f"C5/grad16x4096/L4/{name}+adjoint_l1"] = _entry(
+            ctx, npx, ms, 2 * nb_f, forward_ms=ms_f, adjoint_ms=ms_a,
+            forward_frac=nb_f / (ms_f * 1e-3) / 1e9 / ctx.peak, adjoint_frac=nb_f / (ms_a * 1e-3) / 1e9 / ctx.peak)
+        pl.close()
     return out
+
+
+def oracle_baseline(levels: int):
+    """The oracle on a 4096^2 image of the bench recipe, with OpenMP on all
+    host cores and single-threaded."""
+    import oracle
+    per_s, runs, secs, threads = time_oracle(4096, levels, budget_s=8.0)
+    prev = oracle.threads()
+    oracle.set_threads(1)
+    per_1, runs1, secs1, _ = time_oracle(4096, levels, budget_s=6.0)
+    oracle.set_threads(prev)
+    return {"value": per_s / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "single_thread_value": per_1 / 1e9,
+            "sample": f"oracle (C, FP64 separable lifting, gcc -O3, OpenMP on {threads} threads) on a 4096x4096 "
+                      f"image of the bench recipe, {levels} levels, {runs} runs in {secs:.1f} s; single-threaded "
+                      f"{runs1} runs in {secs1:.1f} s"}
 
 
 def main():
