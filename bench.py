@@ -50,6 +50,9 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--profile", action="store_true",
                     help="warm-up and K steps only (for ncu captures); prints a minimal line")
+    ap.add_argument("--profile-workload", default="main", choices=["main", "batch512", "grad16x4096"],
+                    help="with --profile: the single image (main), the 512-image batch (3 levels; --persistent "
+                         "for the one-launch form) or the 16 x 4096^2 forward + L1 adjoint (4 levels)")
     ap.add_argument("--persistent", action="store_true", help="one persistent launch for the whole pyramid")
     ap.add_argument("--tune-choice", type=int, default=-1,
                     help="apply this dwt2_autotune choice instead of timing the candidates (ncu captures)")
@@ -296,9 +299,66 @@ def run_reference(a):
 
 # -------------------------------------------------------------- GPU arm
 
+def run_profile_workload(a):
+    """--profile on the batching or differentiation workload: warm-up steps,
+    then K timed steps, one short JSON line (for ncu launch lists)."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1704_08657_gb300 import abi, synth
+    from paper_1704_08657_gb300.dwt import Plan
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    flags = abi.DWT2_FLAG_PERSISTENT if a.persistent else 0
+    if a.profile_workload == "batch512":
+        shapes = synth.batch_shapes(512, seed=4)
+        buf, descs = synth.batch_pack(shapes, seed=5)
+        x = torch.from_numpy(buf).to(dev)
+        c = torch.empty_like(x)
+        plan = Plan(descs, 3, flags=flags, device=dev)
+        px = sum(h * w for h, w in shapes)
+
+        def step():
+            plan.forward(x, c, stream)
+    else:
+        side, nimg = 4096, 16
+        descs = [(i * side * side, side, side, side) for i in range(nimg)]
+        x = torch.randint(0, 256, (nimg * side * side,), device=dev,
+                          generator=torch.Generator(dev).manual_seed(6)).float()
+        c = torch.empty_like(x)
+        g = torch.empty_like(x)
+        plan = Plan(descs, 4, scheme="reduced", flags=flags, device=dev)
+        px = nimg * side * side
+        scale = 1.0 / plan.n_detail()
+
+        def step():
+            plan.forward(x, c, stream)
+            plan.adjoint_l1(c, scale, g, stream)
+    tuned = (abi.dwt2_autotune(plan.handle, x.data_ptr(), c.data_ptr(), plan.workspace.data_ptr(),
+                               stream.cuda_stream, a.tune_choice) if a.tune_choice >= 0 else plan.autotune(x, c, stream))
+    for _ in range(max(3, a.warmup)):
+        step()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / a.steps
+    print(json.dumps({"mode": "profile", "workload": a.profile_workload, "persistent": bool(a.persistent),
+                      "ms_per_step": ms, "gpx_s": px / (ms * 1e-3) / 1e9, "status": plan.status(),
+                      "autotuned_choice": tuned}), flush=True)
+
+
 def run_ours(a):
     import numpy as np
     import torch
+
+    if a.profile and a.profile_workload != "main":
+        return run_profile_workload(a)
 
     world, rank, local = dist_env()
     torch.cuda.set_device(local)
@@ -494,6 +554,8 @@ def run_ours(a):
         comp.update(c3_precision(ctx))
         comp.update(c4_batch(ctx))
         comp.update(c5_grad(ctx))
+        comp.update(f_schemes(ctx, x_host if n == 16384 else None))
+        comp.update(inverse_adjoint(ctx, x_host if n == 16384 else None))
         line["compare"] = comp
 
     if rank == 0 and world == 1 and not a.no_cpu:
@@ -839,6 +901,63 @@ def c5_grad(ctx):
             ctx, npx, ms, 2 * nb_f, forward_ms=ms_f, adjoint_ms=ms_a,
             forward_frac=nb_f / (ms_f * 1e-3) / 1e9 / ctx.peak, adjoint_frac=nb_f / (ms_a * 1e-3) / 1e9 / ctx.peak)
         pl.close()
+    return out
+
+
+def f_schemes(ctx, x16384=None):
+    """The paper's other schemes and its third wavelet on the 16384^2 bench
+    image, 1 and 5 levels, FP32: polyconvolution, separable and non-separable
+    convolution (CDF 9/7), and DD 13/7 by non-separable, reduced and separable
+    lifting; each plan autotuned."""
+    import torch
+
+    from paper_1704_08657_gb300 import synth
+    from paper_1704_08657_gb300.dwt import Plan
+    n = 16384
+    x = torch.from_numpy(x16384 if x16384 is not None else synth.gradient(n, n, seed=2)).to(ctx.dev)
+    out = {}
+    for wav, scheme in [("cdf97", "polyconv"), ("cdf97", "conv"), ("cdf97", "nsconv"), ("dd137", "nonsep"),
+                        ("dd137", "reduced"), ("dd137", "sep")]:
+        for levels in (1, 5):
+            p = Plan.single(n, n, levels, wavelet=wav, scheme=scheme, device=ctx.dev)
+            c = torch.empty_like(x)
+            tuned = p.autotune(x, c, ctx.stream)
+            ms = _time(lambda: p.forward(x, c, ctx.stream), 40, ctx.stream, ctx.barrier)
+            l1 = level_ms(p, lambda: p.forward(x, c, ctx.stream), ctx, 1)[0]
+            assert p.status() == 0
+            out[f"F/{n}x{n}/L{levels}/{wav}/{scheme}/f32"] = _entry(
+                ctx, n * n, ms, alg_bytes(n, n, levels), level1_ms=l1,
+                level1_frac=alg_bytes(n, n, 1) / (l1 * 1e-3) / 1e9 / ctx.peak, autotuned_choice=tuned)
+            p.close()
+            del c
+    return out
+
+
+def inverse_adjoint(ctx, x16384=None):
+    """The inverse and the adjoint of the 16384^2 bench image's pyramid (FP32
+    coefficients of the reduced scheme), 1 and 5 levels: 4 B read + 4 B written
+    per pixel and level, like the forward."""
+    import torch
+
+    from paper_1704_08657_gb300 import synth
+    from paper_1704_08657_gb300.dwt import Plan
+    n = 16384
+    x = torch.from_numpy(x16384 if x16384 is not None else synth.gradient(n, n, seed=2)).to(ctx.dev)
+    out = {}
+    for levels in (1, 5):
+        p = Plan.single(n, n, levels, scheme="reduced", device=ctx.dev)
+        coef = p.forward(x, None, ctx.stream)
+        back = torch.empty_like(x)
+        for name, fn in (("inverse", lambda: p.inverse(coef, back, ctx.stream)),
+                         ("adjoint", lambda: p.adjoint(coef, back, ctx.stream))):
+            ms = _time(fn, 40, ctx.stream, ctx.barrier)
+            l1 = level_ms(p, fn, ctx, 1)[0]
+            out[f"I/{n}x{n}/L{levels}/cdf97/{name}/f32"] = _entry(
+                ctx, n * n, ms, alg_bytes(n, n, levels), level1_ms=l1,
+                level1_frac=alg_bytes(n, n, 1) / (l1 * 1e-3) / 1e9 / ctx.peak)
+        assert p.status() == 0
+        p.close()
+        del coef, back
     return out
 
 

@@ -20,7 +20,8 @@
  *   DWT2_NONSEP          spatial predict / update, all terms in one step;
  *   DWT2_NONSEP_REDUCED  the Optimization Approach: the constant parts P0, U0
  *                        applied as separable lifting inside the quad right
- *                        after the non-separable parts P1, U1 (CDF 9/7 only);
+ *                        after the non-separable parts P1, U1 (CDF 9/7 and
+ *                        DD 13/7, whose P1 and U1 keep three taps each);
  *   DWT2_SEP_LIFTING     the separable lifting T^H, T^V, S^H, S^V per pair;
  *   DWT2_POLYCONV        the polyconvolution N_{P,U} (Proposed Schemes): each
  *                        pair applied as one step on pre-pair values, with
@@ -131,8 +132,8 @@ typedef struct {
  *   coef_dtype coefficient element type: F32, F16 or BF16 for CDF 9/7 and
  *              DD 13/7 (the lifting always runs in FP32 and intermediate LL
  *              bands are kept in FP32), I32 for CDF 5/3.
- *   scheme     DWT2_NONSEP, DWT2_NONSEP_REDUCED (CDF 9/7 only; DD 13/7 takes
- *              DWT2_NONSEP and DWT2_SEP_LIFTING, not DWT2_FLAG_PERSISTENT),
+ *   scheme     DWT2_NONSEP, DWT2_NONSEP_REDUCED (CDF 9/7 and DD 13/7; DD 13/7
+ *              takes the three lifting schemes, not DWT2_FLAG_PERSISTENT),
  *              DWT2_SEP_LIFTING, DWT2_POLYCONV, DWT2_CONV or DWT2_NONSEP_CONV
  *              (the last three CDF 9/7 only and not with
  *              DWT2_FLAG_PERSISTENT: DWT2_ERR_UNSUPPORTED).  The inverse and
@@ -141,13 +142,17 @@ typedef struct {
  *   n_images   number of images (>= 1); images is a host array of that many
  *              descriptors, copied into the plan.  With several images
  *              dwt2_forward runs each level as launches of up to 76 images
- *              (the inverse and adjoint up to 200), whose parameter blocks are
+ *              (the inverse and adjoint up to 170), whose parameter blocks are
  *              built at the first call for a set of buffers and reused.
  *   flags      0 or DWT2_FLAG_PERSISTENT: dwt2_forward then runs every level of every
  *              image in one persistent launch whose units take work from a device
  *              queue and wait (bounded by DWT2_TIMEOUT_MS, default 2000) for the
  *              segments of the previous level they read; the plan allocates its
- *              queue tables at creation and the call is CUDA-graph capturable.
+ *              queue tables and a table of TMA tensor maps at creation.  The
+ *              first call for a set of input and workspace buffers writes that
+ *              table (it synchronises the stream); made during a stream capture
+ *              it returns DWT2_ERR_INVALID_ARG.  Later calls on the same buffers
+ *              are asynchronous and CUDA-graph capturable.
  * Alignment: the image (input) buffer's base pointer must be 16-byte aligned
  * and offset_elems and pitch_elems multiples of 4 (16 bytes of 4-byte
  * elements), else DWT2_ERR_MISALIGNED; coefficient buffers need only natural
@@ -155,7 +160,7 @@ typedef struct {
  * tables on the current device.
  * Environment, read when the plan is made (launch tuning only; results do not
  * depend on it): DWT2_TIMEOUT_MS (bounded device waits, default 2000),
- * DWT2_FWD_CFG and DWT2_SEG_ROWS (forward kernel configuration 0-4 and
+ * DWT2_FWD_CFG and DWT2_SEG_ROWS (forward kernel configuration 0-3 and
  * segment height before any dwt2_autotune), DWT2_PDL (0 launches the forward
  * levels without programmatic dependent launch), DWT2_FUSE_SEG and
  * DWT2_FUSE_PAIRS (run level pairs 0-1, 2-3, ... in one fused launch with that

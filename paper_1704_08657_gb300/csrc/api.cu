@@ -187,12 +187,18 @@ struct dwt2_plan_s {
         void* ws = nullptr;
         int adj = -1;
         std::vector<std::unique_ptr<InvGroupLaunch>> blocks;
-        std::vector<int> level, grid;  // per block
+        std::vector<int> level, grid, grid_edge;  // per block; grids of the inner and the edge units
     } icache;
     PmlDesc* d_descs;
     PmlUnit* d_units;
     unsigned* d_counters;  // n_counters segment counters followed by the queue word
     int n_units, n_counters;
+    // the persistent launch's tensor maps (two per descriptor) in device
+    // memory, encoded for the input and workspace buffers they were last
+    // written for
+    CUtensorMap* d_maps;
+    const void* maps_in;
+    const void* maps_ws;
     // profiling: a ring of PROF_RING calls, one event pair per level each
     std::vector<cudaEvent_t> ev0, ev1;  // [slot * levels + level]
     bool prof_on;
@@ -304,10 +310,14 @@ int build_persistent(dwt2_plan_t p) {
     if (p->d_descs) cudaFree(p->d_descs);
     if (p->d_units) cudaFree(p->d_units);
     if (p->d_counters) cudaFree(p->d_counters);
+    if (p->d_maps) cudaFree(p->d_maps);
     p->d_descs = nullptr;
     p->d_units = nullptr;
     p->d_counters = nullptr;
-    if (cudaMalloc(&p->d_descs, descs.size() * sizeof(PmlDesc)) != cudaSuccess ||
+    p->d_maps = nullptr;
+    p->maps_in = p->maps_ws = nullptr;
+    if (cudaMalloc(&p->d_maps, 2 * descs.size() * sizeof(CUtensorMap)) != cudaSuccess ||
+        cudaMalloc(&p->d_descs, descs.size() * sizeof(PmlDesc)) != cudaSuccess ||
         cudaMalloc(&p->d_units, sorted.size() * sizeof(PmlUnit)) != cudaSuccess ||
         cudaMalloc(&p->d_counters, (size_t(ctr) + 1) * sizeof(unsigned)) != cudaSuccess ||
         cudaMemcpy(p->d_descs, descs.data(), descs.size() * sizeof(PmlDesc), cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -362,6 +372,34 @@ InvParams inv_level_params(dwt2_plan_t p, const ImagePlan& ip, int l, const void
     return ipm;
 }
 
+// The inner units of one inverse / adjoint level, in_s0 .. in_g1 of q: the
+// units whose band rows all take paired staged copies (pair-aligned bands)
+// from inside the band columns (the strip's first pixel >= 0 and its quads
+// within the odd-column band) and, for the adjoint, whose weighted quads and
+// rows all carry weight 1 (quads in [1, wh - 2], rows R0 - 4 .. R1 + 1 in
+// [1, hh - 2]).  Each condition is monotone in the strip or the segment
+// index, so these units form a rectangle; the kernels run them with one
+// staged row loop (the unweighted one for the adjoint) and every other unit
+// in a second launch.
+void inv_inner_rect(InvParams& q, int wavelet, bool adj) {
+    const int hq_ = wav_halo(wavelet), outq = 64 - 2 * hq_;
+    const bool staged = q.vec_in_lo && q.vec_in_hi && q.vec_ll;
+    int s0 = q.n_strips, s1 = 0, g0 = q.n_segs, g1 = 0;
+    for (int st = 0; st < q.n_strips && staged; ++st) {
+        const int x0 = st * (2 * outq) - 2 * hq_;
+        bool in = (x0 >= 0) && (x0 / 2 + 64 <= q.wh);
+        if (adj) in = in && (x0 / 2 >= 1) && (x0 / 2 + 63 <= q.wh - 2);
+        if (in) s0 = std::min(s0, st), s1 = st + 1;
+    }
+    for (int g = 0; g < q.n_segs; ++g) {
+        const int R0 = g * q.seg_rows, R1 = std::min(R0 + q.seg_rows, q.hq);
+        const bool in = !adj || ((R0 - 4 >= 1) && (R1 + 1 <= q.hh - 2));
+        if (in) g0 = std::min(g0, g), g1 = g + 1;
+    }
+    if (s0 >= s1 || g0 >= g1) s0 = s1 = g0 = g1 = 0;
+    q.in_s0 = s0, q.in_s1 = s1, q.in_g0 = g0, q.in_g1 = g1;
+}
+
 // Plans of several images: every level, coarsest first, as launches of up to
 // INV_GROUP_MAX images in segments of INV_GROUP_SEG quad rows.
 constexpr int INV_GROUP_SEG = 32;
@@ -371,6 +409,7 @@ int inv_group_build(dwt2_plan_t p, const void* coef, void* out, void* workspace,
     ic.blocks.clear();
     ic.level.clear();
     ic.grid.clear();
+    ic.grid_edge.clear();
     const int n = int(p->imgs.size());
     const size_t csz = adj ? 4 : dtype_size(p->coef_dtype);
     std::vector<int> order(n);
@@ -382,7 +421,7 @@ int inv_group_build(dwt2_plan_t p, const void* coef, void* out, void* workspace,
         for (int i0 = 0; i0 < n; i0 += INV_GROUP_MAX) {
             std::unique_ptr<InvGroupLaunch> g(new (std::nothrow) InvGroupLaunch());
             if (!g) return DWT2_ERR_INVALID_ARG;
-            int units = 0;
+            int units[3] = {0, 0, 0};
             for (int k = 0; k < INV_GROUP_MAX && i0 + k < n; ++k) {
                 const ImagePlan& ip = p->imgs[order[i0 + k]];
                 InvParams ipm = inv_level_params(p, ip, l, coef, out, workspace, csz, false, 0.f);
@@ -390,14 +429,18 @@ int inv_group_build(dwt2_plan_t p, const void* coef, void* out, void* workspace,
                 ipm.seg_rows = std::min(p->seg_env > 0 ? p->seg_env : INV_GROUP_SEG, ipm.hq);
                 ipm.n_segs = (ipm.hq + ipm.seg_rows - 1) / ipm.seg_rows;
                 ipm.n_units = ipm.n_segs * ipm.n_strips;
+                inv_inner_rect(ipm, p->wavelet, adj);
                 g->img[k].p = ipm;
-                g->img[k].u_begin = units;
-                units += ipm.n_units;
+                for (int c = 0; c < 3; ++c) {
+                    g->img[k].u_begin[c] = units[c];
+                    units[c] += inv_class_units(ipm, c);
+                }
                 g->n_img = k + 1;
             }
-            g->n_units = units;
+            for (int c = 0; c < 3; ++c) g->n_units[c] = units[c];
             g->wait_prev = (i0 == 0);
-            ic.grid.push_back((units + INV_NW - 1) / INV_NW);
+            ic.grid.push_back((units[UNITS_INNER] + INV_NW - 1) / INV_NW);
+            ic.grid_edge.push_back((units[UNITS_EDGE] + INV_NW - 1) / INV_NW);
             ic.level.push_back(l);
             ic.blocks.push_back(std::move(g));
         }
@@ -426,21 +469,28 @@ int inverse_grouped(dwt2_plan_t p, const void* coef, void* out, void* workspace,
         const int l = ic.level[b];
         if (b == 0 || ic.level[b - 1] != l) prof_mark(p, l, true, s);
         // the first launch of a level waits for every earlier launch (plain
-        // stream order); the others overlap the launch before them
-        const int pdl = g.wait_prev ? 0 : 1;
-        int e;
-        if (adj) {
-            e = launch_adj_group_f32(g, ic.grid[b], pdl, s);
-        } else {
-            const int sc = inv_scheme(p->scheme);
-            switch (p->coef_dtype) {
-                case DWT2_F32: e = launch_inv_group_f32(p->wavelet, sc, g, ic.grid[b], pdl, s); break;
-                case DWT2_F16: e = launch_inv_group_f16(p->wavelet, sc, g, ic.grid[b], pdl, s); break;
-                case DWT2_BF16: e = launch_inv_group_bf16(p->wavelet, sc, g, ic.grid[b], pdl, s); break;
-                default: e = launch_inv_group_i32(p->wavelet, sc, g, ic.grid[b], pdl, s); break;
+        // stream order); the others (the edge units, the next groups) overlap
+        // the launch before them
+        bool first = g.wait_prev != 0;
+        for (int cls : {UNITS_INNER, UNITS_EDGE}) {
+            const int grid = cls == UNITS_INNER ? ic.grid[b] : ic.grid_edge[b];
+            if (grid == 0) continue;
+            const int pdl = first ? 0 : 1;
+            first = false;
+            int e;
+            if (adj) {
+                e = launch_adj_group_f32(g, grid, pdl, cls, s);
+            } else {
+                const int sc = inv_scheme(p->scheme);
+                switch (p->coef_dtype) {
+                    case DWT2_F32: e = launch_inv_group_f32(p->wavelet, sc, g, grid, pdl, cls, s); break;
+                    case DWT2_F16: e = launch_inv_group_f16(p->wavelet, sc, g, grid, pdl, cls, s); break;
+                    case DWT2_BF16: e = launch_inv_group_bf16(p->wavelet, sc, g, grid, pdl, cls, s); break;
+                    default: e = launch_inv_group_i32(p->wavelet, sc, g, grid, pdl, cls, s); break;
+                }
             }
+            if (e != cudaSuccess) return DWT2_ERR_CUDA;
         }
-        if (e != cudaSuccess) return DWT2_ERR_CUDA;
         if (b + 1 == ic.blocks.size() || ic.level[b + 1] != l) prof_mark(p, l, false, s);
     }
     if (p->prof_on) ++p->prof_calls;
@@ -449,11 +499,8 @@ int inverse_grouped(dwt2_plan_t p, const void* coef, void* out, void* workspace,
 
 int forward_persistent(dwt2_plan_t p, const void* in, void* coef, void* workspace, cudaStream_t s) {
     const size_t csz = dtype_size(p->coef_dtype);
-    if (cudaMemsetAsync(p->d_counters, 0, (size_t(p->n_counters) + 1) * sizeof(unsigned), s) != cudaSuccess)
-        return DWT2_ERR_CUDA;
-    // the launch block is large (tensor maps); keep it off the stack
-    std::unique_ptr<PmlLaunch> lp(new (std::nothrow) PmlLaunch());
-    if (!lp) return DWT2_ERR_INVALID_ARG;
+    PmlLaunch launch{};
+    PmlLaunch* lp = &launch;
     PmlParams& pp = lp->base;
     pp.in = in;
     pp.coef = coef;
@@ -467,27 +514,44 @@ int forward_persistent(dwt2_plan_t p, const void* in, void* coef, void* workspac
     pp.test_drop_signal = (p->flags & DWT2_TESTONLY_DROP_SIGNAL) != 0;
     pp.status = p->d_status;
     pp.timeout_ns = p->timeout_ns;
-    lp->use_tma = int(p->h_descs.size()) <= PML_TMA_MAX_DESCS && !p->pml_force_cpasync;
-    if (lp->use_tma) {
+    lp->use_tma = !p->pml_force_cpasync;
+    lp->maps = p->d_maps;
+    if (lp->use_tma && (p->maps_in != in || p->maps_ws != workspace)) {
+        // (re)write the tensor maps for these buffers: outside any stream
+        // capture, after the launches still reading the old ones
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) return DWT2_ERR_CUDA;
+        if (cs != cudaStreamCaptureStatusNone) return DWT2_ERR_INVALID_ARG;
         const bool is_int = p->wavelet == DWT2_CDF53_INT;
         const int bw = 64 * PML_QL;
+        std::vector<CUtensorMap> maps(2 * p->h_descs.size());
         for (size_t i = 0; i < p->h_descs.size(); ++i) {
             const PmlDesc& d = p->h_descs[i];
             const char* base = d.src_is_ws ? static_cast<const char*>(workspace) : static_cast<const char*>(in);
             const void* src = base + d.src_off * 4;
-            int rc = encode_map(&lp->maps[2 * i], src, d.w, d.h, d.src_pitch, bw, 2 * PML_QR, is_int);
-            if (rc == DWT2_OK) rc = encode_map(&lp->maps[2 * i + 1], src, d.w, d.h, d.src_pitch, bw, 1, is_int);
+            int rc = encode_map(&maps[2 * i], src, d.w, d.h, d.src_pitch, bw, 2 * PML_QR, is_int);
+            if (rc == DWT2_OK) rc = encode_map(&maps[2 * i + 1], src, d.w, d.h, d.src_pitch, bw, 1, is_int);
             if (rc != DWT2_OK) return rc;
         }
+        if (cudaStreamSynchronize(s) != cudaSuccess ||
+            cudaMemcpy(p->d_maps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice) !=
+                cudaSuccess) {
+            cudaGetLastError();
+            return DWT2_ERR_CUDA;
+        }
+        p->maps_in = in;
+        p->maps_ws = workspace;
     }
+    if (cudaMemsetAsync(p->d_counters, 0, (size_t(p->n_counters) + 1) * sizeof(unsigned), s) != cudaSuccess)
+        return DWT2_ERR_CUDA;
     const int grid = p->sm_count * p->pml_bps;
     prof_mark(p, 0, true, s);
     int e;
     switch (p->coef_dtype) {
-        case DWT2_F32: e = launch_pml_f32(p->wavelet, p->scheme, *lp, grid, s); break;
-        case DWT2_F16: e = launch_pml_f16(p->wavelet, p->scheme, *lp, grid, s); break;
-        case DWT2_BF16: e = launch_pml_bf16(p->wavelet, p->scheme, *lp, grid, s); break;
-        default: e = launch_pml_i32(p->wavelet, p->scheme, *lp, grid, s); break;
+        case DWT2_F32: e = launch_pml_f32(p->wavelet, p->scheme, launch, grid, s); break;
+        case DWT2_F16: e = launch_pml_f16(p->wavelet, p->scheme, launch, grid, s); break;
+        case DWT2_BF16: e = launch_pml_bf16(p->wavelet, p->scheme, launch, grid, s); break;
+        default: e = launch_pml_i32(p->wavelet, p->scheme, launch, grid, s); break;
     }
     // the whole pyramid is one launch: it is timed as level 0; the other levels read 0
     prof_mark(p, 0, false, s);
@@ -798,8 +862,9 @@ int dwt2_plan(dwt2_plan_t* out, int wavelet, int levels, int boundary, int in_dt
         if (in_dtype != DWT2_F32 || coef_dtype == DWT2_I32) return DWT2_ERR_UNSUPPORTED;
     } else if (wavelet == DWT2_DD137) {
         if (in_dtype != DWT2_F32 || coef_dtype == DWT2_I32) return DWT2_ERR_UNSUPPORTED;
-        // the lifting schemes (no reduced split, no filter-bank form) and no persistent launch
-        if (scheme != DWT2_NONSEP && scheme != DWT2_SEP_LIFTING) return DWT2_ERR_UNSUPPORTED;
+        // the lifting schemes (no filter-bank form) and no persistent launch
+        if (scheme != DWT2_NONSEP && scheme != DWT2_NONSEP_REDUCED && scheme != DWT2_SEP_LIFTING)
+            return DWT2_ERR_UNSUPPORTED;
         if (flags & DWT2_FLAG_PERSISTENT) return DWT2_ERR_UNSUPPORTED;
     } else {
         if (in_dtype != DWT2_I32 || coef_dtype != DWT2_I32) return DWT2_ERR_UNSUPPORTED;
@@ -856,8 +921,9 @@ int dwt2_plan(dwt2_plan_t* out, int wavelet, int levels, int boundary, int in_dt
     p->fused_bps = fused_blocks_per_sm(wavelet, scheme, coef_dtype);
     p->balanced_env = env_int("DWT2_BALANCED", 0);
     p->cfg_env = env_int("DWT2_FWD_CFG", 0);
-    if (p->cfg_env < 0 || p->cfg_env >= N_FWD_CFGS) p->cfg_env = 0;
     for (int c = 0; c < N_FWD_CFGS; ++c) p->cfg_bps[c] = forward_blocks_per_sm(wavelet, scheme, coef_dtype, FWD_CFGS[c]);
+    // a configuration this plan's pipeline is not compiled for falls back to the default
+    if (p->cfg_env < 0 || p->cfg_env >= N_FWD_CFGS || p->cfg_bps[p->cfg_env] <= 0) p->cfg_env = 0;
     p->inv_bps = inverse_blocks_per_sm(wavelet, inv_scheme(scheme), coef_dtype, false);
     if (cudaGetDevice(&p->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess ||
@@ -872,6 +938,8 @@ int dwt2_plan(dwt2_plan_t* out, int wavelet, int levels, int boundary, int in_dt
     p->d_descs = nullptr;
     p->d_units = nullptr;
     p->d_counters = nullptr;
+    p->d_maps = nullptr;
+    p->maps_in = p->maps_ws = nullptr;
     p->n_units = p->n_counters = 0;
     p->pml_bps = 0;
     p->pml_seg = env_int("DWT2_PML_SEG_ROWS", PML_SEG_DEFAULT);
@@ -911,6 +979,7 @@ void dwt2_destroy(dwt2_plan_t p) {
     if (p->d_descs) cudaFree(p->d_descs);
     if (p->d_units) cudaFree(p->d_units);
     if (p->d_counters) cudaFree(p->d_counters);
+    if (p->d_maps) cudaFree(p->d_maps);
     if (p->d_lvl_ctr) cudaFree(p->d_lvl_ctr);
     for (cudaEvent_t e : p->ev0) cudaEventDestroy(e);
     for (cudaEvent_t e : p->ev1) cudaEventDestroy(e);
@@ -1016,21 +1085,32 @@ static int run_inverse_like(dwt2_plan_t p, const void* coef, void* out, void* wo
             InvParams ipm = inv_level_params(p, ip, l, coef, out, workspace, csz, l1, l1_scale, l1_scale_dev);
             int grid = 0, balanced = 0;
             const Decomp dc = decompose(ip.lv[l], inv_out_quads(p->wavelet), p->sm_count, inv_bps, INV_NW, p->seg_env,
-                                        p->balanced_env, &grid, &balanced);
+                                        0, &grid, &balanced);
             ipm.n_strips = dc.n_strips, ipm.seg_rows = dc.seg_rows, ipm.n_segs = dc.n_segs, ipm.n_units = dc.n_units;
-            ipm.balanced = balanced;
-            int e;
-            if (adj) {
-                e = launch_adjoint_f32(ipm, grid, s);
-            } else {
-                switch (p->coef_dtype) {
-                    case DWT2_F32: e = launch_inverse_f32(p->wavelet, inv_scheme(p->scheme), ipm, grid, s); break;
-                    case DWT2_F16: e = launch_inverse_f16(p->wavelet, inv_scheme(p->scheme), ipm, grid, s); break;
-                    case DWT2_BF16: e = launch_inverse_bf16(p->wavelet, inv_scheme(p->scheme), ipm, grid, s); break;
-                    default: e = launch_inverse_i32(p->wavelet, inv_scheme(p->scheme), ipm, grid, s); break;
+            ipm.balanced = 0;
+            inv_inner_rect(ipm, p->wavelet, adj);
+            // the inner units, then (a programmatic dependent: no shared data)
+            // the others
+            bool first = true;
+            for (int cls : {UNITS_INNER, UNITS_EDGE}) {
+                const int units = inv_class_units(ipm, cls);
+                if (units == 0) continue;
+                const int g = (units + INV_NW - 1) / INV_NW, pdl = first ? 0 : 1;
+                first = false;
+                int e;
+                if (adj) {
+                    e = launch_adjoint_f32(ipm, g, pdl, cls, s);
+                } else {
+                    const int sc = inv_scheme(p->scheme);
+                    switch (p->coef_dtype) {
+                        case DWT2_F32: e = launch_inverse_f32(p->wavelet, sc, ipm, g, pdl, cls, s); break;
+                        case DWT2_F16: e = launch_inverse_f16(p->wavelet, sc, ipm, g, pdl, cls, s); break;
+                        case DWT2_BF16: e = launch_inverse_bf16(p->wavelet, sc, ipm, g, pdl, cls, s); break;
+                        default: e = launch_inverse_i32(p->wavelet, sc, ipm, g, pdl, cls, s); break;
+                    }
                 }
+                if (e != cudaSuccess) return DWT2_ERR_CUDA;
             }
-            if (e != cudaSuccess) return DWT2_ERR_CUDA;
         }
         prof_mark(p, l, false, s);
     }
@@ -1053,6 +1133,9 @@ constexpr int N_TUNE_PML = int(sizeof(TUNE_PML_SEGS) / sizeof(TUNE_PML_SEGS[0]))
 
 static int tune_fields(dwt2_plan_t p) { return std::min(p->levels, TUNE_LEVELS); }
 
+// candidate c's configuration is compiled for this plan's pipeline
+static bool cand_compiled(dwt2_plan_t p, int c) { return p->cfg_bps[c / N_TUNE_SEGS] > 0; }
+
 // persistent plans tune one segment height for all levels
 static bool tune_seg_only(dwt2_plan_t p) { return p->persistent; }
 
@@ -1065,8 +1148,10 @@ static int tune_apply(dwt2_plan_t p, int choice) {
     }
     const int nf = tune_fields(p);
     if (nf * TUNE_BITS < 31 && choice >= (1 << (nf * TUNE_BITS))) return DWT2_ERR_INVALID_ARG;
-    for (int f = 0; f < nf; ++f)
-        if (((choice >> (f * TUNE_BITS)) & ((1 << TUNE_BITS) - 1)) >= N_LVL_CANDS) return DWT2_ERR_INVALID_ARG;
+    for (int f = 0; f < nf; ++f) {
+        const int c = (choice >> (f * TUNE_BITS)) & ((1 << TUNE_BITS) - 1);
+        if (c >= N_LVL_CANDS || !cand_compiled(p, c)) return DWT2_ERR_INVALID_ARG;
+    }
     for (int l = 0; l < p->levels; ++l) p->lvl_cand[l] = (choice >> (std::min(l, nf - 1) * TUNE_BITS)) & ((1 << TUNE_BITS) - 1);
     return DWT2_OK;
 }
@@ -1114,6 +1199,10 @@ int dwt2_autotune(dwt2_plan_t p, const void* in, void* coef, void* workspace, vo
         if (seg_only) {
             rc = tune_apply(p, c);
         } else {
+            if (!cand_compiled(p, c)) {  // never chosen
+                for (int l = 0; l < L; ++l) ms[size_t(c) * L + l] = 1e30f;
+                continue;
+            }
             for (int l = 0; l < L; ++l) p->lvl_cand[l] = c;
         }
         for (int i = 0; i < 2 && rc == DWT2_OK; ++i) rc = dwt2_forward(p, in, coef, workspace, stream);

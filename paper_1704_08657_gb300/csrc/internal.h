@@ -65,6 +65,10 @@ struct InvParams {
     int l1;
     float l1_scale;
     const float* l1_scale_dev;
+    // the inner units: strips [in_s0, in_s1) x segments [in_g0, in_g1), those
+    // that run one unweighted staged row loop (inv_inner_rect); a level runs
+    // them in one kernel and every other unit in a second one
+    int in_s0, in_s1, in_g0, in_g1;
 };
 
 // Persistent forward: one descriptor per (image, level), one entry per unit
@@ -106,23 +110,67 @@ struct PmlParams {
 // Grouped inverse / adjoint (plans of several images): one launch runs one
 // level of up to INV_GROUP_MAX images, their parameters in one
 // __grid_constant__ kernel parameter, as for the grouped forward.
-constexpr int INV_GROUP_MAX = 200;
-static_assert(sizeof(InvParams) <= 152, "INV_GROUP_MAX images of parameters fit the 32 KB parameter space");
+constexpr int INV_GROUP_MAX = 170;
 struct InvGroupImg {
     InvParams p;
-    int u_begin;
+    int u_begin[3];  // first unit of the image among the launch's units, per unit class
 };
 struct InvGroupLaunch {
     InvGroupImg img[INV_GROUP_MAX];
-    int n_img, n_units;
-    int wait_prev;  // 1: the first launch of a level
+    int n_img;
+    int n_units[3];  // per unit class
+    int wait_prev;   // 1: the first launch of a level
 };
+static_assert(sizeof(InvGroupLaunch) <= 32764, "a grouped launch block fits the kernel parameter space");
 
-int launch_inv_group_f32(int wav, int scheme, const InvGroupLaunch& g, int grid, int pdl, cudaStream_t s);
-int launch_inv_group_f16(int wav, int scheme, const InvGroupLaunch& g, int grid, int pdl, cudaStream_t s);
-int launch_inv_group_bf16(int wav, int scheme, const InvGroupLaunch& g, int grid, int pdl, cudaStream_t s);
-int launch_inv_group_i32(int wav, int scheme, const InvGroupLaunch& g, int grid, int pdl, cudaStream_t s);
-int launch_adj_group_f32(const InvGroupLaunch& g, int grid, int pdl, cudaStream_t s);
+// Unit classes of an inverse or adjoint launch: every unit, the inner units
+// only, or every unit but the inner ones.
+enum { UNITS_ALL = 0, UNITS_INNER = 1, UNITS_EDGE = 2 };
+// number of units of class cls, and the (strip, segment) of its lu-th unit
+__host__ __device__ inline int inv_class_units(const InvParams& p, int cls) {
+    const int inner = (p.in_s1 - p.in_s0) * (p.in_g1 - p.in_g0);
+    return cls == UNITS_ALL ? p.n_units : (cls == UNITS_INNER ? inner : p.n_units - inner);
+}
+__host__ __device__ inline void inv_class_unit(const InvParams& p, int cls, int lu, int& s, int& g) {
+    if (cls == UNITS_INNER) {
+        const int ns = p.in_s1 - p.in_s0;
+        s = p.in_s0 + lu % ns;
+        g = p.in_g0 + lu / ns;
+        return;
+    }
+    if (cls == UNITS_EDGE && p.in_s1 > p.in_s0 && p.in_g1 > p.in_g0) {
+        // segments above the inner ones (whole rows of strips), then for each
+        // inner segment its strips left and right of the inner ones, then the
+        // segments below
+        const int top = p.in_g0 * p.n_strips;
+        if (lu < top) {
+            s = lu % p.n_strips;
+            g = lu / p.n_strips;
+            return;
+        }
+        lu -= top;
+        const int side = p.n_strips - (p.in_s1 - p.in_s0);
+        const int mid = (p.in_g1 - p.in_g0) * side;
+        if (lu < mid) {
+            g = p.in_g0 + lu / side;
+            const int k = lu % side;
+            s = k < p.in_s0 ? k : p.in_s1 + (k - p.in_s0);
+            return;
+        }
+        lu -= mid;
+        s = lu % p.n_strips;
+        g = p.in_g1 + lu / p.n_strips;
+        return;
+    }
+    s = lu % p.n_strips;
+    g = lu / p.n_strips;
+}
+
+int launch_inv_group_f32(int wav, int scheme, const InvGroupLaunch& g, int grid, int pdl, int cls, cudaStream_t s);
+int launch_inv_group_f16(int wav, int scheme, const InvGroupLaunch& g, int grid, int pdl, int cls, cudaStream_t s);
+int launch_inv_group_bf16(int wav, int scheme, const InvGroupLaunch& g, int grid, int pdl, int cls, cudaStream_t s);
+int launch_inv_group_i32(int wav, int scheme, const InvGroupLaunch& g, int grid, int pdl, int cls, cudaStream_t s);
+int launch_adj_group_f32(const InvGroupLaunch& g, int grid, int pdl, int cls, cudaStream_t s);
 
 // Two forward levels in one launch (fused.cuh): level l comes through the
 // tensor maps, level l+1 reads the level-l low-low band from a ring of rows in
@@ -195,18 +243,18 @@ int launch_group_f16(int wav, int scheme, const GroupLaunch& g, int grid, const 
 int launch_group_bf16(int wav, int scheme, const GroupLaunch& g, int grid, const FwdCfg& cfg, int pdl, cudaStream_t s);
 int launch_group_i32(int wav, int scheme, const GroupLaunch& g, int grid, const FwdCfg& cfg, int pdl, cudaStream_t s);
 
-int launch_inverse_f32(int wav, int scheme, const InvParams& p, int grid, cudaStream_t s);
-int launch_inverse_f16(int wav, int scheme, const InvParams& p, int grid, cudaStream_t s);
-int launch_inverse_bf16(int wav, int scheme, const InvParams& p, int grid, cudaStream_t s);
-int launch_inverse_i32(int wav, int scheme, const InvParams& p, int grid, cudaStream_t s);
-int launch_adjoint_f32(const InvParams& p, int grid, cudaStream_t s);
+int launch_inverse_f32(int wav, int scheme, const InvParams& p, int grid, int pdl, int cls, cudaStream_t s);
+int launch_inverse_f16(int wav, int scheme, const InvParams& p, int grid, int pdl, int cls, cudaStream_t s);
+int launch_inverse_bf16(int wav, int scheme, const InvParams& p, int grid, int pdl, int cls, cudaStream_t s);
+int launch_inverse_i32(int wav, int scheme, const InvParams& p, int grid, int pdl, int cls, cudaStream_t s);
+int launch_adjoint_f32(const InvParams& p, int grid, int pdl, int cls, cudaStream_t s);
 
-// Plans with at most PML_TMA_MAX_DESCS (image, level) descriptors pass a
-// box map and a single-row map per descriptor as kernel parameters and load
-// with TMA; larger batches load with cp.async.
-constexpr int PML_TMA_MAX_DESCS = 16;
+// The persistent launch loads with TMA through a device-resident table of
+// two tensor maps (a box and a single row) per (image, level) descriptor,
+// written when the plan first runs on a set of buffers; use_tma = 0 selects
+// the cp.async loader instead (DWT2_PML_CPASYNC, for tests).
 struct PmlLaunch {
-    CUtensorMap maps[2 * PML_TMA_MAX_DESCS];  // [2*desc] box, [2*desc+1] single row
+    const CUtensorMap* maps;  // device table: [2*desc] box, [2*desc+1] single row
     PmlParams base;
     int use_tma;
 };
@@ -219,9 +267,10 @@ int pml_blocks_per_sm(int wav, int scheme, int coef_dtype);
 
 // resident blocks per SM of a forward / inverse launch (0 on error)
 int forward_blocks_per_sm(int wav, int scheme, int coef_dtype, const FwdCfg& cfg);
-int inverse_blocks_per_sm(int wav, int scheme, int coef_dtype, bool adjoint);
+int inverse_blocks_per_sm(int wav, int scheme, int coef_dtype, bool adjoint);  // the inner-unit kernel
 
-// the forward configurations compiled in (index 0 is the default)
+// the forward configurations compiled in (index 0 is the default); one with
+// no resident block (forward_blocks_per_sm 0) is skipped by the tuner
 constexpr int N_FWD_CFGS = 4;
 extern const FwdCfg FWD_CFGS[N_FWD_CFGS];
 size_t fwd_smem_bytes_of(const FwdCfg& c);

@@ -8,12 +8,12 @@ int launch_forward_bf16(int wav, int scheme, const CUtensorMap& box, const CUten
     return launch_forward_t<__nv_bfloat16>(wav, scheme, box, row, p, grid, cfg, s);
 }
 
-int launch_inverse_bf16(int wav, int scheme, const InvParams& p, int grid, cudaStream_t s) {
-    return launch_inverse_t<__nv_bfloat16>(wav, scheme, p, grid, s);
+int launch_inverse_bf16(int wav, int scheme, const InvParams& p, int grid, int pdl, int cls, cudaStream_t s) {
+    return launch_inverse_t<__nv_bfloat16>(wav, scheme, p, grid, pdl, cls, s);
 }
 
-int launch_inv_group_bf16(int wav, int scheme, const InvGroupLaunch& g, int grid, int pdl, cudaStream_t s) {
-    return launch_inv_group_t<__nv_bfloat16>(wav, scheme, g, grid, pdl, s);
+int launch_inv_group_bf16(int wav, int scheme, const InvGroupLaunch& g, int grid, int pdl, int cls, cudaStream_t s) {
+    return launch_inv_group_t<__nv_bfloat16>(wav, scheme, g, grid, pdl, cls, s);
 }
 
 int occupancy_forward_bf16(int wav, int scheme, const FwdCfg& cfg) { return occupancy_forward_t<__nv_bfloat16>(wav, scheme, cfg); }

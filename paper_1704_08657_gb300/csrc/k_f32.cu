@@ -8,12 +8,12 @@ int launch_forward_f32(int wav, int scheme, const CUtensorMap& box, const CUtens
     return launch_forward_t<float>(wav, scheme, box, row, p, grid, cfg, s);
 }
 
-int launch_inverse_f32(int wav, int scheme, const InvParams& p, int grid, cudaStream_t s) {
-    return launch_inverse_t<float>(wav, scheme, p, grid, s);
+int launch_inverse_f32(int wav, int scheme, const InvParams& p, int grid, int pdl, int cls, cudaStream_t s) {
+    return launch_inverse_t<float>(wav, scheme, p, grid, pdl, cls, s);
 }
 
-int launch_inv_group_f32(int wav, int scheme, const InvGroupLaunch& g, int grid, int pdl, cudaStream_t s) {
-    return launch_inv_group_t<float>(wav, scheme, g, grid, pdl, s);
+int launch_inv_group_f32(int wav, int scheme, const InvGroupLaunch& g, int grid, int pdl, int cls, cudaStream_t s) {
+    return launch_inv_group_t<float>(wav, scheme, g, grid, pdl, cls, s);
 }
 
 int occupancy_forward_f32(int wav, int scheme, const FwdCfg& cfg) { return occupancy_forward_t<float>(wav, scheme, cfg); }
@@ -40,8 +40,8 @@ int launch_group_f32(int wav, int scheme, const GroupLaunch& g, int grid, const 
 
 namespace dwt2 {
 
-int launch_adjoint_f32(const InvParams& p, int grid, cudaStream_t s) {
-    return launch_inv_one<Adj97<INV_QL>, float, true>(p, grid, s);
+int launch_adjoint_f32(const InvParams& p, int grid, int pdl, int cls, cudaStream_t s) {
+    return launch_inv_one<Adj97<INV_QL>, float, true>(p, grid, pdl, cls, s);
 }
 
 int occupancy_forward_f16(int wav, int scheme, const FwdCfg& cfg);
@@ -60,8 +60,8 @@ int forward_blocks_per_sm(int wav, int scheme, int coef_dtype, const FwdCfg& cfg
     }
 }
 
-int launch_adj_group_f32(const InvGroupLaunch& g, int grid, int pdl, cudaStream_t s) {
-    return launch_inv_group_one<Adj97<INV_QL>, float, true>(g, grid, pdl, s);
+int launch_adj_group_f32(const InvGroupLaunch& g, int grid, int pdl, int cls, cudaStream_t s) {
+    return launch_inv_group_one<Adj97<INV_QL>, float, true>(g, grid, pdl, cls, s);
 }
 
 int occupancy_pml_f16(int wav, int scheme);

@@ -561,7 +561,7 @@ struct PmlView {
 };
 
 template <class Pipe, class OutT, int QL, int QR, int NST, int NW, bool TMA>
-__global__ void __launch_bounds__(NW * 32) pml_kernel(const __grid_constant__ PmlLaunch L) {
+__global__ void __launch_bounds__(NW * 32, FwdMinBlocks<Pipe, NW>::value) pml_kernel(const __grid_constant__ PmlLaunch L) {
     using CT = typename Pipe::CT;
     const PmlParams& P = L.base;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -621,7 +621,11 @@ __global__ void __launch_bounds__(NW * 32) pml_kernel(const __grid_constant__ Pm
         const int R1 = min(R0 + d.seg_rows, d.hq);
         bool ok;
         if constexpr (TMA) {
-            const TmaLoader ld{&L.maps[2 * un.desc], &L.maps[2 * un.desc + 1]};
+            const TmaLoader ld{L.maps + 2 * un.desc, L.maps + 2 * un.desc + 1};
+            if (lane == 0) {
+                tma_prefetch_desc(ld.box);
+                tma_prefetch_desc(ld.row);
+            }
             ok = fwd_unit<Pipe, OutT, QL, QR, NST>(v, ld, un.s, R0, R1, bufs, bars, gstage, lane);
         } else {
             const CT* src = d.src_is_ws ? static_cast<const CT*>(P.ws) + d.src_off
@@ -1051,29 +1055,35 @@ __device__ __forceinline__ bool inv_unit_staged(const InvParams& p, int s, int R
 // inverse / adjoint unit: staged when every band row takes paired copies,
 // else direct loads.  Adjoint units away from the boundary (every quad of
 // the strip and every row the steps weight in [1, half - 2]) run the
-// unweighted pipeline.
-template <class Pipe, class BT, bool ADJ, int QR, int NST>
+// unweighted pipeline.  CLS selects the code compiled in: UNITS_INNER only the
+// staged row loop of the inner units (inv_inner_rect), UNITS_EDGE every other
+// path, UNITS_ALL both.
+template <class Pipe, class BT, bool ADJ, int QR, int NST, int CLS = UNITS_ALL>
 __device__ __forceinline__ bool inv_unit_any(const InvParams& p, int s, int R0, int R1, int lane,
                                              unsigned char* ring, uint64_t* bars, uint32_t& gstage) {
-    constexpr int HQ = PipeGeom<Pipe>::HALO;
-    constexpr int OUTQ = 32 * 2 - 2 * HQ;
-    const int x0 = s * (2 * OUTQ) - 2 * HQ;
-    const bool staged = p.vec_in_lo && p.vec_in_hi && p.vec_ll;
-    const bool interior = (x0 >= 0) && (x0 / 2 + 64 <= p.wh);
-    if constexpr (ADJ) {
-        // the steps weight rows R0-4 .. R1+1 (see Adj97::step) and quads x0/2 .. x0/2+63
-        const bool inner = staged && interior && (x0 / 2 >= 1) && (x0 / 2 + 63 <= p.wh - 2) && (R0 - 4 >= 1) &&
-                           (R1 + 1 <= p.hh - 2);
-        if (inner)
-            return inv_unit_staged<AdjInner97<2>, BT, true, QR, NST, false>(p, s, R0, R1, lane, ring, bars, gstage);
+    using Inner = typename std::conditional<ADJ, AdjInner97<2>, Pipe>::type;
+    if constexpr (CLS == UNITS_INNER) {
+        return inv_unit_staged<Inner, BT, ADJ, QR, NST, false>(p, s, R0, R1, lane, ring, bars, gstage);
+    } else {
+        constexpr int HQ = PipeGeom<Pipe>::HALO;
+        constexpr int OUTQ = 32 * 2 - 2 * HQ;
+        const int x0 = s * (2 * OUTQ) - 2 * HQ;
+        const bool staged = p.vec_in_lo && p.vec_in_hi && p.vec_ll;
+        const bool interior = (x0 >= 0) && (x0 / 2 + 64 <= p.wh);
+        if constexpr (ADJ && CLS == UNITS_ALL) {
+            // the steps weight rows R0-4 .. R1+1 (see Adj97::step) and quads x0/2 .. x0/2+63
+            const bool inner = staged && interior && (x0 / 2 >= 1) && (x0 / 2 + 63 <= p.wh - 2) && (R0 - 4 >= 1) &&
+                               (R1 + 1 <= p.hh - 2);
+            if (inner) return inv_unit_staged<Inner, BT, true, QR, NST, false>(p, s, R0, R1, lane, ring, bars, gstage);
+        }
+        if (staged && interior)
+            return inv_unit_staged<Pipe, BT, ADJ, QR, NST, false>(p, s, R0, R1, lane, ring, bars, gstage);
+        if constexpr (sizeof(BT) == 4) {
+            if (staged) return inv_unit_staged<Pipe, BT, ADJ, QR, NST, true>(p, s, R0, R1, lane, ring, bars, gstage);
+        }
+        inv_unit<Pipe, BT, ADJ, 2>(p, s, R0, R1, lane);
+        return true;
     }
-    if (staged && interior)
-        return inv_unit_staged<Pipe, BT, ADJ, QR, NST, false>(p, s, R0, R1, lane, ring, bars, gstage);
-    if constexpr (sizeof(BT) == 4) {
-        if (staged) return inv_unit_staged<Pipe, BT, ADJ, QR, NST, true>(p, s, R0, R1, lane, ring, bars, gstage);
-    }
-    inv_unit<Pipe, BT, ADJ, 2>(p, s, R0, R1, lane);
-    return true;
 }
 
 template <int QR, int NST, int NW>
@@ -1089,26 +1099,51 @@ __device__ __forceinline__ void inv_ring(unsigned char* smem, int warp, int lane
     __syncwarp();
 }
 
-// One level of one image: the warps take their units from Pieces.
-template <class Pipe, class BT, bool ADJ, int QL, int NW>
-__global__ void __launch_bounds__(NW * 32) inv_kernel(const InvParams p) {
+// resident blocks the inner-unit kernels of the two-quad-halo pipelines
+// (CDF 9/7, CDF 5/3) are held to: one staged row loop fits the register budget
+// of five 4-warp blocks per SM; the DD 13/7 pipelines (six-row rings) and the
+// edge-unit kernels are left to the compiler
+template <class Pipe, int CLS>
+struct InvMinBlocks {
+    static constexpr int value = (CLS == UNITS_INNER && PipeGeom<Pipe>::HALO == 2) ? 5 : 1;
+};
+
+// One level of one image.  UNITS_ALL: the warps take their units from Pieces;
+// otherwise the units of class CLS, dealt round-robin in segment-major order.
+template <class Pipe, class BT, bool ADJ, int QL, int NW, int CLS = UNITS_ALL>
+__global__ void __launch_bounds__(NW * 32, InvMinBlocks<Pipe, CLS>::value) inv_kernel(const InvParams p) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char* ring;
     uint64_t* bars;
     inv_ring<INV_QR, INV_NST, NW>(smem, warp, lane, ring, bars);
+    // a second launch of a level (PDL) shares no data with the first
+    griddep_launch_dependents();
     uint32_t gstage = 0;
-    Pieces<InvParams> pieces(p, blockIdx.x * NW + warp, gridDim.x * NW);
-    int s, R0, R1;
-    while (pieces.next(p, s, R0, R1))
-        if (!inv_unit_any<Pipe, BT, ADJ, INV_QR, INV_NST>(p, s, R0, R1, lane, ring, bars, gstage)) return;
+    if constexpr (CLS == UNITS_ALL) {
+        Pieces<InvParams> pieces(p, blockIdx.x * NW + warp, gridDim.x * NW);
+        int s, R0, R1;
+        while (pieces.next(p, s, R0, R1))
+            if (!inv_unit_any<Pipe, BT, ADJ, INV_QR, INV_NST>(p, s, R0, R1, lane, ring, bars, gstage)) return;
+    } else {
+        const int n = inv_class_units(p, CLS);
+        for (int lu = blockIdx.x * NW + warp; lu < n; lu += gridDim.x * NW) {
+            int s, g;
+            inv_class_unit(p, CLS, lu, s, g);
+            const int R0 = g * p.seg_rows;
+            if (!inv_unit_any<Pipe, BT, ADJ, INV_QR, INV_NST, CLS>(p, s, R0, min(R0 + p.seg_rows, p.hq), lane, ring,
+                                                                    bars, gstage))
+                return;
+        }
+    }
 }
 
-// One level of a group of images (InvGroupLaunch): units in order, the image
-// found by binary search over the group's unit ranges; only the first launch
-// of a level waits for earlier work.
-template <class Pipe, class BT, bool ADJ, int QL, int NW>
-__global__ void __launch_bounds__(NW * 32) inv_group_kernel(const __grid_constant__ InvGroupLaunch L) {
+// One level of a group of images (InvGroupLaunch): the units of class CLS of
+// every image, in order, the image found by binary search over the group's
+// unit ranges; only the first launch of a level waits for earlier work.
+template <class Pipe, class BT, bool ADJ, int QL, int NW, int CLS = UNITS_ALL>
+__global__ void __launch_bounds__(NW * 32, InvMinBlocks<Pipe, CLS>::value)
+    inv_group_kernel(const __grid_constant__ InvGroupLaunch L) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char* ring;
@@ -1117,19 +1152,19 @@ __global__ void __launch_bounds__(NW * 32) inv_group_kernel(const __grid_constan
     if (L.wait_prev) griddep_wait();
     griddep_launch_dependents();
     uint32_t gstage = 0;
-    for (int u = blockIdx.x * NW + warp; u < L.n_units; u += gridDim.x * NW) {
+    for (int u = blockIdx.x * NW + warp; u < L.n_units[CLS]; u += gridDim.x * NW) {
         int lo = 0, hi = L.n_img - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (L.img[mid].u_begin <= u) lo = mid;
+            if (L.img[mid].u_begin[CLS] <= u) lo = mid;
             else hi = mid - 1;
         }
         const InvParams& p = L.img[lo].p;
-        const int lu = u - L.img[lo].u_begin;
-        const int s = lu % p.n_strips;
-        const int R0 = (lu / p.n_strips) * p.seg_rows;
-        if (!inv_unit_any<Pipe, BT, ADJ, INV_QR, INV_NST>(p, s, R0, min(R0 + p.seg_rows, p.hq), lane, ring, bars,
-                                                          gstage))
+        int s, g;
+        inv_class_unit(p, CLS, u - L.img[lo].u_begin[CLS], s, g);
+        const int R0 = g * p.seg_rows;
+        if (!inv_unit_any<Pipe, BT, ADJ, INV_QR, INV_NST, CLS>(p, s, R0, min(R0 + p.seg_rows, p.hq), lane, ring, bars,
+                                                                gstage))
             return;
     }
 }

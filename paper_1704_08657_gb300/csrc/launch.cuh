@@ -87,6 +87,7 @@ int launch_group_t(int wav, int scheme, const GroupLaunch& g, int grid, const Fw
     } else {
         if (wav == WAV_DD137) {
             if (scheme == SCHEME_NONSEP) return launch_group_cfgs<Fwd137, SCHEME_NONSEP, OutT>(g, grid, c, pdl, s);
+            if (scheme == SCHEME_REDUCED) return launch_group_cfgs<Fwd137, SCHEME_REDUCED, OutT>(g, grid, c, pdl, s);
             if (scheme == SCHEME_SEP) return launch_group_cfgs<Fwd137, SCHEME_SEP, OutT>(g, grid, c, pdl, s);
             return cudaErrorInvalidValue;
         }
@@ -104,8 +105,15 @@ int launch_group_t(int wav, int scheme, const GroupLaunch& g, int grid, const Fw
 template <class Pipe, class OutT, int QL, int QR, int NST, int NW, bool SPEC>
 int occupancy_fwd_one() {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fwd_tma_kernel<Pipe, OutT, QL, QR, NST, NW, SPEC>, NW * 32,
-                                                      fwd_smem_bytes<QL, QR, NST, NW>()) != cudaSuccess) {
+    auto k = fwd_tma_kernel<Pipe, OutT, QL, QR, NST, NW, SPEC>;
+    constexpr size_t smem = fwd_smem_bytes<QL, QR, NST, NW>();
+    // above 48 KB the kernel must be allowed its shared memory before the
+    // occupancy query counts it (the launch sets the same attribute)
+    if (smem > 48 * 1024 && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, NW * 32, smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -130,6 +138,7 @@ int occupancy_forward_t(int wav, int scheme, const FwdCfg& c) {
     } else {
         if (wav == WAV_DD137) {
             if (scheme == SCHEME_SEP) return occupancy_fwd_cfgs<Fwd137, SCHEME_SEP, OutT>(c);
+            if (scheme == SCHEME_REDUCED) return occupancy_fwd_cfgs<Fwd137, SCHEME_REDUCED, OutT>(c);
             return occupancy_fwd_cfgs<Fwd137, SCHEME_NONSEP, OutT>(c);
         }
         if (scheme == SCHEME_NONSEP) return occupancy_fwd_cfgs<Fwd97, SCHEME_NONSEP, OutT>(c);
@@ -141,11 +150,13 @@ int occupancy_forward_t(int wav, int scheme, const FwdCfg& c) {
     }
 }
 
+// resident blocks per SM of the inner-unit kernel (the one that carries a level)
 template <class Pipe, class BT, bool ADJ>
 int occupancy_inv_one() {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, inv_kernel<Pipe, BT, ADJ, INV_QL, INV_NW>, INV_NW * 32,
-                                                      inv_smem_bytes<INV_QR, INV_NST, INV_NW>()) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, inv_kernel<Pipe, BT, ADJ, INV_QL, INV_NW, UNITS_INNER>,
+                                                      INV_NW * 32, inv_smem_bytes<INV_QR, INV_NST, INV_NW>()) !=
+        cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -191,6 +202,8 @@ int launch_forward_t(int wav, int scheme, const CUtensorMap& box, const CUtensor
         if (wav == WAV_DD137) {
             if (scheme == SCHEME_NONSEP)
                 return launch_fwd_cfgs<Fwd137, SCHEME_NONSEP, OutT>(box, row, p, grid, c, s);
+            if (scheme == SCHEME_REDUCED)
+                return launch_fwd_cfgs<Fwd137, SCHEME_REDUCED, OutT>(box, row, p, grid, c, s);
             if (scheme == SCHEME_SEP) return launch_fwd_cfgs<Fwd137, SCHEME_SEP, OutT>(box, row, p, grid, c, s);
             return cudaErrorInvalidValue;
         }
@@ -255,64 +268,76 @@ int launch_pml_t(int wav, int scheme, const PmlLaunch* p, int grid, cudaStream_t
     }
 }
 
-template <class Pipe, class BT, bool ADJ>
-int launch_inv_one(const InvParams& p, int grid, cudaStream_t s) {
-    inv_kernel<Pipe, BT, ADJ, INV_QL, INV_NW><<<grid, INV_NW * 32, inv_smem_bytes<INV_QR, INV_NST, INV_NW>(), s>>>(p);
-    return cudaGetLastError();
-}
-
-template <class Pipe, class BT, bool ADJ>
-int launch_inv_group_one(const InvGroupLaunch& g, int grid, int pdl, cudaStream_t s) {
+// One launch of the inverse or adjoint units of class CLS of a level (one
+// image, or a group); pdl: a programmatic dependent of the previous kernel
+// (the edge units of a level, which share no data with its inner units).
+inline cudaLaunchConfig_t inv_launch_config(int grid, int pdl, cudaStream_t s, cudaLaunchAttribute* attr) {
     cudaLaunchConfig_t lc = {};
     lc.gridDim = dim3(grid);
     lc.blockDim = dim3(INV_NW * 32);
     lc.dynamicSmemBytes = inv_smem_bytes<INV_QR, INV_NST, INV_NW>();
     lc.stream = s;
-    cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     lc.attrs = attr;
     lc.numAttrs = pdl ? 1 : 0;
-    return cudaLaunchKernelEx(&lc, inv_group_kernel<Pipe, BT, ADJ, INV_QL, INV_NW>, g);
+    return lc;
+}
+
+template <class Pipe, class BT, bool ADJ>
+int launch_inv_one(const InvParams& p, int grid, int pdl, int cls, cudaStream_t s) {
+    cudaLaunchAttribute attr[1];
+    const cudaLaunchConfig_t lc = inv_launch_config(grid, pdl, s, attr);
+    if (cls == UNITS_INNER) return cudaLaunchKernelEx(&lc, inv_kernel<Pipe, BT, ADJ, INV_QL, INV_NW, UNITS_INNER>, p);
+    return cudaLaunchKernelEx(&lc, inv_kernel<Pipe, BT, ADJ, INV_QL, INV_NW, UNITS_EDGE>, p);
+}
+
+template <class Pipe, class BT, bool ADJ>
+int launch_inv_group_one(const InvGroupLaunch& g, int grid, int pdl, int cls, cudaStream_t s) {
+    cudaLaunchAttribute attr[1];
+    const cudaLaunchConfig_t lc = inv_launch_config(grid, pdl, s, attr);
+    if (cls == UNITS_INNER)
+        return cudaLaunchKernelEx(&lc, inv_group_kernel<Pipe, BT, ADJ, INV_QL, INV_NW, UNITS_INNER>, g);
+    return cudaLaunchKernelEx(&lc, inv_group_kernel<Pipe, BT, ADJ, INV_QL, INV_NW, UNITS_EDGE>, g);
 }
 
 template <class BT>
-int launch_inv_group_t(int wav, int scheme, const InvGroupLaunch& g, int grid, int pdl, cudaStream_t s) {
+int launch_inv_group_t(int wav, int scheme, const InvGroupLaunch& g, int grid, int pdl, int cls, cudaStream_t s) {
     if constexpr (std::is_same<BT, int>::value) {
         if (wav != WAV_CDF53I) return cudaErrorInvalidValue;
-        if (scheme == SCHEME_SEP) return launch_inv_group_one<Inv53<SCHEME_SEP, INV_QL>, int, false>(g, grid, pdl, s);
-        return launch_inv_group_one<Inv53<SCHEME_NONSEP, INV_QL>, int, false>(g, grid, pdl, s);
+        if (scheme == SCHEME_SEP) return launch_inv_group_one<Inv53<SCHEME_SEP, INV_QL>, int, false>(g, grid, pdl, cls, s);
+        return launch_inv_group_one<Inv53<SCHEME_NONSEP, INV_QL>, int, false>(g, grid, pdl, cls, s);
     } else {
         if (wav == WAV_DD137) {
             if (scheme == SCHEME_SEP)
-                return launch_inv_group_one<Inv137<SCHEME_SEP, INV_QL>, BT, false>(g, grid, pdl, s);
-            return launch_inv_group_one<Inv137<SCHEME_NONSEP, INV_QL>, BT, false>(g, grid, pdl, s);
+                return launch_inv_group_one<Inv137<SCHEME_SEP, INV_QL>, BT, false>(g, grid, pdl, cls, s);
+            return launch_inv_group_one<Inv137<SCHEME_NONSEP, INV_QL>, BT, false>(g, grid, pdl, cls, s);
         }
         if (wav != WAV_CDF97) return cudaErrorInvalidValue;
         if (scheme == SCHEME_NONSEP)
-            return launch_inv_group_one<Inv97<SCHEME_NONSEP, INV_QL>, BT, false>(g, grid, pdl, s);
+            return launch_inv_group_one<Inv97<SCHEME_NONSEP, INV_QL>, BT, false>(g, grid, pdl, cls, s);
         if (scheme == SCHEME_REDUCED)
-            return launch_inv_group_one<Inv97<SCHEME_REDUCED, INV_QL>, BT, false>(g, grid, pdl, s);
-        return launch_inv_group_one<Inv97<SCHEME_SEP, INV_QL>, BT, false>(g, grid, pdl, s);
+            return launch_inv_group_one<Inv97<SCHEME_REDUCED, INV_QL>, BT, false>(g, grid, pdl, cls, s);
+        return launch_inv_group_one<Inv97<SCHEME_SEP, INV_QL>, BT, false>(g, grid, pdl, cls, s);
     }
 }
 
 template <class BT>
-int launch_inverse_t(int wav, int scheme, const InvParams& p, int grid, cudaStream_t s) {
+int launch_inverse_t(int wav, int scheme, const InvParams& p, int grid, int pdl, int cls, cudaStream_t s) {
     if constexpr (std::is_same<BT, int>::value) {
         if (wav != WAV_CDF53I) return cudaErrorInvalidValue;
-        if (scheme == SCHEME_SEP) return launch_inv_one<Inv53<SCHEME_SEP, INV_QL>, int, false>(p, grid, s);
-        if (scheme == SCHEME_NONSEP) return launch_inv_one<Inv53<SCHEME_NONSEP, INV_QL>, int, false>(p, grid, s);
+        if (scheme == SCHEME_SEP) return launch_inv_one<Inv53<SCHEME_SEP, INV_QL>, int, false>(p, grid, pdl, cls, s);
+        if (scheme == SCHEME_NONSEP) return launch_inv_one<Inv53<SCHEME_NONSEP, INV_QL>, int, false>(p, grid, pdl, cls, s);
         return cudaErrorInvalidValue;
     } else {
         if (wav == WAV_DD137) {
-            if (scheme == SCHEME_SEP) return launch_inv_one<Inv137<SCHEME_SEP, INV_QL>, BT, false>(p, grid, s);
-            return launch_inv_one<Inv137<SCHEME_NONSEP, INV_QL>, BT, false>(p, grid, s);
+            if (scheme == SCHEME_SEP) return launch_inv_one<Inv137<SCHEME_SEP, INV_QL>, BT, false>(p, grid, pdl, cls, s);
+            return launch_inv_one<Inv137<SCHEME_NONSEP, INV_QL>, BT, false>(p, grid, pdl, cls, s);
         }
         if (wav != WAV_CDF97) return cudaErrorInvalidValue;
-        if (scheme == SCHEME_NONSEP) return launch_inv_one<Inv97<SCHEME_NONSEP, INV_QL>, BT, false>(p, grid, s);
-        if (scheme == SCHEME_REDUCED) return launch_inv_one<Inv97<SCHEME_REDUCED, INV_QL>, BT, false>(p, grid, s);
-        if (scheme == SCHEME_SEP) return launch_inv_one<Inv97<SCHEME_SEP, INV_QL>, BT, false>(p, grid, s);
+        if (scheme == SCHEME_NONSEP) return launch_inv_one<Inv97<SCHEME_NONSEP, INV_QL>, BT, false>(p, grid, pdl, cls, s);
+        if (scheme == SCHEME_REDUCED) return launch_inv_one<Inv97<SCHEME_REDUCED, INV_QL>, BT, false>(p, grid, pdl, cls, s);
+        if (scheme == SCHEME_SEP) return launch_inv_one<Inv97<SCHEME_SEP, INV_QL>, BT, false>(p, grid, pdl, cls, s);
         return cudaErrorInvalidValue;
     }
 }

@@ -1221,6 +1221,87 @@ __device__ __forceinline__ void dd_ns_update(const Row<float, QL>& w0, const Row
     }
 }
 
+// --- reduced operations for DD 13/7 (Optimization Approach, Table 1) --------
+// P = P0 + P1 with P0 = PN (the own quad's near tap) and the three other
+// taps P1 = PN z + PF (z^-1 + z^2); U = U0 + U1 with U0 = UN and
+// U1 = UN z^-1 + UF (z + z^-2).  The non-separable step keeps P1 (U1): 3 taps
+// for each of P1 c1, P1* c1, P1* c2, P1 c3 and 9 for P1 P1* c1, i.e. 21
+// operations; the constant parts follow as separable lifting inside the quad
+// (T_{P0}^H, T_{P0}^V: 4 operations), which is Table 1's 2 x 21 + 8 = 50.
+// P1 x along the row: PN x[q+1] + PF (x[q-1] + x[q+2])
+template <int QL>
+__device__ __forceinline__ void dd_p1h(const float (&x)[QL], float (&o)[QL], float pn, float pf) {
+    float l[QL], r[QL], rr[QL];
+    left_of(x, l);
+    right_of(x, r);
+    right2_of(x, rr);
+#pragma unroll
+    for (int q = 0; q < QL; ++q) o[q] = fmaf(pf, l[q] + rr[q], pn * r[q]);
+}
+// U1 x along the row: UN x[q-1] + UF (x[q-2] + x[q+1])
+template <int QL>
+__device__ __forceinline__ void dd_u1h(const float (&x)[QL], float (&o)[QL], float un, float uf) {
+    float l[QL], ll[QL], r[QL];
+    left_of(x, l);
+    left2_of(x, ll);
+    right_of(x, r);
+#pragma unroll
+    for (int q = 0; q < QL; ++q) o[q] = fmaf(uf, ll[q] + r[q], un * l[q]);
+}
+
+// T_{P1} then T_{P0}^H, T_{P0}^V of row m from the pre-step rows m-1 .. m+2.
+template <int QL>
+__device__ __forceinline__ void dd_rd_predict(const Row<float, QL>& w0, const Row<float, QL>& w1,
+                                              const Row<float, QL>& w2, const Row<float, QL>& w3, Row<float, QL>& o,
+                                              float pn, float pf) {
+    float v1[QL], v2[QL], h1[QL], h3[QL], hv1[QL];
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+        v1[q] = fmaf(pf, w0.c1[q] + w3.c1[q], pn * w2.c1[q]);  // P1* c1
+        v2[q] = fmaf(pf, w0.c2[q] + w3.c2[q], pn * w2.c2[q]);  // P1* c2
+    }
+    dd_p1h(w1.c1, h1, pn, pf);  // P1 c1
+    dd_p1h(w1.c3, h3, pn, pf);  // P1 c3
+    dd_p1h(v1, hv1, pn, pf);    // P1 P1* c1
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+        const float c1 = w1.c1[q];
+        const float c2 = fmaf(pn, c1, w1.c2[q] + h1[q]);           // T_{P1}, then T_{P0}^H on c2
+        const float c3 = w1.c3[q] + v1[q];                         // T_{P1}
+        const float c4 = fmaf(pn, c3, w1.c4[q] + (hv1[q] + v2[q] + h3[q]));  // T_{P1}, T_{P0}^H on c4
+        o.c1[q] = c1;
+        o.c2[q] = c2;
+        o.c3[q] = fmaf(pn, c1, c3);                                 // T_{P0}^V
+        o.c4[q] = fmaf(pn, c2, c4);
+    }
+}
+// S_{U1} then S_{U0}^H, S_{U0}^V of row k from the pre-step rows k-2 .. k+1.
+template <int QL>
+__device__ __forceinline__ void dd_rd_update(const Row<float, QL>& w0, const Row<float, QL>& w1,
+                                             const Row<float, QL>& w2, const Row<float, QL>& w3, Row<float, QL>& o,
+                                             float un, float uf) {
+    float v3[QL], v4[QL], h2[QL], h4[QL], hv4[QL];
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+        v3[q] = fmaf(uf, w0.c3[q] + w3.c3[q], un * w1.c3[q]);  // U1* c3
+        v4[q] = fmaf(uf, w0.c4[q] + w3.c4[q], un * w1.c4[q]);  // U1* c4
+    }
+    dd_u1h(w2.c2, h2, un, uf);  // U1 c2
+    dd_u1h(w2.c4, h4, un, uf);  // U1 c4
+    dd_u1h(v4, hv4, un, uf);    // U1 U1* c4
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+        const float c4 = w2.c4[q];
+        const float c2 = w2.c2[q] + v4[q];                                    // S_{U1}
+        const float c3 = fmaf(un, c4, w2.c3[q] + h4[q]);                      // S_{U1}, then S_{U0}^H on c3
+        const float c1 = fmaf(un, c2, w2.c1[q] + (h2[q] + v3[q] + hv4[q]));   // S_{U1}, S_{U0}^H on c1
+        o.c1[q] = fmaf(un, c3, c1);                                           // S_{U0}^V
+        o.c2[q] = fmaf(un, c4, c2);
+        o.c3[q] = c3;
+        o.c4[q] = c4;
+    }
+}
+
 // Separable steps.  Row-local: T_P^H (c2 += P c1, c4 += P c3) and S_U^H
 // (c1 += U c2, c3 += U c4), in place.
 template <int QL>
@@ -1300,6 +1381,9 @@ struct Fwd137 {
             dd_sp_tv(a[M3], a[M2], a[M1], a[PH], b[M2], CDD::PN, CDD::PF);
             dd_sp_sh(b[M2], CDD::UN, CDD::UF);
             dd_sp_sv(b[M5], b[(PH + 2) % 6], b[M3], b[M2], o, CDD::UN, CDD::UF);
+        } else if constexpr (SCHEME == SCHEME_REDUCED) {
+            dd_rd_predict(a[M3], a[M2], a[M1], a[PH], b[M2], CDD::PN, CDD::PF);
+            dd_rd_update(b[M5], b[(PH + 2) % 6], b[M3], b[M2], o, CDD::UN, CDD::UF);
         } else {
             dd_ns_predict(a[M3], a[M2], a[M1], a[PH], b[M2], CDD::PN, CDD::PF);
             dd_ns_update(b[M5], b[(PH + 2) % 6], b[M3], b[M2], o, CDD::UN, CDD::UF);

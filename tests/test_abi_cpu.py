@@ -58,7 +58,7 @@ def test_strerror_names_every_code(lib):
      abi.DWT2_ERR_UNSUPPORTED),
     ((abi.DWT2_CDF53_INT, 1, 0, abi.DWT2_I32, abi.DWT2_I32, abi.DWT2_NONSEP_CONV, [(0, 16, 16, 16)]),
      abi.DWT2_ERR_UNSUPPORTED),
-    ((abi.DWT2_DD137, 1, 0, 0, 0, abi.DWT2_NONSEP_REDUCED, [(0, 16, 16, 16)]), abi.DWT2_ERR_UNSUPPORTED),
+    ((abi.DWT2_DD137, 1, 0, 0, 0, abi.DWT2_POLYCONV, [(0, 16, 16, 16)]), abi.DWT2_ERR_UNSUPPORTED),
     ((abi.DWT2_DD137, 1, 0, 0, 0, abi.DWT2_CONV, [(0, 16, 16, 16)]), abi.DWT2_ERR_UNSUPPORTED),
     ((abi.DWT2_DD137, 1, 0, abi.DWT2_I32, abi.DWT2_I32, 0, [(0, 16, 16, 16)]), abi.DWT2_ERR_UNSUPPORTED),
     ((3, 1, 0, 0, 0, 0, [(0, 16, 16, 16)]), abi.DWT2_ERR_INVALID_ARG),                       # no such wavelet

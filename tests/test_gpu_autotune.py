@@ -40,8 +40,9 @@ def test_autotune_keeps_results(tmp_path, flags):
 
 @pytest.mark.parametrize("flags,bad", [(0, 1 << 12), (0, 63), (abi.DWT2_FLAG_PERSISTENT, 99)])
 def test_autotune_rejects_bad_choice(flags, bad):
-    # a two-level plan packs 6 bits per level (32 candidates): 2^12 or more, or a
-    # field of 32 or more, is not one of its choices
+    # a two-level plan packs 6 bits per level (32 candidates: 4 configurations x
+    # 8 segment heights): 2^12 or more, or a field of 32 or more, is not one of
+    # its choices
     plan = Plan.single(64, 64, 2, flags=flags)
     x = torch.zeros((64, 64), device="cuda")
     with pytest.raises(abi.Dwt2Error):
@@ -62,3 +63,4 @@ def test_autotune_choice_fields_per_level():
     assert abi.dwt2_autotune(plan.handle, x.data_ptr(), out.data_ptr(), plan.workspace.data_ptr(), 0, choice) == choice
     assert torch.equal(plan.forward(x), ref)
     assert plan.status() == 0
+

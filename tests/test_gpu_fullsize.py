@@ -76,11 +76,12 @@ def test_int53_full_size_bit_exact(scheme):
     plan.close()
 
 
-def test_dd137_full_size():
+@pytest.mark.parametrize("scheme", ["nonsep", "reduced"])
+def test_dd137_full_size(scheme):
     x = synth.gradient(N, N, seed=2)
     ref = oracle.forward137(x.astype(np.float64), LEVELS)
     xd = torch.from_numpy(x).cuda()
-    plan = Plan.single(N, N, LEVELS, wavelet="dd137", scheme="nonsep")
+    plan = Plan.single(N, N, LEVELS, wavelet="dd137", scheme=scheme)
     out = torch.empty_like(xd)
     plan.autotune(xd, out)
     out.fill_(float("nan"))
@@ -89,7 +90,7 @@ def test_dd137_full_size():
     assert plan.status() == 0
     got = out.cpu().numpy()
     assert np.isfinite(got).all()
-    assert_dd_close(got, ref, LEVELS, 255.0, "16384^2 dd137")
+    assert_dd_close(got, ref, LEVELS, 255.0, f"16384^2 dd137 {scheme}")
     back = plan.inverse(out)
     torch.cuda.synchronize()
     assert float((back - xd).abs().max()) <= 2e-3

@@ -81,7 +81,7 @@ def test_dropped_segment_signal_times_out(monkeypatch):
 
 
 @pytest.mark.parametrize("h,w,levels", [(2048, 2048, 5), (1031, 2052, 6), (300, 4100, 4), (66, 66, 3)])
-@pytest.mark.parametrize("scheme", ["nonsep", "sep"])
+@pytest.mark.parametrize("scheme", ["nonsep", "reduced", "sep"])
 def test_overlap_dd137(h, w, levels, scheme, monkeypatch):
     # three warm-up rows: a unit waits for one more row of the previous level
     x = synth.gradient(h, w, seed=h + w)

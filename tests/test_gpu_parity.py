@@ -200,7 +200,7 @@ def test_unpadded_pitch_every_configuration(n, levels, cfg, monkeypatch):
 
 # ------------------------------------------------------------------ DD 13/7
 # one lifting pair with 4-tap steps: strips with a 4-quad halo, 3 warm-up rows
-DD_SCHEMES = ["nonsep", "sep"]
+DD_SCHEMES = ["nonsep", "reduced", "sep"]
 
 
 @pytest.mark.parametrize("scheme", DD_SCHEMES)
@@ -244,12 +244,21 @@ def test_dd137_lowp_storage(h, w, dtype, rel):
     assert np.abs(got - ref_i).max() <= 2e-3 * np.abs(ref_i).max() / 255.0 * 2
 
 
-def test_dd137_has_no_adjoint_or_reduced_form():
+def test_dd137_has_no_adjoint_or_filter_bank_form():
     from paper_1704_08657_gb300 import abi
     with pytest.raises(abi.Dwt2Error) as e:
-        Plan.single(64, 64, 2, wavelet="dd137", scheme="reduced")
+        Plan.single(64, 64, 2, wavelet="dd137", scheme="conv")
     assert e.value.code == abi.DWT2_ERR_UNSUPPORTED
     p = Plan.single(64, 64, 2, wavelet="dd137")
     g = torch.zeros(64, 64, device="cuda")
     rc = abi.raw_call("dwt2_adjoint", p.handle, g.data_ptr(), torch.empty_like(g).data_ptr(), p.workspace.data_ptr(), 0)
     assert rc == abi.DWT2_ERR_UNSUPPORTED
+
+
+def test_dd137_schemes_agree():
+    # the reduced split (Table 1: 2 steps, 50 operations) computes the same
+    # transform as the plain non-separable and the separable lifting
+    x = synth.gradient(300, 260, seed=8)
+    outs = {s: gpu_forward(x, 4, s, wavelet="dd137") for s in DD_SCHEMES}
+    for s in ("reduced", "sep"):
+        assert_dd_close(outs[s], outs["nonsep"].astype(np.float64), 4, 2 * 255.0, f"dd137 {s} vs nonsep")

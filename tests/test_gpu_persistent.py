@@ -34,8 +34,8 @@ def _unpack(flat: np.ndarray, descs):
 @pytest.mark.parametrize("scheme", ["reduced", "nonsep", "sep"])
 @pytest.mark.parametrize("loader", ["tma", "cpasync"])
 def test_persistent_single_image(h, w, levels, scheme, loader, monkeypatch):
-    # single images load with TMA (tensor maps as kernel parameters); the
-    # cp.async loader of large batches is forced here to cover it as well
+    # the persistent launch loads with TMA (a device table of tensor maps);
+    # the cp.async loader is forced here to cover it as well
     monkeypatch.setenv("DWT2_PML_CPASYNC", "1" if loader == "cpasync" else "0")
     x = synth.gradient(h, w, seed=2)
     pitch = (w + 3) // 4 * 4
@@ -112,6 +112,39 @@ def test_persistent_under_cuda_graph():
     for _ in range(3):
         out.zero_()
         g.replay()
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    assert torch.equal(out, ref)
+    del ws
+
+
+def test_persistent_first_call_for_new_buffers_outside_capture():
+    """The first call for a set of buffers writes the plan's tensor-map table
+    (a synchronous copy): made during a stream capture it is refused before
+    anything is recorded; after one call outside the capture the same buffers
+    capture and replay."""
+    shapes = synth.batch_shapes(20, seed=12)
+    buf, descs = _batch(shapes)
+    xd = torch.from_numpy(buf).cuda()
+    plan = Plan(descs, 3, flags=abi.DWT2_FLAG_PERSISTENT)
+    ws = plan.workspace
+    out = torch.zeros_like(xd)
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with pytest.raises(abi.Dwt2Error) as e:
+        with torch.cuda.graph(g, stream=s):
+            plan.forward(xd, out, stream=s)
+    assert e.value.code == abi.DWT2_ERR_INVALID_ARG
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):
+        plan.forward(xd, out, stream=s)
+    torch.cuda.synchronize()
+    ref = out.clone()
+    g2 = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g2, stream=s):
+        plan.forward(xd, out, stream=s)
+    out.zero_()
+    g2.replay()
     torch.cuda.synchronize()
     assert plan.status() == 0
     assert torch.equal(out, ref)
