@@ -54,6 +54,8 @@ def parse_args():
                     help="with --profile: the single image (main), the 512-image batch (3 levels; --persistent "
                          "for the one-launch form) or the 16 x 4096^2 forward + L1 adjoint (4 levels)")
     ap.add_argument("--persistent", action="store_true", help="one persistent launch for the whole pyramid")
+    ap.add_argument("--grad-images", type=int, default=16,
+                    help="with --profile-workload grad16x4096: the number of 4096^2 images (a smaller case for ncu)")
     ap.add_argument("--tune-choice", type=int, default=-1,
                     help="apply this dwt2_autotune choice instead of timing the candidates (ncu captures)")
     return ap.parse_args()
@@ -322,7 +324,7 @@ def run_profile_workload(a):
         def step():
             plan.forward(x, c, stream)
     else:
-        side, nimg = 4096, 16
+        side, nimg = 4096, a.grad_images
         descs = [(i * side * side, side, side, side) for i in range(nimg)]
         x = torch.randint(0, 256, (nimg * side * side,), device=dev,
                           generator=torch.Generator(dev).manual_seed(6)).float()

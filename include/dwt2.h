@@ -142,7 +142,7 @@ typedef struct {
  *   n_images   number of images (>= 1); images is a host array of that many
  *              descriptors, copied into the plan.  With several images
  *              dwt2_forward runs each level as launches of up to 76 images
- *              (the inverse and adjoint up to 170), whose parameter blocks are
+ *              (the inverse and adjoint up to 160), whose parameter blocks are
  *              built at the first call for a set of buffers and reused.
  *   flags      0 or DWT2_FLAG_PERSISTENT: dwt2_forward then runs every level of every
  *              image in one persistent launch whose units take work from a device
@@ -171,8 +171,13 @@ int dwt2_plan(dwt2_plan_t* out, int wavelet, int levels, int boundary, int in_dt
               int coef_dtype, int scheme, int n_images, const dwt2_image_desc* images,
               unsigned flags);
 
-/* Bytes of device workspace the caller passes to every transform call of this
- * plan (intermediate low-low bands); 256-byte alignment is required. */
+/* Bytes of device workspace the caller passes to the transform calls of this
+ * plan; 256-byte alignment is required.  It holds the intermediate low-low
+ * bands of every level but the last (the forward and the inverse use only
+ * these: a one-level plan's forward and inverse may take NULL) and, for CDF
+ * 9/7, the adjoint's side buffers: per level 8 * (h + 8) + 8 * w floats for
+ * the outputs of the transposed lifting past the image edges, which the
+ * adjoint folds back onto their mirrors. */
 size_t dwt2_workspace_bytes(dwt2_plan_t plan);
 
 /*
@@ -182,7 +187,7 @@ size_t dwt2_workspace_bytes(dwt2_plan_t plan);
  *   coef       device pointer to the coefficients (coef_dtype), written; must
  *              not overlap in.
  *   workspace  device pointer to dwt2_workspace_bytes(plan) bytes (may be
- *              NULL when that is 0).
+ *              NULL for a one-level plan).
  *   stream     a cudaStream_t (NULL for the legacy default stream).
  */
 int dwt2_forward(dwt2_plan_t plan, const void* in, void* coef, void* workspace, void* stream);
@@ -193,9 +198,12 @@ int dwt2_forward(dwt2_plan_t plan, const void* in, void* coef, void* workspace, 
 int dwt2_inverse(dwt2_plan_t plan, const void* coef, void* out, void* workspace, void* stream);
 
 /* dwt2_adjoint -- in_grad = W^T(coef_grad), the transpose of the forward
- * operator (not in the paper): the transposed steps in reverse order, with the
- * transposed boundary weights.  CDF 9/7 only; both buffers FP32 and laid out
- * like the image / the coefficients. */
+ * operator (not in the paper).  With the symmetric boundary the forward is
+ * "extend, lift with no boundary cases, keep the inside", so its transpose is
+ * the transposed steps in reverse order on the coefficient gradient extended
+ * by zeros, followed by the fold that adds every output past an edge onto its
+ * whole-sample mirror.  CDF 9/7 only; both buffers FP32 and laid out like the
+ * image / the coefficients; the workspace is required (side buffers). */
 int dwt2_adjoint(dwt2_plan_t plan, const void* coef_grad, void* in_grad, void* workspace,
                  void* stream);
 

@@ -42,6 +42,7 @@ struct ImagePlan {
     dwt2_image_desc d;
     std::vector<LevelGeom> lv;   // lv[l] = input geometry of level l (0-based)
     std::vector<size_t> ws_off;  // ws_off[l] = byte offset of level l's LL band (l < levels-1)
+    std::vector<size_t> side_off;  // CDF 9/7: byte offset of level l's adjoint side buffer
 };
 
 // decomposition of one level into (strip, segment) units
@@ -147,9 +148,11 @@ struct dwt2_plan_s {
     unsigned flags;
     std::vector<ImagePlan> imgs;
     size_t ws_bytes;
+    size_t ws_levels;  // bytes the forward and the inverse use (the low-low bands)
     unsigned* d_status;
     int device, sm_count;
     int cfg_env, seg_env;           // DWT2_FWD_CFG, DWT2_SEG_ROWS
+    int edge_split_env;             // DWT2_EDGE_SPLIT: pieces per inverse / adjoint edge unit
     int cfg_bps[N_FWD_CFGS];        // resident blocks per SM of each forward configuration
     std::vector<int> lvl_cand;      // per level: tuning candidate, or -1 for cfg_env / seg_env
     int inv_bps;                    // resident blocks per SM of the inverse kernel
@@ -187,7 +190,7 @@ struct dwt2_plan_s {
         void* ws = nullptr;
         int adj = -1;
         std::vector<std::unique_ptr<InvGroupLaunch>> blocks;
-        std::vector<int> level, grid, grid_edge;  // per block; grids of the inner and the edge units
+        std::vector<int> level, grid, grid_edge;  // per block: the first launch's grid, the edge launch's
     } icache;
     PmlDesc* d_descs;
     PmlUnit* d_units;
@@ -332,7 +335,7 @@ int build_persistent(dwt2_plan_t p) {
 // The parameters of one image's inverse (or adjoint) level, without the
 // decomposition into units.
 InvParams inv_level_params(dwt2_plan_t p, const ImagePlan& ip, int l, const void* coef, void* out, void* workspace,
-                           size_t csz, bool l1, float l1_scale, const float* l1_scale_dev = nullptr) {
+                           size_t csz, bool adj, bool l1, float l1_scale, const float* l1_scale_dev = nullptr) {
     const char* coef_img = static_cast<const char*>(coef) + ip.d.offset_elems * csz;
     char* out_img = static_cast<char*>(out) + ip.d.offset_elems * 4;
     char* wsb = static_cast<char*>(workspace);
@@ -369,40 +372,73 @@ InvParams inv_level_params(dwt2_plan_t p, const ImagePlan& ip, int l, const void
     ipm.l1 = l1;
     ipm.l1_scale = l1_scale;
     ipm.l1_scale_dev = l1_scale_dev;
+    // the adjoint runs on the domain extended by two quads past every edge
+    ipm.ext = adj ? 2 : 0;
+    ipm.side = adj ? reinterpret_cast<float*>(wsb + ip.side_off[l]) : nullptr;
     return ipm;
 }
 
 // The inner units of one inverse / adjoint level, in_s0 .. in_g1 of q: the
 // units whose band rows all take paired staged copies (pair-aligned bands)
 // from inside the band columns (the strip's first pixel >= 0 and its quads
-// within the odd-column band) and, for the adjoint, whose weighted quads and
-// rows all carry weight 1 (quads in [1, wh - 2], rows R0 - 4 .. R1 + 1 in
-// [1, hh - 2]).  Each condition is monotone in the strip or the segment
-// index, so these units form a rectangle; the kernels run them with one
-// staged row loop (the unweighted one for the adjoint) and every other unit
-// in a second launch.
+// within the odd-column band) and, for the adjoint, whose output rows all lie
+// inside the image (none of its outputs is an extended position).  Each
+// condition is monotone in the strip or the segment index, so these units
+// form a rectangle; the kernels run them with one staged row loop and plain
+// stores, and every other unit in a second launch.
 void inv_inner_rect(InvParams& q, int wavelet, bool adj) {
     const int hq_ = wav_halo(wavelet), outq = 64 - 2 * hq_;
     const bool staged = q.vec_in_lo && q.vec_in_hi && q.vec_ll;
     int s0 = q.n_strips, s1 = 0, g0 = q.n_segs, g1 = 0;
     for (int st = 0; st < q.n_strips && staged; ++st) {
-        const int x0 = st * (2 * outq) - 2 * hq_;
-        bool in = (x0 >= 0) && (x0 / 2 + 64 <= q.wh);
-        if (adj) in = in && (x0 / 2 >= 1) && (x0 / 2 + 63 <= q.wh - 2);
+        const int x0 = st * (2 * outq) - 2 * hq_ - 2 * q.ext;
+        const bool in = (x0 >= 0) && (x0 / 2 + 64 <= q.wh);
         if (in) s0 = std::min(s0, st), s1 = st + 1;
     }
     for (int g = 0; g < q.n_segs; ++g) {
-        const int R0 = g * q.seg_rows, R1 = std::min(R0 + q.seg_rows, q.hq);
-        const bool in = !adj || ((R0 - 4 >= 1) && (R1 + 1 <= q.hh - 2));
+        const int R0 = g * q.seg_rows - q.ext, R1 = std::min(R0 + q.seg_rows, q.hq + q.ext);
+        // adjoint: no output row outside the image (R1 <= hh: every odd pixel row exists)
+        const bool in = !adj || ((R0 >= 0) && (R1 <= q.hh));
         if (in) g0 = std::min(g0, g), g1 = g + 1;
     }
-    if (s0 >= s1 || g0 >= g1) s0 = s1 = g0 = g1 = 0;
+    // the strip and the segment ranges are kept apart (an adjoint level uses
+    // the inner strips also when it has no inner segment)
+    if (s0 >= s1) s0 = s1 = 0;
+    if (g0 >= g1) g0 = g1 = 0;
     q.in_s0 = s0, q.in_s1 = s1, q.in_g0 = g0, q.in_g1 = g1;
 }
 
 // Plans of several images: every level, coarsest first, as launches of up to
-// INV_GROUP_MAX images in segments of INV_GROUP_SEG quad rows.
-constexpr int INV_GROUP_SEG = 32;
+// INV_GROUP_MAX images.  The segment height of a launch is the one of
+// INV_SEG_MIN .. INV_SEG_MAX quad rows that minimises rounds x (rows + the
+// pipeline's WARM + LAG = 4 rows), a round being one unit for every resident
+// warp: the whole level when it fits one round (the coarse levels, whose
+// time is one unit's row chain), 32-row segments on the large ones.
+constexpr int INV_SEG_MIN = 8, INV_SEG_MAX = 32;
+
+// Edge units run in two pieces of a 16-32-row segment when twice their number
+// still fits one round of resident warps: they are then a latency-bound row
+// chain, which a piece halves for four more warm-up rows; when they fill more
+// than a round the extra rows cost more than the shorter chains save
+// (measured on the 16 x 4096^2 adjoint: level 3 35 -> 25 us, level 2 37 ->
+// 45 us with pieces).
+int inv_edge_pieces(int seg, int64_t edge_units, int64_t max_warps, int env) {
+    if (env > 0) return env;
+    return seg >= 16 && 2 * edge_units <= max_warps ? 2 : 1;
+}
+
+int inv_group_seg(const std::vector<InvParams>& ps, int64_t max_warps, int seg_env) {
+    if (seg_env > 0) return seg_env;
+    int best = INV_SEG_MAX;
+    int64_t best_cost = INT64_MAX;
+    for (int seg = INV_SEG_MAX; seg >= INV_SEG_MIN; --seg) {
+        int64_t units = 0;
+        for (const InvParams& q : ps) units += int64_t(q.n_strips) * ((q.hq + 2 * q.ext + seg - 1) / seg);
+        const int64_t cost = (units + max_warps - 1) / max_warps * (seg + 4);
+        if (cost < best_cost) best_cost = cost, best = seg;
+    }
+    return best;
+}
 
 int inv_group_build(dwt2_plan_t p, const void* coef, void* out, void* workspace, bool adj) {
     auto& ic = p->icache;
@@ -417,28 +453,47 @@ int inv_group_build(dwt2_plan_t p, const void* coef, void* out, void* workspace,
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
         return int64_t(p->imgs[a].d.h) * p->imgs[a].d.w > int64_t(p->imgs[b].d.h) * p->imgs[b].d.w;
     });
+    const int inv_bps = adj ? inverse_blocks_per_sm(p->wavelet, inv_scheme(p->scheme), p->coef_dtype, true) : p->inv_bps;
+    const int64_t max_warps = int64_t(p->sm_count) * std::max(inv_bps, 1) * INV_NW;
     for (int l = p->levels - 1; l >= 0; --l) {
         for (int i0 = 0; i0 < n; i0 += INV_GROUP_MAX) {
             std::unique_ptr<InvGroupLaunch> g(new (std::nothrow) InvGroupLaunch());
             if (!g) return DWT2_ERR_INVALID_ARG;
-            int units[3] = {0, 0, 0};
+            std::vector<InvParams> ps;
             for (int k = 0; k < INV_GROUP_MAX && i0 + k < n; ++k) {
                 const ImagePlan& ip = p->imgs[order[i0 + k]];
-                InvParams ipm = inv_level_params(p, ip, l, coef, out, workspace, csz, false, 0.f);
-                ipm.n_strips = (ipm.wq + inv_out_quads(p->wavelet) - 1) / inv_out_quads(p->wavelet);
-                ipm.seg_rows = std::min(p->seg_env > 0 ? p->seg_env : INV_GROUP_SEG, ipm.hq);
-                ipm.n_segs = (ipm.hq + ipm.seg_rows - 1) / ipm.seg_rows;
+                InvParams ipm = inv_level_params(p, ip, l, coef, out, workspace, csz, adj, false, 0.f);
+                // units over the quads and quad rows [-ext, n + ext)
+                const int qw = ipm.wq + 2 * ipm.ext;
+                ipm.n_strips = (qw + inv_out_quads(p->wavelet) - 1) / inv_out_quads(p->wavelet);
+                ps.push_back(ipm);
+            }
+            const int seg = inv_group_seg(ps, max_warps, p->seg_env);
+            int units[3] = {0, 0, 0};
+            for (size_t k = 0; k < ps.size(); ++k) {
+                InvParams& ipm = ps[k];
+                const int qh = ipm.hq + 2 * ipm.ext;
+                ipm.seg_rows = std::min(seg, qh);
+                ipm.n_segs = (qh + ipm.seg_rows - 1) / ipm.seg_rows;
                 ipm.n_units = ipm.n_segs * ipm.n_strips;
+                ipm.edge_split = 1;
                 inv_inner_rect(ipm, p->wavelet, adj);
+            }
+            int64_t edge_units = 0;
+            for (const InvParams& q : ps) edge_units += inv_class_units(q, UNITS_EDGE);
+            const int split = inv_edge_pieces(seg, edge_units, max_warps, p->edge_split_env);
+            for (size_t k = 0; k < ps.size(); ++k) {
+                InvParams& ipm = ps[k];
+                ipm.edge_split = split;
                 g->img[k].p = ipm;
                 for (int c = 0; c < 3; ++c) {
                     g->img[k].u_begin[c] = units[c];
                     units[c] += inv_class_units(ipm, c);
                 }
-                g->n_img = k + 1;
+                g->n_img = int(k) + 1;
             }
             for (int c = 0; c < 3; ++c) g->n_units[c] = units[c];
-            g->wait_prev = (i0 == 0);
+            g->first = (i0 == 0);
             ic.grid.push_back((units[UNITS_INNER] + INV_NW - 1) / INV_NW);
             ic.grid_edge.push_back((units[UNITS_EDGE] + INV_NW - 1) / INV_NW);
             ic.level.push_back(l);
@@ -468,12 +523,11 @@ int inverse_grouped(dwt2_plan_t p, const void* coef, void* out, void* workspace,
         }
         const int l = ic.level[b];
         if (b == 0 || ic.level[b - 1] != l) prof_mark(p, l, true, s);
-        // the first launch of a level waits for every earlier launch (plain
-        // stream order); the others (the edge units, the next groups) overlap
-        // the launch before them
-        bool first = g.wait_prev != 0;
+        // the inner units, then the edge units; the level's first launch is a
+        // plain launch, the others programmatic dependents (inv_group_kernel)
+        bool first = g.first != 0;
         for (int cls : {UNITS_INNER, UNITS_EDGE}) {
-            const int grid = cls == UNITS_INNER ? ic.grid[b] : ic.grid_edge[b];
+            const int grid = cls == UNITS_EDGE ? ic.grid_edge[b] : ic.grid[b];
             if (grid == 0) continue;
             const int pdl = first ? 0 : 1;
             first = false;
@@ -491,7 +545,13 @@ int inverse_grouped(dwt2_plan_t p, const void* coef, void* out, void* workspace,
             }
             if (e != cudaSuccess) return DWT2_ERR_CUDA;
         }
-        if (b + 1 == ic.blocks.size() || ic.level[b + 1] != l) prof_mark(p, l, false, s);
+        const bool level_done = b + 1 == ic.blocks.size() || ic.level[b + 1] != l;
+        if (adj && level_done) {
+            // the fold of every image of the level, once all its units are stored
+            for (size_t f = b + 1; f-- > 0 && ic.level[f] == l;)
+                if (launch_adj_fold_group(*ic.blocks[f], f == b ? 0 : 1, s) != cudaSuccess) return DWT2_ERR_CUDA;
+        }
+        if (level_done) prof_mark(p, l, false, s);
     }
     if (p->prof_on) ++p->prof_calls;
     return DWT2_OK;
@@ -895,6 +955,16 @@ int dwt2_plan(dwt2_plan_t* out, int wavelet, int levels, int boundary, int in_dt
             ws += align256(size_t(g.hq) * size_t(round4(g.wq)) * 4);
         }
     }
+    // the adjoint's side buffers (the outputs past the image edges of every
+    // level, folded back after the level), after every low-low band
+    size_t ws_levels = ws;
+    if (wavelet == DWT2_CDF97) {
+        for (ImagePlan& ip : imgs)
+            for (int l = 0; l < levels; ++l) {
+                ip.side_off.push_back(ws);
+                ws += align256(size_t(adj_side_floats(ip.lv[l].h, ip.lv[l].w)) * 4);
+            }
+    }
     dwt2_plan_s* p = new (std::nothrow) dwt2_plan_s();
     if (!p) return DWT2_ERR_INVALID_ARG;
     p->wavelet = wavelet;
@@ -906,11 +976,13 @@ int dwt2_plan(dwt2_plan_t* out, int wavelet, int levels, int boundary, int in_dt
     p->flags = flags;
     p->imgs.swap(imgs);
     p->ws_bytes = ws;
+    p->ws_levels = ws_levels;
     p->d_status = nullptr;
     p->prof_on = false;
     p->prof_calls = 0;
     p->timeout_ns = uint64_t(env_int("DWT2_TIMEOUT_MS", 2000)) * 1000000ull;
     p->seg_env = env_int("DWT2_SEG_ROWS", 0);
+    p->edge_split_env = env_int("DWT2_EDGE_SPLIT", 0);
     p->pdl = env_int("DWT2_PDL", 1) != 0;
     p->overlap = env_int("DWT2_LEVEL_OVERLAP", 1) != 0;
     p->d_lvl_ctr = nullptr;
@@ -1035,7 +1107,7 @@ int dwt2_status(dwt2_plan_t p, void* stream) {
 
 int dwt2_forward(dwt2_plan_t p, const void* in, void* coef, void* workspace, void* stream) {
     if (!p || !in || !coef) return DWT2_ERR_INVALID_ARG;
-    if (p->ws_bytes && !workspace) return DWT2_ERR_INVALID_ARG;
+    if (p->ws_levels && !workspace) return DWT2_ERR_INVALID_ARG;
     if (!aligned(in, 16) || (workspace && !aligned(workspace, 256))) return DWT2_ERR_MISALIGNED;
     const size_t csz = dtype_size(p->coef_dtype);
     if (!aligned(coef, csz)) return DWT2_ERR_MISALIGNED;
@@ -1069,7 +1141,7 @@ int dwt2_forward(dwt2_plan_t p, const void* in, void* coef, void* workspace, voi
 static int run_inverse_like(dwt2_plan_t p, const void* coef, void* out, void* workspace, void* stream, bool adj,
                             bool l1 = false, float l1_scale = 0.f, const float* l1_scale_dev = nullptr) {
     if (!p || !coef || !out) return DWT2_ERR_INVALID_ARG;
-    if (p->ws_bytes && !workspace) return DWT2_ERR_INVALID_ARG;
+    if ((adj ? p->ws_bytes : p->ws_levels) && !workspace) return DWT2_ERR_INVALID_ARG;
     if (workspace && !aligned(workspace, 256)) return DWT2_ERR_MISALIGNED;
     if (adj && p->wavelet != DWT2_CDF97) return DWT2_ERR_UNSUPPORTED;
     if (l1 && p->coef_dtype != DWT2_F32) return DWT2_ERR_UNSUPPORTED;
@@ -1082,15 +1154,21 @@ static int run_inverse_like(dwt2_plan_t p, const void* coef, void* out, void* wo
     for (int l = p->levels - 1; l >= 0; --l) {
         prof_mark(p, l, true, s);
         for (const ImagePlan& ip : p->imgs) {
-            InvParams ipm = inv_level_params(p, ip, l, coef, out, workspace, csz, l1, l1_scale, l1_scale_dev);
+            InvParams ipm = inv_level_params(p, ip, l, coef, out, workspace, csz, adj, l1, l1_scale, l1_scale_dev);
             int grid = 0, balanced = 0;
-            const Decomp dc = decompose(ip.lv[l], inv_out_quads(p->wavelet), p->sm_count, inv_bps, INV_NW, p->seg_env,
+            LevelGeom ext_geom = ip.lv[l];  // units over the quads and quad rows [-ext, n + ext)
+            ext_geom.wq += 2 * ipm.ext;
+            ext_geom.hq += 2 * ipm.ext;
+            const Decomp dc = decompose(ext_geom, inv_out_quads(p->wavelet), p->sm_count, inv_bps, INV_NW, p->seg_env,
                                         0, &grid, &balanced);
             ipm.n_strips = dc.n_strips, ipm.seg_rows = dc.seg_rows, ipm.n_segs = dc.n_segs, ipm.n_units = dc.n_units;
             ipm.balanced = 0;
+            ipm.edge_split = 1;
             inv_inner_rect(ipm, p->wavelet, adj);
+            ipm.edge_split = inv_edge_pieces(ipm.seg_rows, inv_class_units(ipm, UNITS_EDGE),
+                                             int64_t(p->sm_count) * std::max(inv_bps, 1) * INV_NW, p->edge_split_env);
             // the inner units, then (a programmatic dependent: no shared data)
-            // the others
+            // the edge units
             bool first = true;
             for (int cls : {UNITS_INNER, UNITS_EDGE}) {
                 const int units = inv_class_units(ipm, cls);
@@ -1111,6 +1189,8 @@ static int run_inverse_like(dwt2_plan_t p, const void* coef, void* out, void* wo
                 }
                 if (e != cudaSuccess) return DWT2_ERR_CUDA;
             }
+            // the adjoint: fold the outputs past the edges onto their mirrors
+            if (adj && launch_adj_fold(ipm, s) != cudaSuccess) return DWT2_ERR_CUDA;
         }
         prof_mark(p, l, false, s);
     }

@@ -66,10 +66,24 @@ struct InvParams {
     float l1_scale;
     const float* l1_scale_dev;
     // the inner units: strips [in_s0, in_s1) x segments [in_g0, in_g1), those
-    // that run one unweighted staged row loop (inv_inner_rect); a level runs
-    // them in one kernel and every other unit in a second one
+    // that run one staged row loop with plain stores (inv_inner_rect); a level
+    // runs them in one kernel and every other unit in a second one
     int in_s0, in_s1, in_g0, in_g1;
+    // adjoint: the units cover the quads and quad rows [-ext, n + ext) of the
+    // extended domain (ext = 2; 0 for the inverse); outputs outside the image
+    // go to `side` (adj_side_floats floats) for adj_fold_kernel
+    int ext;
+    // edge units (UNITS_EDGE) run in edge_split pieces of ceil(seg_rows /
+    // edge_split) quad rows each: more, shorter row chains for the units that
+    // run beside the inner ones
+    int edge_split;
+    float* side;
 };
+
+// The side buffer of one adjoint level of an h x w input: the four extended
+// columns on each side of every row -4 .. h+3 (8 per row, corners included),
+// then the four extended rows above and below, w columns each.
+__host__ __device__ inline int64_t adj_side_floats(int h, int w) { return int64_t(8) * (h + 8) + int64_t(8) * w; }
 
 // Persistent forward: one descriptor per (image, level), one entry per unit
 // of work in queue order, counters of completed strips per (image, level,
@@ -110,7 +124,7 @@ struct PmlParams {
 // Grouped inverse / adjoint (plans of several images): one launch runs one
 // level of up to INV_GROUP_MAX images, their parameters in one
 // __grid_constant__ kernel parameter, as for the grouped forward.
-constexpr int INV_GROUP_MAX = 170;
+constexpr int INV_GROUP_MAX = 160;
 struct InvGroupImg {
     InvParams p;
     int u_begin[3];  // first unit of the image among the launch's units, per unit class
@@ -119,26 +133,44 @@ struct InvGroupLaunch {
     InvGroupImg img[INV_GROUP_MAX];
     int n_img;
     int n_units[3];  // per unit class
-    int wait_prev;   // 1: the first launch of a level
+    int first;       // 1: the level's first group (its first launch is a plain launch)
 };
 static_assert(sizeof(InvGroupLaunch) <= 32764, "a grouped launch block fits the kernel parameter space");
 
-// Unit classes of an inverse or adjoint launch: every unit, the inner units
-// only, or every unit but the inner ones.
+// Unit classes of an inverse or adjoint level.  The inner units
+// (inv_inner_rect) run one staged row loop with plain stores; the edge units
+// (every other unit, each in inv_edge_split pieces of its segment) copy from
+// mirrored (inverse) or zero-filled (adjoint) positions and the adjoint's route
+// their stores.  A level runs the inner units in one launch and the edge units
+// in a second, separately compiled one.  Measured on the 16 x 4096^2 adjoint:
+// both row loops in one kernel (its warps running either) 1.6x slower at level
+// 1, the edge loop for every unit 1.46x slower (128 registers against 96, and
+// its per-lane predicates).  UNITS_ALL is every unit in segment-major order.
 enum { UNITS_ALL = 0, UNITS_INNER = 1, UNITS_EDGE = 2 };
-// number of units of class cls, and the (strip, segment) of its lu-th unit
+__host__ __device__ inline int inv_edge_split(const InvParams& p) { return p.edge_split > 1 ? p.edge_split : 1; }
+// number of units of class cls (edge units counted in pieces)
 __host__ __device__ inline int inv_class_units(const InvParams& p, int cls) {
     const int inner = (p.in_s1 - p.in_s0) * (p.in_g1 - p.in_g0);
-    return cls == UNITS_ALL ? p.n_units : (cls == UNITS_INNER ? inner : p.n_units - inner);
+    return cls == UNITS_ALL ? p.n_units : (cls == UNITS_INNER ? inner : (p.n_units - inner) * inv_edge_split(p));
 }
-__host__ __device__ inline void inv_class_unit(const InvParams& p, int cls, int lu, int& s, int& g) {
+// Strip s, segment g and (edge units) piece k of the lu-th unit of class cls;
+// UNITS_ALL and UNITS_INNER in segment-major order.
+__host__ __device__ inline void inv_class_unit(const InvParams& p, int cls, int lu, int& s, int& g, int& k) {
+    k = 0;
+    if (cls == UNITS_ALL) {
+        s = lu % p.n_strips;
+        g = lu / p.n_strips;
+        return;
+    }
     if (cls == UNITS_INNER) {
         const int ns = p.in_s1 - p.in_s0;
         s = p.in_s0 + lu % ns;
         g = p.in_g0 + lu / ns;
         return;
     }
-    if (cls == UNITS_EDGE && p.in_s1 > p.in_s0 && p.in_g1 > p.in_g0) {
+    k = lu % inv_edge_split(p);
+    lu /= inv_edge_split(p);
+    if (p.in_s1 > p.in_s0 && p.in_g1 > p.in_g0) {
         // segments above the inner ones (whole rows of strips), then for each
         // inner segment its strips left and right of the inner ones, then the
         // segments below
@@ -153,8 +185,8 @@ __host__ __device__ inline void inv_class_unit(const InvParams& p, int cls, int 
         const int mid = (p.in_g1 - p.in_g0) * side;
         if (lu < mid) {
             g = p.in_g0 + lu / side;
-            const int k = lu % side;
-            s = k < p.in_s0 ? k : p.in_s1 + (k - p.in_s0);
+            const int j = lu % side;
+            s = j < p.in_s0 ? j : p.in_s1 + (j - p.in_s0);
             return;
         }
         lu -= mid;
@@ -171,6 +203,9 @@ int launch_inv_group_f16(int wav, int scheme, const InvGroupLaunch& g, int grid,
 int launch_inv_group_bf16(int wav, int scheme, const InvGroupLaunch& g, int grid, int pdl, int cls, cudaStream_t s);
 int launch_inv_group_i32(int wav, int scheme, const InvGroupLaunch& g, int grid, int pdl, int cls, cudaStream_t s);
 int launch_adj_group_f32(const InvGroupLaunch& g, int grid, int pdl, int cls, cudaStream_t s);
+// the fold E^T of the adjoint levels in a grouped launch block / of one level
+int launch_adj_fold_group(const InvGroupLaunch& g, int pdl, cudaStream_t s);
+int launch_adj_fold(const InvParams& p, cudaStream_t s);
 
 // Two forward levels in one launch (fused.cuh): level l comes through the
 // tensor maps, level l+1 reads the level-l low-low band from a ring of rows in

@@ -1,4 +1,6 @@
 // k_f32.cu -- kernels whose coefficients are stored as float.
+#include <algorithm>
+
 #include "launch.cuh"
 
 namespace dwt2 {
@@ -62,6 +64,60 @@ int forward_blocks_per_sm(int wav, int scheme, int coef_dtype, const FwdCfg& cfg
 
 int launch_adj_group_f32(const InvGroupLaunch& g, int grid, int pdl, int cls, cudaStream_t s) {
     return launch_inv_group_one<Adj97<INV_QL>, float, true>(g, grid, pdl, cls, s);
+}
+
+// the fold kernels of the adjoint (this translation unit alone defines them);
+// a level's first fold is a plain launch after its units, the folds of its
+// later groups (other images) programmatic dependents of the one before
+__global__ void __launch_bounds__(256) adj_fold_kernel(const InvParams p) {
+    const int n = adj_fold_count(p.h, p.w);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int r, c;
+        adj_fold_index(p.h, p.w, i, r, c);
+        adj_fold_pixel(p, r, c);
+    }
+}
+
+__global__ void __launch_bounds__(256) adj_fold_group_kernel(const __grid_constant__ InvGroupLaunch L) {
+    griddep_launch_dependents();
+    for (int k = blockIdx.y; k < L.n_img; k += gridDim.y) {
+        const InvParams& p = L.img[k].p;
+        const int n = adj_fold_count(p.h, p.w);
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+            int r, c;
+            adj_fold_index(p.h, p.w, i, r, c);
+            adj_fold_pixel(p, r, c);
+        }
+    }
+}
+
+namespace {
+cudaLaunchConfig_t fold_config(dim3 grid, int pdl, cudaStream_t s, cudaLaunchAttribute* attr) {
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = grid;
+    lc.blockDim = dim3(256);
+    lc.stream = s;
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    lc.attrs = attr;
+    lc.numAttrs = pdl ? 1 : 0;
+    return lc;
+}
+}  // namespace
+
+int launch_adj_fold(const InvParams& p, cudaStream_t s) {
+    const int n = adj_fold_count(p.h, p.w);
+    cudaLaunchAttribute attr[1];
+    const cudaLaunchConfig_t lc = fold_config(dim3((n + 255) / 256), 0, s, attr);
+    return cudaLaunchKernelEx(&lc, adj_fold_kernel, p);
+}
+
+int launch_adj_fold_group(const InvGroupLaunch& g, int pdl, cudaStream_t s) {
+    int n = 0;
+    for (int k = 0; k < g.n_img; ++k) n = std::max(n, adj_fold_count(g.img[k].p.h, g.img[k].p.w));
+    cudaLaunchAttribute attr[1];
+    const cudaLaunchConfig_t lc = fold_config(dim3((n + 255) / 256, g.n_img), pdl, s, attr);
+    return cudaLaunchKernelEx(&lc, adj_fold_group_kernel, g);
 }
 
 int occupancy_pml_f16(int wav, int scheme);

@@ -17,11 +17,12 @@
 // lifting needs no boundary cases: every step preserves the symmetry, so the
 // exact per-step mirrored result appears inside the image.
 //
-// Inverse and adjoint: the four bands are read with vector loads, two quad
-// rows ahead of the pipeline.  The inverse reads mirrored band positions at the
-// edges (the extension of the coefficients that the symmetric image extension
-// produces); the adjoint reads zeros there and applies the transposed boundary
-// weights of Adj97 instead.
+// Inverse and adjoint: the four bands are read into a ring of shared-memory
+// stages, two quad rows ahead of the pipeline.  The inverse reads mirrored band
+// positions at the edges (the extension of the coefficients that the symmetric
+// image extension produces); the adjoint reads zeros there, runs on the
+// extended domain two quads past every edge and folds the extended outputs
+// back onto their mirrors (Adj97, adj_fold_kernel).
 #pragma once
 
 #include <type_traits>
@@ -764,10 +765,12 @@ __device__ __forceinline__ void l1_transform(const InvParams& p, Row<CT, QL>& r)
 }
 
 // --------------------------------------------------------- inverse / adjoint
-// One unit (strip s, quad rows [R0, R1)) of one inverse or adjoint level.
-// Pipe: Inv97<S, QL>, Inv53<S, QL> or Adj97<QL>.  BT: coefficient element type.
+// One unit (strip s, quad rows [R0, R1)) of one inverse level with direct
+// band loads (any alignment).  Pipe: Inv97<S, QL>, Inv53<S, QL>, Inv137<S, QL>.
+// BT: coefficient element type.
 template <class Pipe, class BT, bool ADJ, int QL>
 __device__ __forceinline__ void inv_unit(const InvParams& p, int s, int R0, int R1, int lane) {
+    static_assert(!ADJ, "the adjoint runs the staged units with the extended domain");
     using CT = typename Pipe::CT;
     using R = Row<CT, QL>;
     constexpr bool MIRROR = !ADJ;
@@ -789,11 +792,6 @@ __device__ __forceinline__ void inv_unit(const InvParams& p, int s, int R0, int 
 
     Pipe pipe;
     pipe.init();
-    if constexpr (ADJ) {
-#pragma unroll
-        for (int q = 0; q < QL; ++q) pipe.hw[q] = axis_weights(jb + q, p.w);
-        pipe.h = p.h;
-    }
     auto fast_row = [&](int vi) { return fast_cols && vi >= 0 && 2 * vi + 1 < p.h; };
 
     R pf[2];  // rows vi+1 and vi+2 in flight
@@ -855,6 +853,11 @@ __device__ __forceinline__ void cp_async_small(void* dst, const void* src, bool 
                  : "memory");
 }
 
+// 8 bytes to shared memory, the first n (0, 4 or 8) from global, the rest zero
+__device__ __forceinline__ void cp_async_n8(void* dst, const void* src, int n) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(n) : "memory");
+}
+
 template <class T, class CT>
 __device__ __forceinline__ void ld_pair_smem(const unsigned char* p, CT& a, CT& b) {
     if constexpr (std::is_same<T, float>::value) {
@@ -879,13 +882,100 @@ constexpr size_t inv_smem_bytes() {
     return size_t(NW) * NST * QR * 4 * 256 + size_t(NW) * NST * 8;
 }
 
+// Where an adjoint output pixel (r, c) goes: the image, the side buffer (the
+// four extended columns or rows past an edge), or nowhere (beyond them).
+__device__ __forceinline__ void adj_route_store(const InvParams& p, float* img_row, int r, int c, float v) {
+    if (c < -4 || c >= p.w + 4 || r < -4 || r >= p.h + 4) return;
+    const bool rin = (r >= 0) && (r < p.h), cin = (c >= 0) && (c < p.w);
+    if (rin && cin) {
+        img_row[c] = v;
+    } else if (!cin) {  // extended column (corners too)
+        p.side[(r + 4) * 8 + (c < 0 ? c + 4 : 4 + c - p.w)] = v;
+    } else {  // extended row inside the columns
+        p.side[int64_t(8) * (p.h + 8) + int64_t(r < 0 ? r + 4 : 4 + r - p.h) * p.w + c] = v;
+    }
+}
+
+// Stores of the adjoint units: plain (every output inside the image), routed
+// by lane (ROUTE_EDGE: a lane's four output columns lie inside the image, in
+// the four extended columns on one side, or beyond them, fixed for the unit;
+// each pixel row of four goes as one vector store to the image, the side
+// buffer's extended rows or its extended columns), or pixel by pixel
+// (ROUTE_PIXELS, adj_route_store: lanes whose four columns straddle an edge).
+enum { ROUTE_NONE = 0, ROUTE_EDGE = 1, ROUTE_PIXELS = 2 };
+// column class of a lane's four output columns px .. px+3
+enum { CC_IN = 0, CC_SIDE_L = 1, CC_SIDE_R = 2, CC_DROP = 3, CC_MIXED = 4 };
+
+__device__ __forceinline__ int adj_col_class(const InvParams& p, int px) {
+    if (px >= 0 && px + 3 < p.w) return CC_IN;
+    if (px == -4) return CC_SIDE_L;
+    if (px == p.w) return CC_SIDE_R;
+    if (px + 3 < -4 || px >= p.w + 4) return CC_DROP;
+    return CC_MIXED;
+}
+
+// one pixel row of four values of a lane of class cc (not CC_DROP); svec:
+// the side buffer is 16-byte aligned
+__device__ __forceinline__ void adj_edge_store(const InvParams& p, float* img_row, int r, int px, int cc, bool svec,
+                                               const float (&v)[4]) {
+    const bool rin = (r >= 0) && (r < p.h);
+    const bool rext = !rin && (r >= -4) && (r < p.h + 4);
+    if (!rin && !rext) return;
+    float* dst;
+    bool vec;
+    if (cc == CC_IN) {
+        if (rin) {
+            dst = img_row + px;
+            vec = p.vec_out;
+        } else {
+            dst = p.side + int64_t(8) * (p.h + 8) + int64_t(r < 0 ? r + 4 : 4 + r - p.h) * p.w + px;
+            vec = svec && (p.w & 3) == 0;
+        }
+    } else if (cc != CC_MIXED) {  // the four extended columns of one side (corners too)
+        dst = p.side + (r + 4) * 8 + (cc == CC_SIDE_L ? 0 : 4);
+        vec = svec;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) adj_route_store(p, img_row, r, px + k, v[k]);
+        return;
+    }
+    if (vec) {
+        st4<float>(dst, v[0], v[1], v[2], v[3]);
+    } else {
+        dst[0] = v[0], dst[1] = v[1], dst[2] = v[2], dst[3] = v[3];
+    }
+}
+
+// The two pixel rows of one quad row of a ROUTE_EDGE lane, out of line: the
+// row loop keeps only its common case (both rows and every lane's columns
+// inside the image) and branches here around it.
+static __device__ __noinline__ void adj_edge_store_rows(const InvParams& p, float* row_e, int r, int px, int cc, bool svec,
+                                                 float e0, float e1, float e2, float e3, float o0, float o1, float o2,
+                                                 float o3) {
+    if (cc == CC_DROP) return;
+    const float ev[4] = {e0, e1, e2, e3}, od[4] = {o0, o1, o2, o3};
+    adj_edge_store(p, row_e, r, px, cc, svec, ev);
+    adj_edge_store(p, row_e + p.out_pitch, r + 1, px, cc, svec, od);
+}
+
+// one pixel row of four values of a ROUTE_PIXELS lane whose columns all lie
+// inside the image
+__device__ __forceinline__ void adj_row_store(const InvParams& p, float* img_row, int r, int px, const float (&v)[4]) {
+    adj_edge_store(p, img_row, r, px, CC_IN, (reinterpret_cast<uintptr_t>(p.side) & 15) == 0, v);
+}
+
 // One unit of a strip: the bands stream through a ring of NST stages of QR
 // quad rows filled by cp.async (mirrored rows for the inverse, zero rows for
 // the adjoint at the top and bottom).  Interior strips copy each lane's quad
 // pair at once; EDGE strips (the first and last of a row, 4-byte types) copy
 // element by element from the mirrored (inverse) or zero-filled (adjoint)
-// columns.  Returns false when a stage wait timed out.
-template <class Pipe, class BT, bool ADJ, int QR, int NST, bool EDGE>
+// columns.  The adjoint's units lie on the extended domain (p.ext quads and
+// quad rows past every edge; strip s starts 2 * p.ext pixels further left);
+// its ROUTE_EDGE units copy quad pairs too, zero-filled where a pair lies
+// past a band's last column (a pair of an odd-width band that straddles it
+// copies its first element alone), and route their stores.  Returns false
+// when a stage wait timed out.
+template <class Pipe, class BT, bool ADJ, int QR, int NST, bool EDGE, int ROUTE = ROUTE_NONE>
 __device__ __forceinline__ bool inv_unit_staged(const InvParams& p, int s, int R0, int R1, int lane,
                                                 unsigned char* ring, uint64_t* bars, uint32_t& gstage) {
     using CT = typename Pipe::CT;
@@ -896,11 +986,13 @@ __device__ __forceinline__ bool inv_unit_staged(const InvParams& p, int s, int R
     constexpr int PB = 2 * int(sizeof(BT));  // bytes of a coefficient pair
     static_assert(PHASES % QR == 0, "a group of arrivals must cover whole stages");
     static_assert(HQ % 2 == 0, "a lane's two quads are both output or both halo");
+    static_assert(ROUTE == ROUTE_NONE || ADJ, "routed stores belong to the adjoint");
+    static_assert(ROUTE != ROUTE_EDGE || (!EDGE && PB == 8), "routed edge units copy FP32 pairs");
     const int A0 = R0 - WARM;
     const int n_arr = (R1 - R0) + WARM + Pipe::LAG;
     const int n_grp = (n_arr + PHASES - 1) / PHASES;
     const int NT = (n_arr + QR - 1) / QR;
-    const int x0 = s * (2 * OUTQ) - 2 * HQ;
+    const int x0 = s * (2 * OUTQ) - 2 * HQ - (ADJ ? 2 * p.ext : 0);
     const int jb = x0 / 2 + QL * lane;
     const bool mine = (lane >= HQ / 2) && (lane < 32 - HQ / 2);
     const BT* coef = reinterpret_cast<const BT*>(p.coef);
@@ -925,7 +1017,21 @@ __device__ __forceinline__ bool inv_unit_staged(const InvParams& p, int s, int R
         ce[q] = min(max(ce[q], 0), p.wq - 1);
         co[q] = min(max(co[q], 0), max(p.wh - 1, 0));
     }
-
+    // ROUTE_EDGE: bytes of the lane's pair copied from the even-column (LL,
+    // LH) and odd-column (HL, HH) bands: 8 (both inside), 4 (the first only:
+    // the last column of an odd-width band) or 0, the rest zero-filled
+    int nbe = 8, nbo = 8, je = jb, jo = jb, cc = CC_IN;
+    bool svec = false;
+    if constexpr (ROUTE == ROUTE_EDGE) {
+        nbe = jb < 0 ? 0 : (jb + 1 < p.wq ? 8 : (jb < p.wq ? 4 : 0));
+        nbo = jb < 0 ? 0 : (jb + 1 < p.wh ? 8 : (jb < p.wh ? 4 : 0));
+        je = nbe ? jb : 0;
+        jo = nbo ? jb : 0;
+        cc = mine ? adj_col_class(p, 2 * jb) : CC_DROP;
+        svec = (reinterpret_cast<uintptr_t>(p.side) & 15) == 0;
+    }
+    // every output lane's four columns inside the image (warp-uniform)
+    const bool cols_in = ROUTE == ROUTE_EDGE && __all_sync(0xffffffffu, cc == CC_IN || cc == CC_DROP);
     auto issue = [&](int t, int slot) {
         unsigned char* st = ring + slot * STAGEB;
 #pragma unroll
@@ -958,6 +1064,16 @@ __device__ __forceinline__ bool inv_unit_staged(const InvParams& p, int s, int R
                     cp_async_small<4>(d + 2 * BAND + lane * 8 + q * 4, lhr + ce[q], rov && cev[q]);
                     cp_async_small<4>(d + 3 * BAND + lane * 8 + q * 4, hhr + co[q], rov && cov[q]);
                 }
+            } else if constexpr (ROUTE == ROUTE_EDGE) {
+                const void* llr = p.ll_is_ct ? static_cast<const void*>(reinterpret_cast<const CT*>(p.ll) +
+                                                                         int64_t(re) * p.ll_pitch + je)
+                                             : static_cast<const void*>(reinterpret_cast<const BT*>(p.ll) +
+                                                                         int64_t(re) * p.ll_pitch + je);
+                cp_async_n8(d + lane * 8, llr, rev ? nbe : 0);
+                cp_async_n8(d + BAND + lane * 8, coef + int64_t(re) * p.coef_pitch + p.wq + jo, rev ? nbo : 0);
+                cp_async_n8(d + 2 * BAND + lane * 8, coef + int64_t(p.hq + ro) * p.coef_pitch + je, rov ? nbe : 0);
+                cp_async_n8(d + 3 * BAND + lane * 8, coef + int64_t(p.hq + ro) * p.coef_pitch + p.wq + jo,
+                            rov ? nbo : 0);
             } else {
                 if (p.ll_is_ct)
                     cp_async_small<8>(d + lane * 8, reinterpret_cast<const CT*>(p.ll) + int64_t(re) * p.ll_pitch + jb,
@@ -978,11 +1094,6 @@ __device__ __forceinline__ bool inv_unit_staged(const InvParams& p, int s, int R
 
     Pipe pipe;
     pipe.init();
-    if constexpr (ADJ && !std::is_same<Pipe, AdjInner97<2>>::value) {
-#pragma unroll
-        for (int q = 0; q < QL; ++q) pipe.hw[q] = axis_weights(jb + q, p.w);
-        pipe.h = p.h;
-    }
     bool ok = true;
     int t = 0, slot = 0;
     const unsigned char* stage = ring;
@@ -1022,7 +1133,45 @@ __device__ __forceinline__ bool inv_unit_staged(const InvParams& p, int s, int R
             }
             const R& out = pipe.template step<PH>(vi);
             const int oi = vi - Pipe::LAG;
-            if (oi >= R0 && oi < R1) {
+            if constexpr (ROUTE == ROUTE_EDGE) {
+                if (oi >= R0 && oi < R1) {
+                    if (cols_in && oi >= 0 && 2 * oi + 1 < p.h) {  // warp-uniform
+                        if (cc == CC_IN) {
+                            CT* row_o = row_e + p.out_pitch;
+                            if (p.vec_out) {
+                                st4<CT>(row_e + px, out.c1[0], out.c2[0], out.c1[1], out.c2[1]);
+                                st4<CT>(row_o + px, out.c3[0], out.c4[0], out.c3[1], out.c4[1]);
+                            } else {
+                                row_e[px] = out.c1[0], row_e[px + 1] = out.c2[0];
+                                row_e[px + 2] = out.c1[1], row_e[px + 3] = out.c2[1];
+                                row_o[px] = out.c3[0], row_o[px + 1] = out.c4[0];
+                                row_o[px + 2] = out.c3[1], row_o[px + 3] = out.c4[1];
+                            }
+                        }
+                    } else {
+                        adj_edge_store_rows(p, row_e, 2 * oi, px, cc, svec, out.c1[0], out.c2[0], out.c1[1],
+                                            out.c2[1], out.c3[0], out.c4[0], out.c3[1], out.c4[1]);
+                    }
+                    row_e += 2 * p.out_pitch;
+                }
+            } else if constexpr (ROUTE == ROUTE_PIXELS) {
+                if (oi >= R0 && oi < R1 && mine) {
+                    const CT ev[4] = {out.c1[0], out.c2[0], out.c1[1], out.c2[1]};
+                    const CT od[4] = {out.c3[0], out.c4[0], out.c3[1], out.c4[1]};
+                    CT* row_o = row_e + p.out_pitch;
+                    if (px >= 0 && px + 3 < p.w) {  // the lane's columns inside: whole pixel rows
+                        adj_row_store(p, row_e, 2 * oi, px, ev);
+                        adj_row_store(p, row_o, 2 * oi + 1, px, od);
+                    } else {
+#pragma unroll
+                        for (int k2 = 0; k2 < 4; ++k2) {
+                            adj_route_store(p, row_e, 2 * oi, px + k2, ev[k2]);
+                            adj_route_store(p, row_o, 2 * oi + 1, px + k2, od[k2]);
+                        }
+                    }
+                }
+                if (oi >= R0 && oi < R1) row_e += 2 * p.out_pitch;
+            } else if (oi >= R0 && oi < R1) {
                 CT* row_o = row_e + p.out_pitch;
                 const bool has_o = 2 * oi + 1 < p.h;
                 if (mine && p.vec_out && px + 3 < p.w) {
@@ -1052,36 +1201,27 @@ __device__ __forceinline__ bool inv_unit_staged(const InvParams& p, int s, int R
     return ok;
 }
 
-// inverse / adjoint unit: staged when every band row takes paired copies,
-// else direct loads.  Adjoint units away from the boundary (every quad of
-// the strip and every row the steps weight in [1, half - 2]) run the
-// unweighted pipeline.  CLS selects the code compiled in: UNITS_INNER only the
-// staged row loop of the inner units (inv_inner_rect), UNITS_EDGE every other
-// path, UNITS_ALL both.
-template <class Pipe, class BT, bool ADJ, int QR, int NST, int CLS = UNITS_ALL>
+// UNITS_INNER: staged pair copies, plain stores.  UNITS_EDGE of the inverse:
+// staged element copies from mirrored columns (4-byte types) or direct loads;
+// of the adjoint (one pipeline, Adj97, on the extended domain): pair copies
+// with zero fill and stores routed by lane when the bands are pair-aligned,
+// else element copies and stores routed by pixel.
+template <class Pipe, class BT, bool ADJ, int QR, int NST, int CLS>
 __device__ __forceinline__ bool inv_unit_any(const InvParams& p, int s, int R0, int R1, int lane,
                                              unsigned char* ring, uint64_t* bars, uint32_t& gstage) {
-    using Inner = typename std::conditional<ADJ, AdjInner97<2>, Pipe>::type;
+    static_assert(CLS == UNITS_INNER || CLS == UNITS_EDGE, "a level runs its inner and edge units in two launches");
+    const bool staged = p.vec_in_lo && p.vec_in_hi && p.vec_ll;
     if constexpr (CLS == UNITS_INNER) {
-        return inv_unit_staged<Inner, BT, ADJ, QR, NST, false>(p, s, R0, R1, lane, ring, bars, gstage);
+        return inv_unit_staged<Pipe, BT, ADJ, QR, NST, false>(p, s, R0, R1, lane, ring, bars, gstage);
+    } else if constexpr (ADJ) {
+        if (staged)
+            return inv_unit_staged<Pipe, BT, true, QR, NST, false, ROUTE_EDGE>(p, s, R0, R1, lane, ring, bars, gstage);
+        return inv_unit_staged<Pipe, BT, true, QR, NST, true, ROUTE_PIXELS>(p, s, R0, R1, lane, ring, bars, gstage);
     } else {
-        constexpr int HQ = PipeGeom<Pipe>::HALO;
-        constexpr int OUTQ = 32 * 2 - 2 * HQ;
-        const int x0 = s * (2 * OUTQ) - 2 * HQ;
-        const bool staged = p.vec_in_lo && p.vec_in_hi && p.vec_ll;
-        const bool interior = (x0 >= 0) && (x0 / 2 + 64 <= p.wh);
-        if constexpr (ADJ && CLS == UNITS_ALL) {
-            // the steps weight rows R0-4 .. R1+1 (see Adj97::step) and quads x0/2 .. x0/2+63
-            const bool inner = staged && interior && (x0 / 2 >= 1) && (x0 / 2 + 63 <= p.wh - 2) && (R0 - 4 >= 1) &&
-                               (R1 + 1 <= p.hh - 2);
-            if (inner) return inv_unit_staged<Inner, BT, true, QR, NST, false>(p, s, R0, R1, lane, ring, bars, gstage);
-        }
-        if (staged && interior)
-            return inv_unit_staged<Pipe, BT, ADJ, QR, NST, false>(p, s, R0, R1, lane, ring, bars, gstage);
         if constexpr (sizeof(BT) == 4) {
-            if (staged) return inv_unit_staged<Pipe, BT, ADJ, QR, NST, true>(p, s, R0, R1, lane, ring, bars, gstage);
+            if (staged) return inv_unit_staged<Pipe, BT, false, QR, NST, true>(p, s, R0, R1, lane, ring, bars, gstage);
         }
-        inv_unit<Pipe, BT, ADJ, 2>(p, s, R0, R1, lane);
+        inv_unit<Pipe, BT, false, 2>(p, s, R0, R1, lane);
         return true;
     }
 }
@@ -1099,49 +1239,58 @@ __device__ __forceinline__ void inv_ring(unsigned char* smem, int warp, int lane
     __syncwarp();
 }
 
-// resident blocks the inner-unit kernels of the two-quad-halo pipelines
-// (CDF 9/7, CDF 5/3) are held to: one staged row loop fits the register budget
-// of five 4-warp blocks per SM; the DD 13/7 pipelines (six-row rings) and the
-// edge-unit kernels are left to the compiler
+// resident blocks the kernels of the two-quad-halo pipelines (CDF 9/7,
+// CDF 5/3) are held to: the inner row loop fits the register budget of five
+// 4-warp blocks per SM, the edge loops (element copies, predicated copies and
+// routed stores) that of four; the DD 13/7 pipelines (six-row rings) are left
+// to the compiler
 template <class Pipe, int CLS>
 struct InvMinBlocks {
-    static constexpr int value = (CLS == UNITS_INNER && PipeGeom<Pipe>::HALO == 2) ? 5 : 1;
+    static constexpr int value = PipeGeom<Pipe>::HALO == 2 ? (CLS == UNITS_INNER ? 5 : 4) : 1;
 };
 
-// One level of one image.  UNITS_ALL: the warps take their units from Pieces;
-// otherwise the units of class CLS, dealt round-robin in segment-major order.
-template <class Pipe, class BT, bool ADJ, int QL, int NW, int CLS = UNITS_ALL>
+// Strip s and quad rows [R0, R1) of the class's unit lu (on the extended
+// domain of the adjoint); false for an empty piece of an edge unit.
+__device__ __forceinline__ bool inv_unit_rows(const InvParams& p, int cls, int lu, int& s, int& R0, int& R1) {
+    int g, k;
+    inv_class_unit(p, cls, lu, s, g, k);
+    R0 = g * p.seg_rows - p.ext;
+    R1 = min(R0 + p.seg_rows, p.hq + p.ext);
+    if (cls == UNITS_EDGE && inv_edge_split(p) > 1) {
+        const int pr = (p.seg_rows + inv_edge_split(p) - 1) / inv_edge_split(p);
+        R0 += k * pr;
+        R1 = min(R1, R0 + pr);
+    }
+    return R0 < R1;
+}
+
+// Launch order.  The first launch of a level (the inner units of its first
+// group of images) is a plain launch: stream order completes everything before
+// it.  The level's later launches (the edge units, later groups) share no data
+// with the launches before them and are programmatic dependents that start as
+// soon as those have placed all their blocks; none of them waits on the device.
+// One level of one image: the units of class CLS, dealt round-robin.
+template <class Pipe, class BT, bool ADJ, int QL, int NW, int CLS>
 __global__ void __launch_bounds__(NW * 32, InvMinBlocks<Pipe, CLS>::value) inv_kernel(const InvParams p) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char* ring;
     uint64_t* bars;
     inv_ring<INV_QR, INV_NST, NW>(smem, warp, lane, ring, bars);
-    // a second launch of a level (PDL) shares no data with the first
     griddep_launch_dependents();
     uint32_t gstage = 0;
-    if constexpr (CLS == UNITS_ALL) {
-        Pieces<InvParams> pieces(p, blockIdx.x * NW + warp, gridDim.x * NW);
+    const int n = inv_class_units(p, CLS);
+    for (int lu = blockIdx.x * NW + warp; lu < n; lu += gridDim.x * NW) {
         int s, R0, R1;
-        while (pieces.next(p, s, R0, R1))
-            if (!inv_unit_any<Pipe, BT, ADJ, INV_QR, INV_NST>(p, s, R0, R1, lane, ring, bars, gstage)) return;
-    } else {
-        const int n = inv_class_units(p, CLS);
-        for (int lu = blockIdx.x * NW + warp; lu < n; lu += gridDim.x * NW) {
-            int s, g;
-            inv_class_unit(p, CLS, lu, s, g);
-            const int R0 = g * p.seg_rows;
-            if (!inv_unit_any<Pipe, BT, ADJ, INV_QR, INV_NST, CLS>(p, s, R0, min(R0 + p.seg_rows, p.hq), lane, ring,
-                                                                    bars, gstage))
-                return;
-        }
+        if (!inv_unit_rows(p, CLS, lu, s, R0, R1)) continue;
+        if (!inv_unit_any<Pipe, BT, ADJ, INV_QR, INV_NST, CLS>(p, s, R0, R1, lane, ring, bars, gstage)) return;
     }
 }
 
 // One level of a group of images (InvGroupLaunch): the units of class CLS of
 // every image, in order, the image found by binary search over the group's
-// unit ranges; only the first launch of a level waits for earlier work.
-template <class Pipe, class BT, bool ADJ, int QL, int NW, int CLS = UNITS_ALL>
+// unit ranges.
+template <class Pipe, class BT, bool ADJ, int QL, int NW, int CLS>
 __global__ void __launch_bounds__(NW * 32, InvMinBlocks<Pipe, CLS>::value)
     inv_group_kernel(const __grid_constant__ InvGroupLaunch L) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -1149,7 +1298,6 @@ __global__ void __launch_bounds__(NW * 32, InvMinBlocks<Pipe, CLS>::value)
     unsigned char* ring;
     uint64_t* bars;
     inv_ring<INV_QR, INV_NST, NW>(smem, warp, lane, ring, bars);
-    if (L.wait_prev) griddep_wait();
     griddep_launch_dependents();
     uint32_t gstage = 0;
     for (int u = blockIdx.x * NW + warp; u < L.n_units[CLS]; u += gridDim.x * NW) {
@@ -1160,13 +1308,78 @@ __global__ void __launch_bounds__(NW * 32, InvMinBlocks<Pipe, CLS>::value)
             else hi = mid - 1;
         }
         const InvParams& p = L.img[lo].p;
-        int s, g;
-        inv_class_unit(p, CLS, u - L.img[lo].u_begin[CLS], s, g);
-        const int R0 = g * p.seg_rows;
-        if (!inv_unit_any<Pipe, BT, ADJ, INV_QR, INV_NST, CLS>(p, s, R0, min(R0 + p.seg_rows, p.hq), lane, ring, bars,
-                                                                gstage))
-            return;
+        int s, R0, R1;
+        if (!inv_unit_rows(p, CLS, u - L.img[lo].u_begin[CLS], s, R0, R1)) continue;
+        if (!inv_unit_any<Pipe, BT, ADJ, INV_QR, INV_NST, CLS>(p, s, R0, R1, lane, ring, bars, gstage)) return;
     }
+}
+
+// ---------------------------------------------------------------- adjoint fold
+// E^T of one adjoint level: every image pixel within five of an edge (the
+// whole image when a side is at most ten) adds the side-buffer values of the
+// extended positions whose whole-sample mirror it is: extended columns of its
+// row, extended rows of its column, and both at once (corners).  One thread
+// per such pixel, so no two threads write the same pixel.
+// slot (0..7) of the extended position whose mirror is c in a side of n > 10
+// samples, or -1: the mirror of -k is k, that of n-1+k is n-1-k (k = 1..4)
+__device__ __forceinline__ int adj_mirror_slot(int c, int n) {
+    if (c >= 1 && c <= 4) return 4 - c;
+    if (c >= n - 5 && c <= n - 2) return n + 2 - c;
+    return -1;
+}
+
+__device__ __forceinline__ void adj_fold_pixel(const InvParams& p, int r, int c) {
+    const float* L = p.side;
+    const float* T = p.side + int64_t(8) * (p.h + 8);
+    float* o = reinterpret_cast<float*>(p.out) + int64_t(r) * p.out_pitch + c;
+    if (p.h > 10 && p.w > 10) {  // at most one source of each kind
+        const int kc = adj_mirror_slot(c, p.w), kr = adj_mirror_slot(r, p.h);
+        float acc = 0.f;
+        if (kc >= 0) acc += L[(r + 4) * 8 + kc];
+        if (kr >= 0) acc += T[int64_t(kr) * p.w + c];
+        if (kc >= 0 && kr >= 0) acc += L[(kr < 4 ? kr : p.h + kr) * 8 + kc];
+        if (kc >= 0 || kr >= 0) *o += acc;
+        return;
+    }
+    float acc = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int pc = k < 4 ? k - 4 : p.w + (k - 4);  // extended column
+        const int pr = k < 4 ? k - 4 : p.h + (k - 4);  // extended row
+        const bool col_here = fold_ws(pc, p.w) == c;
+        const bool row_here = fold_ws(pr, p.h) == r;
+        if (col_here) acc += L[(r + 4) * 8 + k];  // extended column of this row
+        if (row_here) acc += T[int64_t(k) * p.w + c];  // extended row of this column
+        if (row_here) {
+#pragma unroll
+            for (int kc = 0; kc < 8; ++kc) {  // corners: extended row and column
+                const int pc2 = kc < 4 ? kc - 4 : p.w + (kc - 4);
+                if (fold_ws(pc2, p.w) == c) acc += L[(pr + 4) * 8 + kc];
+            }
+        }
+    }
+    *o += acc;
+}
+
+// the pixels within five of an edge, as one index range: the first and last
+// min(5, h) rows whole, then the first and last min(5, w) columns of the rows
+// between
+__host__ __device__ inline int adj_fold_count(int h, int w) {
+    const int br = h <= 10 ? h : 10, bc = w <= 10 ? w : 10;
+    return br * w + (h - br) * bc;
+}
+__device__ __forceinline__ void adj_fold_index(int h, int w, int i, int& r, int& c) {
+    const int br = h <= 10 ? h : 10, bc = w <= 10 ? w : 10;
+    if (i < br * w) {
+        const int rr = i / w;
+        r = rr < 5 || h <= 10 ? rr : h - 10 + rr;
+        c = i % w;
+        return;
+    }
+    i -= br * w;
+    r = 5 + i / bc;
+    const int cc = i % bc;
+    c = cc < 5 || w <= 10 ? cc : w - 10 + cc;
 }
 
 }  // namespace dwt2

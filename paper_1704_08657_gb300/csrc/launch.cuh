@@ -296,8 +296,7 @@ template <class Pipe, class BT, bool ADJ>
 int launch_inv_group_one(const InvGroupLaunch& g, int grid, int pdl, int cls, cudaStream_t s) {
     cudaLaunchAttribute attr[1];
     const cudaLaunchConfig_t lc = inv_launch_config(grid, pdl, s, attr);
-    if (cls == UNITS_INNER)
-        return cudaLaunchKernelEx(&lc, inv_group_kernel<Pipe, BT, ADJ, INV_QL, INV_NW, UNITS_INNER>, g);
+    if (cls == UNITS_INNER) return cudaLaunchKernelEx(&lc, inv_group_kernel<Pipe, BT, ADJ, INV_QL, INV_NW, UNITS_INNER>, g);
     return cudaLaunchKernelEx(&lc, inv_group_kernel<Pipe, BT, ADJ, INV_QL, INV_NW, UNITS_EDGE>, g);
 }
 

@@ -796,121 +796,22 @@ struct Inv97 {
 };
 
 // ==================================================== adjoint of CDF 9/7
-// The transpose of the forward operator: scaling (symmetric), then for each
-// pair in reverse order S_U^T (reads right / below) and T_P^T (reads left /
-// above).  With the symmetric boundary the transposed 1-D filters carry
-// position-dependent weights:
-//   (U^T s)[k] = b (wO(k) s[k] + wR(k) s[k+1]),  k over odd samples
-//   (P^T d)[m] = a (vL(m) d[m-1] + vO(m) d[m]),  m over even samples
-// wO(0) = 2; wR(nd-1) = 0 (n even) or 2 (n odd); vL(0) = 0; vO(ns-1) = 2
-// (n even) or 0 (n odd); 1 elsewhere, 0 for targets outside the signal.
-struct AxisW {
-    float uO, uR, pL, pO;
-};
-
-__device__ __forceinline__ AxisW axis_weights(int j, int n) {
-    const int ns = (n + 1) >> 1, nd = n >> 1;
-    AxisW w;
-    const bool od = (j >= 0) && (j < nd);   // odd sample j exists
-    const bool ev = (j >= 0) && (j < ns);   // even sample j exists
-    w.uO = od ? (j == 0 ? 2.f : 1.f) : 0.f;
-    w.uR = (od && j + 1 <= ns - 1) ? (((n & 1) && j == nd - 1) ? 2.f : 1.f) : 0.f;
-    w.pL = (ev && j >= 1) ? 1.f : 0.f;
-    w.pO = (ev && j <= nd - 1) ? ((!(n & 1) && j == ns - 1) ? 2.f : 1.f) : 0.f;
-    return w;
-}
-
-// S_U^T on row X (row index i) with the row below D: predict-shaped.
-template <int QL>
-__device__ __forceinline__ void adj_st(Row<float, QL>& X, const Row<float, QL>& D, float b, float bb,
-                                       const AxisW (&hw)[QL], const AxisW& vw) {
-    float r1[QL], r3[QL], dr1[QL];
-    right_of(X.c1, r1);
-    right_of(X.c3, r3);
-    right_of(D.c1, dr1);
-#pragma unroll
-    for (int q = 0; q < QL; ++q) {
-        const float hc1 = hw[q].uO * X.c1[q] + hw[q].uR * r1[q];   // U^T c1 along the row
-        const float hd1 = hw[q].uO * D.c1[q] + hw[q].uR * dr1[q];  // same for the row below
-        const float t4 = vw.uO * hc1 + vw.uR * hd1;                 // U*^T U^T c1
-        const float v2 = vw.uO * X.c2[q] + vw.uR * D.c2[q];         // U*^T c2
-        const float h3 = hw[q].uO * X.c3[q] + hw[q].uR * r3[q];     // U^T c3
-        const float v1 = vw.uO * X.c1[q] + vw.uR * D.c1[q];         // U*^T c1
-        X.c4[q] = fmaf(bb, t4, fmaf(b, v2 + h3, X.c4[q]));
-        X.c2[q] = fmaf(b, hc1, X.c2[q]);
-        X.c3[q] = fmaf(b, v1, X.c3[q]);
-    }
-}
-
-// T_P^T on row X with the carry C of the row above: update-shaped.
-template <int QL>
-__device__ __forceinline__ void adj_tt(Row<float, QL>& X, const Carry3<QL>& C, Carry3<QL>& N, float a, float aa,
-                                       const AxisW (&hw)[QL], const AxisW& vw) {
-    float l2[QL], l4[QL];
-    left_of(X.c2, l2);
-    left_of(X.c4, l4);
-#pragma unroll
-    for (int q = 0; q < QL; ++q) {
-        N.c3[q] = X.c3[q];
-        N.c4[q] = X.c4[q];
-        N.l4[q] = l4[q];
-        const float h2 = hw[q].pL * l2[q] + hw[q].pO * X.c2[q];      // P^T c2
-        const float v3 = vw.pL * C.c3[q] + vw.pO * X.c3[q];          // P*^T c3
-        const float hu4 = hw[q].pL * C.l4[q] + hw[q].pO * C.c4[q];   // P^T c4, row above
-        const float hx4 = hw[q].pL * l4[q] + hw[q].pO * X.c4[q];     // P^T c4
-        const float t1 = vw.pL * hu4 + vw.pO * hx4;                  // P*^T P^T c4
-        const float v4 = vw.pL * C.c4[q] + vw.pO * X.c4[q];          // P*^T c4
-        X.c1[q] = fmaf(aa, t1, fmaf(a, h2 + v3, X.c1[q]));
-        X.c2[q] = fmaf(a, v4, X.c2[q]);
-        X.c3[q] = fmaf(a, hx4, X.c3[q]);
-    }
-}
-
+// The forward operator with the whole-sample symmetric boundary is
+// W = R F E: extend the level's input symmetrically (E), lift on the
+// unbounded extended domain with no boundary cases (F), keep the
+// coefficients inside (R).  Its transpose is W^T = E^T F^T R^T: the
+// coefficient gradient placed on the extended domain with zeros outside (R^T),
+// the transposed lifting with no boundary cases (F^T), and the fold E^T that
+// adds the value of every extended position onto its whole-sample mirror.
+// F^T is the transposed steps in reverse order: scaling (symmetric), then
+// for each pair S_U^T and T_P^T.  Unweighted, U^T = b(1 + z) and
+// P^T = a(1 + z^-1), so S_U^T is a spatial predict with coefficient b and
+// T_P^T a spatial update with coefficient a, and the reduced split applies.
+// Every output within four pixels of the image (two quads) can be nonzero;
+// the kernels write those outside the image to a side buffer and fold them
+// (adj_fold_kernel).
 template <int QL>
 struct Adj97 {
-    static constexpr int LAG = 2;
-    using CT = float;
-    using R = Row<float, QL>;
-    R rw[3];
-    Carry3<QL> ka[2], kb[2];
-    AxisW hw[QL];  // horizontal weights of the lane's quads
-    int h;         // image height of this level
-    __device__ __forceinline__ void init() {
-#pragma unroll
-        for (int i = 0; i < 3; ++i) zero_row(rw[i]);
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            zero_carry(ka[i]);
-            zero_carry(kb[i]);
-        }
-    }
-    template <int PH>
-    __device__ __forceinline__ R& slot() {
-        return rw[PH % 3];
-    }
-    // `row` is the quad-row index of the newest row
-    template <int PH>
-    __device__ __forceinline__ R& step(int row) {
-        R& r0 = rw[PH % 3];
-        R& r1 = rw[(PH + 2) % 3];
-        R& r2 = rw[(PH + 1) % 3];
-        constexpr int c = PH & 1, n = c ^ 1;
-        scale97(r0);
-        const AxisW v1 = axis_weights(row - 1, h), v2 = axis_weights(row - 2, h);
-        adj_st(r1, r0, C97::D, C97::DD, hw, v1);
-        adj_tt(r1, ka[c], ka[n], C97::G, C97::GG, hw, v1);
-        adj_st(r2, r1, C97::B, C97::BB, hw, v2);
-        adj_tt(r2, kb[c], kb[n], C97::A, C97::AA, hw, v2);
-        return r2;
-    }
-};
-
-// Away from the image boundary every weight is 1: U^T = b(1 + z) and
-// P^T = a(1 + z^-1), so S_U^T is a spatial predict with coefficient b and
-// T_P^T a spatial update with coefficient a (the reduced split applies).  A
-// unit whose strip and rows are all interior runs this pipeline.
-template <int QL>
-struct AdjInner97 {
     static constexpr int LAG = 2;
     using CT = float;
     using R = Row<float, QL>;

@@ -152,6 +152,41 @@ def test_adjoint_matches_oracle(h, w):
     assert np.abs(got - ref).max() <= 1e-5 * max(1.0, np.abs(ref).max()) * 2 ** levels
 
 
+@pytest.mark.parametrize("env", [{"DWT2_EDGE_SPLIT": "1"}, {"DWT2_EDGE_SPLIT": "3"}, {"DWT2_EDGE_SPLIT": "7"},
+                                 {"DWT2_SEG_ROWS": "9", "DWT2_EDGE_SPLIT": "2"}])
+def test_inverse_adjoint_unit_pieces_bit_identical(monkeypatch, env):
+    """The edge units of the inverse and the adjoint run in pieces of a
+    segment (each with its own warm-up rows) beside the inner units; a quad's
+    arithmetic does not depend on which unit computes it, so every piece
+    count and segment height gives the same bits, for single-image and
+    grouped plans, and the pieces stay within the oracle's bound."""
+    cases = [(512, 512), (257, 129), (130, 250), (100, 1028), (33, 65), (70, 1000)]
+    base = []
+    for h, w in cases:
+        levels = _levels_max(h, w, 4)
+        rng = np.random.default_rng(h * 7 + w)
+        g = rng.standard_normal((h, w)).astype(np.float32)
+        c = oracle.forward97(synth.uniform(h, w, seed=5).astype(np.float64), levels).astype(np.float32)
+        base.append((gpu_adjoint(g, levels), gpu_inverse(c, levels, "reduced"), g, c, levels))
+    shapes = synth.batch_shapes(12, seed=4)
+    buf, descs = synth.batch_pack(shapes, seed=9)
+    gd = torch.from_numpy(buf).cuda()
+    plan = Plan(descs, 3, scheme="reduced")
+    b_adj, b_inv = plan.adjoint(gd).cpu(), plan.inverse(gd).cpu()
+    for k, v in env.items():
+        monkeypatch.setenv(k, v)
+    for (a0, i0, g, c, levels), (h, w) in zip(base, cases):
+        a1 = gpu_adjoint(g, levels)
+        assert np.array_equal(a1, a0), f"adjoint {h}x{w} {env}"
+        assert np.array_equal(gpu_inverse(c, levels, "reduced"), i0), f"inverse {h}x{w} {env}"
+        ref = oracle.adjoint97(g.astype(np.float64), levels)
+        assert np.abs(a1 - ref).max() <= 1e-5 * max(1.0, np.abs(ref).max()) * 2 ** levels
+    plan2 = Plan(descs, 3, scheme="reduced")
+    assert torch.equal(plan2.adjoint(gd).cpu(), b_adj), f"grouped adjoint {env}"
+    assert torch.equal(plan2.inverse(gd).cpu(), b_inv), f"grouped inverse {env}"
+    assert plan2.status() == 0
+
+
 def test_schemes_agree_with_each_other():
     # every scheme is within the FP32 bound of the oracle, so two schemes are
     # within twice that of each other, band by band

@@ -169,7 +169,7 @@ def test_dropped_signal_times_out_without_hanging(monkeypatch):
 
 def test_batch_inverse_adjoint_and_l1():
     """Multi-image plans run the inverse and adjoint as grouped launches per
-    level (up to 200 images a launch)."""
+    level (up to 160 images a launch)."""
     shapes = synth.batch_shapes(30, seed=11)
     buf, descs = _batch(shapes)
     xd = torch.from_numpy(buf).cuda()
