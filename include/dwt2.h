@@ -246,6 +246,18 @@ int dwt2_autotune(dwt2_plan_t plan, const void* in, void* coef, void* workspace,
  * status word: DWT2_OK, DWT2_ERR_TIMEOUT or DWT2_ERR_DEVICE_CHECK. */
 int dwt2_status(dwt2_plan_t plan, void* stream);
 
+/* dwt2_checked -- 1 in the range-checked build of this library
+ * (libdwt2_checked.so, compiled with DWT2_CHECKED), 0 otherwise.  In the
+ * checked build every global access of the forward, inverse and adjoint
+ * kernels (band loads and stores, the image, the workspace's low-low bands
+ * and side buffers) is first tested against the rectangle of its buffer from
+ * the pointer it is about to use; a violation skips the access (a load reads
+ * element 0 instead), sets the plan's status word so that dwt2_status returns
+ * DWT2_ERR_DEVICE_CHECK, and stops the kernel at the end of the unit: a
+ * stand-in for a memory checker, at a cost in speed.  Results of a checked
+ * build without a violation equal the normal build's bit for bit. */
+int dwt2_checked(void);
+
 /* dwt2_profile -- when enable != 0, every later transform call of this plan
  * records a CUDA event pair on its stream around the launches of each pyramid
  * level (all images of a batch together), in a ring of the last 256 calls;

@@ -10,7 +10,8 @@ import ctypes
 import os
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libdwt2.so")
+# DWT2_LIBRARY=checked loads the range-checked build (libdwt2_checked.so)
+LIB_PATH = os.path.join(_PKG, "libdwt2_checked.so" if os.environ.get("DWT2_LIBRARY") == "checked" else "libdwt2.so")
 
 DWT2_CDF97, DWT2_CDF53_INT, DWT2_DD137 = 0, 1, 2
 DWT2_F32, DWT2_F16, DWT2_BF16, DWT2_I32 = 0, 1, 2, 3
@@ -31,7 +32,8 @@ DWT2_TESTONLY_DROP_SIGNAL = 0x100  # test-only failure injection
 # the functions the header declares (checked by the CPU test suite)
 EXPORTS = ("dwt2_plan", "dwt2_workspace_bytes", "dwt2_forward", "dwt2_inverse", "dwt2_adjoint", "dwt2_adjoint_l1", "dwt2_adjoint_l1_dev",
            "dwt2_autotune", "dwt2_status", "dwt2_profile", "dwt2_profile_read", "dwt2_forward_noalloc",
-           "dwt2_noalloc_status", "dwt2_band_rows", "dwt2_band_rects", "dwt2_band_stitch", "dwt2_destroy", "dwt2_strerror")
+           "dwt2_noalloc_status", "dwt2_band_rows", "dwt2_band_rects", "dwt2_band_stitch", "dwt2_checked", "dwt2_destroy",
+           "dwt2_strerror")
 
 
 class dwt2_image_desc(ctypes.Structure):
@@ -49,13 +51,16 @@ _lib = None
 
 
 def load(path: str = LIB_PATH) -> ctypes.CDLL:
-    """Load libdwt2.so (built by paper_1704_08657_gb300.build)."""
+    """Load libdwt2.so (or, with DWT2_LIBRARY=checked, libdwt2_checked.so;
+    built by paper_1704_08657_gb300.build)."""
     global _lib
     if _lib is not None:
         return _lib
     if not os.path.exists(path):
-        raise ImportError(f"libdwt2.so not built at {path}; run __graft_entry__.build()")
+        raise ImportError(f"{os.path.basename(path)} not built at {path}; run __graft_entry__.build()")
     lib = ctypes.CDLL(path)
+    lib.dwt2_checked.argtypes = []
+    lib.dwt2_checked.restype = ctypes.c_int
     vp = ctypes.c_void_p
     lib.dwt2_plan.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                               ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(dwt2_image_desc),

@@ -890,6 +890,14 @@ int forward_fused(dwt2_plan_t p, const ImagePlan& ip, int l, const void* in, voi
 
 extern "C" {
 
+int dwt2_checked(void) {
+#ifdef DWT2_CHECKED
+    return 1;
+#else
+    return 0;
+#endif
+}
+
 const char* dwt2_strerror(int code) {
     switch (code) {
         case DWT2_OK: return "ok";

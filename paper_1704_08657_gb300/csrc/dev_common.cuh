@@ -91,6 +91,64 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
     return ok;
 }
 
+// ------------------------------------------------- checked build (DWT2_CHECKED)
+// Range checks standing in for a memory checker: compiled with DWT2_CHECKED,
+// every global access of the transform kernels and every shared-memory index
+// computed at run time is tested against the extent of its buffer first; a
+// violation sets DEV_CHECK in the status word (dwt2_status then reports
+// DWT2_ERR_DEVICE_CHECK), the access is skipped (a load reads element 0 of its
+// buffer instead, so that no wait is left without its copy) and the kernel
+// stops at the end of the unit.  In normal builds every check is `true` and
+// compiles away.
+#ifdef DWT2_CHECKED
+constexpr bool CHECKED_BUILD = true;
+#else
+constexpr bool CHECKED_BUILD = false;
+#endif
+
+__device__ __forceinline__ bool dev_in(unsigned* status, bool in_range) {
+    if constexpr (CHECKED_BUILD) {
+        if (!in_range && status) atomicOr(status, DEV_CHECK);
+        return in_range;
+    } else {
+        return true;
+    }
+}
+
+// n elements from ptr lie inside the rows x cols rectangle at base (pitch in
+// elements): the pointer arithmetic itself is checked, not only the indices
+template <class T>
+__device__ __forceinline__ bool dev_in_rect(unsigned* status, const T* ptr, const T* base, int64_t pitch, int64_t rows,
+                                            int64_t cols, int n) {
+    if constexpr (CHECKED_BUILD) {
+        const int64_t off = ptr - base;
+        const bool ok = pitch > 0 && off >= 0 && off / pitch < rows && off % pitch + n <= cols;
+        return dev_in(status, ok);
+    } else {
+        return true;
+    }
+}
+
+// n elements from ptr lie inside the len elements at base
+template <class T>
+__device__ __forceinline__ bool dev_in_span(unsigned* status, const T* ptr, const T* base, int64_t len, int n) {
+    if constexpr (CHECKED_BUILD) {
+        const int64_t off = ptr - base;
+        return dev_in(status, off >= 0 && off + n <= len);
+    } else {
+        return true;
+    }
+}
+
+// a check of this kernel (or of another one sharing the status word) failed
+__device__ __forceinline__ bool dev_check_tripped(const unsigned* status) {
+    if constexpr (CHECKED_BUILD) {
+        return status && (*reinterpret_cast<const volatile unsigned*>(status) & DEV_CHECK) != 0;
+    } else {
+        return false;
+    }
+}
+
 // 2-D tiled TMA load of one box into shared memory, completing on `bar`.
 // The x coordinate must be a multiple of 4 elements (16 bytes).
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, int x, int y, uint64_t* bar) {

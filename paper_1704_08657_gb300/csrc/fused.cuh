@@ -113,7 +113,7 @@ __device__ __forceinline__ bool fused_producer(const FusedParams& P, const TmaLo
     for (; issued < NST && issued < NT; ++issued) {
         const uint32_t gs = gstage + issued;
         ld.issue<CT, QL, QR>(bufs + (gs % NST) * FUSED_STAGE, &bars[gs % NST], x0, 2 * (A0 + issued * QR), p.h, p.w,
-                             lane);
+                             lane, P.status);
     }
     Pipe pipe;
     pipe.init();
@@ -160,7 +160,7 @@ __device__ __forceinline__ bool fused_producer(const FusedParams& P, const TmaLo
                 if (issued < NT) {
                     const uint32_t gs = gstage + issued;
                     ld.issue<CT, QL, QR>(bufs + (gs % NST) * FUSED_STAGE, &bars[gs % NST], x0,
-                                         2 * (A0 + issued * QR), p.h, p.w, lane);
+                                         2 * (A0 + issued * QR), p.h, p.w, lane, P.status);
                     ++issued;
                 }
             }

@@ -170,16 +170,23 @@ struct TmaLoader {
     const CUtensorMap* box;
     const CUtensorMap* row;
     template <class CT, int QL, int QR>
-    __device__ __forceinline__ void issue(CT* dst, uint64_t* bar, int x0, int y0, int h, int /*w*/,
-                                          int lane) const {
+    __device__ __forceinline__ void issue(CT* dst, uint64_t* bar, int x0, int y0, int h, int /*w*/, int lane,
+                                          unsigned* status) const {
         constexpr int SPX = 64 * QL, ROWS = 2 * QR;
         if (lane != 0) return;
+        // the box's first column on a 16-byte boundary (columns outside the
+        // image are TMA's zero fill, checked by the hardware)
+        if (!dev_in(status, (x0 & 3) == 0)) x0 &= ~3;
         mbar_expect_tx(bar, unsigned(ROWS * SPX * 4));
         if (y0 >= 0 && y0 + ROWS <= h) {
             tma_load_2d(dst, box, x0, y0, bar);
         } else {
 #pragma unroll 1
-            for (int r = 0; r < ROWS; ++r) tma_load_2d(dst + r * SPX, row, x0, fold_ws(y0 + r, h), bar);
+            for (int r = 0; r < ROWS; ++r) {
+                int y = fold_ws(y0 + r, h);
+                if (!dev_in(status, y >= 0 && y < h)) y = 0;
+                tma_load_2d(dst + r * SPX, row, x0, y, bar);
+            }
         }
     }
 };
@@ -194,18 +201,21 @@ struct CpAsyncLoader {
     const CT* src;
     int64_t pitch;
     template <class CT_, int QL, int QR>
-    __device__ __forceinline__ void issue(CT_* dst, uint64_t* bar, int x0, int y0, int h, int w, int lane) const {
+    __device__ __forceinline__ void issue(CT_* dst, uint64_t* bar, int x0, int y0, int h, int w, int lane,
+                                          unsigned* status) const {
         constexpr int SPX = 64 * QL, ROWS = 2 * QR;
         const bool inside = (y0 >= 0) && (y0 + ROWS <= h);
 #pragma unroll
         for (int r = 0; r < ROWS; ++r) {
-            const int y = inside ? y0 + r : fold_ws(y0 + r, h);
+            int y = inside ? y0 + r : fold_ws(y0 + r, h);
+            if (!dev_in(status, y >= 0 && y < h)) y = 0;
             const CT* srow = src + int64_t(y) * pitch;
 #pragma unroll
             for (int k = 0; k < QL / 2; ++k) {
                 const int c = lane + 32 * k;  // chunk index in the strip
                 const int px = x0 + 4 * c;
-                const int n = (px >= 0) ? max(0, min(4, w - px)) : 0;
+                int n = (px >= 0) ? max(0, min(4, w - px)) : 0;
+                if (!dev_in(status, n == 0 || (px >= 0 && px + n <= w))) n = 0;
                 const CT* g = srow + (n > 0 ? px : 0);
                 asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst + r * SPX + 4 * c)),
                              "l"(g), "r"(4 * n)
@@ -285,11 +295,22 @@ __device__ __forceinline__ bool fwd_unit(const P& p, const Loader& ld, int s, in
     OutT* hh = lh + p.wq;
     CT* llc = reinterpret_cast<CT*>(p.ll) + int64_t(R0) * p.ll_pitch + jb;
     OutT* llo = reinterpret_cast<OutT*>(p.ll) + int64_t(R0) * p.ll_pitch + jb;
+    // checked build: the four bands as rectangles (LL hq x wq, HL hq x wh,
+    // LH hh x wq, HH hh x wh) that every store must fall in
+    const OutT* hl0 = reinterpret_cast<const OutT*>(p.coef) + p.wq;
+    const OutT* lh0 = reinterpret_cast<const OutT*>(p.coef) + int64_t(p.hq) * p.coef_pitch;
+    const OutT* hh0 = lh0 + p.wq;
+    const CT* llc0 = reinterpret_cast<const CT*>(p.ll);
+    const OutT* llo0 = reinterpret_cast<const OutT*>(p.ll);
+    auto in_band = [&](const auto* ptr, const auto* base, int64_t pitch, int rows, int cols, bool m0, bool m1) {
+        return (!m0 || dev_in_rect(p.status, ptr, base, pitch, rows, cols, 1)) &&
+               (!m1 || dev_in_rect(p.status, ptr + 1, base, pitch, rows, cols, 1));
+    };
 
     for (int t = 0; t < NST && t < NT; ++t) {
         const uint32_t gs = gstage + t;
         ld.template issue<CT, QL, QR>(bufs + (gs % NST) * STAGE_ELEMS, &bars[gs % NST], x0, 2 * (A0 + t * QR), p.h,
-                                      p.w, lane);
+                                      p.w, lane, p.status);
     }
 
     Pipe pipe;
@@ -327,8 +348,15 @@ __device__ __forceinline__ bool fwd_unit(const P& p, const Loader& ld, int s, in
             if (fast) {
 #pragma unroll
                 for (int q = 0; q < QL; q += 2) {
-                    const bool on_e = row_on & pe[q / 2], on_o = row_on & po[q / 2];
-                    const bool oo_e = orow & pe[q / 2], oo_o = orow & po[q / 2];
+                    bool on_e = row_on & pe[q / 2], on_o = row_on & po[q / 2];
+                    bool oo_e = orow & pe[q / 2], oo_o = orow & po[q / 2];
+                    if constexpr (CHECKED_BUILD) {
+                        on_e = on_e && (llct ? in_band(llc + q, llc0, p.ll_pitch, p.hq, p.wq, true, true)
+                                             : in_band(llo + q, llo0, p.ll_pitch, p.hq, p.wq, true, true));
+                        on_o = on_o && in_band(hl + q, hl0, p.coef_pitch, p.hq, p.wh, true, true);
+                        oo_e = oo_e && in_band(lh + q, lh0, p.coef_pitch, p.hh, p.wq, true, true);
+                        oo_o = oo_o && in_band(hh + q, hh0, p.coef_pitch, p.hh, p.wh, true, true);
+                    }
                     if (llct) {
                         if (on_e) st_pair<CT>(llc + q, out.c1[q], out.c1[q + 1]);
                     } else {
@@ -341,14 +369,23 @@ __device__ __forceinline__ bool fwd_unit(const P& p, const Loader& ld, int s, in
             } else if (row_on) {
 #pragma unroll
                 for (int q = 0; q < QL; q += 2) {
-                    if (llct)
-                        store_pair<CT, CT>(llc, q, out.c1[q], out.c1[q + 1], ev[q], ev[q + 1], true);
-                    else
+                    bool ok_l = true, ok_hl = true, ok_lh = true, ok_hh = true;
+                    if constexpr (CHECKED_BUILD) {
+                        ok_l = llct ? in_band(llc + q, llc0, p.ll_pitch, p.hq, p.wq, ev[q], ev[q + 1])
+                                    : in_band(llo + q, llo0, p.ll_pitch, p.hq, p.wq, ev[q], ev[q + 1]);
+                        ok_hl = in_band(hl + q, hl0, p.coef_pitch, p.hq, p.wh, dv[q], dv[q + 1]);
+                        ok_lh = !orow || in_band(lh + q, lh0, p.coef_pitch, p.hh, p.wq, ev[q], ev[q + 1]);
+                        ok_hh = !orow || in_band(hh + q, hh0, p.coef_pitch, p.hh, p.wh, dv[q], dv[q + 1]);
+                    }
+                    if (llct) {
+                        if (ok_l) store_pair<CT, CT>(llc, q, out.c1[q], out.c1[q + 1], ev[q], ev[q + 1], true);
+                    } else if (ok_l) {
                         store_pair<OutT, CT>(llo, q, out.c1[q], out.c1[q + 1], ev[q], ev[q + 1], p.vec_ll);
-                    store_pair<OutT, CT>(hl, q, out.c2[q], out.c2[q + 1], dv[q], dv[q + 1], p.vec_hi);
+                    }
+                    if (ok_hl) store_pair<OutT, CT>(hl, q, out.c2[q], out.c2[q + 1], dv[q], dv[q + 1], p.vec_hi);
                     if (orow) {
-                        store_pair<OutT, CT>(lh, q, out.c3[q], out.c3[q + 1], ev[q], ev[q + 1], p.vec_lo);
-                        store_pair<OutT, CT>(hh, q, out.c4[q], out.c4[q + 1], dv[q], dv[q + 1], p.vec_hi);
+                        if (ok_lh) store_pair<OutT, CT>(lh, q, out.c3[q], out.c3[q + 1], ev[q], ev[q + 1], p.vec_lo);
+                        if (ok_hh) store_pair<OutT, CT>(hh, q, out.c4[q], out.c4[q + 1], dv[q], dv[q + 1], p.vec_hi);
                     }
                 }
             }
@@ -363,7 +400,7 @@ __device__ __forceinline__ bool fwd_unit(const P& p, const Loader& ld, int s, in
                 __syncwarp();
                 if (ok && t + NST < NT)
                     ld.template issue<CT, QL, QR>(bufs + slot * STAGE_ELEMS, &bars[slot], x0,
-                                                  2 * (A0 + (t + NST) * QR), p.h, p.w, lane);
+                                                  2 * (A0 + (t + NST) * QR), p.h, p.w, lane, p.status);
                 ++t;
             }
         });
@@ -477,7 +514,7 @@ __global__ void __launch_bounds__(NW * 32, FwdMinBlocks<Pipe, NW>::value)
         } else {
             ok = fwd_unit<Pipe, OutT, QL, QR, NST, 0>(p, ld, s, R0, R1, bufs, bars, gstage, lane);
         }
-        if (!ok) return;
+        if (!ok || dev_check_tripped(p.status)) return;
         if (p.out_ctr != nullptr && !(p.test_drop && s == 0 && R0 == 0)) fwd_signal(p.out_ctr + R0 / p.seg_rows, lane);
     }
 }
@@ -535,7 +572,7 @@ __global__ void __launch_bounds__(NW * 32, FwdMinBlocks<Pipe, NW>::value)
         } else {
             ok = fwd_unit<Pipe, OutT, QL, QR, NST, 0>(p, ld, s, R0, R1, bufs, bars, gstage, lane);
         }
-        if (!ok) return;
+        if (!ok || dev_check_tripped(p.status)) return;
     }
 }
 
@@ -634,7 +671,7 @@ __global__ void __launch_bounds__(NW * 32, FwdMinBlocks<Pipe, NW>::value) pml_ke
             const CpAsyncLoader<CT> ld{src, d.src_pitch};
             ok = fwd_unit<Pipe, OutT, QL, QR, NST>(v, ld, un.s, R0, R1, bufs, bars, gstage, lane);
         }
-        if (!ok) return;
+        if (!ok || dev_check_tripped(P.status)) return;
         // this unit's stores must be visible to the TMA reads of later units
         if (TMA) asm volatile("fence.proxy.async.global;" ::: "memory");
         __syncwarp();
@@ -689,6 +726,17 @@ __device__ __forceinline__ void load_bands(const InvParams& p, int vi, int jb, b
         const BT* hl = coef + re * p.coef_pitch + p.wq + jb;
         const BT* lh = coef + (p.hq + ro) * p.coef_pitch + jb;
         const BT* hh = lh + p.wq;
+        if constexpr (CHECKED_BUILD) {
+            const bool ok =
+                (p.ll_is_ct ? dev_in_rect(p.status, reinterpret_cast<const CT*>(p.ll) + re * p.ll_pitch + jb,
+                                          reinterpret_cast<const CT*>(p.ll), p.ll_pitch, p.hq, p.wq, QL)
+                            : dev_in_rect(p.status, reinterpret_cast<const BT*>(p.ll) + re * p.ll_pitch + jb,
+                                          reinterpret_cast<const BT*>(p.ll), p.ll_pitch, p.hq, p.wq, QL)) &&
+                dev_in_rect(p.status, hl, coef + p.wq, p.coef_pitch, p.hq, p.wh, QL) &&
+                dev_in_rect(p.status, lh, coef + int64_t(p.hq) * p.coef_pitch, p.coef_pitch, p.hh, p.wq, QL) &&
+                dev_in_rect(p.status, hh, coef + int64_t(p.hq) * p.coef_pitch + p.wq, p.coef_pitch, p.hh, p.wh, QL);
+            if (!ok) return;  // the row keeps its previous values; the status word has DEV_CHECK
+        }
 #pragma unroll
         for (int q = 0; q < QL; q += 2) {
             if (p.ll_is_ct) {
@@ -716,7 +764,10 @@ __device__ __forceinline__ void load_bands(const InvParams& p, int vi, int jb, b
         re = rev ? vi : 0;
         ro = rov ? vi : 0;
     }
-    // defensive clamps keep every address inside the bands
+    // defensive clamps keep every address inside the bands (the checked build
+    // reports a row that needed one)
+    dev_in(p.status, !rev || (re >= 0 && re < p.hq));
+    dev_in(p.status, !rov || (ro >= 0 && ro < p.hh));
     re = min(max(re, 0), p.hq - 1);
     ro = min(max(ro, 0), max(p.hh - 1, 0));
 #pragma unroll
@@ -734,6 +785,8 @@ __device__ __forceinline__ void load_bands(const InvParams& p, int vi, int jb, b
             ce = cev ? j : 0;
             co = cov ? j : 0;
         }
+        dev_in(p.status, !cev || (ce >= 0 && ce < p.wq));
+        dev_in(p.status, !cov || (co >= 0 && co < p.wh));
         ce = min(max(ce, 0), p.wq - 1);
         co = min(max(co, 0), max(p.wh - 1, 0));
         CT v1, v2, v3, v4;
@@ -820,20 +873,25 @@ __device__ __forceinline__ void inv_unit(const InvParams& p, int s, int R0, int 
             if (oi < R0 || oi >= R1) return;
             CT* row_o = row_e + p.out_pitch;
             const bool has_o = 2 * oi + 1 < p.h;
+            const CT* out0 = reinterpret_cast<const CT*>(p.out);
 #pragma unroll
             for (int q = 0; q < QL; q += 2) {
                 const int c = px + 2 * q;
                 if (mine[q] && mine[q + 1] && p.vec_out && c + 3 < p.w) {
-                    st4<CT>(row_e + c, out.c1[q], out.c2[q], out.c1[q + 1], out.c2[q + 1]);
-                    if (has_o) st4<CT>(row_o + c, out.c3[q], out.c4[q], out.c3[q + 1], out.c4[q + 1]);
+                    if (dev_in_rect(p.status, row_e + c, out0, p.out_pitch, p.h, p.w, 4))
+                        st4<CT>(row_e + c, out.c1[q], out.c2[q], out.c1[q + 1], out.c2[q + 1]);
+                    if (has_o && dev_in_rect(p.status, row_o + c, out0, p.out_pitch, p.h, p.w, 4))
+                        st4<CT>(row_o + c, out.c3[q], out.c4[q], out.c3[q + 1], out.c4[q + 1]);
                 } else {
                     const CT ev[4] = {out.c1[q], out.c2[q], out.c1[q + 1], out.c2[q + 1]};
                     const CT od[4] = {out.c3[q], out.c4[q], out.c3[q + 1], out.c4[q + 1]};
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
                         if (mine[q + (k >> 1)] && c + k < p.w) {
-                            row_e[c + k] = ev[k];
-                            if (has_o) row_o[c + k] = od[k];
+                            if (dev_in_rect(p.status, row_e + c + k, out0, p.out_pitch, p.h, p.w, 1))
+                                row_e[c + k] = ev[k];
+                            if (has_o && dev_in_rect(p.status, row_o + c + k, out0, p.out_pitch, p.h, p.w, 1))
+                                row_o[c + k] = od[k];
                         }
                     }
                 }
@@ -887,13 +945,19 @@ constexpr size_t inv_smem_bytes() {
 __device__ __forceinline__ void adj_route_store(const InvParams& p, float* img_row, int r, int c, float v) {
     if (c < -4 || c >= p.w + 4 || r < -4 || r >= p.h + 4) return;
     const bool rin = (r >= 0) && (r < p.h), cin = (c >= 0) && (c < p.w);
+    const int64_t side_len = adj_side_floats(p.h, p.w);
+    float* dst;
     if (rin && cin) {
-        img_row[c] = v;
+        dst = img_row + c;
+        if (!dev_in_rect(p.status, dst, static_cast<float*>(p.out), p.out_pitch, p.h, p.w, 1)) return;
     } else if (!cin) {  // extended column (corners too)
-        p.side[(r + 4) * 8 + (c < 0 ? c + 4 : 4 + c - p.w)] = v;
+        dst = p.side + (r + 4) * 8 + (c < 0 ? c + 4 : 4 + c - p.w);
+        if (!dev_in_span(p.status, dst, p.side, side_len, 1)) return;
     } else {  // extended row inside the columns
-        p.side[int64_t(8) * (p.h + 8) + int64_t(r < 0 ? r + 4 : 4 + r - p.h) * p.w + c] = v;
+        dst = p.side + int64_t(8) * (p.h + 8) + int64_t(r < 0 ? r + 4 : 4 + r - p.h) * p.w + c;
+        if (!dev_in_span(p.status, dst, p.side, side_len, 1)) return;
     }
+    *dst = v;
 }
 
 // Stores of the adjoint units: plain (every output inside the image), routed
@@ -938,6 +1002,12 @@ __device__ __forceinline__ void adj_edge_store(const InvParams& p, float* img_ro
 #pragma unroll
         for (int k = 0; k < 4; ++k) adj_route_store(p, img_row, r, px + k, v[k]);
         return;
+    }
+    if constexpr (CHECKED_BUILD) {
+        const bool ok = (cc == CC_IN && rin)
+                            ? dev_in_rect(p.status, dst, static_cast<const float*>(p.out), p.out_pitch, p.h, p.w, 4)
+                            : dev_in_span(p.status, dst, p.side, adj_side_floats(p.h, p.w), 4);
+        if (!ok) return;
     }
     if (vec) {
         st4<float>(dst, v[0], v[1], v[2], v[3]);
@@ -1032,6 +1102,15 @@ __device__ __forceinline__ bool inv_unit_staged(const InvParams& p, int s, int R
     }
     // every output lane's four columns inside the image (warp-uniform)
     const bool cols_in = ROUTE == ROUTE_EDGE && __all_sync(0xffffffffu, cc == CC_IN || cc == CC_DROP);
+    // checked build: the bands as rectangles (LL hq x wq, HL hq x wh, LH hh x
+    // wq, HH hh x wh) and the output image (h x w) that every access must fall in
+    const CT* ll0c = reinterpret_cast<const CT*>(p.ll);
+    const BT* ll0b = reinterpret_cast<const BT*>(p.ll);
+    const BT* hl0 = coef + p.wq;
+    const BT* lh0 = coef + int64_t(p.hq) * p.coef_pitch;
+    const BT* hh0 = lh0 + p.wq;
+    const CT* out0 = reinterpret_cast<const CT*>(p.out);
+    (void)ll0c, (void)ll0b, (void)hl0, (void)lh0, (void)hh0, (void)out0;
     auto issue = [&](int t, int slot) {
         unsigned char* st = ring + slot * STAGEB;
 #pragma unroll
@@ -1059,32 +1138,62 @@ __device__ __forceinline__ bool inv_unit_staged(const InvParams& p, int s, int R
                 const BT* hhr = lhr + p.wq;
 #pragma unroll
                 for (int q = 0; q < 2; ++q) {
-                    cp_async_small<4>(d + lane * 8 + q * 4, llr + ce[q], rev && cev[q]);
-                    cp_async_small<4>(d + BAND + lane * 8 + q * 4, hlr + co[q], rev && cov[q]);
-                    cp_async_small<4>(d + 2 * BAND + lane * 8 + q * 4, lhr + ce[q], rov && cev[q]);
-                    cp_async_small<4>(d + 3 * BAND + lane * 8 + q * 4, hhr + co[q], rov && cov[q]);
+                    bool v_ll = rev && cev[q], v_hl = rev && cov[q], v_lh = rov && cev[q], v_hh = rov && cov[q];
+                    if constexpr (CHECKED_BUILD) {
+                        v_ll = v_ll && dev_in_rect(p.status, llr + ce[q], ll0c, p.ll_pitch, p.hq, p.wq, 1);
+                        v_hl = v_hl && dev_in_rect(p.status, hlr + co[q], hl0, p.coef_pitch, p.hq, p.wh, 1);
+                        v_lh = v_lh && dev_in_rect(p.status, lhr + ce[q], lh0, p.coef_pitch, p.hh, p.wq, 1);
+                        v_hh = v_hh && dev_in_rect(p.status, hhr + co[q], hh0, p.coef_pitch, p.hh, p.wh, 1);
+                    }
+                    cp_async_small<4>(d + lane * 8 + q * 4, llr + ce[q], v_ll);
+                    cp_async_small<4>(d + BAND + lane * 8 + q * 4, hlr + co[q], v_hl);
+                    cp_async_small<4>(d + 2 * BAND + lane * 8 + q * 4, lhr + ce[q], v_lh);
+                    cp_async_small<4>(d + 3 * BAND + lane * 8 + q * 4, hhr + co[q], v_hh);
                 }
             } else if constexpr (ROUTE == ROUTE_EDGE) {
                 const void* llr = p.ll_is_ct ? static_cast<const void*>(reinterpret_cast<const CT*>(p.ll) +
                                                                          int64_t(re) * p.ll_pitch + je)
                                              : static_cast<const void*>(reinterpret_cast<const BT*>(p.ll) +
                                                                          int64_t(re) * p.ll_pitch + je);
-                cp_async_n8(d + lane * 8, llr, rev ? nbe : 0);
-                cp_async_n8(d + BAND + lane * 8, coef + int64_t(re) * p.coef_pitch + p.wq + jo, rev ? nbo : 0);
-                cp_async_n8(d + 2 * BAND + lane * 8, coef + int64_t(p.hq + ro) * p.coef_pitch + je, rov ? nbe : 0);
-                cp_async_n8(d + 3 * BAND + lane * 8, coef + int64_t(p.hq + ro) * p.coef_pitch + p.wq + jo,
-                            rov ? nbo : 0);
+                const BT* hlr = coef + int64_t(re) * p.coef_pitch + p.wq + jo;
+                const BT* lhr = coef + int64_t(p.hq + ro) * p.coef_pitch + je;
+                const BT* hhr = coef + int64_t(p.hq + ro) * p.coef_pitch + p.wq + jo;
+                int n_ll = rev ? nbe : 0, n_hl = rev ? nbo : 0, n_lh = rov ? nbe : 0, n_hh = rov ? nbo : 0;
+                if constexpr (CHECKED_BUILD) {
+                    const bool ll_ok = p.ll_is_ct ? dev_in_rect(p.status, static_cast<const CT*>(llr), ll0c, p.ll_pitch,
+                                                                p.hq, p.wq, n_ll / 4)
+                                                  : dev_in_rect(p.status, static_cast<const BT*>(llr), ll0b, p.ll_pitch,
+                                                                p.hq, p.wq, n_ll / 4);
+                    n_ll = (n_ll == 0 || ll_ok) ? n_ll : 0;
+                    n_hl = (n_hl == 0 || dev_in_rect(p.status, hlr, hl0, p.coef_pitch, p.hq, p.wh, n_hl / 4)) ? n_hl : 0;
+                    n_lh = (n_lh == 0 || dev_in_rect(p.status, lhr, lh0, p.coef_pitch, p.hh, p.wq, n_lh / 4)) ? n_lh : 0;
+                    n_hh = (n_hh == 0 || dev_in_rect(p.status, hhr, hh0, p.coef_pitch, p.hh, p.wh, n_hh / 4)) ? n_hh : 0;
+                }
+                cp_async_n8(d + lane * 8, llr, n_ll);
+                cp_async_n8(d + BAND + lane * 8, hlr, n_hl);
+                cp_async_n8(d + 2 * BAND + lane * 8, lhr, n_lh);
+                cp_async_n8(d + 3 * BAND + lane * 8, hhr, n_hh);
             } else {
+                const CT* llc = reinterpret_cast<const CT*>(p.ll) + int64_t(re) * p.ll_pitch + jb;
+                const BT* llb = reinterpret_cast<const BT*>(p.ll) + int64_t(re) * p.ll_pitch + jb;
+                const BT* hlr = coef + int64_t(re) * p.coef_pitch + p.wq + jb;
+                const BT* lhr = coef + int64_t(p.hq + ro) * p.coef_pitch + jb;
+                const BT* hhr = coef + int64_t(p.hq + ro) * p.coef_pitch + p.wq + jb;
+                bool v_ll = rev, v_hl = rev, v_lh = rov, v_hh = rov;
+                if constexpr (CHECKED_BUILD) {
+                    v_ll = v_ll && (p.ll_is_ct ? dev_in_rect(p.status, llc, ll0c, p.ll_pitch, p.hq, p.wq, 2)
+                                               : dev_in_rect(p.status, llb, ll0b, p.ll_pitch, p.hq, p.wq, 2));
+                    v_hl = v_hl && dev_in_rect(p.status, hlr, hl0, p.coef_pitch, p.hq, p.wh, 2);
+                    v_lh = v_lh && dev_in_rect(p.status, lhr, lh0, p.coef_pitch, p.hh, p.wq, 2);
+                    v_hh = v_hh && dev_in_rect(p.status, hhr, hh0, p.coef_pitch, p.hh, p.wh, 2);
+                }
                 if (p.ll_is_ct)
-                    cp_async_small<8>(d + lane * 8, reinterpret_cast<const CT*>(p.ll) + int64_t(re) * p.ll_pitch + jb,
-                                      rev);
+                    cp_async_small<8>(d + lane * 8, llc, v_ll);
                 else
-                    cp_async_small<PB>(d + lane * PB,
-                                       reinterpret_cast<const BT*>(p.ll) + int64_t(re) * p.ll_pitch + jb, rev);
-                cp_async_small<PB>(d + BAND + lane * PB, coef + int64_t(re) * p.coef_pitch + p.wq + jb, rev);
-                cp_async_small<PB>(d + 2 * BAND + lane * PB, coef + int64_t(p.hq + ro) * p.coef_pitch + jb, rov);
-                cp_async_small<PB>(d + 3 * BAND + lane * PB, coef + int64_t(p.hq + ro) * p.coef_pitch + p.wq + jb,
-                                   rov);
+                    cp_async_small<PB>(d + lane * PB, llb, v_ll);
+                cp_async_small<PB>(d + BAND + lane * PB, hlr, v_hl);
+                cp_async_small<PB>(d + 2 * BAND + lane * PB, lhr, v_lh);
+                cp_async_small<PB>(d + 3 * BAND + lane * PB, hhr, v_hh);
             }
         }
         asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&bars[slot]))
@@ -1136,7 +1245,10 @@ __device__ __forceinline__ bool inv_unit_staged(const InvParams& p, int s, int R
             if constexpr (ROUTE == ROUTE_EDGE) {
                 if (oi >= R0 && oi < R1) {
                     if (cols_in && oi >= 0 && 2 * oi + 1 < p.h) {  // warp-uniform
-                        if (cc == CC_IN) {
+                        if (cc == CC_IN && (!CHECKED_BUILD ||
+                                            (dev_in_rect(p.status, row_e + px, out0, p.out_pitch, p.h, p.w, 4) &&
+                                             dev_in_rect(p.status, row_e + p.out_pitch + px, out0, p.out_pitch, p.h,
+                                                         p.w, 4)))) {
                             CT* row_o = row_e + p.out_pitch;
                             if (p.vec_out) {
                                 st4<CT>(row_e + px, out.c1[0], out.c2[0], out.c1[1], out.c2[1]);
@@ -1175,16 +1287,20 @@ __device__ __forceinline__ bool inv_unit_staged(const InvParams& p, int s, int R
                 CT* row_o = row_e + p.out_pitch;
                 const bool has_o = 2 * oi + 1 < p.h;
                 if (mine && p.vec_out && px + 3 < p.w) {
-                    st4<CT>(row_e + px, out.c1[0], out.c2[0], out.c1[1], out.c2[1]);
-                    if (has_o) st4<CT>(row_o + px, out.c3[0], out.c4[0], out.c3[1], out.c4[1]);
+                    if (dev_in_rect(p.status, row_e + px, out0, p.out_pitch, p.h, p.w, 4))
+                        st4<CT>(row_e + px, out.c1[0], out.c2[0], out.c1[1], out.c2[1]);
+                    if (has_o && dev_in_rect(p.status, row_o + px, out0, p.out_pitch, p.h, p.w, 4))
+                        st4<CT>(row_o + px, out.c3[0], out.c4[0], out.c3[1], out.c4[1]);
                 } else if (mine) {
                     const CT ev[4] = {out.c1[0], out.c2[0], out.c1[1], out.c2[1]};
                     const CT od[4] = {out.c3[0], out.c4[0], out.c3[1], out.c4[1]};
 #pragma unroll
                     for (int k2 = 0; k2 < 4; ++k2) {
                         if (px + k2 < p.w) {
-                            row_e[px + k2] = ev[k2];
-                            if (has_o) row_o[px + k2] = od[k2];
+                            if (dev_in_rect(p.status, row_e + px + k2, out0, p.out_pitch, p.h, p.w, 1))
+                                row_e[px + k2] = ev[k2];
+                            if (has_o && dev_in_rect(p.status, row_o + px + k2, out0, p.out_pitch, p.h, p.w, 1))
+                                row_o[px + k2] = od[k2];
                         }
                     }
                 }
@@ -1283,7 +1399,9 @@ __global__ void __launch_bounds__(NW * 32, InvMinBlocks<Pipe, CLS>::value) inv_k
     for (int lu = blockIdx.x * NW + warp; lu < n; lu += gridDim.x * NW) {
         int s, R0, R1;
         if (!inv_unit_rows(p, CLS, lu, s, R0, R1)) continue;
-        if (!inv_unit_any<Pipe, BT, ADJ, INV_QR, INV_NST, CLS>(p, s, R0, R1, lane, ring, bars, gstage)) return;
+        if (!inv_unit_any<Pipe, BT, ADJ, INV_QR, INV_NST, CLS>(p, s, R0, R1, lane, ring, bars, gstage) ||
+            dev_check_tripped(p.status))
+            return;
     }
 }
 
@@ -1310,7 +1428,9 @@ __global__ void __launch_bounds__(NW * 32, InvMinBlocks<Pipe, CLS>::value)
         const InvParams& p = L.img[lo].p;
         int s, R0, R1;
         if (!inv_unit_rows(p, CLS, u - L.img[lo].u_begin[CLS], s, R0, R1)) continue;
-        if (!inv_unit_any<Pipe, BT, ADJ, INV_QR, INV_NST, CLS>(p, s, R0, R1, lane, ring, bars, gstage)) return;
+        if (!inv_unit_any<Pipe, BT, ADJ, INV_QR, INV_NST, CLS>(p, s, R0, R1, lane, ring, bars, gstage) ||
+            dev_check_tripped(p.status))
+            return;
     }
 }
 
@@ -1332,6 +1452,10 @@ __device__ __forceinline__ void adj_fold_pixel(const InvParams& p, int r, int c)
     const float* L = p.side;
     const float* T = p.side + int64_t(8) * (p.h + 8);
     float* o = reinterpret_cast<float*>(p.out) + int64_t(r) * p.out_pitch + c;
+    if (!dev_in_rect(p.status, o, static_cast<const float*>(p.out), p.out_pitch, p.h, p.w, 1)) return;
+    if constexpr (CHECKED_BUILD) {  // every side slot read below lies in the side buffer
+        if (!dev_in(p.status, r >= 0 && r < p.h && c >= 0 && c < p.w)) return;
+    }
     if (p.h > 10 && p.w > 10) {  // at most one source of each kind
         const int kc = adj_mirror_slot(c, p.w), kr = adj_mirror_slot(r, p.h);
         float acc = 0.f;

@@ -30,6 +30,25 @@ def test_exports_every_declared_function(lib):
         assert isinstance(getattr(lib, n), ctypes._CFuncPtr)
 
 
+def test_checked_build_exports_the_same_functions(lib):
+    """libdwt2_checked.so (DWT2_CHECKED, built by build_all() or by its GPU
+    test) exports every declared function and says it is the checked build;
+    the normal library says it is not (a child process loads the checked one:
+    the library is chosen per process)."""
+    import subprocess
+    import sys
+    assert lib.dwt2_checked() == 0
+    if not build.up_to_date(checked=True):
+        pytest.skip("libdwt2_checked.so not built here (build.build_all())")
+    code = ("from paper_1704_08657_gb300 import abi; l = abi.load(); "
+            "[getattr(l, n) for n in abi.EXPORTS]; print(l.dwt2_checked(), abi.LIB_PATH)")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True,
+                       env=dict(os.environ, DWT2_LIBRARY="checked"), timeout=300)
+    assert r.returncode == 0, r.stderr
+    flag, path = r.stdout.split()
+    assert flag == "1" and path.endswith("libdwt2_checked.so")
+
+
 def test_strerror_names_every_code(lib):
     for code in (0, -1, -2, -3, -4, -5, -6, -7, -8):
         assert abi.dwt2_strerror(code) and abi.dwt2_strerror(code) != "unknown error"
