@@ -165,7 +165,10 @@ typedef struct {
  * levels without programmatic dependent launch), DWT2_FUSE_SEG and
  * DWT2_FUSE_PAIRS (run level pairs 0-1, 2-3, ... in one fused launch with that
  * segment height; off by default, slower on GB300), DWT2_PML_SEG_ROWS,
- * DWT2_PML_LAG_PCT and DWT2_PML_CPASYNC (persistent forward).
+ * DWT2_PML_LAG_PCT and DWT2_PML_CPASYNC (persistent forward),
+ * DWT2_INV_EDGE_FIRST (1 / 0: an inverse or adjoint level launches its edge
+ * units before / after its inner units; default: before for the adjoint,
+ * after for the inverse).
  */
 int dwt2_plan(dwt2_plan_t* out, int wavelet, int levels, int boundary, int in_dtype,
               int coef_dtype, int scheme, int n_images, const dwt2_image_desc* images,
@@ -229,12 +232,13 @@ int dwt2_adjoint_l1_dev(dwt2_plan_t plan, const void* coef, void* in_grad, const
 /* dwt2_autotune -- choose the plan's launch configuration (not in the paper).
  * With *choice < 0: run the forward on the given buffers (same arguments as
  * dwt2_forward) for each candidate configuration (kernel tile shape and
- * segment height; segment height for persistent plans), a few calls each on
+ * segment height; segment height and queue lag for persistent plans), a few calls each on
  * the stream timed per level with the plan's profile events, keep the fastest
  * candidate of every level (of the whole launch for persistent plans) and
  * store the choice in *choice: 6 bits per level for the first five levels,
- * deeper levels sharing the fifth field (persistent plans and plans of
- * several images: the index of one segment height for every level).  With *choice >= 0: apply that choice without timing (e.g. from a
+ * deeper levels sharing the fifth field (persistent plans: one index 0-11,
+ * segment height 16/24/32/48 times queue lag 300/500/800 % of a GPU round of
+ * units).  With *choice >= 0: apply that choice without timing (e.g. from a
  * cache of an earlier run on the same GPU); DWT2_ERR_INVALID_ARG if it is not
  * a valid choice for this plan.  The coefficient buffer is overwritten and the
  * plan's profile ring is reset.  Synchronises the stream; not for use during

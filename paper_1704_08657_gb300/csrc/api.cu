@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <array>
 #include <memory>
 #include <mutex>
 #include <new>
@@ -153,6 +154,7 @@ struct dwt2_plan_s {
     int device, sm_count;
     int cfg_env, seg_env;           // DWT2_FWD_CFG, DWT2_SEG_ROWS
     int edge_split_env;             // DWT2_EDGE_SPLIT: pieces per inverse / adjoint edge unit
+    int inv_edge_first;             // DWT2_INV_EDGE_FIRST: 1 / 0 edge units before / after a level's inner units, -1 adjoint first
     int cfg_bps[N_FWD_CFGS];        // resident blocks per SM of each forward configuration
     std::vector<int> lvl_cand;      // per level: tuning candidate, or -1 for cfg_env / seg_env
     int inv_bps;                    // resident blocks per SM of the inverse kernel
@@ -440,6 +442,18 @@ int inv_group_seg(const std::vector<InvParams>& ps, int64_t max_warps, int seg_e
     return best;
 }
 
+// Launch order of a level's two unit classes (measured, not derived): the
+// adjoint's edge units (routed stores, zero-filled copies, ~10 % of a level's
+// units at 4096^2) launched before its inner units made the 16 x 4096^2 L1
+// adjoint 2 % faster; the inverse's were 2 % faster after them (16384^2,
+// 5 levels).  The first launch is a plain launch, the second a programmatic
+// dependent that starts once the first has placed all its blocks.
+std::array<int, 2> inv_class_order(dwt2_plan_t p, bool adj) {
+    const bool edge_first = p->inv_edge_first < 0 ? adj : p->inv_edge_first != 0;
+    if (edge_first) return {UNITS_EDGE, UNITS_INNER};
+    return {UNITS_INNER, UNITS_EDGE};
+}
+
 int inv_group_build(dwt2_plan_t p, const void* coef, void* out, void* workspace, bool adj) {
     auto& ic = p->icache;
     ic.blocks.clear();
@@ -523,10 +537,11 @@ int inverse_grouped(dwt2_plan_t p, const void* coef, void* out, void* workspace,
         }
         const int l = ic.level[b];
         if (b == 0 || ic.level[b - 1] != l) prof_mark(p, l, true, s);
-        // the inner units, then the edge units; the level's first launch is a
-        // plain launch, the others programmatic dependents (inv_group_kernel)
+        // the two unit classes in inv_class_order; the level's first launch
+        // is a plain launch, the others programmatic dependents
+        // (inv_group_kernel)
         bool first = g.first != 0;
-        for (int cls : {UNITS_INNER, UNITS_EDGE}) {
+        for (int cls : inv_class_order(p, adj)) {
             const int grid = cls == UNITS_EDGE ? ic.grid_edge[b] : ic.grid[b];
             if (grid == 0) continue;
             const int pdl = first ? 0 : 1;
@@ -991,6 +1006,7 @@ int dwt2_plan(dwt2_plan_t* out, int wavelet, int levels, int boundary, int in_dt
     p->timeout_ns = uint64_t(env_int("DWT2_TIMEOUT_MS", 2000)) * 1000000ull;
     p->seg_env = env_int("DWT2_SEG_ROWS", 0);
     p->edge_split_env = env_int("DWT2_EDGE_SPLIT", 0);
+    p->inv_edge_first = std::max(-1, std::min(1, env_int("DWT2_INV_EDGE_FIRST", -1)));
     p->pdl = env_int("DWT2_PDL", 1) != 0;
     p->overlap = env_int("DWT2_LEVEL_OVERLAP", 1) != 0;
     p->d_lvl_ctr = nullptr;
@@ -1175,10 +1191,10 @@ static int run_inverse_like(dwt2_plan_t p, const void* coef, void* out, void* wo
             inv_inner_rect(ipm, p->wavelet, adj);
             ipm.edge_split = inv_edge_pieces(ipm.seg_rows, inv_class_units(ipm, UNITS_EDGE),
                                              int64_t(p->sm_count) * std::max(inv_bps, 1) * INV_NW, p->edge_split_env);
-            // the inner units, then (a programmatic dependent: no shared data)
-            // the edge units
+            // the two unit classes in inv_class_order, the second a
+            // programmatic dependent of the first (no shared data)
             bool first = true;
-            for (int cls : {UNITS_INNER, UNITS_EDGE}) {
+            for (int cls : inv_class_order(p, adj)) {
                 const int units = inv_class_units(ipm, cls);
                 if (units == 0) continue;
                 const int g = (units + INV_NW - 1) / INV_NW, pdl = first ? 0 : 1;
@@ -1211,9 +1227,14 @@ static int run_inverse_like(dwt2_plan_t p, const void* coef, void* out, void* wo
 // the plan's profile events and keep, level by level, the fastest candidate
 // (the launches of different levels are independent).  The choice packs
 // TUNE_BITS bits per level for the first TUNE_LEVELS levels; deeper levels use
-// the last field.  Persistent plans try a few segment heights.
+// the last field.  Persistent plans try a few segment heights and queue lags.
 static const int TUNE_PML_SEGS[] = {16, 24, 32, 48};
-constexpr int N_TUNE_PML = int(sizeof(TUNE_PML_SEGS) / sizeof(TUNE_PML_SEGS[0]));
+constexpr int N_TUNE_PML_SEGS = int(sizeof(TUNE_PML_SEGS) / sizeof(TUNE_PML_SEGS[0]));
+// queue lag of the persistent order, in percent of one GPU round of units: a
+// longer lag means fewer waits on counters and less L2 reuse of the low-low
+// band (the 512-image batch measured 0.600 ms at 300, 0.577 at 500)
+static const int TUNE_PML_LAGS[] = {300, 500, 800};
+constexpr int N_TUNE_PML = N_TUNE_PML_SEGS * int(sizeof(TUNE_PML_LAGS) / sizeof(TUNE_PML_LAGS[0]));
 // Fused level pairs are not among the candidates: on 16384^2 they measured
 // 2.3x slower than the two per-level launches (the row pipeline is bound by
 // instruction issue as much as by DRAM, and the fused kernel executes ~1.5x
@@ -1231,7 +1252,8 @@ static int tune_apply(dwt2_plan_t p, int choice) {
     if (choice < 0) return DWT2_ERR_INVALID_ARG;
     if (tune_seg_only(p)) {
         if (choice >= N_TUNE_PML) return DWT2_ERR_INVALID_ARG;
-        p->pml_seg = TUNE_PML_SEGS[choice];
+        p->pml_seg = TUNE_PML_SEGS[choice % N_TUNE_PML_SEGS];
+        p->pml_lag_pct = TUNE_PML_LAGS[choice / N_TUNE_PML_SEGS];
         return build_persistent(p);
     }
     const int nf = tune_fields(p);

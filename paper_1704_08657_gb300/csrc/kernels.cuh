@@ -1381,10 +1381,11 @@ __device__ __forceinline__ bool inv_unit_rows(const InvParams& p, int cls, int l
 }
 
 // Launch order.  The first launch of a level (the inner units of its first
-// group of images) is a plain launch: stream order completes everything before
-// it.  The level's later launches (the edge units, later groups) share no data
-// with the launches before them and are programmatic dependents that start as
-// soon as those have placed all their blocks; none of them waits on the device.
+// group of images for the inverse, the edge units for the adjoint) is a
+// plain launch: stream order completes everything before it.  The level's
+// later launches (the other unit class, later groups) share no data with the
+// launches before them and are programmatic dependents that start as soon as
+// those have placed all their blocks; none of them waits on the device.
 // One level of one image: the units of class CLS, dealt round-robin.
 template <class Pipe, class BT, bool ADJ, int QL, int NW, int CLS>
 __global__ void __launch_bounds__(NW * 32, InvMinBlocks<Pipe, CLS>::value) inv_kernel(const InvParams p) {
