@@ -95,7 +95,7 @@ def kernel_hash() -> str:
 
 
 TUNE_SEGS = (0, 2, 4, 8, 12, 16, 24, 32)  # candidate segment heights of dwt2_autotune
-FWD_CFGS = ((2, 3, 3, 4, 0), (2, 2, 4, 4, 0), (2, 2, 4, 8, 0), (2, 2, 4, 8, 1))  # (ql, qr, nst, nw, spec)
+FWD_CFGS = ((2, 3, 3, 4, 0), (2, 2, 4, 4, 0), (2, 2, 4, 8, 0), (2, 2, 4, 8, 1), (2, 2, 4, 4, 1))  # (ql, qr, nst, nw, spec)
 TUNE_BITS, TUNE_LEVELS = 6, 5
 
 

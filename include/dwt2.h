@@ -160,7 +160,7 @@ typedef struct {
  * tables on the current device.
  * Environment, read when the plan is made (launch tuning only; results do not
  * depend on it): DWT2_TIMEOUT_MS (bounded device waits, default 2000),
- * DWT2_FWD_CFG and DWT2_SEG_ROWS (forward kernel configuration 0-3 and
+ * DWT2_FWD_CFG and DWT2_SEG_ROWS (forward kernel configuration 0-4 and
  * segment height before any dwt2_autotune), DWT2_PDL (0 launches the forward
  * levels without programmatic dependent launch), DWT2_FUSE_SEG and
  * DWT2_FUSE_PAIRS (run level pairs 0-1, 2-3, ... in one fused launch with that

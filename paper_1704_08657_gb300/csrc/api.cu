@@ -1358,7 +1358,9 @@ int dwt2_autotune(dwt2_plan_t p, const void* in, void* coef, void* workspace, vo
             // With inter-level overlap the fastest pyramid need not be made of
             // the fastest levels: time the per-level choice, the default, the
             // per-level choice on the first levels only and the best uniform
-            // candidates end to end, overlap on.
+            // candidates (also with the first level's own fastest candidate)
+            // and every configuration with automatic segment heights end to
+            // end, overlap on, then refine the fastest field by field.
             std::vector<int> cands = {best, 0};
             // the per-level choice for the first k fields, the default after them
             for (int k = 1; k < nf; ++k) cands.push_back(best & ((1 << (k * TUNE_BITS)) - 1));
@@ -1369,21 +1371,75 @@ int dwt2_autotune(dwt2_plan_t p, const void* in, void* coef, void* workspace, vo
                 tot.push_back({t, c});
             }
             std::sort(tot.begin(), tot.end());
+            const int mask0 = (1 << TUNE_BITS) - 1;
             for (int k = 0; k < 3 && k < int(tot.size()); ++k) {
                 int u = 0;
                 for (int f = 0; f < nf; ++f) u |= tot[k].second << (f * TUNE_BITS);
                 cands.push_back(u);
+                // the same with the first level's own fastest candidate
+                cands.push_back((u & ~mask0) | (best & mask0));
             }
-            float best_ms = 0.f;
-            int best_c = best;
-            for (size_t k = 0; k < cands.size() && rc == DWT2_OK; ++k) {
-                rc = tune_apply(p, cands[k]);
-                float t = 0.f;
-                if (rc == DWT2_OK) rc = time_whole_call(p, in, coef, workspace, stream, &t);
-                if (rc == DWT2_OK && (k == 0 || t < best_ms)) best_ms = t, best_c = cands[k];
+            // every configuration with the automatic segment height on every level
+            for (int ci = 0; ci < N_FWD_CFGS; ++ci) {
+                if (!cand_compiled(p, ci * N_TUNE_SEGS)) continue;
+                int u = 0;
+                for (int f = 0; f < nf; ++f) u |= (ci * N_TUNE_SEGS) << (f * TUNE_BITS);
+                cands.push_back(u);
+            }
+            std::sort(cands.begin(), cands.end());
+            cands.erase(std::unique(cands.begin(), cands.end()), cands.end());
+            // interleaved rounds: every candidate is timed once per round and
+            // keeps its best round, so that a drift of clocks or L2 contents
+            // during tuning favours none of them
+            std::vector<float> cand_ms(cands.size(), 0.f);
+            for (int r = 0; r < 4 && rc == DWT2_OK; ++r) {
+                for (size_t k = 0; k < cands.size() && rc == DWT2_OK; ++k) {
+                    rc = tune_apply(p, cands[k]);
+                    float t = 0.f;
+                    if (rc == DWT2_OK) rc = time_whole_call(p, in, coef, workspace, stream, &t);
+                    if (rc == DWT2_OK && (r == 0 || t < cand_ms[k])) cand_ms[k] = t;
+                }
             }
             if (rc != DWT2_OK) return rc;
-            best = best_c;
+            size_t kb = 0;
+            for (size_t k = 1; k < cands.size(); ++k)
+                if (cand_ms[k] < cand_ms[kb]) kb = k;
+            best = cands[kb];
+            // Coordinate descent, end to end: each field in turn tries its
+            // four fastest per-level candidates and every configuration with
+            // the automatic segment height, the others fixed; a change is kept
+            // when the whole pyramid gets faster by more than 0.2 %.  A second
+            // pass runs when the first changed anything.
+            float cur = cand_ms[kb];
+            bool changed = true;
+            for (int pass = 0; pass < 2 && changed && rc == DWT2_OK; ++pass) {
+            changed = false;
+            for (int f = 0; f < nf && rc == DWT2_OK; ++f) {
+                const int l_end = (f == nf - 1) ? L : f + 1;
+                std::vector<std::pair<float, int>> lv;
+                for (int c = 0; c < n_cand; ++c) {
+                    float t = 0.f;
+                    for (int l = f; l < l_end; ++l) t += ms[size_t(c) * L + l];
+                    if (t < 1e29f) lv.push_back({t, c});
+                }
+                std::sort(lv.begin(), lv.end());
+                std::vector<int> alts;
+                for (size_t k = 0; k < 4 && k < lv.size(); ++k) alts.push_back(lv[k].second);
+                for (int ci = 0; ci < N_FWD_CFGS; ++ci)
+                    if (cand_compiled(p, ci * N_TUNE_SEGS)) alts.push_back(ci * N_TUNE_SEGS);
+                const int shift = f * TUNE_BITS;
+                for (int a : alts) {
+                    if (((best >> shift) & mask0) == a) continue;
+                    const int c = (best & ~(mask0 << shift)) | (a << shift);
+                    float t = 0.f;
+                    rc = tune_apply(p, c);
+                    if (rc == DWT2_OK) rc = time_whole_call(p, in, coef, workspace, stream, &t);
+                    if (rc != DWT2_OK) break;
+                    if (t < cur * 0.998f) cur = t, best = c, changed = true;
+                }
+            }
+            }
+            if (rc != DWT2_OK) return rc;
         }
     }
     *choice = best;

@@ -306,7 +306,7 @@ int inverse_blocks_per_sm(int wav, int scheme, int coef_dtype, bool adjoint);  /
 
 // the forward configurations compiled in (index 0 is the default); one with
 // no resident block (forward_blocks_per_sm 0) is skipped by the tuner
-constexpr int N_FWD_CFGS = 4;
+constexpr int N_FWD_CFGS = 5;
 extern const FwdCfg FWD_CFGS[N_FWD_CFGS];
 size_t fwd_smem_bytes_of(const FwdCfg& c);
 // the persistent kernel's fixed configuration

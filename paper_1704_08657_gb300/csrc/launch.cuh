@@ -40,7 +40,7 @@ int launch_fwd_one(const CUtensorMap& box, const CUtensorMap& row, const FwdPara
 
 // the compiled forward configurations (quads per lane, quad rows per stage,
 // stages, warps per block, specialised interior loop); the first is the default
-#define DWT2_FWD_CFG_LIST(X) X(0, 2, 3, 3, 4, 0) X(1, 2, 2, 4, 4, 0) X(2, 2, 2, 4, 8, 0) X(3, 2, 2, 4, 8, 1)
+#define DWT2_FWD_CFG_LIST(X) X(0, 2, 3, 3, 4, 0) X(1, 2, 2, 4, 4, 0) X(2, 2, 2, 4, 8, 0) X(3, 2, 2, 4, 8, 1) X(4, 2, 2, 4, 4, 1)
 
 template <class Pipe, class OutT, int QL, int QR, int NST, int NW, bool SPEC>
 int launch_group_one(const GroupLaunch& g, int grid, int pdl, cudaStream_t s) {

@@ -40,8 +40,8 @@ def test_autotune_keeps_results(tmp_path, flags):
 
 @pytest.mark.parametrize("flags,bad", [(0, 1 << 12), (0, 63), (abi.DWT2_FLAG_PERSISTENT, 99)])
 def test_autotune_rejects_bad_choice(flags, bad):
-    # a two-level plan packs 6 bits per level (32 candidates: 4 configurations x
-    # 8 segment heights): 2^12 or more, or a field of 32 or more, is not one of
+    # a two-level plan packs 6 bits per level (40 candidates: 5 configurations x
+    # 8 segment heights): 2^12 or more, or a field of 40 or more, is not one of
     # its choices
     plan = Plan.single(64, 64, 2, flags=flags)
     x = torch.zeros((64, 64), device="cuda")

@@ -216,7 +216,7 @@ def test_plan_errors_on_gpu():
 
 
 @pytest.mark.parametrize("n,levels", [(128, 1), (256, 1), (384, 1), (512, 1), (2048, 4), (2048, 5)])
-@pytest.mark.parametrize("cfg", ["0", "1", "2", "3"])
+@pytest.mark.parametrize("cfg", ["0", "1", "2", "3", "4"])
 def test_unpadded_pitch_every_configuration(n, levels, cfg, monkeypatch):
     """pitch == width, every compiled kernel configuration: every coefficient
     is written (the output starts as NaN) and matches the oracle."""
