@@ -1266,7 +1266,7 @@ static int tune_apply(dwt2_plan_t p, int choice) {
     return DWT2_OK;
 }
 
-// Mean time of one whole forward call: the smallest of three means of eight
+// Mean time of one whole forward call: the smallest of five means of eight
 // calls, timed with one event pair around each group (no per-level events).
 static int time_whole_call(dwt2_plan_t p, const void* in, void* coef, void* workspace, void* stream, float* ms) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1278,7 +1278,7 @@ static int time_whole_call(dwt2_plan_t p, const void* in, void* coef, void* work
     }
     int rc = DWT2_OK;
     for (int i = 0; i < 2 && rc == DWT2_OK; ++i) rc = dwt2_forward(p, in, coef, workspace, stream);
-    for (int r = 0; r < 3 && rc == DWT2_OK; ++r) {
+    for (int r = 0; r < 5 && rc == DWT2_OK; ++r) {
         cudaEventRecord(e0, s);
         for (int i = 0; i < 8 && rc == DWT2_OK; ++i) rc = dwt2_forward(p, in, coef, workspace, stream);
         cudaEventRecord(e1, s);
