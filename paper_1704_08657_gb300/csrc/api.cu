@@ -1406,7 +1406,7 @@ int dwt2_autotune(dwt2_plan_t p, const void* in, void* coef, void* workspace, vo
                 if (cand_ms[k] < cand_ms[kb]) kb = k;
             best = cands[kb];
             // Coordinate descent, end to end: each field in turn tries its
-            // four fastest per-level candidates and every configuration with
+            // eight fastest per-level candidates and every configuration with
             // the automatic segment height, the others fixed; a change is kept
             // when the whole pyramid gets faster by more than 0.2 %.  A second
             // pass runs when the first changed anything.
@@ -1424,7 +1424,7 @@ int dwt2_autotune(dwt2_plan_t p, const void* in, void* coef, void* workspace, vo
                 }
                 std::sort(lv.begin(), lv.end());
                 std::vector<int> alts;
-                for (size_t k = 0; k < 4 && k < lv.size(); ++k) alts.push_back(lv[k].second);
+                for (size_t k = 0; k < 8 && k < lv.size(); ++k) alts.push_back(lv[k].second);
                 for (int ci = 0; ci < N_FWD_CFGS; ++ci)
                     if (cand_compiled(p, ci * N_TUNE_SEGS)) alts.push_back(ci * N_TUNE_SEGS);
                 const int shift = f * TUNE_BITS;
