@@ -1354,8 +1354,9 @@ int dwt2_autotune(dwt2_plan_t p, const void* in, void* coef, void* workspace, vo
             }
             best |= bc << (f * TUNE_BITS);
         }
-        if (overlap && p->d_lvl_ctr) {
-            // With inter-level overlap the fastest pyramid need not be made of
+        if ((overlap && p->d_lvl_ctr) || p->n_images > 1) {
+            // With inter-level overlap (or the overlapping launches of the
+            // image groups of a level) the fastest pyramid need not be made of
             // the fastest levels: time the per-level choice, the default, the
             // per-level choice on the first levels only and the best uniform
             // candidates (also with the first level's own fastest candidate)
@@ -1413,31 +1414,33 @@ int dwt2_autotune(dwt2_plan_t p, const void* in, void* coef, void* workspace, vo
             float cur = cand_ms[kb];
             bool changed = true;
             for (int pass = 0; pass < 2 && changed && rc == DWT2_OK; ++pass) {
-            changed = false;
-            for (int f = 0; f < nf && rc == DWT2_OK; ++f) {
-                const int l_end = (f == nf - 1) ? L : f + 1;
-                std::vector<std::pair<float, int>> lv;
-                for (int c = 0; c < n_cand; ++c) {
-                    float t = 0.f;
-                    for (int l = f; l < l_end; ++l) t += ms[size_t(c) * L + l];
-                    if (t < 1e29f) lv.push_back({t, c});
+                changed = false;
+                for (int f = 0; f < nf && rc == DWT2_OK; ++f) {
+                    const int l_end = (f == nf - 1) ? L : f + 1;
+                    std::vector<std::pair<float, int>> lv;
+                    for (int c = 0; c < n_cand; ++c) {
+                        float t = 0.f;
+                        for (int l = f; l < l_end; ++l) t += ms[size_t(c) * L + l];
+                        if (t < 1e29f) lv.push_back({t, c});
+                    }
+                    std::sort(lv.begin(), lv.end());
+                    std::vector<int> alts;
+                    for (size_t k = 0; k < 8 && k < lv.size(); ++k) alts.push_back(lv[k].second);
+                    for (int ci = 0; ci < N_FWD_CFGS; ++ci)
+                        if (cand_compiled(p, ci * N_TUNE_SEGS)) alts.push_back(ci * N_TUNE_SEGS);
+                    std::sort(alts.begin(), alts.end());
+                    alts.erase(std::unique(alts.begin(), alts.end()), alts.end());
+                    const int shift = f * TUNE_BITS;
+                    for (int a : alts) {
+                        if (((best >> shift) & mask0) == a) continue;
+                        const int c = (best & ~(mask0 << shift)) | (a << shift);
+                        float t = 0.f;
+                        rc = tune_apply(p, c);
+                        if (rc == DWT2_OK) rc = time_whole_call(p, in, coef, workspace, stream, &t);
+                        if (rc != DWT2_OK) break;
+                        if (t < cur * 0.998f) cur = t, best = c, changed = true;
+                    }
                 }
-                std::sort(lv.begin(), lv.end());
-                std::vector<int> alts;
-                for (size_t k = 0; k < 8 && k < lv.size(); ++k) alts.push_back(lv[k].second);
-                for (int ci = 0; ci < N_FWD_CFGS; ++ci)
-                    if (cand_compiled(p, ci * N_TUNE_SEGS)) alts.push_back(ci * N_TUNE_SEGS);
-                const int shift = f * TUNE_BITS;
-                for (int a : alts) {
-                    if (((best >> shift) & mask0) == a) continue;
-                    const int c = (best & ~(mask0 << shift)) | (a << shift);
-                    float t = 0.f;
-                    rc = tune_apply(p, c);
-                    if (rc == DWT2_OK) rc = time_whole_call(p, in, coef, workspace, stream, &t);
-                    if (rc != DWT2_OK) break;
-                    if (t < cur * 0.998f) cur = t, best = c, changed = true;
-                }
-            }
             }
             if (rc != DWT2_OK) return rc;
         }
