@@ -485,65 +485,64 @@ def run_ours(a):
     # coefficients back to pinned host memory.  Steps are pipelined over two
     # device buffer sets and three streams (host-to-device, compute,
     # device-to-host), so one step's copies overlap its neighbours' work.
-    if rank == 0 or True:
-        hin = torch.from_numpy(x_host).pin_memory()
-        hout = [torch.empty_like(hin).pin_memory() for _ in range(2)]
-        xd = [torch.empty_like(x) for _ in range(2)]
-        cd = [torch.empty_like(x) for _ in range(2)]
-        s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
-        ev = {k: [torch.cuda.Event() for _ in range(2)] for k in ("in", "fwd", "out")}
+    hin = torch.from_numpy(x_host).pin_memory()
+    hout = [torch.empty_like(hin).pin_memory() for _ in range(2)]
+    xd = [torch.empty_like(x) for _ in range(2)]
+    cd = [torch.empty_like(x) for _ in range(2)]
+    s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    ev = {k: [torch.cuda.Event() for _ in range(2)] for k in ("in", "fwd", "out")}
 
-        def e2e_steps(k):
-            for i in range(k):
-                b = i % 2
-                if i >= 2:
-                    s_in.wait_event(ev["fwd"][b])  # xd[b] free once step i-2 has read it
-                with torch.cuda.stream(s_in):
-                    xd[b].copy_(hin, non_blocking=True)
-                ev["in"][b].record(s_in)
-                stream.wait_event(ev["in"][b])
-                if i >= 2:
-                    stream.wait_event(ev["out"][b])  # cd[b] free once step i-2 was copied out
-                plan.forward(xd[b], cd[b], stream)
-                ev["fwd"][b].record(stream)
-                s_out.wait_event(ev["fwd"][b])
-                with torch.cuda.stream(s_out):
-                    hout[b].copy_(cd[b], non_blocking=True)
-                ev["out"][b].record(s_out)
-            stream.wait_stream(s_in)
-            stream.wait_stream(s_out)
-        e2e_steps(2)
-        barrier()
-        ee0 = torch.cuda.Event(enable_timing=True)
-        ee1 = torch.cuda.Event(enable_timing=True)
-        ee0.record(stream)
-        s_in.wait_stream(stream)
-        e2e_steps(a.e2e_steps)
-        ee1.record(stream)
-        barrier()
-        e2e_ms = ee0.elapsed_time(ee1) / a.e2e_steps
-        e2e_ms = max_over_ranks(e2e_ms, pg, dev)
-        ok = bool(torch.equal(hout[(a.e2e_steps - 1) % 2], coef.cpu()))
-
-        # the host link of this machine on the same buffers (one direction at a time), for context: the
-        # end-to-end figure is bounded by it and it differs between boxes
-        def link_gbs(dst, src):
+    def e2e_steps(k):
+        for i in range(k):
+            b = i % 2
+            if i >= 2:
+                s_in.wait_event(ev["fwd"][b])  # xd[b] free once step i-2 has read it
             with torch.cuda.stream(s_in):
+                xd[b].copy_(hin, non_blocking=True)
+            ev["in"][b].record(s_in)
+            stream.wait_event(ev["in"][b])
+            if i >= 2:
+                stream.wait_event(ev["out"][b])  # cd[b] free once step i-2 was copied out
+            plan.forward(xd[b], cd[b], stream)
+            ev["fwd"][b].record(stream)
+            s_out.wait_event(ev["fwd"][b])
+            with torch.cuda.stream(s_out):
+                hout[b].copy_(cd[b], non_blocking=True)
+            ev["out"][b].record(s_out)
+        stream.wait_stream(s_in)
+        stream.wait_stream(s_out)
+    e2e_steps(2)
+    barrier()
+    ee0 = torch.cuda.Event(enable_timing=True)
+    ee1 = torch.cuda.Event(enable_timing=True)
+    ee0.record(stream)
+    s_in.wait_stream(stream)
+    e2e_steps(a.e2e_steps)
+    ee1.record(stream)
+    barrier()
+    e2e_ms = ee0.elapsed_time(ee1) / a.e2e_steps
+    e2e_ms = max_over_ranks(e2e_ms, pg, dev)
+    ok = bool(torch.equal(hout[(a.e2e_steps - 1) % 2], coef.cpu()))
+
+    # the host link of this machine on the same buffers (one direction at a time), for context: the
+    # end-to-end figure is bounded by it and it differs between boxes
+    def link_gbs(dst, src):
+        with torch.cuda.stream(s_in):
+            dst.copy_(src, non_blocking=True)
+            l0 = torch.cuda.Event(enable_timing=True)
+            l1 = torch.cuda.Event(enable_timing=True)
+            l0.record(s_in)
+            for _ in range(3):
                 dst.copy_(src, non_blocking=True)
-                l0 = torch.cuda.Event(enable_timing=True)
-                l1 = torch.cuda.Event(enable_timing=True)
-                l0.record(s_in)
-                for _ in range(3):
-                    dst.copy_(src, non_blocking=True)
-                l1.record(s_in)
-            l1.synchronize()
-            return 3 * 4 * n * n / (l0.elapsed_time(l1) * 1e-3) / 1e9
-        link = {"h2d_gbs": link_gbs(xd[0], hin), "d2h_gbs": link_gbs(hout[0], cd[0])}
-        line["e2e"] = {"value": px / (e2e_ms * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": 4 * n * n,
-                       "d2h_bytes_per_step": 4 * n * n, "steps": a.e2e_steps, "ms_per_step": e2e_ms,
-                       "path": "pinned host -> dwt2_forward -> pinned host, pipelined over 2 buffer sets "
-                               "and 3 streams", "result_matches_device_run": ok, "host_link": link}
-        del hin, hout, xd, cd
+            l1.record(s_in)
+        l1.synchronize()
+        return 3 * 4 * n * n / (l0.elapsed_time(l1) * 1e-3) / 1e9
+    link = {"h2d_gbs": link_gbs(xd[0], hin), "d2h_gbs": link_gbs(hout[0], cd[0])}
+    line["e2e"] = {"value": px / (e2e_ms * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": 4 * n * n,
+                   "d2h_bytes_per_step": 4 * n * n, "steps": a.e2e_steps, "ms_per_step": e2e_ms,
+                   "path": "pinned host -> dwt2_forward -> pinned host, pipelined over 2 buffer sets "
+                           "and 3 streams", "result_matches_device_run": ok, "host_link": link}
+    del hin, hout, xd, cd
 
     # every workload of the benchmark's configurations, each with its own
     # roofline fraction (C1 small image, C2 size sweep, C3 precision, C4
